@@ -1,0 +1,105 @@
+"""Seeded synthetic EM-like stacks, shared by the CUDA solver's tests and
+benchmark and by the CPU oracle's tests.
+
+This module only draws inputs.  It holds none of the gradient-domain method's
+arithmetic and imports neither the solver package nor the oracle.
+
+Recipe (one stack = one ``(geom_seed, photo_seed, noise_seed)`` triple):
+
+* Voronoi mosaic per slice; seeds uniform in the slice and drifting smoothly in
+  z (linear drift |v| <= 0.3 px/slice plus a sinusoidal wobble of amplitude
+  <= 2 px and period ~U(20,60) slices).  Cell interiors ~N(160,15), membranes
+  (pixels within 1 px of the bisector of the two nearest seeds) ~N(50,10),
+  both drawn once per cell.
+* Per slice: gain ~U(0.8,1.2), offset ~U(-20,20), a linear ramp running from
+  -a to +a across the slice with a ~U(-15,15) along a direction ~U(0, 2 pi).
+* Per pixel noise ~N(0, sigma), sigma = 3 by default.
+* Clip to [0,255], round half to even, store as uint8.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "synth.c")
+_LIB_PATH = os.path.join(_HERE, "libgdsynth.so")
+_lock = threading.Lock()
+_lib = None
+
+#: cell density of the 1024x1024 / 2000-cell workload, in px^2 per cell
+PX2_PER_CELL = 1024.0 * 1024.0 / 2000.0
+
+
+def build(force: bool = False) -> str:
+    """Compile ``synth.c`` into ``libgdsynth.so`` next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-std=c11",
+               _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            lib.gds_em_window.restype = ctypes.c_int
+            lib.gds_em_window.argtypes = [
+                ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def default_cells(nx: int, ny: int) -> int:
+    """Cell count at the workloads' density (40 on 64^2, 2000 on 1024^2)."""
+    if (nx, ny) == (64, 64):
+        return 40
+    return max(2, int(round(nx * ny / PX2_PER_CELL)))
+
+
+def em_stack(nx: int, ny: int, nz: int, seed: int = 0, ncells: int | None = None,
+             photo_seed: int | None = None, noise_seed: int | None = None,
+             noise_sigma: float = 3.0, window=None) -> np.ndarray:
+    """uint8 array ``[nz][ny][nx]`` (x fastest) of the synthetic stack.
+
+    ``window = (x0, y0, z0, wx, wy, wz)`` returns only that window of the
+    ``nx x ny x nz`` stack (identical to slicing the full stack).
+    """
+    lib = _load()
+    if ncells is None:
+        ncells = default_cells(nx, ny)
+    if photo_seed is None:
+        photo_seed = seed * 2 + 1
+    if noise_seed is None:
+        noise_seed = seed * 2 + 2
+    if window is None:
+        window = (0, 0, 0, nx, ny, nz)
+    x0, y0, z0, wx, wy, wz = (int(v) for v in window)
+    out = np.empty((wz, wy, wx), dtype=np.uint8)
+    rc = lib.gds_em_window(out.ctypes.data, nx, ny, nz, int(ncells),
+                           int(seed) & (2**64 - 1), int(photo_seed) & (2**64 - 1),
+                           int(noise_seed) & (2**64 - 1), float(noise_sigma),
+                           x0, y0, z0, wx, wy, wz)
+    if rc != 0:
+        raise ValueError("gds_em_window failed with status %d" % rc)
+    return out
+
+
+def sp_pair(n: int, seed: int):
+    """(I0, I1) for one square 2D slice of side ``n``: I0 is a noisy slice; I1
+    is the same mosaic with a fresh gain/offset/ramp draw and no noise,
+    standing in for an anisotropic-diffusion output."""
+    i0 = em_stack(n, n, 1, seed=seed)[0]
+    i1 = em_stack(n, n, 1, seed=seed, photo_seed=seed * 2 + 7, noise_sigma=0.0)[0]
+    return i0, i1
