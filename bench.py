@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: voxels/s of the two gradient-domain steps solved to a 1e-6
+relative residual on a 1024 x 1024 x 128 synthetic EM stack.
+
+One step = anisotropic diffusion along z (beta = (1, 1, 10)) followed by the
+per-slice screened Poisson solve (alpha = 0.01), each V(2,2)-cycled down to a
+16 x 16 coarsest grid until ||b - A x|| / ||b|| <= 1e-6, on inputs resident
+in HBM.  Every array (537 MB in float32) is larger than the 126 MB L2, so no
+L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
+own stack (independent problems, no collective on the data path) and the
+value is all ranks' voxels over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxels/s to 1e-6 rel. residual (plain vs mixed-prec+learned); % of HBM peak"
+UNIT = "voxels/s"
+NX, NY, NZ = 1024, 1024, 128
+BETA = (1.0, 1.0, 10.0)
+ALPHA = 0.01
+TOL = 1e-6
+SEED = 2
+WORKLOAD = "gd_ad_then_sp_1024x1024x128"
+
+# DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum per launch, divided by the voxels of that launch), valid
+# only while the kernel source is the one it was taken from.
+NCU_TRAFFIC = {
+    # "rb_sweep_fine": {"bytes_per_voxel": ..., "src_sha256": "..."},
+}
+
+
+def kernel_src_sha() -> str:
+    p = os.path.join(ROOT, "paper_1310_0041_gb300", "csrc", "gd_kernels.cu")
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Max of a scalar over ranks (identity when world == 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th is not None:
+            self.th.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / CPU baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample_step(I0c: np.ndarray) -> tuple:
+    """AD then SP with the oracle's V-cycle (red-black Gauss-Seidel, OpenMP),
+    each to 1e-6, on a crop of the workload; returns (seconds, voxels)."""
+    import oracle
+    t0 = time.perf_counter()
+    I1, _ = oracle.ad_solve(I0c, BETA[0], BETA[1], BETA[2], method="mg", tol=TOL, max_cycles=400)
+    oracle.sp_solve(I0c, I1, ALPHA, method="mg", tol=TOL, max_cycles=400)
+    return time.perf_counter() - t0, I0c.size
+
+
+def oracle_crop():
+    import gdsynth
+    # 256 x 256 x 32 window of the 1024 x 1024 x 128 stack, solved as its own problem
+    return gdsynth.em_stack(NX, NY, NZ, seed=SEED, ncells=2000,
+                            window=(384, 512, 48, 256, 256, 32)).astype(np.float64)
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    I0c = oracle_crop()
+    for _ in range(args.warmup):
+        oracle_sample_step(I0c)
+    times = []
+    for _ in range(args.steps):
+        t, vox = oracle_sample_step(I0c)
+        times.append(t)
+    sec = sum(times) / len(times)
+    value = I0c.size / sec
+    sample = "AD+SP with the FP64 oracle V-cycle to 1e-6 on a 256x256x32 crop of the stack"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "beta": BETA,
+                   "alpha": ALPHA, "rel_tol": TOL, "sample": "256x256x32 crop"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_bounded() -> dict:
+    """The oracle timed once on the bounded sample (about 10-30 s of CPU work)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(1) as pool:
+        res = pool.apply(_cpu_baseline_child)
+    return res
+
+
+def _cpu_baseline_child():
+    import oracle
+    I0c = oracle_crop()
+    t, vox = oracle_sample_step(I0c)
+    return {"value": vox / t, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "AD+SP with the FP64 oracle V-cycle (red-black GS, OpenMP) to 1e-6 on a "
+                      "256x256x32 crop of the 1024x1024x128 stack, one run (%.1f s)" % t}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    world, rank, local = dist_env()
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import gdsynth
+    import paper_1310_0041_gb300 as gd
+    gd.build()
+
+    # the oracle baseline runs first in a spawned process (before heavy GPU work)
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base = cpu_baseline_bounded()
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    I0h = gdsynth.em_stack(NX, NY, NZ, seed=SEED + rank, ncells=2000)
+    I0 = torch.from_numpy(I0h).to(dev).float()
+    I1 = torch.empty_like(I0)
+    I2 = torch.empty_like(I0)
+    stream = torch.cuda.current_stream()
+    s = gd.gd_stack_create(NX, NY, NZ, stream=stream.cuda_stream)
+    ctl = gd.solve_ctl(40, TOL, 2, 2, 16)
+    w_ad = (0.0, BETA[0], BETA[1], BETA[2])
+    reps = []
+
+    def step():
+        r1 = gd.gd_diffuse_z(s, I0, I1, w_ad, ctl)
+        r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, ALPHA, ctl)
+        reps.append((r1, r2))
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    reps.clear()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local if world > 1 else 0)
+    clocks.start()
+    gd.gd_profile_reset(s)
+    gd.gd_profile_enable(s, True)
+    launches0 = gd.gd_launch_count(s)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_local = e0.elapsed_time(e1)
+    launches = gd.gd_launch_count(s) - launches0
+    gd.gd_profile_enable(s, False)
+    prof = gd.gd_profile_all(s)
+    clk = clocks.stop()
+    ms_max = reduce_max(ms_local, world, dev)
+    voxels = NX * NY * NZ
+    value = world * voxels * args.steps / (ms_max * 1e-3)
+
+    # end to end through the C ABI with pinned host buffers: H2D of the input
+    # (once per solve) and D2H of the result inside the timed region
+    I0p = torch.from_numpy(I0h.astype(np.float32)).pin_memory()
+    I2p = torch.empty(I0p.shape, dtype=torch.float32).pin_memory()
+    for _ in range(1):
+        gd.gd_diffuse_z(s, I0p, I1, w_ad, ctl)
+        gd.gd_screened_poisson_slices(s, I0p, I1, I2p, ALPHA, ctl)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    esteps = max(1, min(args.steps, 3))
+    for _ in range(esteps):
+        gd.gd_diffuse_z(s, I0p, I1, w_ad, ctl)
+        gd.gd_screened_poisson_slices(s, I0p, I1, I2p, ALPHA, ctl)
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e_value = world * voxels * esteps / e2e_s
+    gd.gd_destroy(s)
+
+    if rank == 0:
+        peaks = measured_peaks()
+        peak = peaks.get("hbm_gbs")
+        peak_src = "measured" if peak else "fallback"
+        if not peak:
+            peak = 6800.0
+        dom = max(prof, key=lambda q: q[2]) if prof else None
+        roof = None
+        if dom and dom[1] > 0 and dom[2] > 0:
+            name, nl, ms, by = dom
+            achieved = by / (ms * 1e-3) / 1e9
+            tr = NCU_TRAFFIC.get(name)
+            traffic = None
+            if tr and tr.get("src_sha256") == kernel_src_sha():
+                traffic = tr["bytes_per_voxel"] * (by / nl) / tr["alg_bytes_per_voxel"]
+            roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": traffic, "launches": nl, "avg_launch_ms": ms / nl,
+                    "alg_bytes_per_launch": by / nl}
+        r1, r2 = reps[-1]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ, "beta": BETA,
+                       "alpha": ALPHA, "rel_tol": TOL, "cycle": "V(2,2)", "coarsest_xy": 16,
+                       "precision": "fp32 kernels, float-pair fine iterate",
+                       "l2": "inputs larger than L2 (537 MB per array), no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "solver": {"ad_cycles": r1["cycles"], "ad_rel_residual": r1["rel_residual"],
+                       "ad_levels": r1["levels"], "sp_cycles": r2["cycles"],
+                       "sp_rel_residual": r2["rel_residual"], "sp_levels": r2["levels"]},
+            "roofline": roof,
+            "kernels": [{"name": q[0], "launches": q[1], "ms": q[2], "alg_GBps":
+                         (q[3] / (q[2] * 1e-3) / 1e9) if q[2] > 0 else None} for q in prof],
+            "cpu_baseline": cpu_base,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * voxels * 4,
+                    "d2h_bytes_per_step": voxels * 4},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * gd.h -- C ABI of the GB300 gradient-domain multigrid solver (libgd.so).
+ *
+ * Method: Kazhdan et al., "Gradient-Domain Processing for Large EM Image
+ * Stacks".  Two gradient-domain steps on a registered image stack:
+ *
+ *   anisotropic diffusion along z (Sec. 3.1, Eq. anisotropic_diffusion):
+ *       (bx Kx + by Ky + bz Kz) I1 = (bx Kx + by Ky) I0
+ *   screened Poisson per slice (Sec. 3.1, Eq. screened_poisson):
+ *       (alpha + Kx + Ky) I2 = alpha I1 + (Kx + Ky) I0
+ *
+ * both instances of the general screened anisotropic system of Sec. 4,
+ *       (alpha - div W grad) I = alpha I0 - div W G,
+ * discretised with the 6-point "Constant" stencil of Sec. 4.2: face-adjacent
+ * neighbours have coefficient -1 and, with homogeneous Neumann boundaries, the
+ * diagonal is the number of existing neighbours, i.e. along one axis
+ * K_n = tridiag(-1, [1, 2, ..., 2, 1], -1).  Unit voxel spacing on all axes.
+ * The singular AD system (alpha = 0) is solved with mean(I1) = mean(I0).
+ *
+ * Solver: V-cycle multigrid (Sec. 4.1) with red-black Gauss-Seidel
+ * relaxation, residual + down-sampling by summing children, up-sampling by
+ * replication (Constant transfers, Sec. 4.2) and a direct (fast
+ * diagonalisation) solve at the coarsest level; FP32 kernels with the
+ * fine-level iterate kept as an unevaluated float pair and its residual
+ * re-evaluated every cycle (iterative refinement), so the relative residual can
+ * go below what an FP32 array can represent.
+ *
+ * ----------------------------------------------------------------------------
+ * Conventions for every entry point
+ *
+ * Arrays: float32, contiguous, [nz][ny][nx] with x fastest (element
+ *   (i,j,k) at ((k*ny + j)*nx + i)), nx*ny*nz elements.  Pointers may be
+ *   device pointers (cudaMalloc / torch CUDA tensors) or host pointers
+ *   (pinned or pageable); host arrays are copied to internal device buffers
+ *   on the stack's stream and results copied back before the call returns.
+ *   The caller owns every array it passes; the library never frees them.
+ * Streams: all work is enqueued on the stream given to gd_stack_create.
+ *   Calls return after the result is complete (they read the residual norm
+ *   back every cycle).
+ * Status: every function returns a gd_status; a gd_report passed in gets
+ *   the same value in .status.  On GD_ERR_NOT_CONVERGED the output holds the
+ *   last iterate.  On GD_ERR_INVALID_ARG / GD_ERR_UNSUPPORTED nothing is
+ *   written.  GD_ERR_CUDA means a CUDA call failed; gd_last_error() says
+ *   which.
+ * Threads: one stack must not be used from two threads at once; distinct
+ *   stacks are independent.
+ */
+#ifndef GD_H
+#define GD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gd_stack gd_stack; /* opaque: sizes, stream, MG hierarchy and workspace */
+
+typedef enum {
+  GD_OK = 0,
+  GD_ERR_INVALID_ARG = 1,  /* null pointer, bad size, negative / NaN weight, ... */
+  GD_ERR_UNSUPPORTED = 2,  /* valid but not implemented (boundary, discretisation, precision) */
+  GD_ERR_OOM = 3,          /* device or host allocation failed */
+  GD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+  GD_ERR_NOT_CONVERGED = 5,/* max_cycles reached, or residual stalled, above rel_tol */
+  GD_ERR_DIVERGED = 6,     /* residual became non-finite or grew by > 1e3 */
+  GD_ERR_TIMEOUT = 7       /* reserved for bounded device-side waits */
+} gd_status;
+
+enum { GD_BC_NEUMANN = 0 };                                     /* reading of Sec. 3-4: natural BC */
+enum { GD_DISC_CONSTANT = 0, GD_DISC_HYBRID = 1, GD_DISC_LINEAR = 2 }; /* Sec. 4.2 */
+enum { GD_PREC_FP32 = 0, GD_PREC_MIXED = 1 };
+enum { GD_SYSTEM_AD = 0, GD_SYSTEM_SP = 1 };
+
+/* Weights of the general system of Sec. 4: alpha = screening weight, W =
+ * Diag(beta_x, beta_y, beta_z) (Sec. 3.1: all >= 0). */
+typedef struct {
+  double alpha, beta_x, beta_y, beta_z;
+} gd_weights;
+
+/* Solve control.  A V(nu1,nu2) cycle is repeated until the relative residual
+ * ||b - A x||_2 / ||b||_2 (Table 1 caption: residual over the initial
+ * constraints, b being the full right-hand side) is <= rel_tol or
+ * max_cycles cycles have run.  coarsest_xy: x and y are not coarsened below
+ * this many cells (the coarsest level then has coarsest_xy..2*coarsest_xy-1
+ * cells along them); 0 means 16. */
+typedef struct {
+  int max_cycles;
+  double rel_tol;
+  int nu1, nu2;
+  int coarsest_xy;
+  int flags; /* GD_FLAG_* */
+} gd_solve_ctl;
+
+/* also evaluate the relative residual of the float32 output as stored
+ * (one extra pass); reported in gd_report.rel_residual_out */
+#define GD_FLAG_REPORT_OUTPUT_RESIDUAL 1
+
+#define GD_HISTORY 64
+typedef struct {
+  int status;
+  int cycles;               /* V-cycles run */
+  int levels;               /* multigrid levels in the hierarchy used */
+  double rel_residual;      /* ||b - A x|| / ||b|| of the solver's iterate (float pair) */
+  double rel_residual_out;  /* same for the float32 output as stored (NaN unless flagged) */
+  double rho_per_cycle;     /* geometric-mean residual reduction per cycle */
+  double rhs_norm;          /* ||b||_2 */
+  double history[GD_HISTORY]; /* relative residual before cycle 1 and after cycle c (c < 64) */
+} gd_report;
+
+/*
+ * gd_stack_create -- sizes and stream of one stack; allocates nothing on the
+ * device yet (the hierarchy is built on the first solve and reused while the
+ * weights keep the same coarsening plan).
+ *   nx, ny >= 2, nz >= 1:  stack size (voxels) -- Sec. 3.1, slices along z
+ *   bc:   GD_BC_NEUMANN only (others: GD_ERR_UNSUPPORTED)
+ *   disc: GD_DISC_CONSTANT only (Sec. 4.2; others: GD_ERR_UNSUPPORTED)
+ *   prec: GD_PREC_FP32 (others: GD_ERR_UNSUPPORTED)
+ *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream
+ */
+int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, int prec,
+                    void *cuda_stream);
+
+/*
+ * gd_diffuse_z -- anisotropic diffusion, Sec. 3.1 Eq. (anisotropic_diffusion):
+ * solves (bx Kx + by Ky + bz Kz) I1 = (bx Kx + by Ky) I0 with mean(I1) =
+ * mean(I0).  w.alpha is ignored (AD has no screening term); needs
+ * beta_x, beta_y >= 0, beta_z > 0.
+ *   I0 (in), I1 (out): stack arrays; I1 must not alias I0.
+ *   x0 (in, nullable): initial guess (default I0, Sec. 4.1 starts from the
+ *     input); may alias I1.
+ */
+int gd_diffuse_z(gd_stack *s, const float *I0, float *I1, gd_weights w, const gd_solve_ctl *ctl,
+                 const float *x0, gd_report *rep);
+
+/*
+ * gd_screened_poisson_slices -- screened Poisson per slice, Sec. 3.1
+ * Eq. (screened_poisson): (alpha + Kx + Ky) I2 = alpha I1 + (Kx + Ky) I0 on
+ * every slice; the slices are independent systems solved together.
+ *   I0, I1 (in), I2 (out): stack arrays; I2 must alias neither input.
+ *   alpha > 0: screening weight (the paper uses 0.01).
+ *   x0 (in, nullable): initial guess (default I1); may alias I2.
+ */
+int gd_screened_poisson_slices(gd_stack *s, const float *I0, const float *I1, float *I2,
+                               double alpha, const gd_solve_ctl *ctl, const float *x0,
+                               gd_report *rep);
+
+/*
+ * gd_vcycle -- ncycles plain float32 V-cycles (Sec. 4.1) on A x = b with an
+ * explicit right-hand side, A = alpha + bx Kx + by Ky + bz Kz (Sec. 4 general
+ * form).  system: GD_SYSTEM_AD (3D coupling, needs bz > 0) or GD_SYSTEM_SP
+ * (independent slices, needs bz == 0 and alpha > 0).  x is updated in place
+ * (initial guess in, iterate out); no refinement, no mean fix.  The report
+ * gives the relative residual before and after (history[0], history[1]).
+ */
+int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *b, float *x, int ncycles,
+              gd_report *rep);
+
+/* gd_destroy -- frees the stack and its device memory (NULL is a no-op). */
+int gd_destroy(gd_stack *s);
+
+/*
+ * gd_residual -- relative residual ||b - A x|| / ||b|| (FP64 accumulation) of a
+ * float32 x for the AD system (I1 ignored; w.alpha ignored) or the SP system
+ * (w.alpha > 0 used, W fixed to Diag(1,1,0)), with b assembled from I0 (and
+ * I1) as in Sec. 3.1.  Writes *rel (host double).
+ */
+int gd_residual(gd_stack *s, int system, gd_weights w, const float *I0, const float *I1,
+                const float *x, double *rel);
+
+/*
+ * gd_smooth -- nsweeps red-black Gauss-Seidel sweeps (Sec. 4.1 multi-colour
+ * relaxation: red = (i+j+k) even first, then black) of the fine-level system
+ * A x = b, A = alpha + bx Kx + by Ky + bz Kz, x updated in place.
+ */
+int gd_smooth(gd_stack *s, gd_weights w, const float *b, float *x, int nsweeps);
+
+/* Per-kernel event timing, for measurement.  When enabled, the stack records
+ * a CUDA event pair around each launch of its kernels (on its stream).
+ * gd_profile_query(s, k, name, len, &launches, &ms, &bytes) returns kernel
+ * class k's totals since the last reset (GD_ERR_INVALID_ARG past the last
+ * class); bytes is the algorithmic bytes moved by those launches. */
+int gd_profile_enable(gd_stack *s, int on);
+int gd_profile_reset(gd_stack *s);
+int gd_profile_query(gd_stack *s, int k, char *name, int name_len, long long *launches,
+                     double *ms, double *bytes);
+
+/* Number of kernel launches the stack has enqueued since creation. */
+long long gd_launch_count(gd_stack *s);
+
+const char *gd_status_string(int status);
+const char *gd_last_error(gd_stack *s);
+int gd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GD_H */

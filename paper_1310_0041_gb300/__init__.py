@@ -1,0 +1,308 @@
+"""Python binding of libgd.so, the GB300 gradient-domain multigrid solver.
+
+Thin ctypes marshalling over the C ABI declared in ``include/gd.h``: the
+functions here carry the same names and arguments; every step of the solve
+runs in the library's CUDA kernels.  Arrays are torch CUDA tensors (device
+pointers) or numpy arrays (host pointers, staged by the library); float32,
+contiguous, shape (nz, ny, nx).
+
+There is no CPU fallback: if ``libgd.so`` is missing or cannot be loaded,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+from typing import Optional
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgd.so")
+
+GD_OK, GD_ERR_INVALID_ARG, GD_ERR_UNSUPPORTED, GD_ERR_OOM, GD_ERR_CUDA = 0, 1, 2, 3, 4
+GD_ERR_NOT_CONVERGED, GD_ERR_DIVERGED, GD_ERR_TIMEOUT = 5, 6, 7
+GD_BC_NEUMANN = 0
+GD_DISC_CONSTANT, GD_DISC_HYBRID, GD_DISC_LINEAR = 0, 1, 2
+GD_PREC_FP32, GD_PREC_MIXED = 0, 1
+GD_SYSTEM_AD, GD_SYSTEM_SP = 0, 1
+GD_FLAG_REPORT_OUTPUT_RESIDUAL = 1
+GD_HISTORY = 64
+
+# the symbols include/gd.h declares
+EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_vcycle",
+           "gd_destroy", "gd_residual", "gd_smooth", "gd_profile_enable", "gd_profile_reset",
+           "gd_profile_query", "gd_launch_count", "gd_status_string", "gd_last_error",
+           "gd_version")
+
+
+class GdWeights(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta_x", ctypes.c_double),
+                ("beta_y", ctypes.c_double), ("beta_z", ctypes.c_double)]
+
+
+class GdSolveCtl(ctypes.Structure):
+    _fields_ = [("max_cycles", ctypes.c_int), ("rel_tol", ctypes.c_double),
+                ("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("coarsest_xy", ctypes.c_int),
+                ("flags", ctypes.c_int)]
+
+
+class GdReport(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("cycles", ctypes.c_int), ("levels", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("rel_residual_out", ctypes.c_double),
+                ("rho_per_cycle", ctypes.c_double), ("rhs_norm", ctypes.c_double),
+                ("history", ctypes.c_double * GD_HISTORY)]
+
+    def to_dict(self) -> dict:
+        n = min(self.cycles + 1, GD_HISTORY)
+        return dict(status=self.status, cycles=self.cycles, levels=self.levels,
+                    rel_residual=self.rel_residual, rel_residual_out=self.rel_residual_out,
+                    rho_per_cycle=self.rho_per_cycle, rhs_norm=self.rhs_norm,
+                    history=[self.history[i] for i in range(n)])
+
+
+class GdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s (status %d): %s" % (_status_name(status), status, msg))
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _status_name(st: int) -> str:
+    names = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
+             5: "not converged", 6: "diverged", 7: "timeout"}
+    return names.get(st, "unknown")
+
+
+def lib():
+    """The loaded libgd.so (raises if it is missing: build it with build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError("libgd.so not found at %s; build it with "
+                                  "`python -m paper_1310_0041_gb300.buildlib`" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            sig = {
+                "gd_stack_create": (I, [ctypes.POINTER(P), I, I, I, I, I, I, P]),
+                "gd_diffuse_z": (I, [P, P, P, GdWeights, ctypes.POINTER(GdSolveCtl), P,
+                                     ctypes.POINTER(GdReport)]),
+                "gd_screened_poisson_slices": (I, [P, P, P, P, D, ctypes.POINTER(GdSolveCtl), P,
+                                                   ctypes.POINTER(GdReport)]),
+                "gd_vcycle": (I, [P, I, GdWeights, P, P, I, ctypes.POINTER(GdReport)]),
+                "gd_destroy": (I, [P]),
+                "gd_residual": (I, [P, I, GdWeights, P, P, P, ctypes.POINTER(D)]),
+                "gd_smooth": (I, [P, GdWeights, P, P, I]),
+                "gd_profile_enable": (I, [P, I]),
+                "gd_profile_reset": (I, [P]),
+                "gd_profile_query": (I, [P, I, ctypes.c_char_p, I, ctypes.POINTER(ctypes.c_longlong),
+                                         ctypes.POINTER(D), ctypes.POINTER(D)]),
+                "gd_launch_count": (ctypes.c_longlong, [P]),
+                "gd_status_string": (ctypes.c_char_p, [I]),
+                "gd_last_error": (ctypes.c_char_p, [P]),
+                "gd_version": (I, []),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def build(force: bool = False) -> str:
+    """Compile libgd.so in-tree (nvcc, sm_103a)."""
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _ptr(a, n: Optional[int] = None, name: str = "array"):
+    """Pointer of a float32 contiguous torch tensor (device or host) or numpy array."""
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.float32 or not a.is_contiguous():
+                raise ValueError("%s must be a contiguous float32 tensor" % name)
+            if n is not None and a.numel() != n:
+                raise ValueError("%s has %d elements, expected %d" % (name, a.numel(), n))
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    import numpy as np
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("%s must be a C-contiguous float32 array" % name)
+        if n is not None and a.size != n:
+            raise ValueError("%s has %d elements, expected %d" % (name, a.size, n))
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError("%s: expected a torch tensor or numpy array" % name)
+
+
+def _weights(w) -> GdWeights:
+    if isinstance(w, GdWeights):
+        return w
+    if isinstance(w, dict):
+        return GdWeights(w.get("alpha", 0.0), w.get("beta_x", 1.0), w.get("beta_y", 1.0),
+                         w.get("beta_z", 0.0))
+    a, bx, by, bz = w
+    return GdWeights(a, bx, by, bz)
+
+
+def solve_ctl(max_cycles=20, rel_tol=1e-6, nu1=2, nu2=2, coarsest_xy=16, flags=0) -> GdSolveCtl:
+    return GdSolveCtl(max_cycles, rel_tol, nu1, nu2, coarsest_xy, flags)
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class Stack:
+    """Handle returned by gd_stack_create (holds the opaque gd_stack*)."""
+
+    def __init__(self, handle, nx, ny, nz):
+        self.handle = handle
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.n = nx * ny * nz
+
+    def __repr__(self):
+        return "Stack(%dx%dx%d)" % (self.nx, self.ny, self.nz)
+
+    @property
+    def last_error(self) -> str:
+        return gd_last_error(self)
+
+
+def _check(st: int, stack: Optional[Stack], ok=(GD_OK,)):
+    if st not in ok:
+        msg = gd_last_error(stack) if stack is not None else ""
+        raise GdError(st, msg)
+    return st
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, same names
+# ---------------------------------------------------------------------------
+def gd_stack_create(nx: int, ny: int, nz: int, bc: int = GD_BC_NEUMANN,
+                    disc: int = GD_DISC_CONSTANT, prec: int = GD_PREC_FP32, stream=None) -> Stack:
+    if stream is None:
+        stream = _default_stream()
+    h = ctypes.c_void_p()
+    st = lib().gd_stack_create(ctypes.byref(h), nx, ny, nz, bc, disc, prec,
+                               ctypes.c_void_p(stream) if stream else None)
+    _check(st, None)
+    return Stack(h, nx, ny, nz)
+
+
+def gd_destroy(s: Stack) -> int:
+    if s is None or s.handle is None:
+        return GD_OK
+    st = lib().gd_destroy(s.handle)
+    s.handle = None
+    return st
+
+
+def gd_diffuse_z(s: Stack, I0, I1, w, ctl: Optional[GdSolveCtl] = None, x0=None,
+                 raise_on_error: bool = True) -> dict:
+    rep = GdReport()
+    st = lib().gd_diffuse_z(s.handle, _ptr(I0, s.n, "I0"), _ptr(I1, s.n, "I1"), _weights(w),
+                            ctypes.byref(ctl) if ctl is not None else None, _ptr(x0, s.n, "x0"),
+                            ctypes.byref(rep))
+    if raise_on_error:
+        _check(st, s, ok=(GD_OK, GD_ERR_NOT_CONVERGED))
+    return rep.to_dict()
+
+
+def gd_screened_poisson_slices(s: Stack, I0, I1, I2, alpha: float,
+                               ctl: Optional[GdSolveCtl] = None, x0=None,
+                               raise_on_error: bool = True) -> dict:
+    rep = GdReport()
+    st = lib().gd_screened_poisson_slices(s.handle, _ptr(I0, s.n, "I0"), _ptr(I1, s.n, "I1"),
+                                          _ptr(I2, s.n, "I2"), float(alpha),
+                                          ctypes.byref(ctl) if ctl is not None else None,
+                                          _ptr(x0, s.n, "x0"), ctypes.byref(rep))
+    if raise_on_error:
+        _check(st, s, ok=(GD_OK, GD_ERR_NOT_CONVERGED))
+    return rep.to_dict()
+
+
+def gd_vcycle(s: Stack, system: int, w, b, x, ncycles: int, raise_on_error: bool = True) -> dict:
+    rep = GdReport()
+    st = lib().gd_vcycle(s.handle, system, _weights(w), _ptr(b, s.n, "b"), _ptr(x, s.n, "x"),
+                         ncycles, ctypes.byref(rep))
+    if raise_on_error:
+        _check(st, s)
+    return rep.to_dict()
+
+
+def gd_residual(s: Stack, system: int, w, I0, I1, x) -> float:
+    out = ctypes.c_double(math.nan)
+    st = lib().gd_residual(s.handle, system, _weights(w), _ptr(I0, s.n, "I0"),
+                           _ptr(I1, s.n, "I1"), _ptr(x, s.n, "x"), ctypes.byref(out))
+    _check(st, s)
+    return out.value
+
+
+def gd_smooth(s: Stack, w, b, x, nsweeps: int) -> int:
+    return _check(lib().gd_smooth(s.handle, _weights(w), _ptr(b, s.n, "b"), _ptr(x, s.n, "x"),
+                                  nsweeps), s)
+
+
+def gd_profile_enable(s: Stack, on: bool) -> int:
+    return _check(lib().gd_profile_enable(s.handle, 1 if on else 0), s)
+
+
+def gd_profile_reset(s: Stack) -> int:
+    return _check(lib().gd_profile_reset(s.handle), s)
+
+
+def gd_profile_query(s: Stack, k: int):
+    """(name, launches, ms, bytes) of kernel class k, or None past the last class."""
+    name = ctypes.create_string_buffer(64)
+    n, ms, by = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    st = lib().gd_profile_query(s.handle, k, name, 64, ctypes.byref(n), ctypes.byref(ms),
+                                ctypes.byref(by))
+    if st != GD_OK:
+        return None
+    return name.value.decode(), n.value, ms.value, by.value
+
+
+def gd_profile_all(s: Stack) -> list:
+    out, k = [], 0
+    while True:
+        q = gd_profile_query(s, k)
+        if q is None:
+            return out
+        out.append(q)
+        k += 1
+
+
+def gd_launch_count(s: Stack) -> int:
+    return lib().gd_launch_count(s.handle)
+
+
+def gd_status_string(st: int) -> str:
+    return lib().gd_status_string(st).decode()
+
+
+def gd_last_error(s: Optional[Stack]) -> str:
+    r = lib().gd_last_error(s.handle if s is not None else None)
+    return r.decode() if r else ""
+
+
+def gd_version() -> int:
+    return lib().gd_version()

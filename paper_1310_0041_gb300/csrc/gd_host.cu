@@ -1,0 +1,906 @@
+// gd_host.cu -- C ABI, multigrid planning and the solve driver (host code).
+//
+// Structure of one solve (gd_diffuse_z / gd_screened_poisson_slices):
+//   x  <- x0 (default: I0 for AD, I1 for SP), held as a float pair (hi, lo)
+//   r  <- b - A x                    (outer pass, float-pair differences)
+//   repeat: e <- V(nu1,nu2)-cycle on A e = r from e = 0   (FP32 hierarchy)
+//           x <- x + e (+ mean shift for AD);  r <- b - A x;  ||r|| read back
+//   until ||r|| <= rel_tol ||b||.
+// The V-cycle itself is the paper's (Sec. 4.1): relax, compute the residual
+// and down-sample it to the next level's constraints, ..., direct solve at
+// the coarsest level, up-sample and add the correction, relax again.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gd.h"
+#include "gd_internal.h"
+
+namespace {
+
+enum ProfClass {
+  P_SWEEP_FINE = 0,
+  P_SWEEP_COARSE,
+  P_RESTRICT,
+  P_PROLONG,
+  P_OUTER,
+  P_COARSEST,
+  P_REDUCE,
+  P_COPY,
+  P_NUM
+};
+const char *kProfNames[P_NUM] = {"rb_sweep_fine", "rb_sweep_coarse", "residual_restrict",
+                                 "prolong_add",   "outer_update_residual", "coarsest_fdm",
+                                 "reduce",        "copy"};
+
+struct Level {
+  LevelDev d;
+  int fx = 0, fy = 0, fz = 0;  // axes coarsened from this level to the next
+  float *x = nullptr, *b = nullptr, *t = nullptr;
+  size_t n = 0;
+};
+
+struct Plan {
+  bool valid = false;
+  int batch_z = 0;
+  double w[4] = {0, 0, 0, 0};  // alpha, bx, by, bz
+  int cxy = 16;
+  std::vector<Level> L;
+  float *Vx = nullptr, *Vy = nullptr, *Vz = nullptr, *Dinv = nullptr;
+};
+
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+}  // namespace
+
+struct gd_stack {
+  int nx = 0, ny = 0, nz = 0, bc = 0, disc = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  Plan plan;
+  // fine-level outer iterate buffers (second float pair, low parts)
+  float *xh2 = nullptr, *xl1 = nullptr, *xl2 = nullptr;
+  double *partials = nullptr;
+  int partials_cap = 0;  // blocks
+  double *scalars = nullptr;
+  double *h_scalars = nullptr;  // pinned
+  // staging buffers for host pointers
+  float *stage[4] = {nullptr, nullptr, nullptr, nullptr};
+  // profiling
+  bool prof_on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> ev_pool;
+  long long prof_launches[P_NUM] = {0};
+  double prof_ms[P_NUM] = {0}, prof_bytes[P_NUM] = {0};
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+void set_err(gd_stack *s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf;
+}
+
+#define CK(call)                                                                    \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      set_err(s, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, \
+              __LINE__);                                                            \
+      return GD_ERR_CUDA;                                                           \
+    }                                                                               \
+  } while (0)
+
+int report(gd_report *rep, int st) {
+  if (rep) rep->status = st;
+  return st;
+}
+
+// ---- profiling ----
+cudaEvent_t ev_get(gd_stack *s) {
+  if (!s->ev_pool.empty()) {
+    cudaEvent_t e = s->ev_pool.back();
+    s->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  gd_stack *s;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr;
+  ProfScope(gd_stack *s_, int cls_, double bytes_) : s(s_), cls(cls_), bytes(bytes_) {
+    ++s->launches;
+    if (s->prof_on && s->recs.size() < 200000) {
+      a = ev_get(s);
+      cudaEventRecord(a, s->stream);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = ev_get(s);
+      cudaEventRecord(b, s->stream);
+      s->recs.push_back(ProfRec{cls, a, b, bytes});
+    }
+  }
+};
+
+void prof_collect(gd_stack *s) {
+  if (s->recs.empty()) return;
+  cudaStreamSynchronize(s->stream);
+  for (auto &r : s->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      s->prof_ms[r.cls] += ms;
+      s->prof_launches[r.cls] += 1;
+      s->prof_bytes[r.cls] += r.bytes;
+    }
+    s->ev_pool.push_back(r.a);
+    s->ev_pool.push_back(r.b);
+  }
+  s->recs.clear();
+}
+
+// ---- device memory helpers ----
+int dalloc(gd_stack *s, float **p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, n * sizeof(float));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    set_err(s, "cudaMalloc of %zu floats failed: %s", n, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GD_ERR_OOM : GD_ERR_CUDA;
+  }
+  return GD_OK;
+}
+
+void dfree(float *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void plan_free(Plan &P) {
+  for (auto &l : P.L) {
+    dfree(l.x);
+    dfree(l.b);
+    dfree(l.t);
+  }
+  P.L.clear();
+  dfree(P.Vx);
+  dfree(P.Vy);
+  dfree(P.Vz);
+  dfree(P.Dinv);
+  P.valid = false;
+}
+
+int ensure_partials(gd_stack *s, int blocks) {
+  if (blocks <= s->partials_cap) return GD_OK;
+  if (s->partials) cudaFree(s->partials);
+  s->partials = nullptr;
+  s->partials_cap = 0;
+  size_t cap = (size_t)blocks + 1024;
+  if (cudaMalloc((void **)&s->partials, cap * S_NUM * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    set_err(s, "cudaMalloc of the partial-sum buffer failed");
+    return GD_ERR_OOM;
+  }
+  s->partials_cap = (int)cap;
+  return GD_OK;
+}
+
+// Generalised eigen-decomposition of (K_n, M) with K_n the 1D Neumann
+// Laplacian and M = diag(children counts): V^T M V = I, V^T K V = diag(lam).
+void axis_eig(int n, int sfac, int last, std::vector<float> &V, std::vector<double> &lam) {
+  std::vector<double> m(n), a((size_t)n * n, 0.0), v((size_t)n * n), w(n);
+  for (int i = 0; i < n; ++i) m[i] = (i == n - 1) ? last : sfac;
+  for (int i = 0; i + 1 < n; ++i) {  // K_n = sum over edges of e e^T, e = u_i - u_{i+1}
+    a[i * n + i] += 1.0;
+    a[(i + 1) * n + i + 1] += 1.0;
+    a[i * n + i + 1] -= 1.0;
+    a[(i + 1) * n + i] -= 1.0;
+  }
+  for (int i = 0; i < n; ++i)  // C = M^{-1/2} K M^{-1/2}
+    for (int j = 0; j < n; ++j) a[i * n + j] /= std::sqrt(m[i] * m[j]);
+  jacobi_eigen(n, a.data(), w.data(), v.data());
+  V.assign((size_t)n * n, 0.f);
+  lam.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) lam[k] = w[k] < 0 ? 0.0 : w[k];
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) V[(size_t)i * n + k] = (float)(v[i * n + k] / std::sqrt(m[i]));
+}
+
+// Build the multigrid hierarchy for weights w = (alpha, bx, by, bz).
+// Coarsening (anisotropy-aware semi-coarsening): the interior coupling of
+// axis d at a level is c_d = w_d * s_e * s_f (the other axes' children
+// counts); an axis is halved (n_c = ceil(n/2)) when c_d >= max_d' c_d' / 2
+// and it may still be coarsened (x, y: n >= 2*cxy; z: n >= 2 and coupled).
+// When the strongest axis can no longer be halved the level is the coarsest.
+// Coarse stiffness w_d is halved per coarsening of axis d (6-point stencil
+// re-discretised at the coarse spacing); masses are the children counts.
+int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
+  Plan &P = s->plan;
+  if (P.valid && P.batch_z == batch_z && P.cxy == cxy && std::memcmp(P.w, w, sizeof(P.w)) == 0)
+    return GD_OK;
+  plan_free(P);
+  P.batch_z = batch_z;
+  P.cxy = cxy;
+  std::memcpy(P.w, w, sizeof(P.w));
+  Level l0;
+  l0.d = LevelDev{s->nx, s->ny, s->nz, 1, 1, 1, 1, 1, 1, (float)w[1], (float)w[2],
+                  batch_z ? 0.f : (float)w[3], (float)w[0]};
+  P.L.push_back(l0);
+  double wd[3] = {w[1], w[2], batch_z ? 0.0 : w[3]};
+  for (int guard = 0; guard < 64; ++guard) {
+    Level &F = P.L.back();
+    const LevelDev &d = F.d;
+    const bool can[3] = {d.nx >= 2 * cxy, d.ny >= 2 * cxy, d.nz >= 2 && wd[2] > 0.0};
+    const double c[3] = {wd[0] * d.sy * d.sz, wd[1] * d.sx * d.sz, wd[2] * d.sx * d.sy};
+    const double cm = std::fmax(c[0], std::fmax(c[1], c[2]));
+    int f[3];
+    for (int a = 0; a < 3; ++a) f[a] = can[a] && c[a] > 0.0 && c[a] >= 0.5 * cm;
+    if (!f[0] && !f[1] && !f[2]) break;
+    F.fx = f[0];
+    F.fy = f[1];
+    F.fz = f[2];
+    Level C;
+    const int n[3] = {d.nx, d.ny, d.nz}, sf[3] = {d.sx, d.sy, d.sz}, lf[3] = {d.lx, d.ly, d.lz};
+    int nn[3], ns[3], nl[3];
+    for (int a = 0; a < 3; ++a) {
+      if (f[a]) {
+        nn[a] = (n[a] + 1) / 2;
+        ns[a] = 2 * sf[a];
+        nl[a] = (n[a] % 2 == 0) ? sf[a] + lf[a] : lf[a];
+        wd[a] *= 0.5;
+      } else {
+        nn[a] = n[a];
+        ns[a] = sf[a];
+        nl[a] = lf[a];
+      }
+    }
+    C.d = LevelDev{nn[0], nn[1], nn[2], ns[0], ns[1], ns[2], nl[0], nl[1], nl[2],
+                   (float)wd[0], (float)wd[1], (float)wd[2], (float)w[0]};
+    P.L.push_back(C);
+  }
+  // workspace
+  for (size_t li = 0; li < P.L.size(); ++li) {
+    Level &l = P.L[li];
+    l.n = (size_t)l.d.nx * l.d.ny * l.d.nz;
+    int st;
+    if ((st = dalloc(s, &l.x, l.n)) != GD_OK) return st;
+    if ((st = dalloc(s, &l.b, l.n)) != GD_OK) return st;
+    if ((st = dalloc(s, &l.t, l.n)) != GD_OK) return st;
+  }
+  // coarsest-level fast diagonalisation data
+  const LevelDev &c = P.L.back().d;
+  std::vector<float> Vx, Vy, Vz;
+  std::vector<double> lx, ly, lz;
+  axis_eig(c.nx, c.sx, c.lx, Vx, lx);
+  axis_eig(c.ny, c.sy, c.ly, Vy, ly);
+  const int dz = batch_z ? 1 : c.nz;
+  if (!batch_z) axis_eig(c.nz, c.sz, c.lz, Vz, lz);
+  std::vector<double> D((size_t)c.nx * c.ny * dz);
+  double dmax = 0.0;
+  for (int k = 0; k < dz; ++k)
+    for (int j = 0; j < c.ny; ++j)
+      for (int i = 0; i < c.nx; ++i) {
+        double v = c.wx * lx[i] + c.wy * ly[j] + (batch_z ? 0.0 : c.wz * lz[k]) + c.wm;
+        D[((size_t)k * c.ny + j) * c.nx + i] = v;
+        dmax = std::fmax(dmax, std::fabs(v));
+      }
+  std::vector<float> Dinv(D.size());
+  for (size_t q = 0; q < D.size(); ++q)  // pseudo-inverse: the constant mode of AD is dropped
+    Dinv[q] = (D[q] > 1e-9 * dmax) ? (float)(1.0 / D[q]) : 0.f;
+  int st;
+  if ((st = dalloc(s, &P.Vx, Vx.size())) != GD_OK) return st;
+  if ((st = dalloc(s, &P.Vy, Vy.size())) != GD_OK) return st;
+  if (!batch_z && (st = dalloc(s, &P.Vz, Vz.size())) != GD_OK) return st;
+  if ((st = dalloc(s, &P.Dinv, Dinv.size())) != GD_OK) return st;
+  CK(cudaMemcpyAsync(P.Vx, Vx.data(), Vx.size() * 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(P.Vy, Vy.data(), Vy.size() * 4, cudaMemcpyHostToDevice, s->stream));
+  if (!batch_z) CK(cudaMemcpyAsync(P.Vz, Vz.data(), Vz.size() * 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(P.Dinv, Dinv.data(), Dinv.size() * 4, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));  // host vectors go out of scope
+  P.valid = true;
+  return GD_OK;
+}
+
+// ---- kernel wrappers with launch accounting ----
+int sweep(gd_stack *s, Level &l, bool fine, bool zero_in, bool sum_e) {
+  int nb = 0;
+  const double bytes = (double)l.n * (zero_in ? 8.0 : 12.0);
+  double *part = nullptr;
+  if (sum_e) {
+    const int gx = (l.d.nx + 63) / 64, gy = (l.d.ny + 15) / 16;
+    int st = ensure_partials(s, gx * gy * l.d.nz);
+    if (st != GD_OK) return st;
+    part = s->partials;
+  }
+  {
+    ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE, bytes);
+    CK(launch_rb_sweep(l.d, l.x, l.b, l.t, zero_in, part, &nb, s->stream));
+  }
+  std::swap(l.x, l.t);
+  if (sum_e) {
+    ProfScope ps(s, P_REDUCE, (double)nb * S_NUM * 8.0);
+    CK(launch_reduce(s->partials, nb, s->scalars, S_E, S_E + 1, 0, s->stream));
+  }
+  return GD_OK;
+}
+
+int coarsest_solve(gd_stack *s, Level &l) {
+  Plan &P = s->plan;
+  ProfScope ps(s, P_COARSEST, (double)l.n * 4.0 * (P.batch_z ? 8.0 : 12.0));
+  CK(launch_fdm(l.d.nx, l.d.ny, l.d.nz, P.Vx, P.Vy, P.Vz, P.Dinv, P.batch_z, l.b, l.x, l.t,
+                s->stream));
+  s->launches += P.batch_z ? 3 : 5;
+  return GD_OK;
+}
+
+// One V(nu1,nu2) cycle on level 0's (x, b).  zero_init: level 0's x starts at
+// zero (correction form).  sum_e: the last fine sweep also sums its output
+// into scalars[S_E].
+int vcycle(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
+  std::vector<Level> &L = s->plan.L;
+  const int nl = (int)L.size();
+  int st;
+  if (nl == 1) {
+    // the fine level is the coarsest: x = A^-1 b directly (whatever x was);
+    // when the sum of x is wanted, one relaxation sweep (which leaves the
+    // exact solution unchanged up to rounding) computes it
+    if ((st = coarsest_solve(s, L[0])) != GD_OK) return st;
+    if (sum_e && (st = sweep(s, L[0], true, false, true)) != GD_OK) return st;
+    return GD_OK;
+  }
+  for (int l = 0; l < nl - 1; ++l) {
+    const bool zi = (l > 0) || zero_init;
+    for (int k = 0; k < nu1; ++k)
+      if ((st = sweep(s, L[l], l == 0, zi && k == 0, false)) != GD_OK) return st;
+    Level &F = L[l], &C = L[l + 1];
+    ProfScope ps(s, P_RESTRICT, (double)F.n * 8.0 + (double)C.n * 4.0);
+    CK(launch_residual_restrict(F.d, F.x, F.b, F.fx, F.fy, F.fz, C.b, s->stream));
+  }
+  if ((st = coarsest_solve(s, L[nl - 1])) != GD_OK) return st;
+  for (int l = nl - 2; l >= 0; --l) {
+    Level &F = L[l], &C = L[l + 1];
+    {
+      ProfScope ps(s, P_PROLONG, (double)F.n * 8.0 + (double)C.n * 4.0);
+      CK(launch_prolong_add(F.d, F.fx, F.fy, F.fz, C.x, F.x, s->stream));
+    }
+    for (int k = 0; k < nu2; ++k)
+      if ((st = sweep(s, F, l == 0, false, sum_e && l == 0 && k == nu2 - 1)) != GD_OK) return st;
+  }
+  return GD_OK;
+}
+
+int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] */) {
+  a.nx = s->nx;
+  a.ny = s->ny;
+  a.nz = s->nz;
+  a.scalars = s->scalars;
+  a.inv_n = 1.0 / ((double)s->nx * s->ny * s->nz);
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  int dev = 0, sms = 152, st;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((st = ensure_partials(s, sms * 8 + 64)) != GD_OK) return st;
+  a.partials = s->partials;
+  double bytes = 4.0 * (1 + (a.xl_in ? 1 : 0) + (a.e ? 1 : 0) + (a.xh_out ? 2 : 0) +
+                        (a.r_out ? 1 : 0) + (rhs_mode == RHS_SP ? 2 : 1)) * (double)n;
+  int nb = 0;
+  {
+    ProfScope ps(s, P_OUTER, bytes);
+    CK(launch_outer(a, rhs_mode, &nb, s->stream));
+  }
+  {
+    ProfScope ps(s, P_REDUCE, (double)nb * S_NUM * 8.0);
+    CK(launch_reduce(s->partials, nb, s->scalars, S_RR, S_I0 + 1, 0, s->stream));
+  }
+  if (h_out) {
+    CK(cudaMemcpyAsync(s->h_scalars, s->scalars, S_NUM * sizeof(double), cudaMemcpyDeviceToHost,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    std::memcpy(h_out, s->h_scalars, S_NUM * sizeof(double));
+  }
+  return GD_OK;
+}
+
+int ensure_common(gd_stack *s) {
+  if (!s->scalars) {
+    if (cudaMalloc((void **)&s->scalars, 8 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return GD_ERR_OOM;
+    }
+    cudaMemsetAsync(s->scalars, 0, 8 * sizeof(double), s->stream);
+  }
+  if (!s->h_scalars) {
+    if (cudaMallocHost((void **)&s->h_scalars, 8 * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return GD_ERR_OOM;
+    }
+  }
+  return GD_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device view of a caller array: device pointers pass through; host arrays
+// are copied (if `in`) into staging buffer `slot`.
+int resolve(gd_stack *s, const float *p, bool in, int slot, float **dev) {
+  if (!p) {
+    *dev = nullptr;
+    return GD_OK;
+  }
+  if (is_device_ptr(p)) {
+    *dev = const_cast<float *>(p);
+    return GD_OK;
+  }
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  if (!s->stage[slot]) {
+    int st = dalloc(s, &s->stage[slot], n);
+    if (st != GD_OK) return st;
+  }
+  if (in) {
+    CK(cudaMemcpyAsync(s->stage[slot], p, n * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+  }
+  *dev = s->stage[slot];
+  return GD_OK;
+}
+
+bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+int check_ctl(gd_stack *s, const gd_solve_ctl *ctl, gd_solve_ctl *out) {
+  gd_solve_ctl c = {20, 1e-6, 2, 2, 16, 0};
+  if (ctl) c = *ctl;
+  if (c.coarsest_xy == 0) c.coarsest_xy = 16;
+  if (c.max_cycles < 0 || c.nu1 < 1 || c.nu1 > 8 || c.nu2 < 1 || c.nu2 > 8 ||
+      c.coarsest_xy < 2 || c.coarsest_xy > 4096 || !(c.rel_tol >= 0.0) ||
+      (c.rel_tol <= 0.0 && c.max_cycles <= 0)) {
+    set_err(s, "invalid solve control (max_cycles %d, rel_tol %g, nu1 %d, nu2 %d, coarsest_xy %d)",
+            c.max_cycles, c.rel_tol, c.nu1, c.nu2, c.coarsest_xy);
+    return GD_ERR_INVALID_ARG;
+  }
+  *out = c;
+  return GD_OK;
+}
+
+void rep_init(gd_report *rep) {
+  if (!rep) return;
+  std::memset(rep, 0, sizeof(*rep));
+  rep->rel_residual_out = NAN;
+  rep->rel_residual = NAN;
+  rep->rho_per_cycle = NAN;
+}
+
+// Solve one of the two systems with iterative refinement on the float pair.
+int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *outh, double w[4],
+          const gd_solve_ctl *ctl_in, const float *x0h, gd_report *rep) {
+  rep_init(rep);
+  gd_solve_ctl ctl;
+  int st = check_ctl(s, ctl_in, &ctl);
+  if (st != GD_OK) return report(rep, st);
+  if ((st = ensure_common(s)) != GD_OK) return report(rep, st);
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  // device views
+  float *I0 = nullptr, *I1 = nullptr, *out = nullptr, *x0 = nullptr;
+  const bool out_host = !is_device_ptr(outh);
+  if ((st = resolve(s, I0h, true, 0, &I0)) != GD_OK) return report(rep, st);
+  if (system == GD_SYSTEM_SP && (st = resolve(s, I1h, true, 1, &I1)) != GD_OK) return report(rep, st);
+  if ((st = resolve(s, outh, x0h == outh, 2, &out)) != GD_OK) return report(rep, st);
+  if (x0h && x0h != outh && (st = resolve(s, x0h, true, 3, &x0)) != GD_OK) return report(rep, st);
+  if (x0h == outh) x0 = out;
+  if ((st = plan_build(s, w, system == GD_SYSTEM_SP, ctl.coarsest_xy)) != GD_OK) return report(rep, st);
+  Plan &P = s->plan;
+  if (!s->xh2 && (st = dalloc(s, &s->xh2, n)) != GD_OK) return report(rep, st);
+  if (!s->xl1 && (st = dalloc(s, &s->xl1, n)) != GD_OK) return report(rep, st);
+  if (!s->xl2 && (st = dalloc(s, &s->xl2, n)) != GD_OK) return report(rep, st);
+  if (rep) rep->levels = (int)P.L.size();
+
+  // initial iterate in `out`
+  const float *start = x0 ? x0 : (system == GD_SYSTEM_AD ? I0 : I1);
+  if (start != out) {
+    ProfScope ps(s, P_COPY, (double)n * 8.0);
+    CK(launch_copy(out, start, n, s->stream));
+  }
+  OuterArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.bx = (float)w[1];
+  a.by = (float)w[2];
+  a.bz = system == GD_SYSTEM_SP ? 0.f : (float)w[3];
+  a.alpha = system == GD_SYSTEM_SP ? (float)w[0] : 0.f;
+  a.rbx = system == GD_SYSTEM_SP ? 1.f : (float)w[1];
+  a.rby = system == GD_SYSTEM_SP ? 1.f : (float)w[2];
+  a.ralpha = system == GD_SYSTEM_SP ? (float)w[0] : 0.f;
+  a.I0 = I0;
+  a.I1 = I1;
+  const int rhs = system == GD_SYSTEM_SP ? RHS_SP : RHS_AD;
+  const int mean_fix = system == GD_SYSTEM_AD;
+  Level &F = P.L[0];
+
+  // initial residual
+  double h[S_NUM];
+  a.xh_in = out;
+  a.r_out = F.b;
+  if ((st = outer_pass(s, a, rhs, h)) != GD_OK) return report(rep, st);
+  const double bnorm = std::sqrt(h[S_BB]);
+  const double denom = bnorm > 0.0 ? bnorm : 1.0;
+  double rel = std::sqrt(h[S_RR]) / denom;
+  const double rel0 = rel;
+  if (rep) {
+    rep->rhs_norm = bnorm;
+    rep->history[0] = rel;
+  }
+  // float-pair buffers: pass k reads pair c and writes pair 1-c; the low
+  // part of the starting iterate is zero and is not read
+  float *H[2] = {out, s->xh2};
+  float *Lo[2] = {s->xl2, s->xl1};
+  int c = 0;
+  bool lo_zero = true;
+  int cycles = 0;
+  int status = GD_OK;
+  std::vector<double> hist(1, rel);
+  auto update = [&](const float *e) -> int {
+    a.xh_in = H[c];
+    a.xl_in = lo_zero ? nullptr : Lo[c];
+    a.e = e;
+    a.mean_fix = mean_fix;
+    a.xh_out = H[1 - c];
+    a.xl_out = Lo[1 - c];
+    a.r_out = F.b;
+    int r = outer_pass(s, a, rhs, h);
+    c = 1 - c;
+    lo_zero = false;
+    return r;
+  };
+  while (!(rel <= ctl.rel_tol)) {
+    if (cycles >= ctl.max_cycles) {
+      status = GD_ERR_NOT_CONVERGED;
+      break;
+    }
+    if ((st = vcycle(s, ctl.nu1, ctl.nu2, true, mean_fix)) != GD_OK) return report(rep, st);
+    if ((st = update(F.x)) != GD_OK) return report(rep, st);
+    ++cycles;
+    rel = std::sqrt(h[S_RR]) / denom;
+    hist.push_back(rel);
+    if (rep && cycles < GD_HISTORY) rep->history[cycles] = rel;
+    if (!std::isfinite(rel) || rel > 1e3 * std::fmax(rel0, 1e-300)) {
+      status = GD_ERR_DIVERGED;
+      break;
+    }
+    // stall: less than a 30% gain over the last three cycles (precision floor)
+    if (cycles >= 4 && rel > 0.7 * hist[cycles - 3] && rel > ctl.rel_tol) {
+      status = GD_ERR_NOT_CONVERGED;
+      break;
+    }
+  }
+  if (mean_fix && cycles == 0 && x0 != nullptr) {
+    // no cycle ran on a caller's initial guess: still move its mean to mean(I0)
+    CK(launch_fill(F.x, n, 0.f, s->stream));
+    CK(cudaMemsetAsync(s->scalars + S_E, 0, sizeof(double), s->stream));
+    if ((st = update(F.x)) != GD_OK) return report(rep, st);
+    rel = std::sqrt(h[S_RR]) / denom;
+  }
+  float *cur_h = H[c];
+  // result into `out`
+  if (cur_h != out) {
+    ProfScope ps(s, P_COPY, (double)n * 8.0);
+    CK(launch_copy(out, cur_h, n, s->stream));
+  }
+  if (rep) {
+    rep->cycles = cycles;
+    rep->rel_residual = rel;
+    rep->rho_per_cycle = cycles > 0 && rel0 > 0 ? std::pow(rel / rel0, 1.0 / cycles) : NAN;
+  }
+  if (rep && (ctl.flags & GD_FLAG_REPORT_OUTPUT_RESIDUAL)) {
+    OuterArgs b2 = a;
+    b2.xh_in = out;
+    b2.xl_in = nullptr;
+    b2.e = nullptr;
+    b2.xh_out = b2.xl_out = nullptr;
+    b2.r_out = nullptr;
+    b2.mean_fix = 0;
+    if ((st = outer_pass(s, b2, rhs, h)) != GD_OK) return report(rep, st);
+    rep->rel_residual_out = std::sqrt(h[S_RR]) / denom;
+  }
+  if (out_host) {
+    CK(cudaMemcpyAsync(outh, out, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->prof_on) prof_collect(s);
+  return report(rep, status);
+}
+
+bool weights_ok(const gd_weights &w) {
+  return finite_nonneg(w.alpha) && finite_nonneg(w.beta_x) && finite_nonneg(w.beta_y) &&
+         finite_nonneg(w.beta_z);
+}
+
+}  // namespace
+
+extern "C" {
+
+int gd_version(void) { return 1; }
+
+const char *gd_status_string(int st) {
+  switch (st) {
+    case GD_OK: return "ok";
+    case GD_ERR_INVALID_ARG: return "invalid argument";
+    case GD_ERR_UNSUPPORTED: return "unsupported";
+    case GD_ERR_OOM: return "out of memory";
+    case GD_ERR_CUDA: return "CUDA error";
+    case GD_ERR_NOT_CONVERGED: return "not converged";
+    case GD_ERR_DIVERGED: return "diverged";
+    case GD_ERR_TIMEOUT: return "timeout";
+    default: return "unknown status";
+  }
+}
+
+const char *gd_last_error(gd_stack *s) { return s ? s->err.c_str() : "null stack"; }
+
+int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, int prec,
+                    void *cuda_stream) {
+  if (!out) return GD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nz < 1) return GD_ERR_INVALID_ARG;
+  if ((double)nx * ny * nz > 9.0e18 / 64) return GD_ERR_INVALID_ARG;
+  if (bc != GD_BC_NEUMANN) return GD_ERR_UNSUPPORTED;
+  if (disc != GD_DISC_CONSTANT) return disc == GD_DISC_HYBRID || disc == GD_DISC_LINEAR ? GD_ERR_UNSUPPORTED : GD_ERR_INVALID_ARG;
+  if (prec != GD_PREC_FP32) return prec == GD_PREC_MIXED ? GD_ERR_UNSUPPORTED : GD_ERR_INVALID_ARG;
+  gd_stack *s = new (std::nothrow) gd_stack();
+  if (!s) return GD_ERR_OOM;
+  s->nx = nx;
+  s->ny = ny;
+  s->nz = nz;
+  s->bc = bc;
+  s->disc = disc;
+  s->prec = prec;
+  s->stream = (cudaStream_t)cuda_stream;
+  *out = s;
+  return GD_OK;
+}
+
+int gd_destroy(gd_stack *s) {
+  if (!s) return GD_OK;
+  cudaStreamSynchronize(s->stream);
+  plan_free(s->plan);
+  dfree(s->xh2);
+  dfree(s->xl1);
+  dfree(s->xl2);
+  for (auto &p : s->stage) dfree(p);
+  if (s->partials) cudaFree(s->partials);
+  if (s->scalars) cudaFree(s->scalars);
+  if (s->h_scalars) cudaFreeHost(s->h_scalars);
+  for (auto &r : s->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : s->ev_pool) cudaEventDestroy(e);
+  delete s;
+  return GD_OK;
+}
+
+int gd_diffuse_z(gd_stack *s, const float *I0, float *I1, gd_weights w, const gd_solve_ctl *ctl,
+                 const float *x0, gd_report *rep) {
+  rep_init(rep);
+  if (!s || !I0 || !I1) return report(rep, GD_ERR_INVALID_ARG);
+  if (I0 == I1) {
+    set_err(s, "I1 must not alias I0");
+    return report(rep, GD_ERR_INVALID_ARG);
+  }
+  if (!weights_ok(w) || !(w.beta_z > 0.0) || !(w.beta_x + w.beta_y > 0.0)) {
+    set_err(s, "AD needs finite weights with beta_x, beta_y >= 0, beta_x + beta_y > 0, beta_z > 0");
+    return report(rep, GD_ERR_INVALID_ARG);
+  }
+  double wv[4] = {0.0, w.beta_x, w.beta_y, w.beta_z};
+  return solve(s, GD_SYSTEM_AD, I0, nullptr, I1, wv, ctl, x0, rep);
+}
+
+int gd_screened_poisson_slices(gd_stack *s, const float *I0, const float *I1, float *I2,
+                               double alpha, const gd_solve_ctl *ctl, const float *x0,
+                               gd_report *rep) {
+  rep_init(rep);
+  if (!s || !I0 || !I1 || !I2) return report(rep, GD_ERR_INVALID_ARG);
+  if (I2 == I0 || I2 == I1) {
+    set_err(s, "I2 must alias neither I0 nor I1");
+    return report(rep, GD_ERR_INVALID_ARG);
+  }
+  if (!std::isfinite(alpha) || !(alpha > 0.0)) {
+    set_err(s, "SP needs a finite alpha > 0");
+    return report(rep, GD_ERR_INVALID_ARG);
+  }
+  double wv[4] = {alpha, 1.0, 1.0, 0.0};
+  return solve(s, GD_SYSTEM_SP, I0, I1, I2, wv, ctl, x0, rep);
+}
+
+int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh, int ncycles,
+              gd_report *rep) {
+  rep_init(rep);
+  if (!s || !bh || !xh || ncycles < 0 || bh == xh) return report(rep, GD_ERR_INVALID_ARG);
+  if (!weights_ok(w)) return report(rep, GD_ERR_INVALID_ARG);
+  if (system == GD_SYSTEM_AD) {
+    if (!(w.beta_z > 0.0)) return report(rep, GD_ERR_INVALID_ARG);
+  } else if (system == GD_SYSTEM_SP) {
+    if (w.beta_z != 0.0 || !(w.alpha > 0.0)) return report(rep, GD_ERR_INVALID_ARG);
+  } else {
+    return report(rep, GD_ERR_INVALID_ARG);
+  }
+  int st;
+  if ((st = ensure_common(s)) != GD_OK) return report(rep, st);
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  float *b = nullptr, *x = nullptr;
+  const bool x_host = !is_device_ptr(xh);
+  if ((st = resolve(s, bh, true, 0, &b)) != GD_OK) return report(rep, st);
+  if ((st = resolve(s, xh, true, 2, &x)) != GD_OK) return report(rep, st);
+  double wv[4] = {w.alpha, w.beta_x, w.beta_y, w.beta_z};
+  if ((st = plan_build(s, wv, system == GD_SYSTEM_SP, 16)) != GD_OK) return report(rep, st);
+  Level &F = s->plan.L[0];
+  OuterArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.bx = (float)w.beta_x;
+  a.by = (float)w.beta_y;
+  a.bz = (float)w.beta_z;
+  a.alpha = (float)w.alpha;
+  a.b = b;
+  a.xh_in = x;
+  double h[S_NUM];
+  if ((st = outer_pass(s, a, RHS_EXPLICIT, h)) != GD_OK) return report(rep, st);
+  const double bnorm = std::sqrt(h[S_BB]);
+  const double denom = bnorm > 0.0 ? bnorm : 1.0;
+  const double rel0 = std::sqrt(h[S_RR]) / denom;
+  // run the cycles directly on the caller's x (level 0 borrows x and b)
+  float *wsx = F.x, *wst = F.t, *wsb = F.b;
+  F.x = x;
+  F.b = b;
+  F.t = wst;
+  for (int c = 0; c < ncycles && st == GD_OK; ++c) {
+    st = vcycle(s, 2, 2, false, false);
+    if (st == GD_OK && F.x != x) {  // odd number of ping-pong swaps: move back
+      ProfScope ps(s, P_COPY, (double)n * 8.0);
+      if (launch_copy(x, F.x, n, s->stream) != cudaSuccess) st = GD_ERR_CUDA;
+      F.x = x;
+      F.t = wst;
+    }
+  }
+  F.x = wsx;
+  F.t = wst;
+  F.b = wsb;
+  if (st != GD_OK) return report(rep, st);
+  if ((st = outer_pass(s, a, RHS_EXPLICIT, h)) != GD_OK) return report(rep, st);
+  const double rel = std::sqrt(h[S_RR]) / denom;
+  if (rep) {
+    rep->cycles = ncycles;
+    rep->levels = (int)s->plan.L.size();
+    rep->rhs_norm = bnorm;
+    rep->rel_residual = rel;
+    rep->history[0] = rel0;
+    rep->history[1] = rel;
+    rep->rho_per_cycle = ncycles > 0 && rel0 > 0 ? std::pow(rel / rel0, 1.0 / ncycles) : NAN;
+  }
+  if (x_host) CK(cudaMemcpyAsync(xh, x, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->prof_on) prof_collect(s);
+  return report(rep, GD_OK);
+}
+
+int gd_residual(gd_stack *s, int system, gd_weights w, const float *I0h, const float *I1h,
+                const float *xh, double *rel) {
+  if (!s || !I0h || !xh || !rel) return GD_ERR_INVALID_ARG;
+  if (system != GD_SYSTEM_AD && system != GD_SYSTEM_SP) return GD_ERR_INVALID_ARG;
+  if (system == GD_SYSTEM_SP && (!I1h || !(w.alpha > 0.0))) return GD_ERR_INVALID_ARG;
+  if (!weights_ok(w)) return GD_ERR_INVALID_ARG;
+  int st;
+  if ((st = ensure_common(s)) != GD_OK) return st;
+  float *I0 = nullptr, *I1 = nullptr, *x = nullptr;
+  if ((st = resolve(s, I0h, true, 0, &I0)) != GD_OK) return st;
+  if (system == GD_SYSTEM_SP && (st = resolve(s, I1h, true, 1, &I1)) != GD_OK) return st;
+  if ((st = resolve(s, xh, true, 3, &x)) != GD_OK) return st;
+  OuterArgs a;
+  std::memset(&a, 0, sizeof a);
+  const bool sp = system == GD_SYSTEM_SP;
+  a.bx = sp ? 1.f : (float)w.beta_x;
+  a.by = sp ? 1.f : (float)w.beta_y;
+  a.bz = sp ? 0.f : (float)w.beta_z;
+  a.alpha = sp ? (float)w.alpha : 0.f;
+  a.rbx = a.bx;
+  a.rby = a.by;
+  a.ralpha = a.alpha;
+  a.I0 = I0;
+  a.I1 = I1;
+  a.xh_in = x;
+  double h[S_NUM];
+  if ((st = outer_pass(s, a, sp ? RHS_SP : RHS_AD, h)) != GD_OK) return st;
+  const double bn = std::sqrt(h[S_BB]);
+  *rel = std::sqrt(h[S_RR]) / (bn > 0 ? bn : 1.0);
+  return GD_OK;
+}
+
+int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps) {
+  if (!s || !bh || !xh || nsweeps < 0 || bh == xh || !weights_ok(w)) return GD_ERR_INVALID_ARG;
+  int st;
+  if ((st = ensure_common(s)) != GD_OK) return st;
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  float *b = nullptr, *x = nullptr;
+  const bool x_host = !is_device_ptr(xh);
+  if ((st = resolve(s, bh, true, 0, &b)) != GD_OK) return st;
+  if ((st = resolve(s, xh, true, 2, &x)) != GD_OK) return st;
+  Level l;
+  l.d = LevelDev{s->nx, s->ny, s->nz, 1, 1, 1, 1, 1, 1, (float)w.beta_x, (float)w.beta_y,
+                 (float)w.beta_z, (float)w.alpha};
+  l.n = n;
+  l.b = b;
+  l.x = x;
+  if ((st = dalloc(s, &l.t, n)) != GD_OK) return st;
+  float *tmp = l.t;
+  for (int k = 0; k < nsweeps && st == GD_OK; ++k) st = sweep(s, l, true, false, false);
+  if (st == GD_OK && l.x != x) {
+    ProfScope ps(s, P_COPY, (double)n * 8.0);
+    if (launch_copy(x, l.x, n, s->stream) != cudaSuccess) st = GD_ERR_CUDA;
+  }
+  if (st == GD_OK && x_host)
+    if (cudaMemcpyAsync(xh, x, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+      st = GD_ERR_CUDA;
+  cudaStreamSynchronize(s->stream);
+  cudaFree(tmp);
+  if (s->prof_on) prof_collect(s);
+  return st;
+}
+
+int gd_profile_enable(gd_stack *s, int on) {
+  if (!s) return GD_ERR_INVALID_ARG;
+  if (!on) prof_collect(s);
+  s->prof_on = on != 0;
+  return GD_OK;
+}
+
+int gd_profile_reset(gd_stack *s) {
+  if (!s) return GD_ERR_INVALID_ARG;
+  prof_collect(s);
+  for (int k = 0; k < P_NUM; ++k) {
+    s->prof_launches[k] = 0;
+    s->prof_ms[k] = 0;
+    s->prof_bytes[k] = 0;
+  }
+  return GD_OK;
+}
+
+int gd_profile_query(gd_stack *s, int k, char *name, int name_len, long long *launches,
+                     double *ms, double *bytes) {
+  if (!s || k < 0 || k >= P_NUM) return GD_ERR_INVALID_ARG;
+  prof_collect(s);
+  if (name && name_len > 0) {
+    std::strncpy(name, kProfNames[k], (size_t)name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = s->prof_launches[k];
+  if (ms) *ms = s->prof_ms[k];
+  if (bytes) *bytes = s->prof_bytes[k];
+  return GD_OK;
+}
+
+long long gd_launch_count(gd_stack *s) { return s ? s->launches : -1; }
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+// gd_internal.h -- structures shared by the host driver and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+// One multigrid level.  The operator is the Kronecker form
+//   A = wx Kx (x) My (x) Mz + wy Mx (x) Ky (x) Mz + wz Mx (x) My (x) Kz + wm Mx (x) My (x) Mz
+// where K_n is the 1D Neumann Laplacian and M_d = diag(children counts of the
+// level's cells along axis d, counted in fine cells).  Along axis d every cell
+// has s_d children except the last, which has l_d (ragged sizes).
+// At the fine level all M are identity and (wx, wy, wz, wm) = (bx, by, bz, alpha),
+// the 6-point operator of Sec. 4.2.  Coarser levels (see the planner) scale
+// the stiffness wd by 1/2 per coarsening of axis d, which is the 6-point
+// stencil re-discretised at the coarse spacing.
+struct LevelDev {
+  int nx, ny, nz;
+  int sx, sy, sz;
+  int lx, ly, lz;
+  float wx, wy, wz, wm;
+};
+
+// Slots of the per-block partial sums (FP64) and of the reduced scalars.
+enum {
+  S_RR = 0,   // sum r^2
+  S_BB = 1,   // sum b^2
+  S_X = 2,    // sum of the new iterate (hi + lo)
+  S_I0 = 3,   // sum of I0
+  S_E = 4,    // sum of the correction e
+  S_NUM = 5
+};
+
+enum RhsMode { RHS_EXPLICIT = 0, RHS_AD = 1, RHS_SP = 2 };
+
+// Arguments of the fine-level outer pass (update + residual + norms).
+struct OuterArgs {
+  int nx, ny, nz;
+  float bx, by, bz, alpha;      // operator weights (fine level)
+  float rbx, rby, ralpha;       // rhs: b = ralpha*I1 + rbx*Kx I0 + rby*Ky I0
+  const float *b;               // explicit rhs (RHS_EXPLICIT)
+  const float *I0, *I1;         // inputs (RHS_AD / RHS_SP)
+  const float *xh_in;           // iterate, high part
+  const float *xl_in;           // iterate, low part (nullable: zero)
+  const float *e;               // correction to add (nullable: none)
+  float *xh_out, *xl_out;       // new iterate (nullable: not written)
+  float *r_out;                 // residual (nullable: not written)
+  const double *scalars;        // reduced sums of the previous passes (mean fix)
+  int mean_fix;                 // AD: shift the update so that sum x = sum I0
+  double inv_n;                 // 1 / (nx*ny*nz)
+  double *partials;             // [gridDim.x][S_NUM]
+};
+
+// Host-side launchers (gd_kernels.cu).  All enqueue on `st` and return the
+// cudaGetLastError() of the launch.
+cudaError_t launch_rb_sweep(const LevelDev &L, const float *xin, const float *b, float *xout,
+                            bool zero_in, double *partials_sum, int *nblocks_out, cudaStream_t st);
+cudaError_t launch_residual_restrict(const LevelDev &F, const float *x, const float *b, int fx,
+                                     int fy, int fz, float *bc, cudaStream_t st);
+cudaError_t launch_prolong_add(const LevelDev &F, int fx, int fy, int fz, const float *xc,
+                               float *x, cudaStream_t st);
+cudaError_t launch_outer(const OuterArgs &a, int rhs_mode, int *nblocks_out, cudaStream_t st);
+cudaError_t launch_reduce(const double *partials, int nblocks, double *scalars, int slot_lo,
+                          int slot_hi, int accumulate, cudaStream_t st);
+// Coarsest solve by fast diagonalisation: x = V Dinv V^T b (V = Vx (x) Vy (x) Vz).
+// batch_z: z is not transformed (independent slices; Dinv is nx*ny).
+cudaError_t launch_fdm(int nx, int ny, int nz, const float *Vx, const float *Vy, const float *Vz,
+                       const float *Dinv, int batch_z, const float *b, float *x, float *tmp,
+                       cudaStream_t st);
+cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st);
+cudaError_t launch_copy(float *dst, const float *src, size_t n, cudaStream_t st);
+
+// Host: symmetric eigen-decomposition (cyclic Jacobi), FP64, row-major a[n*n].
+// On return w holds the eigenvalues and v (row-major, column k = eigenvector k).
+void jacobi_eigen(int n, double *a, double *w, double *v);

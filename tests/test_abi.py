@@ -1,0 +1,83 @@
+"""The C-ABI library: it loads, exports every symbol include/gd.h declares,
+and rejects bad arguments before touching the GPU (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1310_0041_gb300 as gd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "gd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_ ]+\*?\s*\b(gd_[a-z0-9_]+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gd.build()
+    return gd.lib()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_vcycle", "gd_destroy"):
+        assert f in names
+    assert set(names) == set(gd.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    assert gd.gd_version() == 1
+    assert gd.gd_status_string(gd.GD_OK) == "ok"
+    assert gd.gd_status_string(gd.GD_ERR_NOT_CONVERGED) == "not converged"
+
+
+def test_create_validation_without_gpu(lib):
+    h = ctypes.c_void_p()
+    f = lib.gd_stack_create
+    assert f(None, 8, 8, 8, 0, 0, 0, None) == gd.GD_ERR_INVALID_ARG
+    assert f(ctypes.byref(h), 1, 8, 8, 0, 0, 0, None) == gd.GD_ERR_INVALID_ARG
+    assert f(ctypes.byref(h), 8, 8, 0, 0, 0, 0, None) == gd.GD_ERR_INVALID_ARG
+    assert f(ctypes.byref(h), 8, 8, 8, 1, 0, 0, None) == gd.GD_ERR_UNSUPPORTED
+    assert f(ctypes.byref(h), 8, 8, 8, 0, gd.GD_DISC_LINEAR, 0, None) == gd.GD_ERR_UNSUPPORTED
+    assert f(ctypes.byref(h), 8, 8, 8, 0, 0, 7, None) == gd.GD_ERR_INVALID_ARG
+    assert f(ctypes.byref(h), 8, 8, 8, 0, 0, 0, None) == gd.GD_OK
+    s = gd.Stack(h, 8, 8, 8)
+    # argument checks that return before any CUDA call
+    rep = gd.GdReport()
+    W = gd.GdWeights
+    assert lib.gd_diffuse_z(h, None, None, W(0, 1, 1, 10), None, None, ctypes.byref(rep)) == gd.GD_ERR_INVALID_ARG
+    assert rep.status == gd.GD_ERR_INVALID_ARG
+    p = ctypes.c_void_p(0x1000)
+    assert lib.gd_diffuse_z(h, p, p, W(0, 1, 1, 10), None, None, None) == gd.GD_ERR_INVALID_ARG  # aliasing
+    q = ctypes.c_void_p(0x2000)
+    assert lib.gd_diffuse_z(h, p, q, W(0, 1, 1, 0.0), None, None, None) == gd.GD_ERR_INVALID_ARG  # bz = 0
+    assert lib.gd_diffuse_z(h, p, q, W(0, -1, 1, 1), None, None, None) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_diffuse_z(h, p, q, W(0, float("nan"), 1, 1), None, None, None) == gd.GD_ERR_INVALID_ARG
+    r = ctypes.c_void_p(0x3000)
+    assert lib.gd_screened_poisson_slices(h, p, q, r, 0.0, None, None, None) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_screened_poisson_slices(h, p, q, p, 0.01, None, None, None) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_vcycle(h, 5, W(0.1, 1, 1, 0), p, q, 1, None) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_vcycle(h, gd.GD_SYSTEM_SP, W(0.1, 1, 1, 1), p, q, 1, None) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_vcycle(h, gd.GD_SYSTEM_AD, W(0.0, 1, 1, 0), p, q, 1, None) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_smooth(h, W(0, 1, 1, 1), p, p, 1) == gd.GD_ERR_INVALID_ARG
+    assert gd.gd_destroy(s) == gd.GD_OK
+    assert lib.gd_destroy(None) == gd.GD_OK
+
+
+def test_binding_marshalling_rejects_wrong_dtype(lib):
+    import numpy as np
+    with pytest.raises(ValueError):
+        gd._ptr(np.zeros(8, np.float64), 8, "x")
+    with pytest.raises(ValueError):
+        gd._ptr(np.zeros(7, np.float32), 8, "x")
+    assert gd._ptr(None) is None

@@ -1,0 +1,45 @@
+"""Parity at the full 1024 x 1024 x 128 workload, in the launch configuration
+the benchmark times: AD (beta_z = 10) then SP (alpha = 0.01), each to a
+relative residual of 1e-6, against the exact discrete solutions (DCT closed
+form, FP64) on the whole stack.  Bar: max |GPU - exact| <= 1e-3 on the
+0..255 scale; solver residuals <= 1e-6."""
+import numpy as np
+import pytest
+
+import gdsynth
+from oracle import closed_form as cf
+import paper_1310_0041_gb300 as gd
+
+pytestmark = pytest.mark.gpu
+
+
+def test_fullsize_1024x1024x128():
+    import torch
+    gd.build()
+    nx, ny, nz = 1024, 1024, 128
+    I0n = gdsynth.em_stack(nx, ny, nz, seed=2, ncells=2000)
+    I0 = torch.from_numpy(I0n).cuda().float()
+    I1 = torch.empty_like(I0)
+    I2 = torch.empty_like(I0)
+    s = gd.gd_stack_create(nx, ny, nz)
+    try:
+        ctl = gd.solve_ctl(30, 1e-6, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL)
+        r1 = gd.gd_diffuse_z(s, I0, I1, (0.0, 1.0, 1.0, 10.0), ctl)
+        r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, 0.01, ctl)
+    finally:
+        gd.gd_destroy(s)
+    assert r1["status"] == gd.GD_OK and r1["rel_residual"] <= 1e-6, r1
+    assert r2["status"] == gd.GD_OK and r2["rel_residual"] <= 1e-6, r2
+    i0 = I0n.astype(np.float64)
+    a1 = I1.cpu().numpy().astype(np.float64)
+    ref1 = cf.ad(i0, 1.0, 1.0, 10.0)
+    err1 = np.abs(a1 - ref1).max()
+    del ref1
+    a2 = I2.cpu().numpy().astype(np.float64)
+    ref2 = cf.sp(i0, a1, 0.01)
+    err2 = np.abs(a2 - ref2).max()
+    print("fullsize: AD cycles %d rel %.3g (fp32 out %.3g) max|d| %.3g; SP cycles %d rel %.3g max|d| %.3g"
+          % (r1["cycles"], r1["rel_residual"], r1["rel_residual_out"], err1, r2["cycles"],
+             r2["rel_residual"], err2))
+    assert err1 <= 1e-3
+    assert err2 <= 1e-3

@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+References are the oracle's (tests-only) routes: the DCT closed form, which
+is the exact discrete solution of the 6-point Neumann systems, and the C
+oracle's red-black sweep.  Bars (stated with each test):
+  * solves: max |GPU - exact| <= 1e-3 on the 0..255 intensity scale, and the
+    solver's relative residual ||b - A x|| / ||b|| <= the requested tolerance;
+  * one or two relaxation sweeps: FP32 kernel vs FP64 oracle on the same
+    float32 inputs, max |diff| <= 1e-3 (FP32 rounding of values up to 255 is
+    ~1.5e-5 per operation).
+"""
+import numpy as np
+import pytest
+
+import gdsynth
+import oracle
+from oracle import closed_form as cf
+import paper_1310_0041_gb300 as gd
+
+pytestmark = pytest.mark.gpu
+
+TOL_INTENSITY = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    assert _t.cuda.is_available(), "these tests need a CUDA GPU"
+    gd.build()
+    gd.lib()
+    return _t
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def stack_u8(nx, ny, nz, seed, **kw):
+    return gdsynth.em_stack(nx, ny, nz, seed=seed, **kw).astype(np.float32)
+
+
+def ad_gpu(torch, I0, bz, tol=1e-6, max_cycles=30, bx=1.0, by=1.0, x0=None, flags=0, host=False):
+    nz, ny, nx = I0.shape
+    s = gd.gd_stack_create(nx, ny, nz)
+    try:
+        if host:
+            i0 = np.ascontiguousarray(I0, np.float32)
+            out = np.zeros_like(i0)
+        else:
+            i0 = dev(torch, I0)
+            out = torch.zeros_like(i0)
+        rep = gd.gd_diffuse_z(s, i0, out, (0.0, bx, by, bz),
+                              gd.solve_ctl(max_cycles, tol, flags=flags), x0=x0)
+        res = out if host else out.cpu().numpy()
+    finally:
+        gd.gd_destroy(s)
+    return res.astype(np.float64), rep
+
+
+def sp_gpu(torch, I0, I1, alpha, tol=1e-6, max_cycles=30, flags=0):
+    nz, ny, nx = I0.shape
+    s = gd.gd_stack_create(nx, ny, nz)
+    try:
+        i0, i1 = dev(torch, I0), dev(torch, I1)
+        out = torch.zeros_like(i0)
+        rep = gd.gd_screened_poisson_slices(s, i0, i1, out, alpha, gd.solve_ctl(max_cycles, tol, flags=flags))
+        res = out.cpu().numpy()
+    finally:
+        gd.gd_destroy(s)
+    return res.astype(np.float64), rep
+
+
+# ---------------------------------------------------------------------------
+# kernel-level: one and two red-black sweeps vs the oracle's red-black sweep
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(5, 37, 70), (40, 19, 9), (1, 16, 64), (3, 2, 2), (9, 130, 67)])
+@pytest.mark.parametrize("w", [(0.0, 1.0, 1.0, 10.0), (0.01, 1.0, 1.0, 0.0), (0.3, 1.0, 2.0, 0.5)])
+@pytest.mark.parametrize("nsweeps", [1, 2])
+def test_rb_sweep_matches_oracle(torch, shape, w, nsweeps):
+    rng = np.random.default_rng(hash((shape, w, nsweeps)) % 2**32)
+    b = rng.uniform(-50, 50, size=shape).astype(np.float32)
+    x = rng.uniform(0, 255, size=shape).astype(np.float32)
+    want = oracle.gs_sweeps(b, x, *w, order="redblack", nsweeps=nsweeps)
+    nz, ny, nx = shape
+    s = gd.gd_stack_create(nx, ny, nz)
+    try:
+        xd = dev(torch, x)
+        gd.gd_smooth(s, w, dev(torch, b), xd, nsweeps)
+        got = xd.cpu().numpy().astype(np.float64)
+    finally:
+        gd.gd_destroy(s)
+    assert np.abs(got - want).max() <= TOL_INTENSITY
+
+
+def test_rb_sweep_host_pointers(torch):
+    """Host (numpy) arrays go through the library's staging copies."""
+    shape = (6, 21, 33)
+    rng = np.random.default_rng(3)
+    b = rng.uniform(-50, 50, size=shape).astype(np.float32)
+    x = rng.uniform(0, 255, size=shape).astype(np.float32)
+    w = (0.0, 1.0, 1.0, 10.0)
+    want = oracle.gs_sweeps(b, x, *w, nsweeps=3)
+    s = gd.gd_stack_create(33, 21, 6)
+    try:
+        gd.gd_smooth(s, w, b, x, 3)
+    finally:
+        gd.gd_destroy(s)
+    assert np.abs(x - want).max() <= TOL_INTENSITY
+
+
+# ---------------------------------------------------------------------------
+# solves: oracle-size stack (64x64x16), both z weights, to 1e-8
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("bz", [10.0, 0.1])
+def test_ad_64x64x16(torch, bz):
+    I0 = stack_u8(64, 64, 16, seed=1)
+    got, rep = ad_gpu(torch, I0, bz, tol=1e-8, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL)
+    assert rep["status"] == gd.GD_OK, rep
+    assert rep["rel_residual"] <= 1e-8
+    want = cf.ad(I0, 1.0, 1.0, bz)
+    assert np.abs(got - want).max() <= TOL_INTENSITY
+    assert abs(got.mean() - I0.astype(np.float64).mean()) < 1e-4
+    # the library's residual of the float32 output agrees with the oracle's
+    b = oracle.rhs_ad(I0, 1.0, 1.0)
+    ro = oracle.rel_residual(b, got, 0.0, 1.0, 1.0, bz)
+    assert abs(rep["rel_residual_out"] - ro) <= 0.05 * ro + 1e-9
+
+
+def test_sp_64x64x16(torch):
+    I0 = stack_u8(64, 64, 16, seed=2)
+    I1 = cf.ad(I0, 1.0, 1.0, 10.0).astype(np.float32)
+    got, rep = sp_gpu(torch, I0, I1, 0.01, tol=1e-8)
+    assert rep["status"] == gd.GD_OK, rep
+    assert rep["rel_residual"] <= 1e-8
+    want = cf.sp(I0, I1, 0.01)
+    assert np.abs(got - want).max() <= TOL_INTENSITY
+    # slice means of I1 are kept (Sec. 3.1 consequence)
+    np.testing.assert_allclose(got.mean(axis=(1, 2)), I1.astype(np.float64).mean(axis=(1, 2)), atol=1e-3)
+
+
+def test_pipeline_64x64x16(torch):
+    """AD then SP on the GPU against the closed form of both steps."""
+    I0 = stack_u8(64, 64, 16, seed=3)
+    I1, r1 = ad_gpu(torch, I0, 10.0, tol=1e-8)
+    I2, r2 = sp_gpu(torch, I0, I1.astype(np.float32), 0.01, tol=1e-8)
+    want = cf.sp(I0, cf.ad(I0, 1.0, 1.0, 10.0), 0.01)
+    assert np.abs(I2 - want).max() <= TOL_INTENSITY
+
+
+# ---------------------------------------------------------------------------
+# solves: the 256x256x32 crop of the 1024x1024x128 stack, solved as its own
+# problem, to 1e-6 (several tiles, several z chunks, ragged-free and ragged)
+# ---------------------------------------------------------------------------
+def crop_256():
+    return gdsynth.em_stack(1024, 1024, 128, seed=7, ncells=2000,
+                            window=(384, 512, 48, 256, 256, 32)).astype(np.float32)
+
+
+def test_ad_sp_crop_256x256x32(torch):
+    I0 = crop_256()
+    I1, r1 = ad_gpu(torch, I0, 10.0, tol=1e-6)
+    assert r1["status"] == gd.GD_OK and r1["rel_residual"] <= 1e-6, r1
+    assert np.abs(I1 - cf.ad(I0, 1.0, 1.0, 10.0)).max() <= TOL_INTENSITY
+    assert r1["rho_per_cycle"] < 0.2
+    I2, r2 = sp_gpu(torch, I0, I1.astype(np.float32), 0.01, tol=1e-6)
+    assert r2["status"] == gd.GD_OK and r2["rel_residual"] <= 1e-6, r2
+    assert np.abs(I2 - cf.sp(I0, I1, 0.01)).max() <= TOL_INTENSITY
+
+
+@pytest.mark.parametrize("shape", [(13, 75, 100), (7, 61, 47), (3, 33, 40), (1, 50, 30), (2, 2, 2),
+                                   (1, 2, 2), (33, 17, 65)])
+def test_ragged_sizes(torch, shape):
+    nz, ny, nx = shape
+    I0 = stack_u8(nx, ny, nz, seed=11)
+    for bz in (10.0, 0.1):
+        got, rep = ad_gpu(torch, I0, bz, tol=1e-7)
+        assert rep["status"] == gd.GD_OK, (bz, rep)
+        assert np.abs(got - cf.ad(I0, 1.0, 1.0, bz)).max() <= TOL_INTENSITY
+    I1 = cf.ad(I0, 1.0, 1.0, 10.0).astype(np.float32)
+    for alpha in (0.001, 0.1):
+        got, rep = sp_gpu(torch, I0, I1, alpha, tol=1e-7)
+        assert rep["status"] == gd.GD_OK, (alpha, rep)
+        assert np.abs(got - cf.sp(I0, I1, alpha)).max() <= TOL_INTENSITY
+
+
+# ---------------------------------------------------------------------------
+# degenerate inputs and options
+# ---------------------------------------------------------------------------
+def test_z_constant_stack_is_a_fixed_point(torch):
+    sl = stack_u8(80, 48, 1, seed=12)
+    I0 = np.repeat(sl, 9, axis=0)
+    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-6)
+    assert rep["status"] == gd.GD_OK
+    assert rep["cycles"] == 0  # b - A I0 = -bz Kz I0 = 0: converged at the start
+    np.testing.assert_array_equal(got, I0)
+
+
+def test_slice_constant_stack(torch):
+    """b = 0 (each slice constant): the solution is the global mean."""
+    I0 = np.broadcast_to(np.arange(6, dtype=np.float32)[:, None, None] * 10.0, (6, 20, 24)).copy()
+    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-6)
+    np.testing.assert_allclose(got, I0.mean(), atol=1e-3)
+
+
+def test_self_reproduction(torch):
+    I0 = stack_u8(96, 64, 4, seed=13)
+    got, rep = sp_gpu(torch, I0, I0, 0.01, tol=1e-6)
+    assert rep["cycles"] == 0
+    np.testing.assert_array_equal(got, I0)
+
+
+def test_initial_guess_and_host_arrays(torch):
+    I0 = stack_u8(64, 48, 8, seed=14)
+    want = cf.ad(I0, 1.0, 1.0, 10.0)
+    # a caller's initial guess with the wrong mean: the mean is still fixed
+    x0 = dev(torch, I0 + 7.0)
+    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-7, x0=x0)
+    assert np.abs(got - want).max() <= TOL_INTENSITY
+    # x0 aliasing the output buffer
+    nz, ny, nx = I0.shape
+    s = gd.gd_stack_create(nx, ny, nz)
+    try:
+        i0 = dev(torch, I0)
+        out = dev(torch, want)  # exact solution as the start: no cycle needed
+        rep = gd.gd_diffuse_z(s, i0, out, (0, 1, 1, 10.0), gd.solve_ctl(10, 1e-6), x0=out)
+        assert rep["cycles"] <= 1
+        assert np.abs(out.cpu().numpy() - want).max() <= TOL_INTENSITY
+    finally:
+        gd.gd_destroy(s)
+    # host arrays in and out
+    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-7, host=True)
+    assert np.abs(got - want).max() <= TOL_INTENSITY
+
+
+def test_max_cycles_and_status(torch):
+    I0 = stack_u8(64, 64, 8, seed=15)
+    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-12, max_cycles=2)
+    assert rep["status"] == gd.GD_ERR_NOT_CONVERGED
+    assert rep["cycles"] == 2
+    assert rep["history"][2] < rep["history"][0]
+
+
+def test_deterministic(torch):
+    I0 = stack_u8(128, 96, 12, seed=16)
+    a, _ = ad_gpu(torch, I0, 10.0, tol=1e-7)
+    b, _ = ad_gpu(torch, I0, 10.0, tol=1e-7)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_vcycle_primitive(torch):
+    """gd_vcycle: plain FP32 V-cycles on an explicit right-hand side."""
+    I0 = stack_u8(128, 128, 16, seed=17)
+    b = oracle.rhs_ad(I0, 1.0, 1.0).astype(np.float32)
+    s = gd.gd_stack_create(128, 128, 16)
+    try:
+        x = dev(torch, I0)
+        rep = gd.gd_vcycle(s, gd.GD_SYSTEM_AD, (0, 1, 1, 10.0), dev(torch, b), x, 4)
+        assert rep["rho_per_cycle"] < 0.2, rep
+        xs = x.cpu().numpy().astype(np.float64)
+        want = cf.ad(I0, 1.0, 1.0, 10.0)
+        xs += want.mean() - xs.mean()
+        assert np.abs(xs - want).max() < 0.05
+        # residual definition agrees with the oracle
+        ro = oracle.rel_residual(b, x.cpu().numpy(), 0.0, 1.0, 1.0, 10.0)
+        assert abs(rep["rel_residual"] - ro) <= 0.02 * ro
+        # SP system with odd sweep parity handled
+        bsp = oracle.rhs_sp(I0, I0 * 0.5, 0.05).astype(np.float32)
+        y = dev(torch, I0)
+        rep = gd.gd_vcycle(s, gd.GD_SYSTEM_SP, (0.05, 1, 1, 0.0), dev(torch, bsp), y, 3)
+        assert rep["rel_residual"] < 1e-3
+    finally:
+        gd.gd_destroy(s)
+
+
+def test_residual_entry_point(torch):
+    I0 = stack_u8(64, 40, 6, seed=18)
+    x = (cf.ad(I0, 1.0, 1.0, 10.0) + np.random.default_rng(0).normal(0, 0.1, I0.shape)).astype(np.float32)
+    s = gd.gd_stack_create(64, 40, 6)
+    try:
+        rel = gd.gd_residual(s, gd.GD_SYSTEM_AD, (0, 1, 1, 10.0), dev(torch, I0), None, dev(torch, x))
+    finally:
+        gd.gd_destroy(s)
+    ro = oracle.rel_residual(oracle.rhs_ad(I0, 1.0, 1.0), x, 0.0, 1.0, 1.0, 10.0)
+    assert abs(rel - ro) <= 1e-4 * ro
