@@ -473,6 +473,23 @@ int resolve(gd_stack *s, const float *p, bool in, int slot, float **dev) {
 
 bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
+// w = hi + lo with hi = fl32(w): the weights of the outer residual as float pairs
+void split(double w, float &hi, float &lo) {
+  hi = (float)w;
+  lo = (float)(w - (double)hi);
+}
+
+void set_weights(OuterArgs &a, double bx, double by, double bz, double alpha, double rbx,
+                 double rby, double ralpha) {
+  split(bx, a.bx, a.bx_lo);
+  split(by, a.by, a.by_lo);
+  split(bz, a.bz, a.bz_lo);
+  split(alpha, a.alpha, a.alpha_lo);
+  split(rbx, a.rbx, a.rbx_lo);
+  split(rby, a.rby, a.rby_lo);
+  split(ralpha, a.ralpha, a.ralpha_lo);
+}
+
 int check_ctl(gd_stack *s, const gd_solve_ctl *ctl, gd_solve_ctl *out) {
   gd_solve_ctl c = {20, 1e-6, 2, 2, 16, 0};
   if (ctl) c = *ctl;
@@ -528,13 +545,10 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   }
   OuterArgs a;
   std::memset(&a, 0, sizeof a);
-  a.bx = (float)w[1];
-  a.by = (float)w[2];
-  a.bz = system == GD_SYSTEM_SP ? 0.f : (float)w[3];
-  a.alpha = system == GD_SYSTEM_SP ? (float)w[0] : 0.f;
-  a.rbx = system == GD_SYSTEM_SP ? 1.f : (float)w[1];
-  a.rby = system == GD_SYSTEM_SP ? 1.f : (float)w[2];
-  a.ralpha = system == GD_SYSTEM_SP ? (float)w[0] : 0.f;
+  if (system == GD_SYSTEM_SP)
+    set_weights(a, w[1], w[2], 0.0, w[0], 1.0, 1.0, w[0]);
+  else
+    set_weights(a, w[1], w[2], w[3], 0.0, w[1], w[2], 0.0);
   a.I0 = I0;
   a.I1 = I1;
   const int rhs = system == GD_SYSTEM_SP ? RHS_SP : RHS_AD;
@@ -760,10 +774,7 @@ int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh,
   Level &F = s->plan.L[0];
   OuterArgs a;
   std::memset(&a, 0, sizeof a);
-  a.bx = (float)w.beta_x;
-  a.by = (float)w.beta_y;
-  a.bz = (float)w.beta_z;
-  a.alpha = (float)w.alpha;
+  set_weights(a, w.beta_x, w.beta_y, w.beta_z, w.alpha, 0.0, 0.0, 0.0);
   a.b = b;
   a.xh_in = x;
   double h[S_NUM];
@@ -821,13 +832,10 @@ int gd_residual(gd_stack *s, int system, gd_weights w, const float *I0h, const f
   OuterArgs a;
   std::memset(&a, 0, sizeof a);
   const bool sp = system == GD_SYSTEM_SP;
-  a.bx = sp ? 1.f : (float)w.beta_x;
-  a.by = sp ? 1.f : (float)w.beta_y;
-  a.bz = sp ? 0.f : (float)w.beta_z;
-  a.alpha = sp ? (float)w.alpha : 0.f;
-  a.rbx = a.bx;
-  a.rby = a.by;
-  a.ralpha = a.alpha;
+  if (sp)
+    set_weights(a, 1.0, 1.0, 0.0, w.alpha, 1.0, 1.0, w.alpha);
+  else
+    set_weights(a, w.beta_x, w.beta_y, w.beta_z, 0.0, w.beta_x, w.beta_y, 0.0);
   a.I0 = I0;
   a.I1 = I1;
   a.xh_in = x;

@@ -35,8 +35,12 @@ enum RhsMode { RHS_EXPLICIT = 0, RHS_AD = 1, RHS_SP = 2 };
 // Arguments of the fine-level outer pass (update + residual + norms).
 struct OuterArgs {
   int nx, ny, nz;
-  float bx, by, bz, alpha;      // operator weights (fine level)
-  float rbx, rby, ralpha;       // rhs: b = ralpha*I1 + rbx*Kx I0 + rby*Ky I0
+  // operator weights (fine level) and rhs weights (b = ralpha*I1 + rbx*Kx I0 +
+  // rby*Ky I0), each as a float pair (w, w_lo) with w + w_lo = the double weight
+  float bx, by, bz, alpha;
+  float bx_lo, by_lo, bz_lo, alpha_lo;
+  float rbx, rby, ralpha;
+  float rbx_lo, rby_lo, ralpha_lo;
   const float *b;               // explicit rhs (RHS_EXPLICIT)
   const float *I0, *I1;         // inputs (RHS_AD / RHS_SP)
   const float *xh_in;           // iterate, high part

@@ -1,8 +1,10 @@
 """Parity at the full 1024 x 1024 x 128 workload, in the launch configuration
 the benchmark times: AD (beta_z = 10) then SP (alpha = 0.01), each to a
-relative residual of 1e-6, against the exact discrete solutions (DCT closed
-form, FP64) on the whole stack.  Bar: max |GPU - exact| <= 1e-3 on the
-0..255 scale; solver residuals <= 1e-6."""
+relative residual of 1e-6 (AD) and 1e-7 (SP), against the exact discrete
+solutions (DCT closed form, FP64) on the whole stack.  Bar: max |GPU - exact|
+<= 1e-3 on the 0..255 scale; solver residuals <= the tolerances.  SP needs the
+tighter tolerance for the max |d| bar: alpha = 0.01 scales the slice-smooth
+error to ~100x the residual."""
 import numpy as np
 import pytest
 
@@ -23,13 +25,14 @@ def test_fullsize_1024x1024x128():
     I2 = torch.empty_like(I0)
     s = gd.gd_stack_create(nx, ny, nz)
     try:
-        ctl = gd.solve_ctl(30, 1e-6, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL)
-        r1 = gd.gd_diffuse_z(s, I0, I1, (0.0, 1.0, 1.0, 10.0), ctl)
-        r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, 0.01, ctl)
+        r1 = gd.gd_diffuse_z(s, I0, I1, (0.0, 1.0, 1.0, 10.0),
+                             gd.solve_ctl(30, 1e-6, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL))
+        r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, 0.01,
+                                           gd.solve_ctl(30, 1e-7, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL))
     finally:
         gd.gd_destroy(s)
     assert r1["status"] == gd.GD_OK and r1["rel_residual"] <= 1e-6, r1
-    assert r2["status"] == gd.GD_OK and r2["rel_residual"] <= 1e-6, r2
+    assert r2["status"] == gd.GD_OK and r2["rel_residual"] <= 1e-7, r2
     i0 = I0n.astype(np.float64)
     a1 = I1.cpu().numpy().astype(np.float64)
     ref1 = cf.ad(i0, 1.0, 1.0, 10.0)

@@ -113,6 +113,8 @@ def test_rb_sweep_host_pointers(torch):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("bz", [10.0, 0.1])
 def test_ad_64x64x16(torch, bz):
+    """Oracle-size stack solved to 1e-8 (the float-pair iterate with a
+    double-float residual goes well below what a float32 array represents)."""
     I0 = stack_u8(64, 64, 16, seed=1)
     got, rep = ad_gpu(torch, I0, bz, tol=1e-8, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL)
     assert rep["status"] == gd.GD_OK, rep
@@ -124,6 +126,7 @@ def test_ad_64x64x16(torch, bz):
     b = oracle.rhs_ad(I0, 1.0, 1.0)
     ro = oracle.rel_residual(b, got, 0.0, 1.0, 1.0, bz)
     assert abs(rep["rel_residual_out"] - ro) <= 0.05 * ro + 1e-9
+    assert ro < 2e-6  # the float32 representation floor (~1.2e-6 for bz = 10)
 
 
 def test_sp_64x64x16(torch):
@@ -157,13 +160,15 @@ def crop_256():
 
 
 def test_ad_sp_crop_256x256x32(torch):
+    """AD to 1e-6 and SP to 1e-7: with alpha = 0.01 the slice-smooth error of
+    SP is ~100x its residual, so 1e-6 alone does not give max|d| <= 1e-3."""
     I0 = crop_256()
     I1, r1 = ad_gpu(torch, I0, 10.0, tol=1e-6)
     assert r1["status"] == gd.GD_OK and r1["rel_residual"] <= 1e-6, r1
     assert np.abs(I1 - cf.ad(I0, 1.0, 1.0, 10.0)).max() <= TOL_INTENSITY
     assert r1["rho_per_cycle"] < 0.2
-    I2, r2 = sp_gpu(torch, I0, I1.astype(np.float32), 0.01, tol=1e-6)
-    assert r2["status"] == gd.GD_OK and r2["rel_residual"] <= 1e-6, r2
+    I2, r2 = sp_gpu(torch, I0, I1.astype(np.float32), 0.01, tol=1e-7)
+    assert r2["status"] == gd.GD_OK and r2["rel_residual"] <= 1e-7, r2
     assert np.abs(I2 - cf.sp(I0, I1, 0.01)).max() <= TOL_INTENSITY
 
 
@@ -254,12 +259,12 @@ def test_vcycle_primitive(torch):
     s = gd.gd_stack_create(128, 128, 16)
     try:
         x = dev(torch, I0)
-        rep = gd.gd_vcycle(s, gd.GD_SYSTEM_AD, (0, 1, 1, 10.0), dev(torch, b), x, 4)
+        rep = gd.gd_vcycle(s, gd.GD_SYSTEM_AD, (0, 1, 1, 10.0), dev(torch, b), x, 8)
         assert rep["rho_per_cycle"] < 0.2, rep
         xs = x.cpu().numpy().astype(np.float64)
         want = cf.ad(I0, 1.0, 1.0, 10.0)
         xs += want.mean() - xs.mean()
-        assert np.abs(xs - want).max() < 0.05
+        assert np.abs(xs - want).max() < 0.01
         # residual definition agrees with the oracle
         ro = oracle.rel_residual(b, x.cpu().numpy(), 0.0, 1.0, 1.0, 10.0)
         assert abs(rep["rel_residual"] - ro) <= 0.02 * ro
