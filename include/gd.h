@@ -62,7 +62,7 @@ typedef enum {
   GD_ERR_CUDA = 4,         /* a CUDA runtime call failed */
   GD_ERR_NOT_CONVERGED = 5,/* max_cycles reached, or residual stalled, above rel_tol */
   GD_ERR_DIVERGED = 6,     /* residual became non-finite or grew by > 1e3 */
-  GD_ERR_TIMEOUT = 7       /* reserved for bounded device-side waits */
+  GD_ERR_TIMEOUT = 7       /* a kernel gave up a bounded wait for its own asynchronous copies */
 } gd_status;
 
 enum { GD_BC_NEUMANN = 0 };                                     /* reading of Sec. 3-4: natural BC */
@@ -115,6 +115,9 @@ typedef struct {
  *   disc: GD_DISC_CONSTANT only (Sec. 4.2; others: GD_ERR_UNSUPPORTED)
  *   prec: GD_PREC_FP32 (others: GD_ERR_UNSUPPORTED)
  *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream
+ * If the environment variable GD_DISABLE_TMA is set (and not "0") when the
+ * stack is created, the stack runs only the plain kernels (no TMA pipeline,
+ * no fused transfers); results are the same up to rounding.
  */
 int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, int prec,
                     void *cuda_stream);

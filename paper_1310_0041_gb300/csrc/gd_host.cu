@@ -81,6 +81,7 @@ struct gd_stack {
   long long prof_launches[P_NUM] = {0};
   double prof_ms[P_NUM] = {0}, prof_bytes[P_NUM] = {0};
   long long launches = 0;
+  bool no_tma = false;  // GD_DISABLE_TMA set at creation: plain (unfused) kernels only
   std::string err;
 };
 
@@ -135,6 +136,10 @@ struct ProfScope {
     }
   }
   ~ProfScope() {
+    if (a && bytes <= 0.0) {
+      s->ev_pool.push_back(a);  // cancelled: nothing was launched
+      a = nullptr;
+    }
     if (a) {
       cudaEvent_t b = ev_get(s);
       cudaEventRecord(b, s->stream);
@@ -323,9 +328,17 @@ int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
 }
 
 // ---- kernel wrappers with launch accounting ----
-int sweep(gd_stack *s, Level &l, bool fine, bool zero_in, bool sum_e) {
+// One red-black sweep of level l (x -> t, then the pointers swap), with the
+// optional fusions: prolong (x += P x_{l+1} first), restrict (the residual
+// summed into level l+1's b afterwards), sum (block sums of the output into
+// scalars[S_E]).  Levels whose arrays TMA cannot address run the plain
+// kernels with the fused steps as separate passes.
+int sweep(gd_stack *s, int li, bool zero_in, bool prolong, bool restrict_, bool sum_e) {
+  std::vector<Level> &LV = s->plan.L;
+  Level &l = LV[li];
+  Level *C = (prolong || restrict_) ? &LV[li + 1] : nullptr;
+  const bool fine = li == 0;
   int nb = 0;
-  const double bytes = (double)l.n * (zero_in ? 8.0 : 12.0);
   double *part = nullptr;
   if (sum_e) {
     const int gx = (l.d.nx + 63) / 64, gy = (l.d.ny + 15) / 16;
@@ -333,9 +346,53 @@ int sweep(gd_stack *s, Level &l, bool fine, bool zero_in, bool sum_e) {
     if (st != GD_OK) return st;
     part = s->partials;
   }
-  {
-    ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE, bytes);
-    CK(launch_rb_sweep(l.d, l.x, l.b, l.t, zero_in, part, &nb, s->stream));
+  bool done = false;
+  if (!s->no_tma && zmarch_usable(l.d)) {
+    ZSweepArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.L = l.d;
+    a.xout = l.t;
+    a.partials = part;
+    a.err = s->scalars + S_ERR;
+    if (C) {
+      a.xc = C->x;
+      a.ncx = C->d.nx;
+      a.ncy = C->d.ny;
+      a.fx = l.fx;
+      a.fy = l.fy;
+      a.fz = l.fz;
+      a.bc = C->b;
+    }
+    double bytes = (double)l.n * (zero_in ? 8.0 : 12.0) + (C ? 4.0 * (double)C->n : 0.0);
+    cudaError_t e;
+    {
+      ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE, bytes);
+      e = launch_zsweep(a, l.x, l.b, zero_in, prolong, restrict_, sum_e, &nb, s->stream);
+      if (e == cudaErrorNotSupported) {
+        s->launches -= 1;
+        ps.bytes = 0;
+        cudaGetLastError();
+      }
+    }
+    if (e == cudaSuccess) done = true;
+    else if (e != cudaErrorNotSupported) {
+      set_err(s, "TMA sweep launch failed: %s", cudaGetErrorString(e));
+      return GD_ERR_CUDA;
+    }
+  }
+  if (!done) {
+    if (prolong) {
+      ProfScope ps(s, P_PROLONG, (double)l.n * 8.0 + (double)C->n * 4.0);
+      CK(launch_prolong_add(l.d, l.fx, l.fy, l.fz, C->x, l.x, s->stream));
+    }
+    {
+      ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE, (double)l.n * (zero_in ? 8.0 : 12.0));
+      CK(launch_rb_sweep(l.d, l.x, l.b, l.t, zero_in, part, &nb, s->stream));
+    }
+    if (restrict_) {
+      ProfScope ps(s, P_RESTRICT, (double)l.n * 8.0 + (double)C->n * 4.0);
+      CK(launch_residual_restrict(l.d, l.t, l.b, l.fx, l.fy, l.fz, C->b, s->stream));
+    }
   }
   std::swap(l.x, l.t);
   if (sum_e) {
@@ -356,7 +413,8 @@ int coarsest_solve(gd_stack *s, Level &l) {
 
 // One V(nu1,nu2) cycle on level 0's (x, b).  zero_init: level 0's x starts at
 // zero (correction form).  sum_e: the last fine sweep also sums its output
-// into scalars[S_E].
+// into scalars[S_E].  The last pre-sweep of a level carries the residual and
+// its down-sampling; the first post-sweep carries the up-sampled correction.
 int vcycle(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
   std::vector<Level> &L = s->plan.L;
   const int nl = (int)L.size();
@@ -366,26 +424,19 @@ int vcycle(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
     // when the sum of x is wanted, one relaxation sweep (which leaves the
     // exact solution unchanged up to rounding) computes it
     if ((st = coarsest_solve(s, L[0])) != GD_OK) return st;
-    if (sum_e && (st = sweep(s, L[0], true, false, true)) != GD_OK) return st;
+    if (sum_e && (st = sweep(s, 0, false, false, false, true)) != GD_OK) return st;
     return GD_OK;
   }
   for (int l = 0; l < nl - 1; ++l) {
     const bool zi = (l > 0) || zero_init;
     for (int k = 0; k < nu1; ++k)
-      if ((st = sweep(s, L[l], l == 0, zi && k == 0, false)) != GD_OK) return st;
-    Level &F = L[l], &C = L[l + 1];
-    ProfScope ps(s, P_RESTRICT, (double)F.n * 8.0 + (double)C.n * 4.0);
-    CK(launch_residual_restrict(F.d, F.x, F.b, F.fx, F.fy, F.fz, C.b, s->stream));
+      if ((st = sweep(s, l, zi && k == 0, false, k == nu1 - 1, false)) != GD_OK) return st;
   }
   if ((st = coarsest_solve(s, L[nl - 1])) != GD_OK) return st;
   for (int l = nl - 2; l >= 0; --l) {
-    Level &F = L[l], &C = L[l + 1];
-    {
-      ProfScope ps(s, P_PROLONG, (double)F.n * 8.0 + (double)C.n * 4.0);
-      CK(launch_prolong_add(F.d, F.fx, F.fy, F.fz, C.x, F.x, s->stream));
-    }
     for (int k = 0; k < nu2; ++k)
-      if ((st = sweep(s, F, l == 0, false, sum_e && l == 0 && k == nu2 - 1)) != GD_OK) return st;
+      if ((st = sweep(s, l, false, k == 0, false, sum_e && l == 0 && k == nu2 - 1)) != GD_OK)
+        return st;
   }
   return GD_OK;
 }
@@ -401,23 +452,37 @@ int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if ((st = ensure_partials(s, sms * 8 + 64)) != GD_OK) return st;
+  if ((st = ensure_partials(s, zouter_max_blocks(s->nx, s->ny, s->nz))) != GD_OK) return st;
   a.partials = s->partials;
   double bytes = 4.0 * (1 + (a.xl_in ? 1 : 0) + (a.e ? 1 : 0) + (a.xh_out ? 2 : 0) +
                         (a.r_out ? 1 : 0) + (rhs_mode == RHS_SP ? 2 : 1)) * (double)n;
   int nb = 0;
   {
     ProfScope ps(s, P_OUTER, bytes);
-    CK(launch_outer(a, rhs_mode, &nb, s->stream));
+    cudaError_t e = s->no_tma ? cudaErrorNotSupported
+                              : launch_zouter(a, rhs_mode, s->scalars + S_ERR, &nb, s->stream);
+    if (e == cudaErrorNotSupported) {
+      cudaGetLastError();
+      e = launch_outer(a, rhs_mode, &nb, s->stream);
+    }
+    if (e != cudaSuccess) {
+      set_err(s, "outer pass launch failed: %s", cudaGetErrorString(e));
+      return GD_ERR_CUDA;
+    }
   }
   {
     ProfScope ps(s, P_REDUCE, (double)nb * S_NUM * 8.0);
     CK(launch_reduce(s->partials, nb, s->scalars, S_RR, S_I0 + 1, 0, s->stream));
   }
   if (h_out) {
-    CK(cudaMemcpyAsync(s->h_scalars, s->scalars, S_NUM * sizeof(double), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(s->h_scalars, s->scalars, 8 * sizeof(double), cudaMemcpyDeviceToHost,
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
     std::memcpy(h_out, s->h_scalars, S_NUM * sizeof(double));
+    if (s->h_scalars[S_ERR] != 0.0) {
+      set_err(s, "a kernel's bounded wait for its TMA loads gave up");
+      return GD_ERR_TIMEOUT;
+    }
   }
   return GD_OK;
 }
@@ -693,6 +758,8 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
   s->disc = disc;
   s->prec = prec;
   s->stream = (cudaStream_t)cuda_stream;
+  const char *nt = std::getenv("GD_DISABLE_TMA");
+  s->no_tma = nt && nt[0] && std::strcmp(nt, "0") != 0;
   *out = s;
   return GD_OK;
 }
@@ -855,24 +922,34 @@ int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps
   const bool x_host = !is_device_ptr(xh);
   if ((st = resolve(s, bh, true, 0, &b)) != GD_OK) return st;
   if ((st = resolve(s, xh, true, 2, &x)) != GD_OK) return st;
+  // a one-level plan of the given weights, borrowing the caller's arrays
+  Plan saved = s->plan;
+  s->plan = Plan();
   Level l;
   l.d = LevelDev{s->nx, s->ny, s->nz, 1, 1, 1, 1, 1, 1, (float)w.beta_x, (float)w.beta_y,
                  (float)w.beta_z, (float)w.alpha};
   l.n = n;
   l.b = b;
   l.x = x;
-  if ((st = dalloc(s, &l.t, n)) != GD_OK) return st;
+  if ((st = dalloc(s, &l.t, n)) != GD_OK) {
+    s->plan = saved;
+    return st;
+  }
   float *tmp = l.t;
-  for (int k = 0; k < nsweeps && st == GD_OK; ++k) st = sweep(s, l, true, false, false);
-  if (st == GD_OK && l.x != x) {
+  s->plan.L.push_back(l);
+  for (int k = 0; k < nsweeps && st == GD_OK; ++k) st = sweep(s, 0, false, false, false, false);
+  Level &lr = s->plan.L[0];
+  if (st == GD_OK && lr.x != x) {
     ProfScope ps(s, P_COPY, (double)n * 8.0);
-    if (launch_copy(x, l.x, n, s->stream) != cudaSuccess) st = GD_ERR_CUDA;
+    if (launch_copy(x, lr.x, n, s->stream) != cudaSuccess) st = GD_ERR_CUDA;
   }
   if (st == GD_OK && x_host)
     if (cudaMemcpyAsync(xh, x, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
       st = GD_ERR_CUDA;
   cudaStreamSynchronize(s->stream);
   cudaFree(tmp);
+  s->plan.L.clear();
+  s->plan = saved;
   if (s->prof_on) prof_collect(s);
   return st;
 }

@@ -29,6 +29,8 @@ enum {
   S_E = 4,    // sum of the correction e
   S_NUM = 5
 };
+// scalars[S_ERR] is set to 1 by a kernel whose bounded wait gave up
+constexpr int S_ERR = 7;
 
 enum RhsMode { RHS_EXPLICIT = 0, RHS_AD = 1, RHS_SP = 2 };
 
@@ -53,6 +55,29 @@ struct OuterArgs {
   double inv_n;                 // 1 / (nx*ny*nz)
   double *partials;             // [gridDim.x][S_NUM]
 };
+
+// Arguments of the TMA z-march sweep (gd_zmarch.cu).
+struct ZSweepArgs {
+  LevelDev L;
+  float *xout;          // relaxed iterate (a different array from the input)
+  const float *xc;      // PROLONG: coarse correction (next level's x)
+  int ncx, ncy;         // next level's x, y sizes (PROLONG / RESTRICT)
+  int fx, fy, fz;       // axes coarsened from this level to the next
+  float *bc;            // RESTRICT: next level's right-hand side
+  int zchunk;           // set by the launcher
+  double *partials;     // SUM: per-block sums of the output, slot S_E
+  double *err;          // set to 1 when a bounded wait gives up
+};
+
+// TMA z-march launchers (gd_zmarch.cu); cudaErrorNotSupported when the arrays
+// do not meet TMA's alignment rules (nx % 4, 16-byte base) -- the caller then
+// uses the plain kernels.
+bool zmarch_usable(const LevelDev &L);
+cudaError_t launch_zsweep(ZSweepArgs a, const float *xin, const float *b, bool zero_in, bool prolong,
+                          bool restrict_, bool sum, int *nblocks_out, cudaStream_t st);
+cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nblocks_out,
+                          cudaStream_t st);
+int zouter_max_blocks(int nx, int ny, int nz);
 
 // Host-side launchers (gd_kernels.cu).  All enqueue on `st` and return the
 // cudaGetLastError() of the launch.
