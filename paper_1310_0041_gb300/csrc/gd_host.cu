@@ -480,8 +480,14 @@ int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] 
     CK(cudaStreamSynchronize(s->stream));
     std::memcpy(h_out, s->h_scalars, S_NUM * sizeof(double));
     if (s->h_scalars[S_ERR] != 0.0) {
-      set_err(s, "a kernel's bounded wait for its TMA loads gave up");
-      return GD_ERR_TIMEOUT;
+      const int code = (int)s->h_scalars[S_ERR];
+      if (code == 1) {
+        set_err(s, "a kernel's bounded wait for its TMA loads gave up");
+        return GD_ERR_TIMEOUT;
+      }
+      set_err(s, "a TMA kernel refused to start (preflight code %d: 2 smem base, 3 tensor "
+                 "map, 4 smem size)", code);
+      return GD_ERR_CUDA;
     }
   }
   return GD_OK;

@@ -88,6 +88,19 @@ __device__ __forceinline__ float mass_of(int i, int n, int s, int l) {
   return (float)((i == n - 1) ? l : s);
 }
 
+// Checks a CTA makes before any TMA: the dynamic shared-memory base is
+// 128-byte aligned (slot offsets are multiples of 128 bytes), it holds `bytes`
+// within the CTA's shared window, and the tensor-map parameter is 64-byte
+// aligned.  Returns 0 or an error code (2: smem base, 3: tensor map, 4: size).
+__device__ __forceinline__ int tma_preflight(const void *smem_base, size_t bytes, const void *map) {
+  uint32_t dyn = 0;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  if ((su32(smem_base) & 127u) != 0) return 2;
+  if (((uintptr_t)map & 63u) != 0) return 3;
+  if (bytes > dyn) return 4;
+  return 0;
+}
+
 __device__ __forceinline__ double block_sum(double v, double *sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -125,7 +138,7 @@ struct SweepGeo {
   static constexpr int BR = (RESTRICT ? 3 : 2) + PF;
   static constexpr int XS = pad32(XH * BOXW);    // floats per x slot
   static constexpr int BS = pad32(BH * BOXW);
-  static constexpr size_t smem_bytes() {
+  __host__ __device__ static constexpr size_t smem_bytes() {
     return sizeof(float) * ((size_t)XR * XS + (size_t)BR * BS + ZX * ZY) +
            sizeof(uint64_t) * (XR + BR) + sizeof(double) * 32 + 16;
   }
@@ -168,11 +181,19 @@ __global__ void __launch_bounds__(ZNT) k_zsweep(const __grid_constant__ CUtensor
 
   if (tid == 0) {
     abort_flag = 0;
-    for (int s = 0; s < G::XR; ++s) mbar_init(&xbar[s], 1);
-    for (int s = 0; s < G::BR; ++s) mbar_init(&bbar[s], 1);
-    fence_mbar_init();
+    int e = tma_preflight(smem, G::smem_bytes(), &tmx);
+    if (!e) e = tma_preflight(smem, G::smem_bytes(), &tmb);
+    if (e) {
+      abort_flag = e;
+      a.err[0] = (double)e;
+    } else {
+      for (int s = 0; s < G::XR; ++s) mbar_init(&xbar[s], 1);
+      for (int s = 0; s < G::BR; ++s) mbar_init(&bbar[s], 1);
+      fence_mbar_init();
+    }
   }
   __syncthreads();
+  if (abort_flag) return;  // nothing issued yet
 
   int xissued = rx.lo - 1, bissued = rb.lo - 1;  // meaningful in thread 0
   auto issue_x = [&](int p) {
@@ -390,9 +411,9 @@ struct OuterGeo {
   static constexpr int BH = ZY + 2;              // rows: tile + 1 halo
   static constexpr int S = pad32(BH * BOXW);
   static constexpr int XR = 3 + PF;              // x_new planes t-1..t+1 + in flight
-  static constexpr int ER = 1 + PF;
+  static constexpr int ER = 3 + PF;              // corrections: same planes and lag as x
   static constexpr int IR = 1 + PF;
-  static constexpr size_t smem_bytes() {
+  __host__ __device__ static constexpr size_t smem_bytes() {
     return sizeof(float) * (size_t)S * (2 * XR + ER + 2 * IR) +
            sizeof(uint64_t) * (2 * XR + ER + 2 * IR) + sizeof(double) * 32 + 16;
   }
@@ -431,7 +452,7 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
   Ring<G::XR> rx;
   rx.lo = zc ? max(zs - 1, 0) : zs;
   rx.hi = zc ? min(ze, nz - 1) : ze - 1;
-  Ring<G::ER> re;  // same planes as x, shallower ring
+  Ring<G::ER> re;  // same planes as x
   re.lo = rx.lo;
   re.hi = rx.hi;
   Ring<G::IR> ri;
@@ -442,12 +463,23 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
 
   if (tid == 0) {
     abort_flag = 0;
-    for (int s = 0; s < G::XR; ++s) { mbar_init(&hb[s], 1); mbar_init(&lb[s], 1); }
-    for (int s = 0; s < G::ER; ++s) mbar_init(&eb[s], 1);
-    for (int s = 0; s < G::IR; ++s) { mbar_init(&ib0[s], 1); mbar_init(&ib1[s], 1); }
-    fence_mbar_init();
+    int e = tma_preflight(smem, G::smem_bytes(), &tmh);
+    if (!e && HAS_XL) e = tma_preflight(smem, G::smem_bytes(), &tml);
+    if (!e && HAS_E) e = tma_preflight(smem, G::smem_bytes(), &tme);
+    if (!e) e = tma_preflight(smem, G::smem_bytes(), &tmi0);
+    if (!e && SP) e = tma_preflight(smem, G::smem_bytes(), &tmi1);
+    if (e) {
+      abort_flag = e;
+      err[0] = (double)e;
+    } else {
+      for (int s = 0; s < G::XR; ++s) { mbar_init(&hb[s], 1); mbar_init(&lb[s], 1); }
+      for (int s = 0; s < G::ER; ++s) mbar_init(&eb[s], 1);
+      for (int s = 0; s < G::IR; ++s) { mbar_init(&ib0[s], 1); mbar_init(&ib1[s], 1); }
+      fence_mbar_init();
+    }
   }
   __syncthreads();
+  if (abort_flag) return;  // nothing issued yet
 
   int xissued = rx.lo - 1, iissued = ri.lo - 1;  // meaningful in thread 0
   auto issue_x = [&](int p) {
