@@ -346,52 +346,68 @@ int sweep(gd_stack *s, int li, bool zero_in, bool prolong, bool restrict_, bool 
     if (st != GD_OK) return st;
     part = s->partials;
   }
-  bool done = false;
-  if (!s->no_tma && zmarch_usable(l.d)) {
-    ZSweepArgs a;
-    std::memset(&a, 0, sizeof a);
-    a.L = l.d;
-    a.xout = l.t;
-    a.partials = part;
-    a.err = s->scalars + S_ERR;
-    if (C) {
-      a.xc = C->x;
-      a.ncx = C->d.nx;
-      a.ncy = C->d.ny;
-      a.fx = l.fx;
-      a.fy = l.fy;
-      a.fz = l.fz;
-      a.bc = C->b;
-    }
-    double bytes = (double)l.n * (zero_in ? 8.0 : 12.0) + (C ? 4.0 * (double)C->n : 0.0);
+  ZSweepArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.L = l.d;
+  a.xout = l.t;
+  a.partials = part;
+  a.err = s->scalars + S_ERR;
+  if (C) {
+    a.xc = C->x;
+    a.ncx = C->d.nx;
+    a.ncy = C->d.ny;
+    a.fx = l.fx;
+    a.fy = l.fy;
+    a.fz = l.fz;
+    a.bc = C->b;
+  }
+  const bool tma = !s->no_tma && zmarch_usable(l.d);
+  bool swept = false;
+  if (tma) {
     cudaError_t e;
     {
-      ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE, bytes);
-      e = launch_zsweep(a, l.x, l.b, zero_in, prolong, restrict_, sum_e, &nb, s->stream);
+      ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE,
+                   (double)l.n * (zero_in ? 8.0 : 12.0) + (prolong ? 4.0 * (double)C->n : 0.0));
+      e = launch_zsweep(a, l.x, l.b, zero_in, prolong, sum_e, &nb, s->stream);
       if (e == cudaErrorNotSupported) {
         s->launches -= 1;
         ps.bytes = 0;
         cudaGetLastError();
       }
     }
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) swept = true;
     else if (e != cudaErrorNotSupported) {
       set_err(s, "TMA sweep launch failed: %s", cudaGetErrorString(e));
       return GD_ERR_CUDA;
     }
   }
-  if (!done) {
+  if (!swept) {
     if (prolong) {
       ProfScope ps(s, P_PROLONG, (double)l.n * 8.0 + (double)C->n * 4.0);
       CK(launch_prolong_add(l.d, l.fx, l.fy, l.fz, C->x, l.x, s->stream));
     }
-    {
-      ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE, (double)l.n * (zero_in ? 8.0 : 12.0));
-      CK(launch_rb_sweep(l.d, l.x, l.b, l.t, zero_in, part, &nb, s->stream));
-    }
-    if (restrict_) {
+    ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE, (double)l.n * (zero_in ? 8.0 : 12.0));
+    CK(launch_rb_sweep(l.d, l.x, l.b, l.t, zero_in, part, &nb, s->stream));
+  }
+  if (restrict_) {
+    // residual of the relaxed iterate (now in l.t) down-sampled into C->b
+    cudaError_t e = cudaErrorNotSupported;
+    if (tma) {
       ProfScope ps(s, P_RESTRICT, (double)l.n * 8.0 + (double)C->n * 4.0);
-      CK(launch_residual_restrict(l.d, l.t, l.b, l.fx, l.fy, l.fz, C->b, s->stream));
+      e = launch_zrestrict(a, l.t, l.b, s->stream);
+      if (e == cudaErrorNotSupported) {
+        s->launches -= 1;
+        ps.bytes = 0;
+        cudaGetLastError();
+      }
+    }
+    if (e == cudaErrorNotSupported) {
+      ProfScope ps(s, P_RESTRICT, (double)l.n * 8.0 + (double)C->n * 4.0);
+      e = launch_residual_restrict(l.d, l.t, l.b, l.fx, l.fy, l.fz, C->b, s->stream);
+    }
+    if (e != cudaSuccess) {
+      set_err(s, "restriction launch failed: %s", cudaGetErrorString(e));
+      return GD_ERR_CUDA;
     }
   }
   std::swap(l.x, l.t);
@@ -454,8 +470,9 @@ int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] 
   if ((st = ensure_partials(s, sms * 8 + 64)) != GD_OK) return st;
   if ((st = ensure_partials(s, zouter_max_blocks(s->nx, s->ny, s->nz))) != GD_OK) return st;
   a.partials = s->partials;
-  double bytes = 4.0 * (1 + (a.xl_in ? 1 : 0) + (a.e ? 1 : 0) + (a.xh_out ? 2 : 0) +
-                        (a.r_out ? 1 : 0) + (rhs_mode == RHS_SP ? 2 : 1)) * (double)n;
+  double bytes = 4.0 * (1 + (a.xl_in ? 1 : 0) + (a.e ? 1 : 0) + (a.xh_out ? 1 : 0) +
+                        (a.xl_out ? 1 : 0) + (a.r_out ? 1 : 0) + (rhs_mode == RHS_SP ? 2 : 1)) *
+                 (double)n;
   int nb = 0;
   {
     ProfScope ps(s, P_OUTER, bytes);
@@ -648,17 +665,24 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   int cycles = 0;
   int status = GD_OK;
   std::vector<double> hist(1, rel);
+  bool exact = false;
   auto update = [&](const float *e) -> int {
+    // Plain FP32 passes while the residual is large: their rounding error
+    // (~1e-7 of the local terms) and the dropped low word of the iterate are
+    // then far below the residual.  From 1e-4 on (and from then on always)
+    // the iterate is a float pair and the residual is evaluated exactly.
+    if (rel < 1e-4) exact = true;
+    a.accurate = exact ? 1 : 0;
     a.xh_in = H[c];
     a.xl_in = lo_zero ? nullptr : Lo[c];
     a.e = e;
     a.mean_fix = mean_fix;
     a.xh_out = H[1 - c];
-    a.xl_out = Lo[1 - c];
+    a.xl_out = exact ? Lo[1 - c] : nullptr;
     a.r_out = F.b;
     int r = outer_pass(s, a, rhs, h);
     c = 1 - c;
-    lo_zero = false;
+    if (exact) lo_zero = false;
     return r;
   };
   while (!(rel <= ctl.rel_tol)) {
@@ -708,6 +732,7 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
     b2.xh_out = b2.xl_out = nullptr;
     b2.r_out = nullptr;
     b2.mean_fix = 0;
+    b2.accurate = 1;
     if ((st = outer_pass(s, b2, rhs, h)) != GD_OK) return report(rep, st);
     rep->rel_residual_out = std::sqrt(h[S_RR]) / denom;
   }
@@ -848,6 +873,7 @@ int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh,
   OuterArgs a;
   std::memset(&a, 0, sizeof a);
   set_weights(a, w.beta_x, w.beta_y, w.beta_z, w.alpha, 0.0, 0.0, 0.0);
+  a.accurate = 1;
   a.b = b;
   a.xh_in = x;
   double h[S_NUM];
@@ -912,6 +938,7 @@ int gd_residual(gd_stack *s, int system, gd_weights w, const float *I0h, const f
   a.I0 = I0;
   a.I1 = I1;
   a.xh_in = x;
+  a.accurate = 1;
   double h[S_NUM];
   if ((st = outer_pass(s, a, sp ? RHS_SP : RHS_AD, h)) != GD_OK) return st;
   const double bn = std::sqrt(h[S_BB]);

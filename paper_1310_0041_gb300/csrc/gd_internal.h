@@ -52,6 +52,7 @@ struct OuterArgs {
   float *r_out;                 // residual (nullable: not written)
   const double *scalars;        // reduced sums of the previous passes (mean fix)
   int mean_fix;                 // AD: shift the update so that sum x = sum I0
+  int accurate;                 // residual by error-free transformations (else plain FP32)
   double inv_n;                 // 1 / (nx*ny*nz)
   double *partials;             // [gridDim.x][S_NUM]
 };
@@ -60,10 +61,10 @@ struct OuterArgs {
 struct ZSweepArgs {
   LevelDev L;
   float *xout;          // relaxed iterate (a different array from the input)
-  const float *xc;      // PROLONG: coarse correction (next level's x)
-  int ncx, ncy;         // next level's x, y sizes (PROLONG / RESTRICT)
+  const float *xc;      // prolongation: coarse correction (next level's x)
+  int ncx, ncy;         // next level's x, y sizes (prolongation / restriction)
   int fx, fy, fz;       // axes coarsened from this level to the next
-  float *bc;            // RESTRICT: next level's right-hand side
+  float *bc;            // restriction: next level's right-hand side
   int zchunk;           // set by the launcher
   double *partials;     // SUM: per-block sums of the output, slot S_E
   double *err;          // set to 1 when a bounded wait gives up
@@ -74,7 +75,9 @@ struct ZSweepArgs {
 // uses the plain kernels.
 bool zmarch_usable(const LevelDev &L);
 cudaError_t launch_zsweep(ZSweepArgs a, const float *xin, const float *b, bool zero_in, bool prolong,
-                          bool restrict_, bool sum, int *nblocks_out, cudaStream_t st);
+                          bool sum, int *nblocks_out, cudaStream_t st);
+// residual of (x, b) on level a.L summed into the next level's b (a.bc)
+cudaError_t launch_zrestrict(ZSweepArgs a, const float *x, const float *b, cudaStream_t st);
 cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nblocks_out,
                           cudaStream_t st);
 int zouter_max_blocks(int nx, int ny, int nz);

@@ -349,10 +349,8 @@ __global__ void __launch_bounds__(NT) k_outer(OuterArgs a) {
     }
     const ff rr = ff_add(bv, ff_neg(ax));
     const float r = __fadd_rn(rr.h, rr.l);
-    if (a.xh_out) {
-      a.xh_out[p] = xc.h;
-      a.xl_out[p] = xc.l;
-    }
+    if (a.xh_out) a.xh_out[p] = xc.h;
+    if (a.xl_out) a.xl_out[p] = xc.l;
     if (a.r_out) a.r_out[p] = r;
     const double rd = (double)rr.h + (double)rr.l;
     const double bd = (double)bv.h + (double)bv.l;

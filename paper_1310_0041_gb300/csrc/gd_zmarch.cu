@@ -13,14 +13,15 @@
 //     PROLONG   x <- x + P x_c before relaxing (first post-sweep: the
 //               up-sampled coarse correction of Sec. 4.1, replication
 //               stencil of Sec. 4.2);
-//     RESTRICT  after relaxing, r = b - A x is summed over the children into
-//               the coarse right-hand side (last pre-sweep: residual and
-//               down-sampling of Sec. 4.1);
 //     SUM       the block sums of the written iterate (mean fix of AD).
-//   Pipeline per step t: red of plane t on the tile + (H-1) ring, black of
-//   plane t-1 on the tile + (H-2) ring, store plane t-1, residual of plane
-//   t-2 (RESTRICT).  Ring margins recompute neighbours' values exactly as the
-//   neighbouring CTA does, so the result is the textbook red-black sweep.
+//   Pipeline per step t: red of plane t on the tile + 1 ring, black of plane
+//   t-1 on the tile, store plane t-1.  The ring recomputes the neighbouring
+//   CTA's red values exactly as it does, so the result is the textbook
+//   red-black sweep.
+//
+// k_zrestrict: residual r = b - A x and its down-sampling (sum over the
+//   children of each coarse cell, Sec. 4.1 / 4.2) into the next level's
+//   right-hand side.
 //
 // k_zouter: fine-level outer pass of the iterative refinement: x_new = x + e
 //   (+ mean shift) as a float pair, r = b - A x_new in double-float arithmetic
@@ -30,6 +31,7 @@
 
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 
 #include "gd_internal.h"
 
@@ -38,6 +40,7 @@ namespace {
 constexpr int ZX = 64;            // tile x extent
 constexpr int ZY = 16;            // tile y extent
 constexpr int ZNT = 256;          // threads per CTA
+constexpr int NTY = ZNT / ZX;      // thread rows of the tile-cell map
 constexpr int BOXW = ZX + 8;      // box width: tile + 4 on each side (16-byte aligned start)
 constexpr int PF = 2;             // planes in flight ahead of use
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier polling
@@ -118,59 +121,63 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 
 // Ring bookkeeping for one input array: planes [lo, hi] are loaded, plane p
 // lives in slot (p - lo) % DEPTH and completes phase ((p - lo) / DEPTH) & 1.
+// (p - lo) is never negative; power-of-two depths make these masks and shifts.
 template <int DEPTH>
 struct Ring {
   int lo, hi;
   __device__ __forceinline__ bool has(int p) const { return p >= lo && p <= hi; }
-  __device__ __forceinline__ int slot(int p) const { return (p - lo) % DEPTH; }
-  __device__ __forceinline__ uint32_t parity(int p) const { return ((p - lo) / DEPTH) & 1; }
+  __device__ __forceinline__ int slot(int p) const { return (int)((uint32_t)(p - lo) % DEPTH); }
+  __device__ __forceinline__ uint32_t parity(int p) const {
+    return ((uint32_t)(p - lo) / DEPTH) & 1;
+  }
 };
 
 // ===========================================================================
 // red-black sweep
 // ===========================================================================
-template <bool RESTRICT>
+// Dynamic shared memory of the z-march kernels, addressed with 32-bit float
+// offsets (slots are multiples of 32 floats, i.e. 128 bytes).
+extern __shared__ __align__(128) float zsm[];
+
 struct SweepGeo {
-  static constexpr int H = RESTRICT ? 3 : 2;     // x box halo in y
+  static constexpr int H = 2;                    // x box halo in y
   static constexpr int XH = ZY + 2 * H;          // x box rows
   static constexpr int BH = ZY + 2 * (H - 1);    // b box rows
-  static constexpr int XR = (RESTRICT ? 5 : 4) + PF;
-  static constexpr int BR = (RESTRICT ? 3 : 2) + PF;
+  // ring depths: planes in use plus PF in flight, rounded up to a power of two
+  static constexpr int XR = 8;                   // needs 4 + PF
+  static constexpr int BR = 4;                   // needs 2 + PF
+  static_assert(XR >= 4 + PF && BR >= 2 + PF, "ring depth");
   static constexpr int XS = pad32(XH * BOXW);    // floats per x slot
   static constexpr int BS = pad32(BH * BOXW);
+  static constexpr int BOFF = XR * XS;           // b slots
+  static constexpr int MOFF = BOFF + BR * BS;    // mbarriers
   __host__ __device__ static constexpr size_t smem_bytes() {
-    return sizeof(float) * ((size_t)XR * XS + (size_t)BR * BS + ZX * ZY) +
-           sizeof(uint64_t) * (XR + BR) + sizeof(double) * 32 + 16;
+    return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + sizeof(double) * 32 + 16;
   }
 };
 
-template <bool ZERO_IN, bool PROLONG, bool RESTRICT, bool SUM>
-__global__ void __launch_bounds__(ZNT) k_zsweep(const __grid_constant__ CUtensorMap tmx,
-                                                const __grid_constant__ CUtensorMap tmb,
-                                                const ZSweepArgs a) {
-  using G = SweepGeo<RESTRICT>;
+template <bool ZERO_IN, bool PROLONG, bool SUM, bool UNIFORM>
+__global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
+                                                   const __grid_constant__ CUtensorMap tmb,
+                                                   const ZSweepArgs a) {
+  using G = SweepGeo;
   constexpr int H = G::H;
-  extern __shared__ __align__(128) unsigned char smem[];
-  float *xs = reinterpret_cast<float *>(smem);
-  float *bs = xs + G::XR * G::XS;
-  float *acc = bs + G::BR * G::BS;
-  uint64_t *xbar = reinterpret_cast<uint64_t *>(acc + ZX * ZY);
+  uint64_t *xbar = reinterpret_cast<uint64_t *>(zsm + G::MOFF);
   uint64_t *bbar = xbar + G::XR;
   double *dsh = reinterpret_cast<double *>(bbar + G::BR);
   __shared__ int abort_flag;
 
   const LevelDev &L = a.L;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * ZY;
   const int zs = blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, nz);
   const bool zc = (L.wz != 0.f) && (nz > 1);
-  const int R = RESTRICT ? 1 : 0;
-  const int t0 = zc ? zs - 1 - R : zs;
-  const int t1 = zc ? ze + R : ze - 1;
-  const int lagb = zc ? 1 : 0, lagr = zc ? 2 : 0;
-  const int red_lo = zc ? max(zs - 1 - R, 0) : zs, red_hi = zc ? min(ze + R, nz - 1) : ze - 1;
-  const int blk_lo = zc ? max(zs - R, 0) : zs, blk_hi = zc ? min(ze - 1 + R, nz - 1) : ze - 1;
+  const int t0 = zc ? zs - 1 : zs;
+  const int t1 = zc ? ze : ze - 1;
+  const int lagb = zc ? 1 : 0;
+  const int red_lo = zc ? max(zs - 1, 0) : zs, red_hi = zc ? min(ze, nz - 1) : ze - 1;
+  const int blk_lo = zs, blk_hi = ze - 1;
   Ring<G::XR> rx;
   rx.lo = zc ? max(t0 - 1, 0) : zs;
   rx.hi = zc ? min(t1 + 1, nz - 1) : ze - 1;
@@ -181,161 +188,219 @@ __global__ void __launch_bounds__(ZNT) k_zsweep(const __grid_constant__ CUtensor
 
   if (tid == 0) {
     abort_flag = 0;
-    int e = tma_preflight(smem, G::smem_bytes(), &tmx);
-    if (!e) e = tma_preflight(smem, G::smem_bytes(), &tmb);
+    int e = tma_preflight(zsm, G::smem_bytes(), &tmx);
+    if (!e) e = tma_preflight(zsm, G::smem_bytes(), &tmb);
     if (e) {
       abort_flag = e;
       a.err[0] = (double)e;
     } else {
-      for (int s = 0; s < G::XR; ++s) mbar_init(&xbar[s], 1);
-      for (int s = 0; s < G::BR; ++s) mbar_init(&bbar[s], 1);
+      for (int q = 0; q < G::XR; ++q) mbar_init(&xbar[q], 1);
+      for (int q = 0; q < G::BR; ++q) mbar_init(&bbar[q], 1);
       fence_mbar_init();
     }
+  }
+  if (ZERO_IN) {
+    // x is never loaded: cells outside the domain must read 0 for good, and
+    // every cell inside is written before it is read
+    for (int q = tid; q < G::XR * G::XS; q += ZNT) zsm[q] = 0.f;
   }
   __syncthreads();
   if (abort_flag) return;  // nothing issued yet
 
-  int xissued = rx.lo - 1, bissued = rb.lo - 1;  // meaningful in thread 0
+  int xissued = rx.lo - 1, bissued = rb.lo - 1;  // thread 0
   auto issue_x = [&](int p) {
     if (ZERO_IN || !rx.has(p)) return;
-    const int s = rx.slot(p);
-    mbar_expect_tx(&xbar[s], (uint32_t)(G::XH * BOXW * sizeof(float)));
-    tma_plane(xs + s * G::XS, &tmx, i0 - 4, j0 - H, p, &xbar[s]);
+    const int q = rx.slot(p);
+    mbar_expect_tx(&xbar[q], (uint32_t)(G::XH * BOXW * sizeof(float)));
+    tma_plane(zsm + q * G::XS, &tmx, i0 - 4, j0 - H, p, &xbar[q]);
     xissued = p;
   };
   auto issue_b = [&](int p) {
     if (!rb.has(p)) return;
-    const int s = rb.slot(p);
-    mbar_expect_tx(&bbar[s], (uint32_t)(G::BH * BOXW * sizeof(float)));
-    tma_plane(bs + s * G::BS, &tmb, i0 - 4, j0 - (H - 1), p, &bbar[s]);
+    const int q = rb.slot(p);
+    mbar_expect_tx(&bbar[q], (uint32_t)(G::BH * BOXW * sizeof(float)));
+    tma_plane(zsm + G::BOFF + q * G::BS, &tmb, i0 - 4, j0 - (H - 1), p, &bbar[q]);
     bissued = p;
   };
-  const int xnext0 = zc ? t0 + 1 + PF : t0 + PF;  // first plane issued inside the loop
+  const int xnext0 = zc ? t0 + 1 + PF : t0 + PF;
   if (tid == 0) {
     for (int p = rx.lo; p < xnext0 && p <= rx.hi; ++p) issue_x(p);
     for (int p = rb.lo; p < t0 + PF && p <= rb.hi; ++p) issue_b(p);
   }
-  int xready = rx.lo - 1, bready = rb.lo - 1;
-  auto xslot = [&](int p) -> float * { return xs + rx.slot(p) * G::XS; };
-  auto bslot = [&](int p) -> float * { return bs + rb.slot(p) * G::BS; };
+  int xready = rx.lo - 1, bready = rb.lo - 1;  // planes made usable (all threads)
+  int xwait = rx.lo - 1, bwait = rb.lo - 1;    // planes whose wait succeeded (warp 0)
+  auto xo = [&](int p) { return rx.slot(p) * G::XS; };
+  auto bo = [&](int p) { return G::BOFF + rb.slot(p) * G::BS; };
 
-  // Make x planes up to `upto` usable: wait for TMA (or zero-fill), add P x_c.
-  auto ready_x = [&](int upto) {
-    upto = min(upto, rx.hi);
-    for (int p = xready + 1; p <= upto; ++p) {
-      float *X = xslot(p);
-      if (ZERO_IN) {
-        for (int q = tid; q < G::XH * BOXW; q += ZNT) X[q] = 0.f;
+  // ---- per-thread constants ----
+  // Tile cells: thread (tx, ty) owns column tx and rows of the row pairs
+  // ty, ty + NTY, ...; in a colour phase it takes the row of each pair with the
+  // right parity, so the 32 lanes of a warp alternate between two rows
+  // (row stride 72 floats = 8 banks) and never share a bank.
+  const int tx = tid % ZX, ty = tid / ZX;
+  const int gi = i0 + tx;
+  const bool col_in = gi < nx;
+  const float nbx = (float)((gi > 0) + (gi < nx - 1));
+  const float cxu = L.wx * (float)L.sy * (float)L.sz;
+  const float cyu = L.wy * (float)L.sx * (float)L.sz;
+  const float czu = zc ? L.wz * (float)L.sx * (float)L.sy : 0.f;
+  const float mmu = L.wm * (float)L.sx * (float)L.sy * (float)L.sz;
+
+  // Gauss-Seidel update of one cell: x = (b + sum_n c_n x_n) / diag.  Cells
+  // outside the domain read 0 and are never written; missing neighbours are
+  // left out of the diagonal by the neighbour counts.  RED0: the first red
+  // pass of a zero iterate (all neighbours are 0).
+  auto cell = [&](auto red0_c, int xop, int xmo, int xpo, int bop, int so, int gci, int gcj,
+                  float mz, float zmf, float zpf, float nbxc) {
+    constexpr bool RED0 = decltype(red0_c)::value;
+    float cx = cxu, cy = cyu, cz = czu, mm = mmu;
+    if (!UNIFORM) {
+      const float mx = mass_of(gci, nx, L.sx, L.lx), my = mass_of(gcj, ny, L.sy, L.ly);
+      cx = L.wx * my * mz;
+      cy = L.wy * mx * mz;
+      cz = zc ? L.wz * mx * my : 0.f;
+      mm = L.wm * mx * my * mz;
+    }
+    const float nby = (float)((gcj > 0) + (gcj < ny - 1));
+    const float dg = cx * nbxc + cy * nby + cz * (zmf + zpf) + mm;
+    const float bv = zsm[bop + so - BOXW];
+    float v;
+    if (RED0) {
+      v = __fdividef(bv, dg);
+    } else {
+      float sacc = cx * (zsm[xop + so - 1] + zsm[xop + so + 1]) +
+                   cy * (zsm[xop + so - BOXW] + zsm[xop + so + BOXW]);
+      if (zc) sacc += cz * (zmf * zsm[xmo + so] + zpf * zsm[xpo + so]);
+      v = __fdividef(bv + sacc, dg);
+    }
+    zsm[xop + so] = v;
+  };
+  // Fast path: a uniform level and a tile whose cells and their neighbours
+  // all lie inside the domain in x and y (z faces are handled by zmf / zpf).
+  const bool fast = UNIFORM && (i0 >= 3) && (i0 + ZX + 3 <= nx) && (j0 >= 3) && (j0 + ZY + 3 <= ny);
+  // Ring cells of this thread (red ring H-1, black ring H-2), decoded once.
+  constexpr int RMAX = 1;  // ring cells per thread: ceil(164 / 256)
+  int rso[RMAX], rpar[RMAX], rgi[RMAX], rgj[RMAX], rring[RMAX];
+#pragma unroll
+  for (int m = 0; m < RMAX; ++m) {
+    rso[m] = -1;
+    rpar[m] = rgi[m] = rgj[m] = rring[m] = 0;
+    const int RG = H - 1;  // widest ring (the red one)
+    const int WR = ZX + 2 * RG, NTB = RG * WR, NLR = ZY * RG;
+    const int q = tid + m * ZNT;
+    if (q < 2 * NTB + 2 * NLR) {
+      int row, col;
+      if (q < NTB) {
+        row = -RG + q / WR; col = -RG + q % WR;
+      } else if (q < 2 * NTB) {
+        row = ZY + (q - NTB) / WR; col = -RG + (q - NTB) % WR;
+      } else if (q < 2 * NTB + NLR) {
+        row = (q - 2 * NTB) / RG; col = -RG + (q - 2 * NTB) % RG;
       } else {
-        if (!mbar_wait(&xbar[rx.slot(p)], rx.parity(p))) {
-          abort_flag = 1;
-          return;
-        }
-        if (PROLONG) {
-          const size_t cpl = (size_t)(p >> a.fz) * a.ncy;
-          for (int q = tid; q < G::XH * BOXW; q += ZNT) {
-            const int r = q / BOXW, c = q - r * BOXW;
-            const int gi = i0 - 4 + c, gj = j0 - H + r;
-            if (gi >= 0 && gi < nx && gj >= 0 && gj < ny)
-              X[q] += __ldg(a.xc + (cpl + (gj >> a.fy)) * a.ncx + (gi >> a.fx));
-          }
-        }
+        row = (q - 2 * NTB - NLR) / RG; col = ZX + (q - 2 * NTB - NLR) % RG;
       }
-      xready = p;
-    }
-  };
-  auto ready_b = [&](int upto) {
-    upto = min(upto, rb.hi);
-    for (int p = bready + 1; p <= upto; ++p) {
-      if (!mbar_wait(&bbar[rb.slot(p)], rb.parity(p))) {
-        abort_flag = 1;
-        return;
+      const int gci = i0 + col, gcj = j0 + row;
+      if (gci >= 0 && gci < nx && gcj >= 0 && gcj < ny) {
+        rso[m] = (row + H) * BOXW + 4 + col;
+        rpar[m] = (gci + gcj) & 1;
+        rgi[m] = gci;
+        rgj[m] = gcj;
+        // distance of the cell outside the tile (1 or 2)
+        const int dx = col < 0 ? -col : (col >= ZX ? col - ZX + 1 : 0);
+        const int dy = row < 0 ? -row : (row >= ZY ? row - ZY + 1 : 0);
+        rring[m] = dx > dy ? dx : dy;
       }
-      bready = p;
     }
-  };
-
-  // (A x)_p terms at one voxel, difference form; returns A x, diag in *dg.
-  auto apply_at = [&](const float *X, const float *Xm, const float *Xp, int sy, int sx, int gi,
-                      int gj, int p, float &dg) -> float {
-    const float mx = mass_of(gi, nx, L.sx, L.lx);
-    const float my = mass_of(gj, ny, L.sy, L.ly);
+  }
+  auto relax = [&](auto ring_c, auto colour_c, int p) {
+    constexpr int RING = decltype(ring_c)::value;
+    constexpr int COLOUR = decltype(colour_c)::value;
+    constexpr bool RED0 = ZERO_IN && COLOUR == 0;
+    const std::integral_constant<bool, RED0> red0;
+    const int xop = xo(p);
+    const bool hm = zc && p > 0, hp = zc && p < nz - 1;
+    const int xmo = hm ? xo(p - 1) : xop, xpo = hp ? xo(p + 1) : xop;
+    const int bop = bo(p);
+    const float zmf = hm ? 1.f : 0.f, zpf = hp ? 1.f : 0.f;
     const float mz = mass_of(p, nz, L.sz, L.lz);
-    const float cx = L.wx * my * mz, cy = L.wy * mx * mz, cz = L.wz * mx * my;
-    const float mm = L.wm * mx * my * mz;
-    const int o = sy * BOXW + sx;
-    const float xc = X[o];
-    float ax = mm * xc;
-    dg = mm;
-    if (gi > 0) { ax += cx * (xc - X[o - 1]); dg += cx; }
-    if (gi < nx - 1) { ax += cx * (xc - X[o + 1]); dg += cx; }
-    if (gj > 0) { ax += cy * (xc - X[o - BOXW]); dg += cy; }
-    if (gj < ny - 1) { ax += cy * (xc - X[o + BOXW]); dg += cy; }
-    if (zc && p > 0) { ax += cz * (xc - Xm[o]); dg += cz; }
-    if (zc && p < nz - 1) { ax += cz * (xc - Xp[o]); dg += cz; }
-    return ax;
-  };
-  auto relax_plane = [&](int p, int ring, int colour) {
-    float *X = xslot(p);
-    const float *Xm = (zc && p > 0) ? xslot(p - 1) : X;
-    const float *Xp = (zc && p < nz - 1) ? xslot(p + 1) : X;
-    const float *B = bslot(p);
-    const int W = ZX + 2 * ring, Hh = ZY + 2 * ring;
-    const int half = W / 2;
-    for (int q = tid; q < Hh * half; q += ZNT) {
-      const int r = q / half, c2 = q - r * half;
-      const int gj = j0 - ring + r;
-      // colour 0 (red): gi + gj + p even; gi = i0 - ring + col, i0 even
-      const int col = 2 * c2 + ((ring + gj + p + colour) & 1);
-      const int gi = i0 - ring + col;
-      if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) continue;
-      const int sy = gj - (j0 - H), sx = gi - (i0 - 4);
-      float dg;
-      const float ax = apply_at(X, Xm, Xp, sy, sx, gi, gj, p, dg);
-      const float bv = B[(gj - (j0 - (H - 1))) * BOXW + sx];
-      if (dg > 0.f) X[sy * BOXW + sx] = X[sy * BOXW + sx] + (bv - ax) / dg;
-    }
-  };
-  double sum = 0.0;
-  auto store = [&](int p) {
-    const float *X = xslot(p);
-    const int r = tid >> 4, c = (tid & 15) * 4;
-    const int gi = i0 + c, gj = j0 + r;
-    if (gi < nx && gj < ny) {
-      const float4 v = *reinterpret_cast<const float4 *>(X + (r + H) * BOXW + 4 + c);
-      *reinterpret_cast<float4 *>(a.xout + (size_t)p * plane + (size_t)gj * nx + gi) = v;
-      if (SUM) sum += (double)v.x + (double)v.y + (double)v.z + (double)v.w;
-    }
-  };
-  auto restrict_plane = [&](int p) {
-    const float *X = xslot(p);
-    const float *Xm = (zc && p > 0) ? xslot(p - 1) : X;
-    const float *Xp = (zc && p < nz - 1) ? xslot(p + 1) : X;
-    const float *B = bslot(p);
-    const int fx = a.fx, fy = a.fy, fz = a.fz;
-    const int CW = ZX >> fx, CH = ZY >> fy;
-    const size_t cpl = (size_t)(p >> fz) * a.ncy;
-    for (int q = tid; q < CW * CH; q += ZNT) {
-      const int cr = q / CW, cc = q - cr * CW;
-      float s = 0.f;
-      for (int dr = 0; dr <= fy; ++dr)
-        for (int dc = 0; dc <= fx; ++dc) {
-          const int gi = i0 + (cc << fx) + dc, gj = j0 + (cr << fy) + dr;
-          if (gi >= nx || gj >= ny) continue;
-          const int sy = gj - (j0 - H), sx = gi - (i0 - 4);
-          float dg;
-          const float ax = apply_at(X, Xm, Xp, sy, sx, gi, gj, p, dg);
-          s += B[(gj - (j0 - (H - 1))) * BOXW + sx] - ax;
+    const int d = (tx + p + COLOUR) & 1;  // i0, j0 even
+    if (fast) {
+      const float idg = 1.f / (2.f * (cxu + cyu) + czu * (zmf + zpf) + mmu);
+      const float czm = czu * zmf, czp = czu * zpf;
+#pragma unroll
+      for (int k = 0; k < ZY / (2 * NTY); ++k) {
+        const int so = (2 * (ty + NTY * k) + d + H) * BOXW + 4 + tx;
+        const float bv = zsm[bop + so - BOXW];
+        float v;
+        if (RED0) {
+          v = bv * idg;
+        } else {
+          const float *xc = zsm + xop + so;
+          float sacc = cxu * (xc[-1] + xc[1]) + cyu * (xc[-BOXW] + xc[BOXW]);
+          if (zc) sacc += czm * zsm[xmo + so] + czp * zsm[xpo + so];
+          v = (bv + sacc) * idg;
         }
-      const int I = (i0 >> fx) + cc, J = (j0 >> fy) + cr;
-      if (fz && (p & 1) == 0 && p != nz - 1) {
-        acc[q] = s;  // first child plane: keep for the second
-      } else {
-        if (fz && (p & 1) == 1) s += acc[q];
-        if (I < a.ncx && J < a.ncy) a.bc[(cpl + J) * a.ncx + I] = s;
+        zsm[xop + so] = v;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < ZY / (2 * NTY); ++k) {
+        const int row = 2 * (ty + NTY * k) + d;
+        const int gj = j0 + row;
+        if (col_in && gj < ny)
+          cell(red0, xop, xmo, xpo, bop, (row + H) * BOXW + 4 + tx, gi, gj, mz, zmf, zpf, nbx);
+      }
+    }
+    if constexpr (RING > 0) {
+#pragma unroll
+      for (int m = 0; m < RMAX; ++m) {
+        if (rso[m] >= 0 && rring[m] <= RING && ((rpar[m] + p) & 1) == COLOUR) {
+          const float nbxc = (float)((rgi[m] > 0) + (rgi[m] < nx - 1));
+          cell(red0, xop, xmo, xpo, bop, rso[m], rgi[m], rgj[m], mz, zmf, zpf, nbxc);
+        }
       }
     }
   };
+  // double-float block sums in FP32 (the FP64 pipe is narrow)
+  float sum_h = 0.f, sum_l = 0.f;
+  auto store = [&](int p) {
+    const int xop = xo(p);
+#pragma unroll
+    for (int q = tid; q < ZX * ZY / 4; q += ZNT) {
+      const int r = q >> 4, c = (q & 15) * 4;
+      const int gci = i0 + c, gcj = j0 + r;
+      if (gci < nx && gcj < ny) {
+        const float4 v = *reinterpret_cast<const float4 *>(zsm + xop + (r + H) * BOXW + 4 + c);
+        *reinterpret_cast<float4 *>(a.xout + (size_t)p * plane + (size_t)gcj * nx + gci) = v;
+        if (SUM) {
+          const float s4 = (v.x + v.y) + (v.z + v.w);
+          const float sn = sum_h + s4;
+          const float bb = sn - sum_h;
+          sum_l += (sum_h - (sn - bb)) + (s4 - bb);
+          sum_h = sn;
+        }
+      }
+    }
+  };
+  // Prolongation: this thread's slot cells (columns 4-H .. 68+H-1 are the
+  // only ones any stage reads) and their offsets within a coarse plane.
+  constexpr int PW = ZX + 2 * H;
+  constexpr int PMAX = PROLONG ? (G::XH * PW + ZNT - 1) / ZNT : 1;
+  int pso[PMAX], pco[PMAX];
+#pragma unroll
+  for (int m = 0; m < PMAX; ++m) {
+    pso[m] = -1;
+    pco[m] = 0;
+    const int q = tid + m * ZNT;
+    if (PROLONG && q < G::XH * PW) {
+      const int r = q / PW, c = q - r * PW + (4 - H);
+      const int gci = i0 - 4 + c, gcj = j0 - H + r;
+      if (gci >= 0 && gci < nx && gcj >= 0 && gcj < ny) {
+        pso[m] = r * BOXW + c;
+        pco[m] = (gcj >> a.fy) * a.ncx + (gci >> a.fx);
+      }
+    }
+  }
 
   for (int t = t0; t <= t1; ++t) {
     if (tid == 0) {
@@ -343,37 +408,233 @@ __global__ void __launch_bounds__(ZNT) k_zsweep(const __grid_constant__ CUtensor
       issue_x(zc ? t + 1 + PF : t + PF);
       issue_b(t + PF);
     }
-    ready_x(zc ? t + 1 : t);
-    ready_b(t);
+    // one warp waits for the planes of this step, then the barrier releases all
+    const int ux = min(zc ? t + 1 : t, rx.hi), ub = min(t, rb.hi);
+    if (warp == 0) {
+      bool ok = true;
+      if (!ZERO_IN)
+        for (int p = xwait + 1; p <= ux && ok; ++p) {
+          ok = mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
+          if (ok) xwait = p;
+        }
+      for (int p = bwait + 1; p <= ub && ok; ++p) {
+        ok = mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
+        if (ok) bwait = p;
+      }
+      if (!ok && lane == 0) abort_flag = 1;
+    }
+    const int xprev = xready;
+    if (ux > xready) xready = ux;
+    if (ub > bready) bready = ub;
     __syncthreads();
     if (abort_flag) break;
-    if (t >= red_lo && t <= red_hi) relax_plane(t, H - 1, 0);
+    if (PROLONG && xready > xprev) {
+      // the up-sampled coarse correction, added once to every plane loaded
+      for (int p = xprev + 1; p <= xready; ++p) {
+        const float *xcp = a.xc + (size_t)(p >> a.fz) * a.ncy * a.ncx;
+        const int xop = xo(p);
+#pragma unroll
+        for (int m = 0; m < PMAX; ++m)
+          if (pso[m] >= 0) zsm[xop + pso[m]] += __ldg(xcp + pco[m]);
+      }
+      __syncthreads();
+    }
+    if (t >= red_lo && t <= red_hi)
+      relax(std::integral_constant<int, H - 1>(), std::integral_constant<int, 0>(), t);
     __syncthreads();
     const int pb = t - lagb;
-    if (pb >= blk_lo && pb <= blk_hi) relax_plane(pb, H - 2, 1);
+    if (pb >= blk_lo && pb <= blk_hi)
+      relax(std::integral_constant<int, H - 2>(), std::integral_constant<int, 1>(), pb);
     __syncthreads();
     if (pb >= zs && pb < ze) store(pb);
-    if (RESTRICT) {
-      const int pr = t - lagr;
-      if (pr >= zs && pr < ze) restrict_plane(pr);
-    }
-    __syncthreads();
+    // the next issue targets x(t-2) / b(t-1), whose last reads (black of
+    // plane t-1) precede the barrier above
   }
   if (abort_flag) {
     // a TMA completion did not arrive in time: flag it, give the copies this
     // CTA still has in flight a bounded wait to land, and leave
     if (tid == 0) {
       a.err[0] = 1.0;
-      for (int p = xready + 1; p <= xissued; ++p) mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
-      for (int p = bready + 1; p <= bissued; ++p) mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
+      for (int p = xwait + 1; p <= xissued; ++p) mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
+      for (int p = bwait + 1; p <= bissued; ++p) mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
     }
     return;
   }
   if (SUM) {
-    const double s = block_sum(sum, dsh);
+    const double sv = block_sum((double)sum_h + (double)sum_l, dsh);
     if (tid == 0) {
       const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-      a.partials[blk * S_NUM + S_E] = s;
+      a.partials[blk * S_NUM + S_E] = sv;
+    }
+  }
+}
+
+// ===========================================================================
+// residual + down-sampling
+// ===========================================================================
+struct RestrictGeo {
+  static constexpr int XH = ZY + 2;              // x box rows: tile + 1 halo
+  static constexpr int XR = 8;                   // x planes t-1..t+1 + PF in flight
+  static constexpr int BR = 4;                   // b plane t + PF in flight
+  static_assert(XR >= 3 + PF && BR >= 1 + PF, "ring depth");
+  static constexpr int XS = pad32(XH * BOXW);
+  static constexpr int BS = pad32(ZY * ZX);      // b box: the tile only
+  static constexpr int BOFF = XR * XS;
+  static constexpr int ROFF = BOFF + BR * BS;    // residual of one plane
+  static constexpr int AOFF = ROFF + ZX * ZY;    // first child plane's sums
+  static constexpr int MOFF = AOFF + ZX * ZY;
+  __host__ __device__ static constexpr size_t smem_bytes() {
+    return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + 16;
+  }
+};
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CUtensorMap tmx,
+                                                      const __grid_constant__ CUtensorMap tmb,
+                                                      const ZSweepArgs a) {
+  using G = RestrictGeo;
+  uint64_t *xbar = reinterpret_cast<uint64_t *>(zsm + G::MOFF);
+  uint64_t *bbar = xbar + G::XR;
+  __shared__ int abort_flag;
+  const LevelDev &L = a.L;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * ZY;
+  const int zs = blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, nz);
+  const bool zc = (L.wz != 0.f) && (nz > 1);
+  Ring<G::XR> rx;
+  rx.lo = zc ? max(zs - 1, 0) : zs;
+  rx.hi = zc ? min(ze, nz - 1) : ze - 1;
+  Ring<G::BR> rb;
+  rb.lo = zs;
+  rb.hi = ze - 1;
+  if (tid == 0) {
+    abort_flag = 0;
+    int e = tma_preflight(zsm, G::smem_bytes(), &tmx);
+    if (!e) e = tma_preflight(zsm, G::smem_bytes(), &tmb);
+    if (e) {
+      abort_flag = e;
+      a.err[0] = (double)e;
+    } else {
+      for (int q = 0; q < G::XR; ++q) mbar_init(&xbar[q], 1);
+      for (int q = 0; q < G::BR; ++q) mbar_init(&bbar[q], 1);
+      fence_mbar_init();
+    }
+  }
+  __syncthreads();
+  if (abort_flag) return;
+  int xissued = rx.lo - 1, bissued = rb.lo - 1;  // thread 0
+  auto issue_x = [&](int p) {
+    if (!rx.has(p)) return;
+    const int q = rx.slot(p);
+    mbar_expect_tx(&xbar[q], (uint32_t)(G::XH * BOXW * sizeof(float)));
+    tma_plane(zsm + q * G::XS, &tmx, i0 - 4, j0 - 1, p, &xbar[q]);
+    xissued = p;
+  };
+  auto issue_b = [&](int p) {
+    if (!rb.has(p)) return;
+    const int q = rb.slot(p);
+    mbar_expect_tx(&bbar[q], (uint32_t)(ZY * ZX * sizeof(float)));
+    tma_plane(zsm + G::BOFF + q * G::BS, &tmb, i0, j0, p, &bbar[q]);
+    bissued = p;
+  };
+  // step t: residual of plane t (needs x of t-1, t, t+1)
+  const int t0 = zs, t1 = ze - 1;
+  const int xnext0 = zc ? t0 + 1 + PF : t0 + PF;
+  if (tid == 0) {
+    for (int p = rx.lo; p < xnext0 && p <= rx.hi; ++p) issue_x(p);
+    for (int p = rb.lo; p < t0 + PF && p <= rb.hi; ++p) issue_b(p);
+  }
+  int xwait = rx.lo - 1, bwait = rb.lo - 1;  // warp 0
+  const int tx = tid % ZX, ty = tid / ZX;
+  const int gi = i0 + tx;
+  const bool col_in = gi < nx;
+  const float nbx = (float)((gi > 0) + (gi < nx - 1));
+  const float cxu = L.wx * (float)L.sy * (float)L.sz;
+  const float cyu = L.wy * (float)L.sx * (float)L.sz;
+  const float czu = zc ? L.wz * (float)L.sx * (float)L.sy : 0.f;
+  const float mmu = L.wm * (float)L.sx * (float)L.sy * (float)L.sz;
+  const int fx = a.fx, fy = a.fy, fz = a.fz;
+  const int CW = ZX >> fx, CH = ZY >> fy;
+  for (int t = t0; t <= t1; ++t) {
+    if (tid == 0) {
+      fence_proxy_async();
+      issue_x(zc ? t + 1 + PF : t + PF);
+      issue_b(t + PF);
+    }
+    const int ux = min(zc ? t + 1 : t, rx.hi), ub = min(t, rb.hi);
+    if (warp == 0) {
+      bool ok = true;
+      for (int p = xwait + 1; p <= ux && ok; ++p) {
+        ok = mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
+        if (ok) xwait = p;
+      }
+      for (int p = bwait + 1; p <= ub && ok; ++p) {
+        ok = mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
+        if (ok) bwait = p;
+      }
+      if (!ok && lane == 0) abort_flag = 1;
+    }
+    __syncthreads();
+    if (abort_flag) break;
+    const int p = t;
+    const int xop = rx.slot(p) * G::XS;
+    const bool hm = zc && p > 0, hp = zc && p < nz - 1;
+    const int xmo = hm ? rx.slot(p - 1) * G::XS : xop, xpo = hp ? rx.slot(p + 1) * G::XS : xop;
+    const int bop = G::BOFF + rb.slot(p) * G::BS;
+    const float zmf = hm ? 1.f : 0.f, zpf = hp ? 1.f : 0.f;
+    const float mz = mass_of(p, nz, L.sz, L.lz);
+    const float czm = czu * zmf, czp = czu * zpf;
+#pragma unroll
+    for (int k = 0; k < ZY / NTY; ++k) {
+      const int row = ty + NTY * k, gj = j0 + row;
+      float rv = 0.f;
+      if (col_in && gj < ny) {
+        const int so = (row + 1) * BOXW + 4 + tx;
+        float cx = cxu, cy = cyu, cz = czu, mm = mmu;
+        if (!UNIFORM) {
+          const float mx = mass_of(gi, nx, L.sx, L.lx), my = mass_of(gj, ny, L.sy, L.ly);
+          cx = L.wx * my * mz;
+          cy = L.wy * mx * mz;
+          cz = zc ? L.wz * mx * my : 0.f;
+          mm = L.wm * mx * my * mz;
+        }
+        const float nby = (float)((gj > 0) + (gj < ny - 1));
+        const float dg = cx * nbx + cy * nby + cz * (zmf + zpf) + mm;
+        const float *xc = zsm + xop + so;
+        float sacc = cx * (xc[-1] + xc[1]) + cy * (xc[-BOXW] + xc[BOXW]);
+        if (zc) sacc += (UNIFORM ? czm : cz * zmf) * zsm[xmo + so] + (UNIFORM ? czp : cz * zpf) * zsm[xpo + so];
+        rv = zsm[bop + row * ZX + tx] + sacc - dg * xc[0];  // b - A x
+      }
+      zsm[G::ROFF + row * ZX + tx] = rv;
+    }
+    __syncthreads();
+    const size_t cpl = (size_t)(p >> fz) * a.ncy;
+    for (int q = tid; q < CW * CH; q += ZNT) {
+      const int cr = q / CW, cc = q - cr * CW;
+      const float *r0 = zsm + G::ROFF + (cr << fy) * ZX + (cc << fx);
+      float sv = r0[0];
+      if (fx) sv += r0[1];
+      if (fy) {
+        sv += r0[ZX];
+        if (fx) sv += r0[ZX + 1];
+      }
+      const int I = (i0 >> fx) + cc, J = (j0 >> fy) + cr;
+      if (fz && (p & 1) == 0 && p != nz - 1) {
+        zsm[G::AOFF + q] = sv;  // first child plane: keep for the second
+      } else {
+        if (fz && (p & 1) == 1) sv += zsm[G::AOFF + q];
+        if (I < a.ncx && J < a.ncy) a.bc[(cpl + J) * a.ncx + I] = sv;
+      }
+    }
+    // the next issue targets x(t-2) / b(t-1): dead; the residual plane is
+    // rewritten only after the next step's first barrier
+  }
+  if (abort_flag) {
+    if (tid == 0) {
+      a.err[0] = 1.0;
+      for (int p = xwait + 1; p <= xissued; ++p) mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
+      for (int p = bwait + 1; p <= bissued; ++p) mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
     }
   }
 }
@@ -398,29 +659,20 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   const ff s = two_sum(a.h, b.h);
   return quick_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
 }
-__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, {-b.h, -b.l}); }
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = __fmul_rn(a.h, b.h);
-  float e = __fmaf_rn(a.h, b.h, -p);
-  e = __fmaf_rn(a.h, b.l, e);
-  e = __fmaf_rn(a.l, b.h, e);
-  return quick_two_sum(p, e);
-}
-
 struct OuterGeo {
   static constexpr int BH = ZY + 2;              // rows: tile + 1 halo
   static constexpr int S = pad32(BH * BOXW);
   static constexpr int XR = 3 + PF;              // x_new planes t-1..t+1 + in flight
   static constexpr int ER = 3 + PF;              // corrections: same planes and lag as x
-  static constexpr int IR = 1 + PF;
+  static constexpr int IR = 1 + PF;              // inputs: plane t + in flight
   __host__ __device__ static constexpr size_t smem_bytes() {
     return sizeof(float) * (size_t)S * (2 * XR + ER + 2 * IR) +
            sizeof(uint64_t) * (2 * XR + ER + 2 * IR) + sizeof(double) * 32 + 16;
   }
 };
 
-template <int RHS, bool HAS_XL, bool HAS_E>
-__global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensorMap tmh,
+template <int RHS, bool HAS_XL, bool HAS_E, bool ACCURATE>
+__global__ void __launch_bounds__(ZNT, 2) k_zouter(const __grid_constant__ CUtensorMap tmh,
                                                 const __grid_constant__ CUtensorMap tml,
                                                 const __grid_constant__ CUtensorMap tme,
                                                 const __grid_constant__ CUtensorMap tmi0,
@@ -428,8 +680,7 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
                                                 const OuterArgs a, int zchunk, double *err) {
   using G = OuterGeo;
   constexpr int S = G::S;
-  extern __shared__ __align__(128) unsigned char smem[];
-  float *hs = reinterpret_cast<float *>(smem);    // XR slots: x_new high parts
+  float *hs = zsm;                                // XR slots: x_new high parts
   float *ls = hs + G::XR * S;                     // XR slots: x_new low parts
   float *es = ls + G::XR * S;                     // ER slots: corrections
   float *i0s = es + G::ER * S;                    // IR slots: I0 (or explicit b)
@@ -459,15 +710,18 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
   ri.lo = zs;
   ri.hi = ze - 1;
   constexpr bool SP = RHS == RHS_SP;
+  // the low word of the float pair is carried only in exact passes (and read
+  // whenever the caller passes one)
+  constexpr bool USE_L = HAS_XL || (HAS_E && ACCURATE);
   constexpr uint32_t BOXB = (uint32_t)(G::BH * BOXW * sizeof(float));
 
   if (tid == 0) {
     abort_flag = 0;
-    int e = tma_preflight(smem, G::smem_bytes(), &tmh);
-    if (!e && HAS_XL) e = tma_preflight(smem, G::smem_bytes(), &tml);
-    if (!e && HAS_E) e = tma_preflight(smem, G::smem_bytes(), &tme);
-    if (!e) e = tma_preflight(smem, G::smem_bytes(), &tmi0);
-    if (!e && SP) e = tma_preflight(smem, G::smem_bytes(), &tmi1);
+    int e = tma_preflight(zsm, G::smem_bytes(), &tmh);
+    if (!e && HAS_XL) e = tma_preflight(zsm, G::smem_bytes(), &tml);
+    if (!e && HAS_E) e = tma_preflight(zsm, G::smem_bytes(), &tme);
+    if (!e) e = tma_preflight(zsm, G::smem_bytes(), &tmi0);
+    if (!e && SP) e = tma_preflight(zsm, G::smem_bytes(), &tmi1);
     if (e) {
       abort_flag = e;
       err[0] = (double)e;
@@ -532,15 +786,20 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
       }
       float *Hs = hs + s * S, *Ls = ls + s * S;
       const float *Es = es + re.slot(p) * S;
-      for (int q = tid; q < G::BH * BOXW; q += ZNT) {
-        const float h = Hs[q];
-        const float l = HAS_XL ? Ls[q] : 0.f;
-        if (HAS_E) {
-          const ff v = ff_add({h, l}, {__fadd_rn(Es[q], shift), 0.f});
-          Hs[q] = v.h;
-          Ls[q] = v.l;
-        } else if (!HAS_XL) {
-          Ls[q] = 0.f;
+      if (HAS_E || (USE_L && !HAS_XL)) {
+        for (int q = tid; q < G::BH * BOXW; q += ZNT) {
+          const float h = Hs[q];
+          const float l = HAS_XL ? Ls[q] : 0.f;
+          if (HAS_E && ACCURATE) {
+            const ff v = ff_add({h, l}, {__fadd_rn(Es[q], shift), 0.f});
+            Hs[q] = v.h;
+            Ls[q] = v.l;
+          } else if (HAS_E) {
+            Hs[q] = __fadd_rn(h, __fadd_rn(Es[q], shift));
+            if (USE_L) Ls[q] = l;
+          } else {
+            Ls[q] = 0.f;
+          }
         }
       }
       xready = p;
@@ -558,10 +817,14 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
       iready = p;
     }
   };
-  const ff Wx = {a.bx, a.bx_lo}, Wy = {a.by, a.by_lo}, Wz = {a.bz, a.bz_lo};
-  const ff Wa = {a.alpha, a.alpha_lo};
-  const ff Rx = {a.rbx, a.rbx_lo}, Ry = {a.rby, a.rby_lo}, Ra = {a.ralpha, a.ralpha_lo};
-  double srr = 0.0, sbb = 0.0, sx = 0.0, si = 0.0;
+  // per-thread sums in FP32 (r^2, b^2, I0) and double-float (x); FP64 only
+  // once per block
+  float srr = 0.f, sbb = 0.f, si = 0.f, sxh = 0.f, sxl = 0.f;
+  auto add_x = [&](float v) {
+    const ff t = two_sum(sxh, v);
+    sxh = t.h;
+    sxl += t.l;
+  };
 
   auto residual_plane = [&](int p) {
     const int s = rx.slot(p);
@@ -570,48 +833,113 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
     const float *Hm = hm ? hs + rx.slot(p - 1) * S : Hc, *Lm = hm ? ls + rx.slot(p - 1) * S : Lc;
     const float *Hp = hp ? hs + rx.slot(p + 1) * S : Hc, *Lp = hp ? ls + rx.slot(p + 1) * S : Lc;
     const float *I0 = i0s + ri.slot(p) * S, *I1 = i1s + ri.slot(p) * S;
+#pragma unroll 1
     for (int q = tid; q < ZX * ZY; q += ZNT) {
       const int r = q >> 6, c = q & 63;
       const int gi = i0 + c, gj = j0 + r;
       if (gi >= nx || gj >= ny) continue;
       const int o = (r + 1) * BOXW + 4 + c;
-      const ff xc = {Hc[o], Lc[o]};
-      ff dx = {0.f, 0.f}, dy = {0.f, 0.f}, dz = {0.f, 0.f};
-      if (gi > 0) dx = ff_add(dx, ff_sub(xc, {Hc[o - 1], Lc[o - 1]}));
-      if (gi < nx - 1) dx = ff_add(dx, ff_sub(xc, {Hc[o + 1], Lc[o + 1]}));
-      if (gj > 0) dy = ff_add(dy, ff_sub(xc, {Hc[o - BOXW], Lc[o - BOXW]}));
-      if (gj < ny - 1) dy = ff_add(dy, ff_sub(xc, {Hc[o + BOXW], Lc[o + BOXW]}));
-      if (hm) dz = ff_add(dz, ff_sub(xc, {Hm[o], Lm[o]}));
-      if (hp) dz = ff_add(dz, ff_sub(xc, {Hp[o], Lp[o]}));
-      ff ax = ff_add(ff_mul(dx, Wx), ff_mul(dy, Wy));
-      ax = ff_add(ax, ff_mul(dz, Wz));
-      ax = ff_add(ax, ff_mul(xc, Wa));
-      ff bv;
+      const bool w = gi > 0, e = gi < nx - 1, so = gj > 0, no = gj < ny - 1;
+      const float hc = Hc[o], lc = USE_L ? Lc[o] : 0.f;
+      // right-hand side: I0 differences are exact (integer-valued inputs)
+      float gx = 0.f, gy = 0.f, bh, bl = 0.f;
       if (RHS == RHS_EXPLICIT) {
-        bv = {I0[o], 0.f};
+        bh = I0[o];
       } else {
         const float ic = I0[o];
-        float gx = 0.f, gy = 0.f;
-        if (gi > 0) gx += ic - I0[o - 1];
-        if (gi < nx - 1) gx += ic - I0[o + 1];
-        if (gj > 0) gy += ic - I0[o - BOXW];
-        if (gj < ny - 1) gy += ic - I0[o + BOXW];
-        bv = ff_add(ff_mul({gx, 0.f}, Rx), ff_mul({gy, 0.f}, Ry));
-        if (SP) bv = ff_add(bv, ff_mul({I1[o], 0.f}, Ra));
-        si += (double)ic;
+        if (w) gx += ic - I0[o - 1];
+        if (e) gx += ic - I0[o + 1];
+        if (so) gy += ic - I0[o - BOXW];
+        if (no) gy += ic - I0[o + BOXW];
+        si += ic;
       }
-      const ff rr = ff_sub(bv, ax);
+      float rv, rr_h, rr_l;
+      if (!ACCURATE) {
+        // FP32 differences of the float pair: error ~1e-7 of the local terms
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        if (USE_L) {
+          if (w) dx += (hc - Hc[o - 1]) + (lc - Lc[o - 1]);
+          if (e) dx += (hc - Hc[o + 1]) + (lc - Lc[o + 1]);
+          if (so) dy += (hc - Hc[o - BOXW]) + (lc - Lc[o - BOXW]);
+          if (no) dy += (hc - Hc[o + BOXW]) + (lc - Lc[o + BOXW]);
+          if (hm) dz += (hc - Hm[o]) + (lc - Lm[o]);
+          if (hp) dz += (hc - Hp[o]) + (lc - Lp[o]);
+        } else {
+          if (w) dx += hc - Hc[o - 1];
+          if (e) dx += hc - Hc[o + 1];
+          if (so) dy += hc - Hc[o - BOXW];
+          if (no) dy += hc - Hc[o + BOXW];
+          if (hm) dz += hc - Hm[o];
+          if (hp) dz += hc - Hp[o];
+        }
+        const float ax = a.bx * dx + a.by * dy + a.bz * dz + a.alpha * (hc + lc);
+        if (RHS != RHS_EXPLICIT) {
+          bh = a.rbx * gx + a.rby * gy;
+          if (SP) bh += a.ralpha * I1[o];
+        }
+        rv = bh - ax;
+        rr_h = rv;
+        rr_l = 0.f;
+      } else {
+        // compensated evaluation: every rounding error of the hi parts is
+        // captured by an error-free transformation and summed into `lo`
+        float lo = 0.f;
+        auto axis = [&](bool has1, float h1, float l1, bool has2, float h2, float l2, float wh,
+                        float wl, float &ph) {
+          float t1 = 0.f, t2 = 0.f, la = 0.f;
+          if (has1) { const ff d = two_sum(hc, -h1); t1 = d.h; la += d.l + (lc - l1); }
+          if (has2) { const ff d = two_sum(hc, -h2); t2 = d.h; la += d.l + (lc - l2); }
+          const ff S2 = two_sum(t1, t2);
+          la += S2.l;
+          const float pp = S2.h * wh;
+          lo += __fmaf_rn(S2.h, wh, -pp) + S2.h * wl + la * wh;
+          ph = pp;
+        };
+        float px, py, pz = 0.f;
+        auto lo_at = [&](const float *Ls, int oo) { return USE_L ? Ls[oo] : 0.f; };
+        axis(w, w ? Hc[o - 1] : 0.f, w ? lo_at(Lc, o - 1) : 0.f, e, e ? Hc[o + 1] : 0.f,
+             e ? lo_at(Lc, o + 1) : 0.f, a.bx, a.bx_lo, px);
+        axis(so, so ? Hc[o - BOXW] : 0.f, so ? lo_at(Lc, o - BOXW) : 0.f, no,
+             no ? Hc[o + BOXW] : 0.f, no ? lo_at(Lc, o + BOXW) : 0.f, a.by, a.by_lo, py);
+        if (zc) axis(hm, Hm[o], lo_at(Lm, o), hp, Hp[o], lo_at(Lp, o), a.bz, a.bz_lo, pz);
+        const float pa = hc * a.alpha;
+        lo += __fmaf_rn(hc, a.alpha, -pa) + hc * a.alpha_lo + lc * a.alpha;
+        ff A = two_sum(px, py);
+        lo += A.l;
+        A = two_sum(A.h, pz);
+        lo += A.l;
+        A = two_sum(A.h, pa);
+        lo += A.l;
+        // b as a pair
+        if (RHS != RHS_EXPLICIT) {
+          const float qx = gx * a.rbx, qy = gy * a.rby;
+          bl = __fmaf_rn(gx, a.rbx, -qx) + gx * a.rbx_lo + __fmaf_rn(gy, a.rby, -qy) + gy * a.rby_lo;
+          ff Bv = two_sum(qx, qy);
+          bl += Bv.l;
+          if (SP) {
+            const float i1 = I1[o];
+            const float qa = i1 * a.ralpha;
+            bl += __fmaf_rn(i1, a.ralpha, -qa) + i1 * a.ralpha_lo;
+            Bv = two_sum(Bv.h, qa);
+            bl += Bv.l;
+          }
+          bh = Bv.h;
+        }
+        const ff Rv = two_sum(bh, -A.h);
+        rr_h = Rv.h;
+        rr_l = Rv.l + (bl - lo);
+        rv = rr_h + rr_l;
+      }
       const size_t g = (size_t)p * plane + (size_t)gj * nx + gi;
-      if (a.xh_out) {
-        a.xh_out[g] = xc.h;
-        a.xl_out[g] = xc.l;
-      }
-      if (a.r_out) a.r_out[g] = __fadd_rn(rr.h, rr.l);
-      const double rd = (double)rr.h + (double)rr.l;
-      const double bd = (double)bv.h + (double)bv.l;
-      srr += rd * rd;
-      sbb += bd * bd;
-      sx += (double)xc.h + (double)xc.l;
+      if (a.xh_out) a.xh_out[g] = hc;
+      if (USE_L && a.xl_out) a.xl_out[g] = lc;
+      if (a.r_out) a.r_out[g] = rv;
+      srr += rv * rv;
+      sbb += bh * bh;
+      add_x(hc);
+      sxl += lc;
+      (void)rr_h;
+      (void)rr_l;
     }
   };
 
@@ -645,13 +973,13 @@ __global__ void __launch_bounds__(ZNT) k_zouter(const __grid_constant__ CUtensor
   }
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   double v;
-  v = block_sum(srr, dsh);
+  v = block_sum((double)srr, dsh);
   if (tid == 0) a.partials[blk * S_NUM + S_RR] = v;
-  v = block_sum(sbb, dsh);
+  v = block_sum((double)sbb, dsh);
   if (tid == 0) a.partials[blk * S_NUM + S_BB] = v;
-  v = block_sum(sx, dsh);
+  v = block_sum((double)sxh + (double)sxl, dsh);
   if (tid == 0) a.partials[blk * S_NUM + S_X] = v;
-  v = block_sum(si, dsh);
+  v = block_sum((double)si, dsh);
   if (tid == 0) a.partials[blk * S_NUM + S_I0] = v;
 }
 
@@ -678,13 +1006,13 @@ bool encoder() {
   return g_encode_state == 1;
 }
 
-// 3D map over a float32 [nz][ny][nx] array with a (BOXW x rows x 1) box.
-bool make_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int rows) {
+// 3D map over a float32 [nz][ny][nx] array with a (width x rows x 1) box.
+bool make_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int width, int rows) {
   if (!encoder() || !base) return false;
   if (((uintptr_t)base & 15) != 0 || (nx & 3) != 0) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
   const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
-  const cuuint32_t box[3] = {(cuuint32_t)BOXW, (cuuint32_t)rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)width, (cuuint32_t)rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
   return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides,
                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -724,31 +1052,51 @@ int pick_zchunk(int tiles, int nz, bool coupled, int ctas_per_sm) {
   return zc;
 }
 
-template <bool Z, bool P, bool R, bool S>
-cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a, dim3 grid,
-                       cudaStream_t st) {
-  const size_t bytes = SweepGeo<R>::smem_bytes();
+template <bool Z, bool P, bool S, bool U>
+cudaError_t run_zsweep_u(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
+                         dim3 grid, cudaStream_t st) {
+  const size_t bytes = SweepGeo::smem_bytes();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_zsweep<Z, P, R, S>, bytes);
+    cudaError_t e = set_smem(k_zsweep<Z, P, S, U>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zsweep<Z, P, R, S><<<grid, ZNT, bytes, st>>>(mx, mb, a);
+  k_zsweep<Z, P, S, U><<<grid, ZNT, bytes, st>>>(mx, mb, a);
+  return cudaGetLastError();
+}
+bool level_uniform(const LevelDev &L) { return L.sx == L.lx && L.sy == L.ly && L.sz == L.lz; }
+template <bool Z, bool P, bool S>
+cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a, dim3 grid,
+                       cudaStream_t st) {
+  if (level_uniform(a.L)) return run_zsweep_u<Z, P, S, true>(mx, mb, a, grid, st);
+  return run_zsweep_u<Z, P, S, false>(mx, mb, a, grid, st);
+}
+template <bool U>
+cudaError_t run_zrestrict(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
+                          dim3 grid, cudaStream_t st) {
+  const size_t bytes = RestrictGeo::smem_bytes();
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = set_smem(k_zrestrict<U>, bytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_zrestrict<U><<<grid, ZNT, bytes, st>>>(mx, mb, a);
   return cudaGetLastError();
 }
 
-template <int RHS, bool XL, bool E>
+template <int RHS, bool XL, bool E, bool ACC>
 cudaError_t run_zouter(const CUtensorMap *m, const OuterArgs &a, int zchunk, double *err, dim3 grid,
                        cudaStream_t st) {
   const size_t bytes = OuterGeo::smem_bytes();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_zouter<RHS, XL, E>, bytes);
+    cudaError_t e = set_smem(k_zouter<RHS, XL, E, ACC>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zouter<RHS, XL, E><<<grid, ZNT, bytes, st>>>(m[0], m[1], m[2], m[3], m[4], a, zchunk, err);
+  k_zouter<RHS, XL, E, ACC><<<grid, ZNT, bytes, st>>>(m[0], m[1], m[2], m[3], m[4], a, zchunk, err);
   return cudaGetLastError();
 }
 
@@ -757,31 +1105,41 @@ cudaError_t run_zouter(const CUtensorMap *m, const OuterArgs &a, int zchunk, dou
 bool zmarch_usable(const LevelDev &L) { return encoder() && (L.nx & 3) == 0; }
 
 cudaError_t launch_zsweep(ZSweepArgs a, const float *xin, const float *b, bool zero_in, bool prolong,
-                          bool restrict_, bool sum, int *nblocks_out, cudaStream_t st) {
+                          bool sum, int *nblocks_out, cudaStream_t st) {
   const LevelDev &L = a.L;
-  const bool R = restrict_;
-  const int rows_x = ZY + 2 * (R ? 3 : 2), rows_b = ZY + 2 * (R ? 2 : 1);
+  const int rows_x = ZY + 2 * SweepGeo::H, rows_b = ZY + 2 * (SweepGeo::H - 1);
   CUtensorMap mx, mb;
   std::memset(&mx, 0, sizeof mx);
-  if (!zero_in && !make_map(&mx, xin, L.nx, L.ny, L.nz, rows_x)) return cudaErrorNotSupported;
-  if (zero_in && !make_map(&mx, b, L.nx, L.ny, L.nz, rows_x)) return cudaErrorNotSupported;
-  if (!make_map(&mb, b, L.nx, L.ny, L.nz, rows_b)) return cudaErrorNotSupported;
+  if (!make_map(&mx, zero_in ? b : xin, L.nx, L.ny, L.nz, BOXW, rows_x)) return cudaErrorNotSupported;
+  if (!make_map(&mb, b, L.nx, L.ny, L.nz, BOXW, rows_b)) return cudaErrorNotSupported;
   if (((uintptr_t)a.xout & 15) != 0) return cudaErrorNotSupported;
   const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + ZY - 1) / ZY;
   const bool coupled = (L.wz != 0.f) && (L.nz > 1);
-  a.zchunk = pick_zchunk(gx * gy, L.nz, coupled, R ? 2 : 3);
+  a.zchunk = pick_zchunk(gx * gy, L.nz, coupled, 3);
   const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
   if (nblocks_out) *nblocks_out = gx * gy * gz;
   dim3 grid(gx, gy, gz);
-  if (zero_in && !prolong && !R && !sum) return run_zsweep<true, false, false, false>(mx, mb, a, grid, st);
-  if (zero_in && !prolong && R && !sum) return run_zsweep<true, false, true, false>(mx, mb, a, grid, st);
-  if (!zero_in && !prolong && R && !sum) return run_zsweep<false, false, true, false>(mx, mb, a, grid, st);
-  if (!zero_in && prolong && !R && !sum) return run_zsweep<false, true, false, false>(mx, mb, a, grid, st);
-  if (!zero_in && prolong && !R && sum) return run_zsweep<false, true, false, true>(mx, mb, a, grid, st);
-  if (!zero_in && !prolong && !R && !sum) return run_zsweep<false, false, false, false>(mx, mb, a, grid, st);
-  if (!zero_in && !prolong && !R && sum) return run_zsweep<false, false, false, true>(mx, mb, a, grid, st);
-  if (!zero_in && prolong && R && !sum) return run_zsweep<false, true, true, false>(mx, mb, a, grid, st);
+  if (zero_in && !prolong && !sum) return run_zsweep<true, false, false>(mx, mb, a, grid, st);
+  if (!zero_in && prolong && !sum) return run_zsweep<false, true, false>(mx, mb, a, grid, st);
+  if (!zero_in && prolong && sum) return run_zsweep<false, true, true>(mx, mb, a, grid, st);
+  if (!zero_in && !prolong && !sum) return run_zsweep<false, false, false>(mx, mb, a, grid, st);
+  if (!zero_in && !prolong && sum) return run_zsweep<false, false, true>(mx, mb, a, grid, st);
   return cudaErrorNotSupported;
+}
+
+cudaError_t launch_zrestrict(ZSweepArgs a, const float *x, const float *b, cudaStream_t st) {
+  const LevelDev &L = a.L;
+  CUtensorMap mx, mb;
+  if (!make_map(&mx, x, L.nx, L.ny, L.nz, BOXW, ZY + 2)) return cudaErrorNotSupported;
+  if (!make_map(&mb, b, L.nx, L.ny, L.nz, ZX, ZY)) return cudaErrorNotSupported;
+  const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + ZY - 1) / ZY;
+  const bool coupled = (L.wz != 0.f) && (L.nz > 1);
+  a.zchunk = pick_zchunk(gx * gy, L.nz, coupled || a.fz, 3);
+  if (a.fz && (a.zchunk & 1)) ++a.zchunk;  // both children of a coarse plane in one chunk
+  const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
+  dim3 grid(gx, gy, gz);
+  if (level_uniform(L)) return run_zrestrict<true>(mx, mb, a, grid, st);
+  return run_zrestrict<false>(mx, mb, a, grid, st);
 }
 
 cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nblocks_out,
@@ -791,11 +1149,12 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nb
   CUtensorMap m[5];
   std::memset(m, 0, sizeof m);
   const float *rhs0 = rhs_mode == RHS_EXPLICIT ? a.b : a.I0;
-  if (!make_map(&m[0], a.xh_in, a.nx, a.ny, a.nz, rows)) return cudaErrorNotSupported;
-  if (a.xl_in && !make_map(&m[1], a.xl_in, a.nx, a.ny, a.nz, rows)) return cudaErrorNotSupported;
-  if (a.e && !make_map(&m[2], a.e, a.nx, a.ny, a.nz, rows)) return cudaErrorNotSupported;
-  if (!make_map(&m[3], rhs0, a.nx, a.ny, a.nz, rows)) return cudaErrorNotSupported;
-  if (rhs_mode == RHS_SP && !make_map(&m[4], a.I1, a.nx, a.ny, a.nz, rows)) return cudaErrorNotSupported;
+  if (!make_map(&m[0], a.xh_in, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
+  if (a.xl_in && !make_map(&m[1], a.xl_in, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
+  if (a.e && !make_map(&m[2], a.e, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
+  if (!make_map(&m[3], rhs0, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
+  if (rhs_mode == RHS_SP && !make_map(&m[4], a.I1, a.nx, a.ny, a.nz, BOXW, rows))
+    return cudaErrorNotSupported;
   const int gx = (a.nx + ZX - 1) / ZX, gy = (a.ny + ZY - 1) / ZY;
   const bool coupled = (a.bz != 0.f) && (a.nz > 1);
   const int zchunk = pick_zchunk(gx * gy, a.nz, coupled, 2);
@@ -803,11 +1162,17 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nb
   if (nblocks_out) *nblocks_out = gx * gy * gz;
   dim3 grid(gx, gy, gz);
   const bool xl = a.xl_in != nullptr, e = a.e != nullptr;
-#define GD_ZO(R)                                                     \
-  if (xl && e) return run_zouter<R, true, true>(m, a, zchunk, err, grid, st);   \
-  if (xl) return run_zouter<R, true, false>(m, a, zchunk, err, grid, st);       \
-  if (e) return run_zouter<R, false, true>(m, a, zchunk, err, grid, st);        \
-  return run_zouter<R, false, false>(m, a, zchunk, err, grid, st);
+#define GD_ZO2(R, ACC)                                                          \
+  if (xl && e) return run_zouter<R, true, true, ACC>(m, a, zchunk, err, grid, st);  \
+  if (xl) return run_zouter<R, true, false, ACC>(m, a, zchunk, err, grid, st);      \
+  if (e) return run_zouter<R, false, true, ACC>(m, a, zchunk, err, grid, st);       \
+  return run_zouter<R, false, false, ACC>(m, a, zchunk, err, grid, st);
+#define GD_ZO(R)                \
+  if (a.accurate) {             \
+    GD_ZO2(R, true)             \
+  } else {                      \
+    GD_ZO2(R, false)            \
+  }
   if (rhs_mode == RHS_EXPLICIT) { GD_ZO(RHS_EXPLICIT) }
   if (rhs_mode == RHS_AD) { GD_ZO(RHS_AD) }
   GD_ZO(RHS_SP)

@@ -309,9 +309,15 @@ def test_tma_pipeline_matches_plain_kernels(torch, shape, monkeypatch):
         out[mode] = (a, ra, b, rb)
     a1, r1, b1, s1 = out["tma"]
     a2, r2, b2, s2 = out["plain"]
+    # the TMA path's early outer passes keep only the high word of the iterate
+    # (plain FP32 while the residual is above 1e-4); the plain kernels always
+    # keep both words, so below 1e-4 the histories agree only in rate
     for h1, h2 in ((r1["history"], r2["history"]), (s1["history"], s2["history"])):
         assert len(h1) == len(h2)
         for u, v in zip(h1, h2):
-            assert abs(u - v) <= 0.02 * max(u, v) + 1e-9, (h1, h2)
+            if max(u, v) > 1e-4:
+                assert abs(u - v) <= 0.02 * max(u, v), (h1, h2)
+            else:
+                assert max(u, v) <= 1.5 * min(u, v) + 1e-10, (h1, h2)
     assert np.abs(a1 - a2).max() < 1e-3
     assert np.abs(b1 - b2).max() < 1e-3
