@@ -343,6 +343,25 @@ def run_gpu(args):
     return 0
 
 
+def run_ncu_case(args):
+    """A small case for detailed ncu captures (not a benchmark): one AD
+    V-cycle on a 1024 x 512 x 64 stack (arrays of 134 MB, above L2; about
+    2 GB on the device)."""
+    import torch
+    import gdsynth
+    import paper_1310_0041_gb300 as gd
+    gd.build()
+    nx, ny, nz = 1024, 512, 64
+    I0 = torch.from_numpy(gdsynth.em_stack(nx, ny, nz, seed=SEED, ncells=1000)).cuda().float()
+    I1 = torch.empty_like(I0)
+    s = gd.gd_stack_create(nx, ny, nz)
+    rep = gd.gd_diffuse_z(s, I0, I1, (0.0,) + BETA, gd.solve_ctl(1, TOL), raise_on_error=False)
+    gd.gd_destroy(s)
+    print(json.dumps({"ncu_case": "ad_1024x512x64_one_vcycle", "status": rep["status"],
+                      "cycles": rep["cycles"]}))
+    return 0 if rep["status"] in (0, 5) else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -350,7 +369,11 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run the small profiling case instead of the benchmark")
     args = ap.parse_args(argv)
+    if args.ncu_case:
+        return run_ncu_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
