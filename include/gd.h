@@ -186,6 +186,33 @@ int gd_profile_reset(gd_stack *s);
 int gd_profile_query(gd_stack *s, int k, char *name, int name_len, long long *launches,
                      double *ms, double *bytes);
 
+/*
+ * gd_smooth_noalloc -- the red-black relaxation of gd_smooth for callers that
+ * must not allocate device memory: plug-ins whose host application owns the
+ * whole device pool, and latency-bound loops that cannot afford the implicit
+ * synchronisation of cudaMalloc / cudaFree.  gd_smooth allocates the second
+ * array of its out-of-place sweep on every call; this entry point uses a
+ * fixed scratch array compiled into the library instead (every GPU that
+ * loads the library holds its GD_NOALLOC_MAX_VOXELS floats, 16 MB, until the
+ * process exits).  The paper has no counterpart: it is an interface for such
+ * callers, not a step of the method.
+ *   nx, ny >= 2, nz >= 1, nx*ny*nz <= GD_NOALLOC_MAX_VOXELS (else
+ *     GD_ERR_INVALID_ARG, nothing launched);
+ *   w: weights of A = alpha + bx Kx + by Ky + bz Kz (as gd_smooth);
+ *   b (in), x (in/out): device arrays only (host arrays would need staging
+ *     buffers, i.e. allocations: GD_ERR_INVALID_ARG);
+ *   cuda_stream: a cudaStream_t or NULL; returns after the sweeps complete.
+ * It allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the one scratch
+ * array, which keeps the last call's contents (each call overwrites what it
+ * reads): calls that overlap on the GPU (other streams, other threads) race.
+ */
+#define GD_NOALLOC_MAX_VOXELS (4 * 1024 * 1024)
+int gd_smooth_noalloc(int nx, int ny, int nz, gd_weights w, const float *b, float *x, int nsweeps,
+                      void *cuda_stream);
+
 /* Number of kernel launches the stack has enqueued since creation. */
 long long gd_launch_count(gd_stack *s);
 

@@ -33,7 +33,8 @@ GD_HISTORY = 64
 EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_vcycle",
            "gd_destroy", "gd_residual", "gd_smooth", "gd_profile_enable", "gd_profile_reset",
            "gd_profile_query", "gd_launch_count", "gd_status_string", "gd_last_error",
-           "gd_version")
+           "gd_version", "gd_smooth_noalloc")
+GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
 class GdWeights(ctypes.Structure):
@@ -105,6 +106,7 @@ def lib():
                 "gd_status_string": (ctypes.c_char_p, [I]),
                 "gd_last_error": (ctypes.c_char_p, [P]),
                 "gd_version": (I, []),
+                "gd_smooth_noalloc": (I, [I, I, I, GdWeights, P, P, I, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -260,6 +262,16 @@ def gd_residual(s: Stack, system: int, w, I0, I1, x) -> float:
 def gd_smooth(s: Stack, w, b, x, nsweeps: int) -> int:
     return _check(lib().gd_smooth(s.handle, _weights(w), _ptr(b, s.n, "b"), _ptr(x, s.n, "x"),
                                   nsweeps), s)
+
+
+def gd_smooth_noalloc(nx: int, ny: int, nz: int, w, b, x, nsweeps: int, stream=None) -> int:
+    """Red-black sweeps like gd_smooth with no device allocation (device
+    arrays only, at most GD_NOALLOC_MAX_VOXELS voxels); returns the status."""
+    if stream is None:
+        stream = _default_stream()
+    n = nx * ny * nz
+    return lib().gd_smooth_noalloc(nx, ny, nz, _weights(w), _ptr(b, n, "b"), _ptr(x, n, "x"),
+                                   nsweeps, ctypes.c_void_p(stream) if stream else None)
 
 
 def gd_profile_enable(s: Stack, on: bool) -> int:

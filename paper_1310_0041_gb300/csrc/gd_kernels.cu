@@ -8,6 +8,10 @@
 //   cx = wx My(j) Mz(k), cy = wy Mx(i) Mz(k), cz = wz Mx(i) My(j), m = wm Mx My Mz,
 // evaluated in difference form (x_p - x_n), which keeps the rounding error
 // relative to the local differences rather than to the voxel values.
+#include <cmath>
+#include <mutex>
+
+#include "gd.h"
 #include "gd_internal.h"
 
 namespace {
@@ -543,4 +547,68 @@ cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st) {
 cudaError_t launch_copy(float *dst, const float *src, size_t n, cudaStream_t st) {
   k_copy<<<grid_for(n, NT, num_sms() * 8), NT, 0, st>>>(dst, src, n);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free relaxation (gd_smooth_noalloc): the out-of-place sweep's
+// second array lives in this file-scope device array instead of a per-call
+// cudaMalloc.  Host code must not use the symbol as a device address: the
+// address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) float g_noalloc_scratch[GD_NOALLOC_MAX_VOXELS];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+bool noalloc_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool noalloc_weight_ok(double v) { return std::isfinite(v) && v >= 0.0; }
+}  // namespace
+
+extern "C" int gd_smooth_noalloc(int nx, int ny, int nz, gd_weights w, const float *b, float *x,
+                                 int nsweeps, void *cuda_stream) {
+  if (nx < 2 || ny < 2 || nz < 1 || !b || !x || b == x || nsweeps < 0) return GD_ERR_INVALID_ARG;
+  if ((double)nx * (double)ny * (double)nz > (double)GD_NOALLOC_MAX_VOXELS) return GD_ERR_INVALID_ARG;
+  if (!noalloc_weight_ok(w.alpha) || !noalloc_weight_ok(w.beta_x) || !noalloc_weight_ok(w.beta_y) ||
+      !noalloc_weight_ok(w.beta_z))
+    return GD_ERR_INVALID_ARG;
+  if (!noalloc_device_ptr(b) || !noalloc_device_ptr(x)) return GD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return GD_ERR_CUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return GD_ERR_UNSUPPORTED;
+  float *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return GD_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = static_cast<float *>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const size_t n = (size_t)nx * ny * nz;
+  const LevelDev L = {nx, ny, nz, 1, 1, 1, 1, 1, 1, (float)w.beta_x, (float)w.beta_y,
+                      (float)w.beta_z, (float)w.alpha};
+  // sweep k reads x (k even) or the scratch (k odd) and writes the other one
+  for (int k = 0; k < nsweeps; ++k) {
+    const float *in = (k & 1) ? scratch : x;
+    float *out = (k & 1) ? x : scratch;
+    if (launch_rb_sweep(L, in, b, out, false, nullptr, nullptr, st) != cudaSuccess) return GD_ERR_CUDA;
+  }
+  if ((nsweeps & 1) && launch_copy(x, scratch, n, st) != cudaSuccess) return GD_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return GD_ERR_CUDA;
+  return GD_OK;
 }
