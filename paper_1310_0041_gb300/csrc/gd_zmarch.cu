@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
 
   const LevelDev &L = a.L;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * ZY;
   const int zs = blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, nz);
   const bool zc = (L.wz != 0.f) && (nz > 1);
@@ -387,10 +387,13 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
   constexpr int PW = ZX + 2 * H;
   constexpr int PMAX = PROLONG ? (G::XH * PW + ZNT - 1) / ZNT : 1;
   int pso[PMAX], pco[PMAX];
+  float pv[PMAX];
+  int pf_plane = -1;  // plane whose coarse values are in pv
 #pragma unroll
   for (int m = 0; m < PMAX; ++m) {
     pso[m] = -1;
     pco[m] = 0;
+    pv[m] = 0.f;
     const int q = tid + m * ZNT;
     if (PROLONG && q < G::XH * PW) {
       const int r = q / PW, c = q - r * PW + (4 - H);
@@ -410,7 +413,10 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
     }
     // one warp waits for the planes of this step, then the barrier releases all
     const int ux = min(zc ? t + 1 : t, rx.hi), ub = min(t, rb.hi);
-    if (warp == 0) {
+    // Without the prolongation every warp waits for this step's planes itself
+    // (no barrier needed); with it, warp 0 waits, the barrier releases the CTA
+    // and the coarse correction is added before anyone relaxes.
+    if (!PROLONG || warp == 0) {
       bool ok = true;
       if (!ZERO_IN)
         for (int p = xwait + 1; p <= ux && ok; ++p) {
@@ -421,27 +427,41 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
         ok = mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
         if (ok) bwait = p;
       }
-      if (!ok && lane == 0) abort_flag = 1;
+      if (!ok) abort_flag = 1;
     }
     const int xprev = xready;
     if (ux > xready) xready = ux;
     if (ub > bready) bready = ub;
-    __syncthreads();
-    if (abort_flag) break;
-    if (PROLONG && xready > xprev) {
-      // the up-sampled coarse correction, added once to every plane loaded
+    if (PROLONG) {
+      __syncthreads();
+      if (abort_flag) break;
+      // the up-sampled coarse correction, added once to every plane loaded;
+      // the values of the next plane were requested one step ahead
       for (int p = xprev + 1; p <= xready; ++p) {
-        const float *xcp = a.xc + (size_t)(p >> a.fz) * a.ncy * a.ncx;
         const int xop = xo(p);
+        if (p == pf_plane) {
 #pragma unroll
-        for (int m = 0; m < PMAX; ++m)
-          if (pso[m] >= 0) zsm[xop + pso[m]] += __ldg(xcp + pco[m]);
+          for (int m = 0; m < PMAX; ++m)
+            if (pso[m] >= 0) zsm[xop + pso[m]] += pv[m];
+        } else {
+          const float *xcp = a.xc + (size_t)(p >> a.fz) * a.ncy * a.ncx;
+#pragma unroll
+          for (int m = 0; m < PMAX; ++m)
+            if (pso[m] >= 0) zsm[xop + pso[m]] += __ldg(xcp + pco[m]);
+        }
+      }
+      pf_plane = xready + 1;
+      if (pf_plane <= rx.hi) {
+        const float *xcp = a.xc + (size_t)(pf_plane >> a.fz) * a.ncy * a.ncx;
+#pragma unroll
+        for (int m = 0; m < PMAX; ++m) pv[m] = pso[m] >= 0 ? __ldg(xcp + pco[m]) : 0.f;
       }
       __syncthreads();
     }
     if (t >= red_lo && t <= red_hi)
       relax(std::integral_constant<int, H - 1>(), std::integral_constant<int, 0>(), t);
     __syncthreads();
+    if (abort_flag) break;
     const int pb = t - lagb;
     if (pb >= blk_lo && pb <= blk_hi)
       relax(std::integral_constant<int, H - 2>(), std::integral_constant<int, 1>(), pb);
@@ -480,8 +500,8 @@ struct RestrictGeo {
   static constexpr int XS = pad32(XH * BOXW);
   static constexpr int BS = pad32(ZY * ZX);      // b box: the tile only
   static constexpr int BOFF = XR * XS;
-  static constexpr int ROFF = BOFF + BR * BS;    // residual of one plane
-  static constexpr int AOFF = ROFF + ZX * ZY;    // first child plane's sums
+  static constexpr int ROFF = BOFF + BR * BS;    // residual of a plane, two buffers
+  static constexpr int AOFF = ROFF + 2 * ZX * ZY;  // first child plane's sums
   static constexpr int MOFF = AOFF + ZX * ZY;
   __host__ __device__ static constexpr size_t smem_bytes() {
     return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + 16;
@@ -498,7 +518,7 @@ __global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CU
   __shared__ int abort_flag;
   const LevelDev &L = a.L;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x;
   const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * ZY;
   const int zs = blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, nz);
   const bool zc = (L.wz != 0.f) && (nz > 1);
@@ -563,7 +583,8 @@ __global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CU
       issue_b(t + PF);
     }
     const int ux = min(zc ? t + 1 : t, rx.hi), ub = min(t, rb.hi);
-    if (warp == 0) {
+    {
+      // every warp waits for its planes itself
       bool ok = true;
       for (int p = xwait + 1; p <= ux && ok; ++p) {
         ok = mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
@@ -573,11 +594,10 @@ __global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CU
         ok = mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
         if (ok) bwait = p;
       }
-      if (!ok && lane == 0) abort_flag = 1;
+      if (!ok) abort_flag = 1;
     }
-    __syncthreads();
-    if (abort_flag) break;
     const int p = t;
+    const int roff = G::ROFF + (t & 1) * ZX * ZY;  // residual buffer of this step
     const int xop = rx.slot(p) * G::XS;
     const bool hm = zc && p > 0, hp = zc && p < nz - 1;
     const int xmo = hm ? rx.slot(p - 1) * G::XS : xop, xpo = hp ? rx.slot(p + 1) * G::XS : xop;
@@ -606,13 +626,14 @@ __global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CU
         if (zc) sacc += (UNIFORM ? czm : cz * zmf) * zsm[xmo + so] + (UNIFORM ? czp : cz * zpf) * zsm[xpo + so];
         rv = zsm[bop + row * ZX + tx] + sacc - dg * xc[0];  // b - A x
       }
-      zsm[G::ROFF + row * ZX + tx] = rv;
+      zsm[roff + row * ZX + tx] = rv;
     }
     __syncthreads();
+    if (abort_flag) break;
     const size_t cpl = (size_t)(p >> fz) * a.ncy;
     for (int q = tid; q < CW * CH; q += ZNT) {
       const int cr = q / CW, cc = q - cr * CW;
-      const float *r0 = zsm + G::ROFF + (cr << fy) * ZX + (cc << fx);
+      const float *r0 = zsm + roff + (cr << fy) * ZX + (cc << fx);
       float sv = r0[0];
       if (fx) sv += r0[1];
       if (fy) {
@@ -627,8 +648,9 @@ __global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CU
         if (I < a.ncx && J < a.ncy) a.bc[(cpl + J) * a.ncx + I] = sv;
       }
     }
-    // the next issue targets x(t-2) / b(t-1): dead; the residual plane is
-    // rewritten only after the next step's first barrier
+    // The next issue targets x(t-5) / b(t-2): dead.  The next step writes the
+    // other residual buffer; this one is rewritten two steps on, after the
+    // next step's barrier.
   }
   if (abort_flag) {
     if (tid == 0) {
