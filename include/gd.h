@@ -117,7 +117,10 @@ typedef struct {
  *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream
  * If the environment variable GD_DISABLE_TMA is set (and not "0") when the
  * stack is created, the stack runs only the plain kernels (no TMA pipeline,
- * no fused transfers); results are the same up to rounding.
+ * no fused transfers); results are the same up to rounding.  The V-cycle of a
+ * solve is captured once as a CUDA graph and replayed (on the stack's
+ * stream); GD_DISABLE_GRAPHS set at creation launches every kernel directly
+ * instead (identical results).
  */
 int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, int prec,
                     void *cuda_stream);

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "gd.h"
@@ -45,6 +46,28 @@ struct Level {
   size_t n = 0;
 };
 
+struct ProfRec {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes;
+};
+
+// A V-cycle captured as a CUDA graph.  Every cycle of a solve launches the
+// same kernels on the same buffers (each level's ping-pong pointers return to
+// their start after an even number of sweeps), so one capture serves all of
+// them.  With profiling on, the per-kernel event pairs are graph nodes too.
+struct VGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<ProfRec> recs;
+  long long launches = 0;  // kernels per replay
+  int nu1 = 0, nu2 = 0;
+  bool zero_init = false, sum_e = false, prof = false, usable = false;
+};
+
+// A multigrid hierarchy for one set of weights.  Level 0's three arrays are
+// the stack's fine workspace, shared by all cached plans (one solve runs at a
+// time); coarser levels, the coarsest-level factors and the captured
+// V-cycle graphs belong to the plan.
 struct Plan {
   bool valid = false;
   int batch_z = 0;
@@ -52,20 +75,23 @@ struct Plan {
   int cxy = 16;
   std::vector<Level> L;
   float *Vx = nullptr, *Vy = nullptr, *Vz = nullptr, *Dinv = nullptr;
+  std::vector<std::unique_ptr<VGraph>> graphs;
+  unsigned long long last_use = 0;
 };
 
-struct ProfRec {
-  int cls;
-  cudaEvent_t a, b;
-  double bytes;
-};
+// Plans kept per stack: a solve alternating AD and SP (or a few weight sets)
+// rebuilds nothing after the first use of each.
+constexpr int kMaxPlans = 4;
 
 }  // namespace
 
 struct gd_stack {
   int nx = 0, ny = 0, nz = 0, bc = 0, disc = 0, prec = 0;
   cudaStream_t stream = nullptr;
-  Plan plan;
+  std::vector<std::unique_ptr<Plan>> plans;  // cache, least recently used evicted
+  Plan *cur = nullptr;                       // the plan of the running call
+  unsigned long long use_clock = 0;
+  float *f_x = nullptr, *f_b = nullptr, *f_t = nullptr;  // fine-level workspace
   // fine-level outer iterate buffers (second float pair, low parts)
   float *xh2 = nullptr, *xl1 = nullptr, *xl2 = nullptr;
   double *partials = nullptr;
@@ -81,7 +107,11 @@ struct gd_stack {
   long long prof_launches[P_NUM] = {0};
   double prof_ms[P_NUM] = {0}, prof_bytes[P_NUM] = {0};
   long long launches = 0;
-  bool no_tma = false;  // GD_DISABLE_TMA set at creation: plain (unfused) kernels only
+  bool no_tma = false;     // GD_DISABLE_TMA set at creation: plain (unfused) kernels only
+  bool no_graph = false;   // GD_DISABLE_GRAPHS set at creation: direct launches only
+  std::vector<VGraph *> replayed;  // graphs replayed since the last collection (profiling)
+  cudaStream_t cap_stream = nullptr;
+  bool capturing = false;  // events become graph nodes (external event records)
   std::string err;
 };
 
@@ -132,17 +162,28 @@ struct ProfScope {
     ++s->launches;
     if (s->prof_on && s->recs.size() < 200000) {
       a = ev_get(s);
-      cudaEventRecord(a, s->stream);
+      record(a);
     }
+  }
+  void record(cudaEvent_t e) {
+    if (s->capturing)
+      cudaEventRecordWithFlags(e, s->stream, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, s->stream);
   }
   ~ProfScope() {
     if (a && bytes <= 0.0) {
-      s->ev_pool.push_back(a);  // cancelled: nothing was launched
+      // cancelled: nothing was launched.  A captured record is a graph node
+      // now, so the event stays with the graph (class -1 is never summed).
+      if (s->capturing)
+        s->recs.push_back(ProfRec{-1, a, nullptr, 0.0});
+      else
+        s->ev_pool.push_back(a);
       a = nullptr;
     }
     if (a) {
       cudaEvent_t b = ev_get(s);
-      cudaEventRecord(b, s->stream);
+      record(b);
       s->recs.push_back(ProfRec{cls, a, b, bytes});
     }
   }
@@ -164,6 +205,39 @@ void prof_collect(gd_stack *s) {
   s->recs.clear();
 }
 
+// Adds the timings of graphs replayed since the last call (their event pairs
+// hold the latest replay); the stream must have been synchronised.
+void prof_collect_graphs(gd_stack *s) {
+  for (VGraph *g : s->replayed) {
+    for (auto &r : g->recs) {
+      if (r.cls < 0) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+        s->prof_ms[r.cls] += ms;
+        s->prof_launches[r.cls] += 1;
+        s->prof_bytes[r.cls] += r.bytes;
+      }
+    }
+  }
+  s->replayed.clear();
+}
+
+void release_recs(gd_stack *s, std::vector<ProfRec> &recs) {
+  for (auto &r : recs) {
+    if (r.a) s->ev_pool.push_back(r.a);
+    if (r.b) s->ev_pool.push_back(r.b);
+  }
+  recs.clear();
+}
+
+void graphs_free(gd_stack *s, Plan &P) {
+  for (auto &g : P.graphs) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    release_recs(s, g->recs);
+  }
+  P.graphs.clear();
+}
+
 // ---- device memory helpers ----
 int dalloc(gd_stack *s, float **p, size_t n) {
   if (n == 0) n = 1;
@@ -182,11 +256,14 @@ void dfree(float *&p) {
   p = nullptr;
 }
 
-void plan_free(Plan &P) {
-  for (auto &l : P.L) {
-    dfree(l.x);
-    dfree(l.b);
-    dfree(l.t);
+// Frees what the plan owns (level 0's arrays are the stack's); the stream
+// must be idle and the plan's graph timings collected.
+void plan_free(gd_stack *s, Plan &P) {
+  graphs_free(s, P);
+  for (size_t li = 1; li < P.L.size(); ++li) {
+    dfree(P.L[li].x);
+    dfree(P.L[li].b);
+    dfree(P.L[li].t);
   }
   P.L.clear();
   dfree(P.Vx);
@@ -240,11 +317,45 @@ void axis_eig(int n, int sfac, int last, std::vector<float> &V, std::vector<doub
 // When the strongest axis can no longer be halved the level is the coarsest.
 // Coarse stiffness w_d is halved per coarsening of axis d (6-point stencil
 // re-discretised at the coarse spacing); masses are the children counts.
+int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cxy);
+
+// Makes the plan for these weights current: from the cache, else built (the
+// least recently used plan is freed when the cache is full).
 int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
-  Plan &P = s->plan;
-  if (P.valid && P.batch_z == batch_z && P.cxy == cxy && std::memcmp(P.w, w, sizeof(P.w)) == 0)
-    return GD_OK;
-  plan_free(P);
+  s->cur = nullptr;
+  for (auto &p : s->plans)
+    if (p->valid && p->batch_z == batch_z && p->cxy == cxy &&
+        std::memcmp(p->w, w, sizeof(p->w)) == 0) {
+      p->last_use = ++s->use_clock;
+      s->cur = p.get();
+      return GD_OK;
+    }
+  CK(cudaStreamSynchronize(s->stream));
+  if (!s->replayed.empty()) prof_collect_graphs(s);
+  if ((int)s->plans.size() >= kMaxPlans) {
+    size_t v = 0;
+    for (size_t k = 1; k < s->plans.size(); ++k)
+      if (s->plans[k]->last_use < s->plans[v]->last_use) v = k;
+    plan_free(s, *s->plans[v]);
+    s->plans.erase(s->plans.begin() + v);
+  }
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  int st;
+  if (!s->f_x && (st = dalloc(s, &s->f_x, n)) != GD_OK) return st;
+  if (!s->f_b && (st = dalloc(s, &s->f_b, n)) != GD_OK) return st;
+  if (!s->f_t && (st = dalloc(s, &s->f_t, n)) != GD_OK) return st;
+  std::unique_ptr<Plan> P(new Plan);
+  if ((st = plan_build_into(s, *P, w, batch_z, cxy)) != GD_OK) {
+    plan_free(s, *P);
+    return st;
+  }
+  P->last_use = ++s->use_clock;
+  s->cur = P.get();
+  s->plans.push_back(std::move(P));
+  return GD_OK;
+}
+
+int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cxy) {
   P.batch_z = batch_z;
   P.cxy = cxy;
   std::memcpy(P.w, w, sizeof(P.w));
@@ -288,6 +399,12 @@ int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
   for (size_t li = 0; li < P.L.size(); ++li) {
     Level &l = P.L[li];
     l.n = (size_t)l.d.nx * l.d.ny * l.d.nz;
+    if (li == 0) {
+      l.x = s->f_x;
+      l.b = s->f_b;
+      l.t = s->f_t;
+      continue;
+    }
     int st;
     if ((st = dalloc(s, &l.x, l.n)) != GD_OK) return st;
     if ((st = dalloc(s, &l.b, l.n)) != GD_OK) return st;
@@ -334,7 +451,7 @@ int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
 // scalars[S_E]).  Levels whose arrays TMA cannot address run the plain
 // kernels with the fused steps as separate passes.
 int sweep(gd_stack *s, int li, bool zero_in, bool prolong, bool restrict_, bool sum_e) {
-  std::vector<Level> &LV = s->plan.L;
+  std::vector<Level> &LV = s->cur->L;
   Level &l = LV[li];
   Level *C = (prolong || restrict_) ? &LV[li + 1] : nullptr;
   const bool fine = li == 0;
@@ -419,7 +536,7 @@ int sweep(gd_stack *s, int li, bool zero_in, bool prolong, bool restrict_, bool 
 }
 
 int coarsest_solve(gd_stack *s, Level &l) {
-  Plan &P = s->plan;
+  Plan &P = *s->cur;
   ProfScope ps(s, P_COARSEST, (double)l.n * 4.0 * (P.batch_z ? 8.0 : 12.0));
   CK(launch_fdm(l.d.nx, l.d.ny, l.d.nz, P.Vx, P.Vy, P.Vz, P.Dinv, P.batch_z, l.b, l.x, l.t,
                 s->stream));
@@ -432,7 +549,7 @@ int coarsest_solve(gd_stack *s, Level &l) {
 // into scalars[S_E].  The last pre-sweep of a level carries the residual and
 // its down-sampling; the first post-sweep carries the up-sampled correction.
 int vcycle(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
-  std::vector<Level> &L = s->plan.L;
+  std::vector<Level> &L = s->cur->L;
   const int nl = (int)L.size();
   int st;
   if (nl == 1) {
@@ -454,6 +571,82 @@ int vcycle(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
       if ((st = sweep(s, l, false, k == 0, false, sum_e && l == 0 && k == nu2 - 1)) != GD_OK)
         return st;
   }
+  return GD_OK;
+}
+
+// One V-cycle, replayed from a captured graph when possible.  The first cycle
+// with a given shape runs directly (it also performs any lazy allocation),
+// and is then captured on a private stream without executing.
+int vcycle_run(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
+  if (s->no_graph) return vcycle(s, nu1, nu2, zero_init, sum_e);
+  Plan &P = *s->cur;
+  for (auto &gp : P.graphs) {
+    VGraph &g = *gp;
+    if (g.nu1 == nu1 && g.nu2 == nu2 && g.zero_init == zero_init &&
+        g.sum_e == sum_e && g.prof == s->prof_on) {
+      if (!g.usable) return vcycle(s, nu1, nu2, zero_init, sum_e);
+      CK(cudaGraphLaunch(g.exec, s->stream));
+      s->launches += g.launches;
+      if (g.prof) s->replayed.push_back(&g);
+      return GD_OK;
+    }
+  }
+  const size_t r_direct = s->recs.size();
+  int st = vcycle(s, nu1, nu2, zero_init, sum_e);
+  if (st != GD_OK) return st;
+  std::unique_ptr<VGraph> gp(new VGraph);
+  VGraph &g = *gp;
+  g.nu1 = nu1;
+  g.nu2 = nu2;
+  g.zero_init = zero_init;
+  g.sum_e = sum_e;
+  g.prof = s->prof_on;
+  if (!s->cap_stream) CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  // the capture creates no events: take them from the pool
+  if (s->prof_on) {
+    const size_t need = 2 * (s->recs.size() - r_direct) + 16;
+    while (s->ev_pool.size() < need) {
+      cudaEvent_t e = nullptr;
+      CK(cudaEventCreate(&e));
+      s->ev_pool.push_back(e);
+    }
+  }
+  std::vector<float *> saved;
+  for (auto &l : P.L) {
+    saved.push_back(l.x);
+    saved.push_back(l.t);
+  }
+  cudaStream_t user = s->stream;
+  const size_t rec0 = s->recs.size();
+  const long long l0 = s->launches;
+  s->stream = s->cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    s->capturing = true;
+    st = vcycle(s, nu1, nu2, zero_init, sum_e);
+    s->capturing = false;
+    e = cudaStreamEndCapture(s->cap_stream, &graph);
+  }
+  s->stream = user;
+  g.launches = s->launches - l0;
+  s->launches = l0;
+  g.recs.assign(s->recs.begin() + rec0, s->recs.end());
+  s->recs.resize(rec0);
+  bool same = true;
+  size_t k = 0;
+  for (auto &l : P.L) {
+    same = same && l.x == saved[k] && l.t == saved[k + 1];
+    l.x = saved[k];
+    l.t = saved[k + 1];
+    k += 2;
+  }
+  if (e == cudaSuccess && st == GD_OK && same && graph)
+    g.usable = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();  // a failed capture leaves an error behind: fall back to direct launches
+  if (!g.usable) release_recs(s, g.recs);
+  P.graphs.push_back(std::move(gp));
   return GD_OK;
 }
 
@@ -495,6 +688,7 @@ int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] 
     CK(cudaMemcpyAsync(s->h_scalars, s->scalars, 8 * sizeof(double), cudaMemcpyDeviceToHost,
                        s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    if (!s->replayed.empty()) prof_collect_graphs(s);
     std::memcpy(h_out, s->h_scalars, S_NUM * sizeof(double));
     if (s->h_scalars[S_ERR] != 0.0) {
       const int code = (int)s->h_scalars[S_ERR];
@@ -619,7 +813,7 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   if (x0h && x0h != outh && (st = resolve(s, x0h, true, 3, &x0)) != GD_OK) return report(rep, st);
   if (x0h == outh) x0 = out;
   if ((st = plan_build(s, w, system == GD_SYSTEM_SP, ctl.coarsest_xy)) != GD_OK) return report(rep, st);
-  Plan &P = s->plan;
+  Plan &P = *s->cur;
   if (!s->xh2 && (st = dalloc(s, &s->xh2, n)) != GD_OK) return report(rep, st);
   if (!s->xl1 && (st = dalloc(s, &s->xl1, n)) != GD_OK) return report(rep, st);
   if (!s->xl2 && (st = dalloc(s, &s->xl2, n)) != GD_OK) return report(rep, st);
@@ -690,7 +884,7 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
       status = GD_ERR_NOT_CONVERGED;
       break;
     }
-    if ((st = vcycle(s, ctl.nu1, ctl.nu2, true, mean_fix)) != GD_OK) return report(rep, st);
+    if ((st = vcycle_run(s, ctl.nu1, ctl.nu2, true, mean_fix)) != GD_OK) return report(rep, st);
     if ((st = update(F.x)) != GD_OK) return report(rep, st);
     ++cycles;
     rel = std::sqrt(h[S_RR]) / denom;
@@ -791,6 +985,8 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
   s->stream = (cudaStream_t)cuda_stream;
   const char *nt = std::getenv("GD_DISABLE_TMA");
   s->no_tma = nt && nt[0] && std::strcmp(nt, "0") != 0;
+  const char *ng = std::getenv("GD_DISABLE_GRAPHS");
+  s->no_graph = ng && ng[0] && std::strcmp(ng, "0") != 0;
   *out = s;
   return GD_OK;
 }
@@ -798,7 +994,13 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
 int gd_destroy(gd_stack *s) {
   if (!s) return GD_OK;
   cudaStreamSynchronize(s->stream);
-  plan_free(s->plan);
+  if (!s->replayed.empty()) prof_collect_graphs(s);
+  for (auto &p : s->plans) plan_free(s, *p);
+  s->plans.clear();
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  dfree(s->f_x);
+  dfree(s->f_b);
+  dfree(s->f_t);
   dfree(s->xh2);
   dfree(s->xl1);
   dfree(s->xl2);
@@ -869,7 +1071,7 @@ int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh,
   if ((st = resolve(s, xh, true, 2, &x)) != GD_OK) return report(rep, st);
   double wv[4] = {w.alpha, w.beta_x, w.beta_y, w.beta_z};
   if ((st = plan_build(s, wv, system == GD_SYSTEM_SP, 16)) != GD_OK) return report(rep, st);
-  Level &F = s->plan.L[0];
+  Level &F = s->cur->L[0];
   OuterArgs a;
   std::memset(&a, 0, sizeof a);
   set_weights(a, w.beta_x, w.beta_y, w.beta_z, w.alpha, 0.0, 0.0, 0.0);
@@ -903,7 +1105,7 @@ int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh,
   const double rel = std::sqrt(h[S_RR]) / denom;
   if (rep) {
     rep->cycles = ncycles;
-    rep->levels = (int)s->plan.L.size();
+    rep->levels = (int)s->cur->L.size();
     rep->rhs_norm = bnorm;
     rep->rel_residual = rel;
     rep->history[0] = rel0;
@@ -956,8 +1158,9 @@ int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps
   if ((st = resolve(s, bh, true, 0, &b)) != GD_OK) return st;
   if ((st = resolve(s, xh, true, 2, &x)) != GD_OK) return st;
   // a one-level plan of the given weights, borrowing the caller's arrays
-  Plan saved = s->plan;
-  s->plan = Plan();
+  Plan *saved = s->cur;
+  Plan tmp_plan;
+  s->cur = &tmp_plan;
   Level l;
   l.d = LevelDev{s->nx, s->ny, s->nz, 1, 1, 1, 1, 1, 1, (float)w.beta_x, (float)w.beta_y,
                  (float)w.beta_z, (float)w.alpha};
@@ -965,13 +1168,13 @@ int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps
   l.b = b;
   l.x = x;
   if ((st = dalloc(s, &l.t, n)) != GD_OK) {
-    s->plan = saved;
+    s->cur = saved;
     return st;
   }
   float *tmp = l.t;
-  s->plan.L.push_back(l);
+  tmp_plan.L.push_back(l);
   for (int k = 0; k < nsweeps && st == GD_OK; ++k) st = sweep(s, 0, false, false, false, false);
-  Level &lr = s->plan.L[0];
+  Level &lr = tmp_plan.L[0];
   if (st == GD_OK && lr.x != x) {
     ProfScope ps(s, P_COPY, (double)n * 8.0);
     if (launch_copy(x, lr.x, n, s->stream) != cudaSuccess) st = GD_ERR_CUDA;
@@ -981,14 +1184,16 @@ int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps
       st = GD_ERR_CUDA;
   cudaStreamSynchronize(s->stream);
   cudaFree(tmp);
-  s->plan.L.clear();
-  s->plan = saved;
+  tmp_plan.L.clear();
+  s->cur = saved;
   if (s->prof_on) prof_collect(s);
   return st;
 }
 
 int gd_profile_enable(gd_stack *s, int on) {
   if (!s) return GD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(s->stream);
+  if (!s->replayed.empty()) prof_collect_graphs(s);
   if (!on) prof_collect(s);
   s->prof_on = on != 0;
   return GD_OK;

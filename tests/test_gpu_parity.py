@@ -321,3 +321,79 @@ def test_tma_pipeline_matches_plain_kernels(torch, shape, monkeypatch):
                 assert max(u, v) <= 1.5 * min(u, v) + 1e-10, (h1, h2)
     assert np.abs(a1 - a2).max() < 1e-3
     assert np.abs(b1 - b2).max() < 1e-3
+
+
+@pytest.mark.parametrize("shape,prof", [((24, 96, 128), False), ((13, 75, 100), True), ((5, 37, 68), False)])
+def test_graph_replay_matches_direct_launches(torch, shape, prof, monkeypatch):
+    """A solve replays its V-cycle from a captured CUDA graph; with
+    GD_DISABLE_GRAPHS every kernel is launched directly.  Both run the same
+    kernels on the same buffers, so results and histories are bitwise equal,
+    and the per-class profile sees the same launches."""
+    nz, ny, nx = shape
+    I0 = stack_u8(nx, ny, nz, seed=23)
+    out = {}
+    for mode in ("graph", "direct"):
+        if mode == "direct":
+            monkeypatch.setenv("GD_DISABLE_GRAPHS", "1")
+        else:
+            monkeypatch.delenv("GD_DISABLE_GRAPHS", raising=False)
+        s = gd.gd_stack_create(nx, ny, nz)
+        try:
+            gd.gd_profile_enable(s, 1 if prof else 0)
+            x0 = dev(torch, I0)
+            y = torch.empty_like(x0)
+            z = torch.empty_like(x0)
+            r1 = gd.gd_diffuse_z(s, x0, y, (0.0, 1.0, 1.0, 10.0), gd.solve_ctl(12, 1e-9))
+            r2 = gd.gd_screened_poisson_slices(s, x0, y, z, 0.01, gd.solve_ctl(12, 1e-9))
+            # a second solve on the same stack reuses the captured graphs
+            r3 = gd.gd_diffuse_z(s, x0, y, (0.0, 1.0, 1.0, 10.0), gd.solve_ctl(12, 1e-9))
+            torch.cuda.synchronize()
+            prof_rows = gd.gd_profile_all(s) if prof else None
+        finally:
+            gd.gd_destroy(s)
+        out[mode] = (y.cpu().numpy(), z.cpu().numpy(), r1, r2, r3, prof_rows)
+    g, d = out["graph"], out["direct"]
+    assert np.array_equal(g[0], d[0]) and np.array_equal(g[1], d[1])
+    for i in (2, 3, 4):
+        assert g[i]["status"] == gd.GD_OK
+        assert g[i]["cycles"] == d[i]["cycles"]
+        assert list(g[i]["history"]) == list(d[i]["history"])
+    if prof:
+        lg = {row[0]: row[1] for row in g[5]}
+        ld = {row[0]: row[1] for row in d[5]}
+        assert lg == ld
+        assert all(row[2] > 0 for row in g[5] if row[1] > 0)
+
+
+def test_plan_cache_eviction_keeps_results(torch):
+    """A stack keeps a few hierarchies (one per weight set); cycling through
+    more weight sets than it keeps evicts and rebuilds them.  Every solve on
+    the shared stack equals the same solve on a fresh stack, bit for bit."""
+    nx, ny, nz = 70, 33, 20
+    I0 = stack_u8(nx, ny, nz, seed=29)
+    x0 = dev(torch, I0)
+    betas = [10.0, 3.0, 1.0, 0.5, 20.0, 10.0, 3.0]
+    s = gd.gd_stack_create(nx, ny, nz)
+    shared = []
+    try:
+        for bz in betas:
+            y = torch.empty_like(x0)
+            r = gd.gd_diffuse_z(s, x0, y, (0.0, 1.0, 1.0, bz), gd.solve_ctl(20, 1e-8))
+            assert r["status"] == gd.GD_OK
+            z = torch.empty_like(x0)
+            r2 = gd.gd_screened_poisson_slices(s, x0, y, z, 0.01, gd.solve_ctl(20, 1e-8))
+            assert r2["status"] == gd.GD_OK
+            shared.append((y.cpu().numpy(), z.cpu().numpy()))
+    finally:
+        gd.gd_destroy(s)
+    for bz, (y_s, z_s) in zip(betas, shared):
+        f = gd.gd_stack_create(nx, ny, nz)
+        try:
+            y = torch.empty_like(x0)
+            gd.gd_diffuse_z(f, x0, y, (0.0, 1.0, 1.0, bz), gd.solve_ctl(20, 1e-8))
+            z = torch.empty_like(x0)
+            gd.gd_screened_poisson_slices(f, x0, y, z, 0.01, gd.solve_ctl(20, 1e-8))
+        finally:
+            gd.gd_destroy(f)
+        assert np.array_equal(y.cpu().numpy(), y_s)
+        assert np.array_equal(z.cpu().numpy(), z_s)
