@@ -15,9 +15,9 @@
 //               stencil of Sec. 4.2);
 //     SUM       the block sums of the written iterate (mean fix of AD).
 //   Pipeline per step t: red of plane t on the tile + 1 ring, black of plane
-//   t-1 on the tile, store plane t-1.  The ring recomputes the neighbouring
-//   CTA's red values exactly as it does, so the result is the textbook
-//   red-black sweep.
+//   t-1 on the tile, stored from registers.  The ring recomputes the
+//   neighbouring CTA's red values exactly as it does, so the result is the
+//   textbook red-black sweep.
 //
 // k_zrestrict: residual r = b - A x and its down-sampling (sum over the
 //   children of each coarse cell, Sec. 4.1 / 4.2) into the next level's
@@ -43,7 +43,7 @@ constexpr int ZNT = 256;          // threads per CTA
 constexpr int NTY = ZNT / ZX;      // thread rows of the tile-cell map
 constexpr int BOXW = ZX + 8;      // box width: tile + 4 on each side (16-byte aligned start)
 constexpr int PF = 2;             // planes in flight ahead of use
-constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier polling
+constexpr uint32_t WAIT_LIMIT = 1u << 21;  // bounded mbarrier polling (at most ~1 s)
 
 __host__ __device__ constexpr int pad32(int n) { return (n + 31) & ~31; }  // 128-byte slots
 
@@ -58,15 +58,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  // each try_wait may suspend the thread up to the hint (ns) while the phase
+  // is incomplete, so a waiting warp issues few instructions
   const uint32_t a = su32(bar);
+  const uint32_t hint_ns = 500;
   for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(hint_ns)
         : "memory");
     if (done) return true;
   }
@@ -139,29 +142,57 @@ struct Ring {
 // offsets (slots are multiples of 32 floats, i.e. 128 bytes).
 extern __shared__ __align__(128) float zsm[];
 
+// Sweep tiles are 64 x 32: eight tile warps (two float4 cells per thread)
+// and one service warp (TMA issue, mbarrier polling, the red ring).
+constexpr int SY = 32;  // sweep tile rows
+
 struct SweepGeo {
-  static constexpr int H = 2;                    // x box halo in y
-  static constexpr int XH = ZY + 2 * H;          // x box rows
-  static constexpr int BH = ZY + 2 * (H - 1);    // b box rows
-  // ring depths: planes in use plus PF in flight, rounded up to a power of two
-  static constexpr int XR = 8;                   // needs 4 + PF
-  static constexpr int BR = 4;                   // needs 2 + PF
-  static_assert(XR >= 4 + PF && BR >= 2 + PF, "ring depth");
+  static constexpr int H = 2;                    // x box halo rows
+  static constexpr int XH = SY + 2 * H;          // x box rows j0-2 .. j0+SY+1
+  static constexpr int BH = SY + 2 * (H - 1);    // b box rows j0-1 .. j0+SY
+  static constexpr int PFS = 2;                  // planes in flight ahead of use
+  // ring depths: an x plane is last read two steps after its red pass (its
+  // red cells are the z-neighbours of the next black pass but one), a b
+  // plane one step after it (by the black pass)
+  static constexpr int XR = 6;                   // needs PFS + 4
+  static constexpr int BR = 4;                   // needs PFS + 2 (power of two)
+  static_assert(XR >= PFS + 4 && BR >= PFS + 2, "ring depth");
   static constexpr int XS = pad32(XH * BOXW);    // floats per x slot
   static constexpr int BS = pad32(BH * BOXW);
   static constexpr int BOFF = XR * XS;           // b slots
   static constexpr int MOFF = BOFF + BR * BS;    // mbarriers
+  static constexpr int TILE_WARPS = 8;
+  static constexpr int NT = 32 * (TILE_WARPS + 1);  // + the service warp
+  static constexpr int SVC = 32 * TILE_WARPS;       // first thread of the service warp
+  // red ring cells of one colour: the in-plane neighbours of tile cells that
+  // lie outside the tile (corners are nobody's neighbour)
+  static constexpr int NRING = ZX + SY;          // (2 ZX + 2 SY) / 2
+  static constexpr int RING_IT = NRING / 32;
+  static_assert(NRING % 32 == 0, "ring cells per lane");
   __host__ __device__ static constexpr size_t smem_bytes() {
     return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + sizeof(double) * 32 + 16;
   }
 };
 
-template <bool ZERO_IN, bool PROLONG, bool SUM, bool UNIFORM>
-__global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
-                                                   const __grid_constant__ CUtensorMap tmb,
-                                                   const ZSweepArgs a) {
+__device__ __forceinline__ float4 lds4(int off) { return *reinterpret_cast<const float4 *>(zsm + off); }
+__device__ __forceinline__ void sts4(int off, float4 v) { *reinterpret_cast<float4 *>(zsm + off) = v; }
+
+// Thread layout of the tile: a tile thread owns two float4 cells, rows r and
+// r + 16 of one column of four, where warp w's half-warps take rows
+// r = 4 (w / 2) + (w % 2) and r + 2.  All rows of a warp have the same
+// parity, so colour branches are warp-uniform.  The z-neighbours of a cell
+// are the same thread's (its previous plane in registers, older planes and b
+// from the shared-memory rings), so one CTA barrier per plane orders all the
+// in-plane exchanges.
+template <bool ZERO_IN, bool PROLONG, bool SUM, bool UNIFORM, bool COUPLED>
+__global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
+                                                            const __grid_constant__ CUtensorMap tmb,
+                                                            const ZSweepArgs a) {
   using G = SweepGeo;
   constexpr int H = G::H;
+  constexpr int PFS = G::PFS;
+  constexpr int XS = G::XS;
+  constexpr bool zc = COUPLED;  // the launcher passes wz != 0 && nz > 1
   uint64_t *xbar = reinterpret_cast<uint64_t *>(zsm + G::MOFF);
   uint64_t *bbar = xbar + G::XR;
   double *dsh = reinterpret_cast<double *>(bbar + G::BR);
@@ -169,13 +200,13 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
 
   const LevelDev &L = a.L;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * ZY;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool svc = warp == G::TILE_WARPS;
+  const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * SY;
   const int zs = blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, nz);
-  const bool zc = (L.wz != 0.f) && (nz > 1);
   const int t0 = zc ? zs - 1 : zs;
   const int t1 = zc ? ze : ze - 1;
-  const int lagb = zc ? 1 : 0;
+  constexpr int lagb = zc ? 1 : 0;
   const int red_lo = zc ? max(zs - 1, 0) : zs, red_hi = zc ? min(ze, nz - 1) : ze - 1;
   const int blk_lo = zs, blk_hi = ze - 1;
   Ring<G::XR> rx;
@@ -186,7 +217,7 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
   rb.hi = zc ? min(t1, nz - 1) : ze - 1;
   const size_t plane = (size_t)nx * ny;
 
-  if (tid == 0) {
+  if (tid == G::SVC) {
     abort_flag = 0;
     int e = tma_preflight(zsm, G::smem_bytes(), &tmx);
     if (!e) e = tma_preflight(zsm, G::smem_bytes(), &tmb);
@@ -199,20 +230,21 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
       fence_mbar_init();
     }
   }
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (ZERO_IN) {
-    // x is never loaded: cells outside the domain must read 0 for good, and
-    // every cell inside is written before it is read
-    for (int q = tid; q < G::XR * G::XS; q += ZNT) zsm[q] = 0.f;
+    // x is never loaded: cells outside the domain and the black ring must
+    // read 0 for good; every other cell is written before it is read
+    for (int q = tid; q < G::XR * XS / 4; q += G::NT) sts4(4 * q, zero4);
   }
   __syncthreads();
   if (abort_flag) return;  // nothing issued yet
 
-  int xissued = rx.lo - 1, bissued = rb.lo - 1;  // thread 0
+  int xissued = rx.lo - 1, bissued = rb.lo - 1;  // issuing thread
   auto issue_x = [&](int p) {
     if (ZERO_IN || !rx.has(p)) return;
     const int q = rx.slot(p);
     mbar_expect_tx(&xbar[q], (uint32_t)(G::XH * BOXW * sizeof(float)));
-    tma_plane(zsm + q * G::XS, &tmx, i0 - 4, j0 - H, p, &xbar[q]);
+    tma_plane(zsm + q * XS, &tmx, i0 - 4, j0 - H, p, &xbar[q]);
     xissued = p;
   };
   auto issue_b = [&](int p) {
@@ -222,258 +254,392 @@ __global__ void __launch_bounds__(ZNT, 2) k_zsweep(const __grid_constant__ CUten
     tma_plane(zsm + G::BOFF + q * G::BS, &tmb, i0 - 4, j0 - (H - 1), p, &bbar[q]);
     bissued = p;
   };
-  const int xnext0 = zc ? t0 + 1 + PF : t0 + PF;
-  if (tid == 0) {
-    for (int p = rx.lo; p < xnext0 && p <= rx.hi; ++p) issue_x(p);
-    for (int p = rb.lo; p < t0 + PF && p <= rb.hi; ++p) issue_b(p);
+  // x plane issued at step t, and the last x plane a step reads or corrects
+  auto x_issue_at = [&](int t) { return t + (zc ? 1 : 0) + PFS; };
+  auto x_need_at = [&](int t) { return t + (zc ? 1 : 0) + (PROLONG ? 1 : 0); };
+  if (tid == G::SVC) {
+    for (int p = rx.lo; p < x_issue_at(t0) && p <= rx.hi; ++p) issue_x(p);
+    for (int p = rb.lo; p < t0 + PFS && p <= rb.hi; ++p) issue_b(p);
   }
-  int xready = rx.lo - 1, bready = rb.lo - 1;  // planes made usable (all threads)
-  int xwait = rx.lo - 1, bwait = rb.lo - 1;    // planes whose wait succeeded (warp 0)
-  auto xo = [&](int p) { return rx.slot(p) * G::XS; };
+  int xwait = rx.lo - 1, bwait = rb.lo - 1;  // planes whose wait succeeded (service warp)
+  auto wait_planes = [&](int ux, int ub) -> bool {
+    bool ok = true;
+    if (!ZERO_IN)
+      for (int p = xwait + 1; p <= min(ux, rx.hi) && ok; ++p) {
+        ok = mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
+        if (ok) xwait = p;
+      }
+    for (int p = bwait + 1; p <= min(ub, rb.hi) && ok; ++p) {
+      ok = mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
+      if (ok) bwait = p;
+    }
+    return ok;
+  };
+  auto xo = [&](int p) { return rx.slot(p) * XS; };
   auto bo = [&](int p) { return G::BOFF + rb.slot(p) * G::BS; };
 
-  // ---- per-thread constants ----
-  // Tile cells: thread (tx, ty) owns column tx and rows of the row pairs
-  // ty, ty + NTY, ...; in a colour phase it takes the row of each pair with the
-  // right parity, so the 32 lanes of a warp alternate between two rows
-  // (row stride 72 floats = 8 banks) and never share a bank.
-  const int tx = tid % ZX, ty = tid / ZX;
-  const int gi = i0 + tx;
-  const bool col_in = gi < nx;
-  const float nbx = (float)((gi > 0) + (gi < nx - 1));
+  // ---- coefficients ----
   const float cxu = L.wx * (float)L.sy * (float)L.sz;
   const float cyu = L.wy * (float)L.sx * (float)L.sz;
   const float czu = zc ? L.wz * (float)L.sx * (float)L.sy : 0.f;
   const float mmu = L.wm * (float)L.sx * (float)L.sy * (float)L.sz;
-
-  // Gauss-Seidel update of one cell: x = (b + sum_n c_n x_n) / diag.  Cells
-  // outside the domain read 0 and are never written; missing neighbours are
-  // left out of the diagonal by the neighbour counts.  RED0: the first red
-  // pass of a zero iterate (all neighbours are 0).
-  auto cell = [&](auto red0_c, int xop, int xmo, int xpo, int bop, int so, int gci, int gcj,
-                  float mz, float zmf, float zpf, float nbxc) {
+  // Fast path: a uniform level and a tile whose cells, ring and the ring's
+  // neighbours all lie inside the domain in x and y (z faces: zmf / zpf).
+  const bool fast = UNIFORM && (i0 >= 3) && (i0 + ZX + 3 <= nx) && (j0 >= 3) && (j0 + SY + 3 <= ny);
+  // inverse diagonals of the fast path with two / one z-neighbours
+  const float idg2 = 1.f / (2.f * (cxu + cyu) + 2.f * czu + mmu);
+  const float idg1 = 1.f / (2.f * (cxu + cyu) + czu + mmu);
+  struct PlaneK {
+    float mz, zmf, zpf, idg, czm, czp;
+  };
+  auto plane_k = [&](int p) {
+    PlaneK k;
+    const bool hm = zc && p > 0, hp = zc && p < nz - 1;
+    k.zmf = hm ? 1.f : 0.f;
+    k.zpf = hp ? 1.f : 0.f;
+    k.mz = mass_of(p, nz, L.sz, L.lz);
+    k.czm = hm ? czu : 0.f;
+    k.czp = hp ? czu : 0.f;
+    k.idg = (hm && hp) ? idg2 : idg1;
+    return k;
+  };
+  // Gauss-Seidel value of cell (ci, cj):
+  //   (b + cx (x-neighbours) + cy (y-neighbours) + cz (z-neighbours)) / diag
+  // sxn / syn are the sums of the x / y neighbours.  Cells outside the domain
+  // read 0; the neighbour counts leave them out of the diagonal.
+  auto gs = [&](auto fast_c, auto red0_c, const PlaneK &k, float bv, float sxn, float syn, float zm,
+                float zp, int ci, int cj) -> float {
     constexpr bool RED0 = decltype(red0_c)::value;
+    if constexpr (decltype(fast_c)::value) {
+      if (RED0) return bv * k.idg;
+      return (bv + cxu * sxn + cyu * syn + k.czm * zm + k.czp * zp) * k.idg;
+    }
     float cx = cxu, cy = cyu, cz = czu, mm = mmu;
     if (!UNIFORM) {
-      const float mx = mass_of(gci, nx, L.sx, L.lx), my = mass_of(gcj, ny, L.sy, L.ly);
-      cx = L.wx * my * mz;
-      cy = L.wy * mx * mz;
+      const float mx = mass_of(ci, nx, L.sx, L.lx), my = mass_of(cj, ny, L.sy, L.ly);
+      cx = L.wx * my * k.mz;
+      cy = L.wy * mx * k.mz;
       cz = zc ? L.wz * mx * my : 0.f;
-      mm = L.wm * mx * my * mz;
+      mm = L.wm * mx * my * k.mz;
     }
-    const float nby = (float)((gcj > 0) + (gcj < ny - 1));
-    const float dg = cx * nbxc + cy * nby + cz * (zmf + zpf) + mm;
-    const float bv = zsm[bop + so - BOXW];
-    float v;
-    if (RED0) {
-      v = __fdividef(bv, dg);
+    const float nbx = (float)((ci > 0) + (ci < nx - 1));
+    const float nby = (float)((cj > 0) + (cj < ny - 1));
+    const float dg = cx * nbx + cy * nby + cz * (k.zmf + k.zpf) + mm;
+    if (RED0) return __fdividef(bv, dg);
+    return __fdividef(bv + cx * sxn + cy * syn + cz * (k.zmf * zm + k.zpf * zp), dg);
+  };
+
+  // ---- tile threads: two float4 cells ----
+  const int c4 = lane & 15;
+  const int r0 = 4 * ((warp & 7) >> 1) + (warp & 1) + 2 * (lane >> 4);
+  const int gi = i0 + 4 * c4, gj0 = j0 + r0, gj1 = gj0 + 16;
+  const bool act0 = !svc && gi < nx && gj0 < ny;  // nx % 4 == 0: all four cells or none
+  const bool act1 = !svc && gi < nx && gj1 < ny;
+  const int so0 = (r0 + H) * BOXW + 4 + 4 * c4, so1 = so0 + 16 * BOXW;
+  const int go0 = gj0 * nx + gi, go1 = go0 + 16 * nx;  // in-plane offsets
+
+  // ---- service warp: red ring cell m of this lane for colour class P ----
+  // Class P holds the cells with (col + row) & 1 = P (i0 + j0 even), so the
+  // red ring of plane t is class t & 1.  Decoded on the fly (no registers
+  // held across the loop); off < 0 marks a cell outside the domain.
+  auto ring_cell = [&](int m, int P, int &off, int &ci, int &cj) {
+    const int q = lane + 32 * m;
+    int row, col;
+    if (q < ZX / 2) {
+      row = -1;
+      col = (P ^ 1) + 2 * q;
+    } else if (q < ZX) {
+      row = SY;
+      col = P + 2 * (q - ZX / 2);
+    } else if (q < ZX + SY / 2) {
+      col = -1;
+      row = (P ^ 1) + 2 * (q - ZX);
     } else {
-      float sacc = cx * (zsm[xop + so - 1] + zsm[xop + so + 1]) +
-                   cy * (zsm[xop + so - BOXW] + zsm[xop + so + BOXW]);
-      if (zc) sacc += cz * (zmf * zsm[xmo + so] + zpf * zsm[xpo + so]);
-      v = __fdividef(bv + sacc, dg);
+      col = ZX;
+      row = P + 2 * (q - ZX - SY / 2);
     }
-    zsm[xop + so] = v;
+    ci = i0 + col;
+    cj = j0 + row;
+    off = (ci >= 0 && ci < nx && cj >= 0 && cj < ny) ? (row + H) * BOXW + 4 + col : -1;
   };
-  // Fast path: a uniform level and a tile whose cells and their neighbours
-  // all lie inside the domain in x and y (z faces are handled by zmf / zpf).
-  const bool fast = UNIFORM && (i0 >= 3) && (i0 + ZX + 3 <= nx) && (j0 >= 3) && (j0 + ZY + 3 <= ny);
-  // Ring cells of this thread (red ring H-1, black ring H-2), decoded once.
-  constexpr int RMAX = 1;  // ring cells per thread: ceil(164 / 256)
-  int rso[RMAX], rpar[RMAX], rgi[RMAX], rgj[RMAX], rring[RMAX];
+
+  // ---- prolongation by replication: every float4 of the x box inside the
+  // domain gets the coarse value of each of its cells (with x coarsened the
+  // four cells take two coarse values; nx % 4 == 0 keeps both loads aligned)
+  constexpr int PQ = G::XH * (BOXW / 4);
+  constexpr int PMAX = PROLONG ? (PQ + G::NT - 1) / G::NT : 1;
+  int corrected = rx.lo - 1;  // planes that hold the coarse correction
+  auto correct_upto = [&](int u) {
+    for (int p = corrected + 1; p <= min(u, rx.hi); ++p) {
+      const int xop = xo(p);
+      const float *xcp = a.xc + (size_t)(p >> a.fz) * a.ncy * a.ncx;
 #pragma unroll
-  for (int m = 0; m < RMAX; ++m) {
-    rso[m] = -1;
-    rpar[m] = rgi[m] = rgj[m] = rring[m] = 0;
-    const int RG = H - 1;  // widest ring (the red one)
-    const int WR = ZX + 2 * RG, NTB = RG * WR, NLR = ZY * RG;
-    const int q = tid + m * ZNT;
-    if (q < 2 * NTB + 2 * NLR) {
-      int row, col;
-      if (q < NTB) {
-        row = -RG + q / WR; col = -RG + q % WR;
-      } else if (q < 2 * NTB) {
-        row = ZY + (q - NTB) / WR; col = -RG + (q - NTB) % WR;
-      } else if (q < 2 * NTB + NLR) {
-        row = (q - 2 * NTB) / RG; col = -RG + (q - 2 * NTB) % RG;
-      } else {
-        row = (q - 2 * NTB - NLR) / RG; col = ZX + (q - 2 * NTB - NLR) % RG;
-      }
-      const int gci = i0 + col, gcj = j0 + row;
-      if (gci >= 0 && gci < nx && gcj >= 0 && gcj < ny) {
-        rso[m] = (row + H) * BOXW + 4 + col;
-        rpar[m] = (gci + gcj) & 1;
-        rgi[m] = gci;
-        rgj[m] = gcj;
-        // distance of the cell outside the tile (1 or 2)
-        const int dx = col < 0 ? -col : (col >= ZX ? col - ZX + 1 : 0);
-        const int dy = row < 0 ? -row : (row >= ZY ? row - ZY + 1 : 0);
-        rring[m] = dx > dy ? dx : dy;
-      }
-    }
-  }
-  auto relax = [&](auto ring_c, auto colour_c, int p) {
-    constexpr int RING = decltype(ring_c)::value;
-    constexpr int COLOUR = decltype(colour_c)::value;
-    constexpr bool RED0 = ZERO_IN && COLOUR == 0;
-    const std::integral_constant<bool, RED0> red0;
-    const int xop = xo(p);
-    const bool hm = zc && p > 0, hp = zc && p < nz - 1;
-    const int xmo = hm ? xo(p - 1) : xop, xpo = hp ? xo(p + 1) : xop;
-    const int bop = bo(p);
-    const float zmf = hm ? 1.f : 0.f, zpf = hp ? 1.f : 0.f;
-    const float mz = mass_of(p, nz, L.sz, L.lz);
-    const int d = (tx + p + COLOUR) & 1;  // i0, j0 even
-    if (fast) {
-      const float idg = 1.f / (2.f * (cxu + cyu) + czu * (zmf + zpf) + mmu);
-      const float czm = czu * zmf, czp = czu * zpf;
-#pragma unroll
-      for (int k = 0; k < ZY / (2 * NTY); ++k) {
-        const int so = (2 * (ty + NTY * k) + d + H) * BOXW + 4 + tx;
-        const float bv = zsm[bop + so - BOXW];
-        float v;
-        if (RED0) {
-          v = bv * idg;
-        } else {
-          const float *xc = zsm + xop + so;
-          float sacc = cxu * (xc[-1] + xc[1]) + cyu * (xc[-BOXW] + xc[BOXW]);
-          if (zc) sacc += czm * zsm[xmo + so] + czp * zsm[xpo + so];
-          v = (bv + sacc) * idg;
-        }
-        zsm[xop + so] = v;
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < ZY / (2 * NTY); ++k) {
-        const int row = 2 * (ty + NTY * k) + d;
-        const int gj = j0 + row;
-        if (col_in && gj < ny)
-          cell(red0, xop, xmo, xpo, bop, (row + H) * BOXW + 4 + tx, gi, gj, mz, zmf, zpf, nbx);
-      }
-    }
-    if constexpr (RING > 0) {
-#pragma unroll
-      for (int m = 0; m < RMAX; ++m) {
-        if (rso[m] >= 0 && rring[m] <= RING && ((rpar[m] + p) & 1) == COLOUR) {
-          const float nbxc = (float)((rgi[m] > 0) + (rgi[m] < nx - 1));
-          cell(red0, xop, xmo, xpo, bop, rso[m], rgi[m], rgj[m], mz, zmf, zpf, nbxc);
+      for (int m = 0; m < PMAX; ++m) {
+        const int q = tid + m * G::NT;
+        const int rr = q / (BOXW / 4), cq = q - rr * (BOXW / 4);
+        const int gci = i0 - 4 + 4 * cq, gcj = j0 - H + rr;
+        if (q < PQ && gci >= 0 && gci < nx && gcj >= 0 && gcj < ny) {
+          const int pc = (gcj >> a.fy) * a.ncx + (gci >> a.fx);
+          float4 c;
+          if (a.fx) {
+            const float2 c2 = __ldg(reinterpret_cast<const float2 *>(xcp + pc));
+            c = make_float4(c2.x, c2.x, c2.y, c2.y);
+          } else {
+            c = __ldg(reinterpret_cast<const float4 *>(xcp + pc));
+          }
+          const int so = xop + rr * BOXW + 4 * cq;
+          float4 v = lds4(so);
+          v.x += c.x;
+          v.y += c.y;
+          v.z += c.z;
+          v.w += c.w;
+          sts4(so, v);
         }
       }
+      corrected = p;
     }
   };
-  // double-float block sums in FP32 (the FP64 pipe is narrow)
-  float sum_h = 0.f, sum_l = 0.f;
-  auto store = [&](int p) {
-    const int xop = xo(p);
-#pragma unroll
-    for (int q = tid; q < ZX * ZY / 4; q += ZNT) {
-      const int r = q >> 4, c = (q & 15) * 4;
-      const int gci = i0 + c, gcj = j0 + r;
-      if (gci < nx && gcj < ny) {
-        const float4 v = *reinterpret_cast<const float4 *>(zsm + xop + (r + H) * BOXW + 4 + c);
-        *reinterpret_cast<float4 *>(a.xout + (size_t)p * plane + (size_t)gcj * nx + gci) = v;
-        if (SUM) {
-          const float s4 = (v.x + v.y) + (v.z + v.w);
-          const float sn = sum_h + s4;
-          const float bb = sn - sum_h;
-          sum_l += (sum_h - (sn - bb)) + (s4 - bb);
-          sum_h = sn;
-        }
-      }
-    }
-  };
-  // Prolongation: this thread's slot cells (columns 4-H .. 68+H-1 are the
-  // only ones any stage reads) and their offsets within a coarse plane.
-  constexpr int PW = ZX + 2 * H;
-  constexpr int PMAX = PROLONG ? (G::XH * PW + ZNT - 1) / ZNT : 1;
-  int pso[PMAX], pco[PMAX];
-  float pv[PMAX];
-  int pf_plane = -1;  // plane whose coarse values are in pv
-#pragma unroll
-  for (int m = 0; m < PMAX; ++m) {
-    pso[m] = -1;
-    pco[m] = 0;
-    pv[m] = 0.f;
-    const int q = tid + m * ZNT;
-    if (PROLONG && q < G::XH * PW) {
-      const int r = q / PW, c = q - r * PW + (4 - H);
-      const int gci = i0 - 4 + c, gcj = j0 - H + r;
-      if (gci >= 0 && gci < nx && gcj >= 0 && gcj < ny) {
-        pso[m] = r * BOXW + c;
-        pco[m] = (gcj >> a.fy) * a.ncx + (gci >> a.fx);
-      }
-    }
+
+  // The service warp polls the mbarriers for the planes of the next step
+  // just before the CTA barrier that releases that step.
+  bool failed = false;
+  if (svc) failed = !wait_planes(x_need_at(t0), t0);
+  if (__syncthreads_or(failed)) abort_flag = 1;
+  if (PROLONG && !abort_flag) {
+    // the planes the first step reads get their correction before it
+    correct_upto(zc ? t0 + 1 : t0);
+    __syncthreads();
   }
 
-  for (int t = t0; t <= t1; ++t) {
-    if (tid == 0) {
-      fence_proxy_async();
-      issue_x(zc ? t + 1 + PF : t + PF);
-      issue_b(t + PF);
-    }
-    // one warp waits for the planes of this step, then the barrier releases all
-    const int ux = min(zc ? t + 1 : t, rx.hi), ub = min(t, rb.hi);
-    // Without the prolongation every warp waits for this step's planes itself
-    // (no barrier needed); with it, warp 0 waits, the barrier releases the CTA
-    // and the coarse correction is added before anyone relaxes.
-    if (!PROLONG || warp == 0) {
-      bool ok = true;
-      if (!ZERO_IN)
-        for (int p = xwait + 1; p <= ux && ok; ++p) {
-          ok = mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
-          if (ok) xwait = p;
-        }
-      for (int p = bwait + 1; p <= ub && ok; ++p) {
-        ok = mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
-        if (ok) bwait = p;
+  float4 cp0 = zero4, cp1 = zero4;    // plane t-1 after its red pass
+  bool have_prev = false;             // cp holds plane t-1
+  // double-float block sums in FP32 (the FP64 pipe is narrow)
+  float sum_h = 0.f, sum_l = 0.f;
+  auto acc = [&](float4 f) {
+    const float s4 = (f.x + f.y) + (f.z + f.w);
+    const float sn = sum_h + s4;
+    const float bb = sn - sum_h;
+    sum_l += (sum_h - (sn - bb)) + (s4 - bb);
+    sum_h = sn;
+  };
+  const unsigned FULL = 0xffffffffu;
+
+  // The step loop, specialised for fast tiles (constant coefficients) and
+  // the rest, so that neither path pays for the other.
+  auto march = [&](auto fast_c) {
+    const std::integral_constant<bool, ZERO_IN> red0;
+    const std::false_type nored0;
+    // red value of the two cells of a float4 with colour pattern E (cells 0
+    // and 2 when E, else 1 and 3); e is the neighbour across the float4 edge
+    auto red2 = [&](auto e_c, const PlaneK &k, float4 xc, float4 xu, float4 xd, float4 xm, float4 xp,
+                    float4 bv, float e, int cj, float4 &out) {
+      if constexpr (decltype(e_c)::value) {
+        out.x = gs(fast_c, red0, k, bv.x, e + xc.y, xu.x + xd.x, xm.x, xp.x, gi, cj);
+        out.z = gs(fast_c, red0, k, bv.z, xc.y + xc.w, xu.z + xd.z, xm.z, xp.z, gi + 2, cj);
+        out.y = xc.y;
+        out.w = xc.w;
+      } else {
+        out.y = gs(fast_c, red0, k, bv.y, xc.x + xc.z, xu.y + xd.y, xm.y, xp.y, gi + 1, cj);
+        out.w = gs(fast_c, red0, k, bv.w, xc.z + e, xu.w + xd.w, xm.w, xp.w, gi + 3, cj);
+        out.x = xc.x;
+        out.z = xc.z;
       }
-      if (!ok) abort_flag = 1;
-    }
-    const int xprev = xready;
-    if (ux > xready) xready = ux;
-    if (ub > bready) bready = ub;
-    if (PROLONG) {
-      __syncthreads();
-      if (abort_flag) break;
-      // the up-sampled coarse correction, added once to every plane loaded;
-      // the values of the next plane were requested one step ahead
-      for (int p = xprev + 1; p <= xready; ++p) {
-        const int xop = xo(p);
-        if (p == pf_plane) {
-#pragma unroll
-          for (int m = 0; m < PMAX; ++m)
-            if (pso[m] >= 0) zsm[xop + pso[m]] += pv[m];
+    };
+    auto black2 = [&](auto e_c, const PlaneK &k, float4 yc, float4 yu, float4 yd, float4 ym, float4 yp,
+                      float4 yb, float e, int cj, float4 &out) {
+      out = yc;
+      if constexpr (decltype(e_c)::value) {
+        out.x = gs(fast_c, nored0, k, yb.x, e + yc.y, yu.x + yd.x, ym.x, yp.x, gi, cj);
+        out.z = gs(fast_c, nored0, k, yb.z, yc.y + yc.w, yu.z + yd.z, ym.z, yp.z, gi + 2, cj);
+      } else {
+        out.y = gs(fast_c, nored0, k, yb.y, yc.x + yc.z, yu.y + yd.y, ym.y, yp.y, gi + 1, cj);
+        out.w = gs(fast_c, nored0, k, yb.w, yc.z + e, yu.w + yd.w, ym.w, yp.w, gi + 3, cj);
+      }
+    };
+    int xs_t = ((t0 - rx.lo + G::XR) % G::XR) * XS;  // slot offset of plane t (rolled each step)
+    for (int t = t0; t <= t1; ++t) {
+      if (tid == G::SVC) {
+        fence_proxy_async();
+        issue_x(x_issue_at(t));
+        issue_b(t + PFS);
+      }
+      const int xs_p = (xs_t == (G::XR - 1) * XS) ? 0 : xs_t + XS;   // plane t + 1
+      const int xs_m = (xs_t == 0) ? (G::XR - 1) * XS : xs_t - XS;   // plane t - 1
+      const int xs_mm = (xs_m == 0) ? (G::XR - 1) * XS : xs_m - XS;  // plane t - 2
+      if (PROLONG) correct_upto(zc ? t + 2 : t + 1);
+
+      // ---- red pass of plane t ----
+      const bool do_red = t >= red_lo && t <= red_hi;
+      float4 cc0 = cp0, cc1 = cp1, bv0 = zero4, bv1 = zero4;
+      if (do_red) {
+        const PlaneK k = plane_k(t);
+        const int bs = bo(t) - BOXW;  // b rows start one row below x rows
+        if (!svc) {
+          bv0 = lds4(bs + so0);
+          bv1 = lds4(bs + so1);
+          float4 xc0 = zero4, xu0 = zero4, xd0 = zero4, xp0 = zero4, xm0 = zero4;
+          float4 xc1 = zero4, xu1 = zero4, xd1 = zero4, xp1 = zero4, xm1 = zero4;
+          if (!ZERO_IN) {
+            xc0 = lds4(xs_t + so0);
+            xu0 = lds4(xs_t + so0 - BOXW);
+            xd0 = lds4(xs_t + so0 + BOXW);
+            xc1 = lds4(xs_t + so1);
+            xu1 = lds4(xs_t + so1 - BOXW);
+            xd1 = lds4(xs_t + so1 + BOXW);
+            if (zc) {
+              if (k.zpf != 0.f) {
+                xp0 = lds4(xs_p + so0);
+                xp1 = lds4(xs_p + so1);
+              }
+              if (k.zmf != 0.f) {
+                if (have_prev) {
+                  xm0 = cp0;
+                  xm1 = cp1;
+                } else {
+                  xm0 = lds4(xs_m + so0);
+                  xm1 = lds4(xs_m + so1);
+                }
+              }
+            }
+          }
+          if (((gj0 + t) & 1) == 0) {  // red cells 0 and 2
+            float e0 = 0.f, e1 = 0.f;
+            if (!ZERO_IN) {
+              e0 = __shfl_up_sync(FULL, xc0.w, 1, 16);
+              e1 = __shfl_up_sync(FULL, xc1.w, 1, 16);
+              if (c4 == 0) {
+                e0 = zsm[xs_t + so0 - 1];
+                e1 = zsm[xs_t + so1 - 1];
+              }
+            }
+            red2(std::true_type(), k, xc0, xu0, xd0, xm0, xp0, bv0, e0, gj0, cc0);
+            red2(std::true_type(), k, xc1, xu1, xd1, xm1, xp1, bv1, e1, gj1, cc1);
+          } else {  // red cells 1 and 3
+            float e0 = 0.f, e1 = 0.f;
+            if (!ZERO_IN) {
+              e0 = __shfl_down_sync(FULL, xc0.x, 1, 16);
+              e1 = __shfl_down_sync(FULL, xc1.x, 1, 16);
+              if (c4 == 15) {
+                e0 = zsm[xs_t + so0 + 4];
+                e1 = zsm[xs_t + so1 + 4];
+              }
+            }
+            red2(std::false_type(), k, xc0, xu0, xd0, xm0, xp0, bv0, e0, gj0, cc0);
+            red2(std::false_type(), k, xc1, xu1, xd1, xm1, xp1, bv1, e1, gj1, cc1);
+          }
+          if (act0) sts4(xs_t + so0, cc0);
+          else cc0 = zero4;
+          if (act1) sts4(xs_t + so1, cc1);
+          else cc1 = zero4;
         } else {
-          const float *xcp = a.xc + (size_t)(p >> a.fz) * a.ncy * a.ncx;
+          // red ring cells of plane t
 #pragma unroll
-          for (int m = 0; m < PMAX; ++m)
-            if (pso[m] >= 0) zsm[xop + pso[m]] += __ldg(xcp + pco[m]);
+          for (int m = 0; m < G::RING_IT; ++m) {
+            int off, ci, cj;
+            ring_cell(m, t & 1, off, ci, cj);
+            if (off >= 0) {
+              const float bq = zsm[bs + off];
+              float v;
+              if (ZERO_IN) {
+                v = gs(fast_c, red0, k, bq, 0.f, 0.f, 0.f, 0.f, ci, cj);
+              } else {
+                const float *xq = zsm + xs_t + off;
+                const float zm = (zc && k.zmf != 0.f) ? zsm[xs_m + off] : 0.f;
+                const float zp = (zc && k.zpf != 0.f) ? zsm[xs_p + off] : 0.f;
+                v = gs(fast_c, red0, k, bq, xq[-1] + xq[1], xq[-BOXW] + xq[BOXW], zm, zp, ci, cj);
+              }
+              zsm[xs_t + off] = v;
+            }
+          }
         }
       }
-      pf_plane = xready + 1;
-      if (pf_plane <= rx.hi) {
-        const float *xcp = a.xc + (size_t)(pf_plane >> a.fz) * a.ncy * a.ncx;
-#pragma unroll
-        for (int m = 0; m < PMAX; ++m) pv[m] = pso[m] >= 0 ? __ldg(xcp + pco[m]) : 0.f;
+      if (!zc) {
+        // uncoupled planes: the black pass of plane t reads this red pass
+        if (svc && !failed && t < t1) failed = !wait_planes(x_need_at(t + 1), t + 1);
+        if (__syncthreads_or(failed)) {
+          abort_flag = 1;
+          break;
+        }
       }
-      __syncthreads();
+
+      // ---- black pass of plane pb = t - lagb ----
+      const int pb = t - lagb;
+      if (!svc) {
+        if (pb >= blk_lo && pb <= blk_hi) {
+          const PlaneK k = plane_k(pb);
+          const int xob = zc ? xs_m : xs_t;
+          const float4 yc0 = zc ? cp0 : cc0, yc1 = zc ? cp1 : cc1;  // plane pb after red
+          const int bsb = bo(pb) - BOXW;
+          const float4 yb0 = lds4(bsb + so0), yb1 = lds4(bsb + so1);  // b(pb)
+          const float4 yu0 = lds4(xob + so0 - BOXW), yd0 = lds4(xob + so0 + BOXW);
+          const float4 yu1 = lds4(xob + so1 - BOXW), yd1 = lds4(xob + so1 + BOXW);
+          // red cells of plane pb - 1 (z-neighbours below; coupled case)
+          float4 ym0 = zero4, ym1 = zero4;
+          if (zc && k.zmf != 0.f) {
+            ym0 = lds4(xs_mm + so0);
+            ym1 = lds4(xs_mm + so1);
+          }
+          float4 f0, f1;
+          if (((gj0 + pb) & 1) != 0) {  // black cells 0 and 2
+            float e0 = __shfl_up_sync(FULL, yc0.w, 1, 16);
+            float e1 = __shfl_up_sync(FULL, yc1.w, 1, 16);
+            if (c4 == 0) {
+              e0 = zsm[xob + so0 - 1];
+              e1 = zsm[xob + so1 - 1];
+            }
+            black2(std::true_type(), k, yc0, yu0, yd0, ym0, cc0, yb0, e0, gj0, f0);
+            black2(std::true_type(), k, yc1, yu1, yd1, ym1, cc1, yb1, e1, gj1, f1);
+          } else {  // black cells 1 and 3
+            float e0 = __shfl_down_sync(FULL, yc0.x, 1, 16);
+            float e1 = __shfl_down_sync(FULL, yc1.x, 1, 16);
+            if (c4 == 15) {
+              e0 = zsm[xob + so0 + 4];
+              e1 = zsm[xob + so1 + 4];
+            }
+            black2(std::false_type(), k, yc0, yu0, yd0, ym0, cc0, yb0, e0, gj0, f0);
+            black2(std::false_type(), k, yc1, yu1, yd1, ym1, cc1, yb1, e1, gj1, f1);
+          }
+          float *xo_pb = a.xout + (size_t)pb * plane;
+          if (act0) {
+            *reinterpret_cast<float4 *>(xo_pb + go0) = f0;
+            if (SUM) acc(f0);
+          }
+          if (act1) {
+            *reinterpret_cast<float4 *>(xo_pb + go1) = f1;
+            if (SUM) acc(f1);
+          }
+        }
+        if (zc) {
+          cp0 = cc0;
+          cp1 = cc1;
+        }
+      }
+      have_prev = do_red;
+      if (zc) {
+        // the next black pass reads this red pass; slots of old planes are free
+        if (svc && !failed && t < t1) failed = !wait_planes(x_need_at(t + 1), t + 1);
+        if (__syncthreads_or(failed)) {
+          abort_flag = 1;
+          break;
+        }
+      }
+      xs_t = xs_p;
     }
-    if (t >= red_lo && t <= red_hi)
-      relax(std::integral_constant<int, H - 1>(), std::integral_constant<int, 0>(), t);
-    __syncthreads();
-    if (abort_flag) break;
-    const int pb = t - lagb;
-    if (pb >= blk_lo && pb <= blk_hi)
-      relax(std::integral_constant<int, H - 2>(), std::integral_constant<int, 1>(), pb);
-    __syncthreads();
-    if (pb >= zs && pb < ze) store(pb);
-    // the next issue targets x(t-2) / b(t-1), whose last reads (black of
-    // plane t-1) precede the barrier above
+  };
+  if (!abort_flag) {
+    if constexpr (UNIFORM) {
+      if (fast)
+        march(std::true_type());
+      else
+        march(std::false_type());
+    } else {
+      march(std::false_type());
+    }
   }
   if (abort_flag) {
     // a TMA completion did not arrive in time: flag it, give the copies this
     // CTA still has in flight a bounded wait to land, and leave
-    if (tid == 0) {
+    if (tid == G::SVC) {
       a.err[0] = 1.0;
       for (int p = xwait + 1; p <= xissued; ++p) mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
       for (int p = bwait + 1; p <= bissued; ++p) mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
@@ -1074,25 +1240,29 @@ int pick_zchunk(int tiles, int nz, bool coupled, int ctas_per_sm) {
   return zc;
 }
 
-template <bool Z, bool P, bool S, bool U>
-cudaError_t run_zsweep_u(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
-                         dim3 grid, cudaStream_t st) {
+template <bool Z, bool P, bool S, bool U, bool C>
+cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
+                          dim3 grid, cudaStream_t st) {
   const size_t bytes = SweepGeo::smem_bytes();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_zsweep<Z, P, S, U>, bytes);
+    cudaError_t e = set_smem(k_zsweep<Z, P, S, U, C>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zsweep<Z, P, S, U><<<grid, ZNT, bytes, st>>>(mx, mb, a);
+  k_zsweep<Z, P, S, U, C><<<grid, SweepGeo::NT, bytes, st>>>(mx, mb, a);
   return cudaGetLastError();
 }
 bool level_uniform(const LevelDev &L) { return L.sx == L.lx && L.sy == L.ly && L.sz == L.lz; }
+bool level_coupled(const LevelDev &L) { return L.wz != 0.f && L.nz > 1; }
 template <bool Z, bool P, bool S>
 cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a, dim3 grid,
                        cudaStream_t st) {
-  if (level_uniform(a.L)) return run_zsweep_u<Z, P, S, true>(mx, mb, a, grid, st);
-  return run_zsweep_u<Z, P, S, false>(mx, mb, a, grid, st);
+  const bool u = level_uniform(a.L), c = level_coupled(a.L);
+  if (u && c) return run_zsweep_uc<Z, P, S, true, true>(mx, mb, a, grid, st);
+  if (u) return run_zsweep_uc<Z, P, S, true, false>(mx, mb, a, grid, st);
+  if (c) return run_zsweep_uc<Z, P, S, false, true>(mx, mb, a, grid, st);
+  return run_zsweep_uc<Z, P, S, false, false>(mx, mb, a, grid, st);
 }
 template <bool U>
 cudaError_t run_zrestrict(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
@@ -1129,15 +1299,14 @@ bool zmarch_usable(const LevelDev &L) { return encoder() && (L.nx & 3) == 0; }
 cudaError_t launch_zsweep(ZSweepArgs a, const float *xin, const float *b, bool zero_in, bool prolong,
                           bool sum, int *nblocks_out, cudaStream_t st) {
   const LevelDev &L = a.L;
-  const int rows_x = ZY + 2 * SweepGeo::H, rows_b = ZY + 2 * (SweepGeo::H - 1);
+  const int rows_x = SweepGeo::XH, rows_b = SweepGeo::BH;
   CUtensorMap mx, mb;
   std::memset(&mx, 0, sizeof mx);
   if (!make_map(&mx, zero_in ? b : xin, L.nx, L.ny, L.nz, BOXW, rows_x)) return cudaErrorNotSupported;
   if (!make_map(&mb, b, L.nx, L.ny, L.nz, BOXW, rows_b)) return cudaErrorNotSupported;
   if (((uintptr_t)a.xout & 15) != 0) return cudaErrorNotSupported;
-  const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + ZY - 1) / ZY;
-  const bool coupled = (L.wz != 0.f) && (L.nz > 1);
-  a.zchunk = pick_zchunk(gx * gy, L.nz, coupled, 3);
+  const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
+  a.zchunk = pick_zchunk(gx * gy, L.nz, level_coupled(L), 2);
   const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
   if (nblocks_out) *nblocks_out = gx * gy * gz;
   dim3 grid(gx, gy, gz);
