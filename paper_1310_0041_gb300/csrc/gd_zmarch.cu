@@ -40,7 +40,6 @@ namespace {
 constexpr int ZX = 64;            // tile x extent
 constexpr int ZY = 16;            // tile y extent
 constexpr int ZNT = 256;          // threads per CTA
-constexpr int NTY = ZNT / ZX;      // thread rows of the tile-cell map
 constexpr int BOXW = ZX + 8;      // box width: tile + 4 on each side (16-byte aligned start)
 constexpr int PF = 2;             // planes in flight ahead of use
 constexpr uint32_t WAIT_LIMIT = 1u << 21;  // bounded mbarrier polling (at most ~1 s)
@@ -658,43 +657,66 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
 // ===========================================================================
 // residual + down-sampling
 // ===========================================================================
+// Producer/consumer rings for the streaming kernels: the service warp's
+// first lane issues each plane once its slot has been released by all tile
+// warps (an "empty" mbarrier per slot, one arrival per tile warp); tile warps
+// wait on the slot's "full" mbarrier (TMA completion) and release it after
+// their last read.  No CTA barrier is needed inside the plane loop.
+template <int DEPTH>
+struct PcRing {
+  int lo, hi;
+  __device__ __forceinline__ bool has(int p) const { return p >= lo && p <= hi; }
+  __device__ __forceinline__ int slot(int p) const { return (p - lo) % DEPTH; }
+  __device__ __forceinline__ uint32_t parity(int p) const { return ((p - lo) / DEPTH) & 1; }
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
 struct RestrictGeo {
-  static constexpr int XH = ZY + 2;              // x box rows: tile + 1 halo
-  static constexpr int XR = 8;                   // x planes t-1..t+1 + PF in flight
-  static constexpr int BR = 4;                   // b plane t + PF in flight
-  static_assert(XR >= 3 + PF && BR >= 1 + PF, "ring depth");
+  static constexpr int XH = SY + 2;              // x box rows j0-1 .. j0+SY
+  static constexpr int XR = 6;                   // x planes t, t+1 + 4 in flight
+  static constexpr int BR = 4;                   // b plane t + 3 in flight
   static constexpr int XS = pad32(XH * BOXW);
-  static constexpr int BS = pad32(ZY * ZX);      // b box: the tile only
+  static constexpr int BS = ZX * SY;             // b box: the tile only
   static constexpr int BOFF = XR * XS;
-  static constexpr int ROFF = BOFF + BR * BS;    // residual of a plane, two buffers
-  static constexpr int AOFF = ROFF + 2 * ZX * ZY;  // first child plane's sums
-  static constexpr int MOFF = AOFF + ZX * ZY;
+  static constexpr int MOFF = BOFF + BR * BS;
+  static constexpr int TILE_WARPS = 8;
+  static constexpr int NT = 32 * (TILE_WARPS + 1);
+  static constexpr int SVC = 32 * TILE_WARPS;
   __host__ __device__ static constexpr size_t smem_bytes() {
-    return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + 16;
+    return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * 2 * (XR + BR) + 16;
   }
 };
 
-template <bool UNIFORM>
-__global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CUtensorMap tmx,
-                                                      const __grid_constant__ CUtensorMap tmb,
-                                                      const ZSweepArgs a) {
+// Residual r = b - A x of a level and its down-sampling into the next
+// level's right-hand side.  A tile thread owns rows 2k and 2k + 1 of one
+// column of four cells, so the children of a coarse cell in x and y are its
+// own; children in z are two consecutive planes of the march.
+template <bool UNIFORM, bool COUPLED>
+__global__ void __launch_bounds__(RestrictGeo::NT, 2) k_zrestrict(const __grid_constant__ CUtensorMap tmx,
+                                                                 const __grid_constant__ CUtensorMap tmb,
+                                                                 const ZSweepArgs a) {
   using G = RestrictGeo;
-  uint64_t *xbar = reinterpret_cast<uint64_t *>(zsm + G::MOFF);
-  uint64_t *bbar = xbar + G::XR;
+  constexpr bool zc = COUPLED;
+  uint64_t *xfull = reinterpret_cast<uint64_t *>(zsm + G::MOFF);
+  uint64_t *bfull = xfull + G::XR;
+  uint64_t *xempty = bfull + G::BR;
+  uint64_t *bempty = xempty + G::XR;
   __shared__ int abort_flag;
   const LevelDev &L = a.L;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * ZY;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * SY;
   const int zs = blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, nz);
-  const bool zc = (L.wz != 0.f) && (nz > 1);
-  Ring<G::XR> rx;
+  PcRing<G::XR> rx;
   rx.lo = zc ? max(zs - 1, 0) : zs;
   rx.hi = zc ? min(ze, nz - 1) : ze - 1;
-  Ring<G::BR> rb;
+  PcRing<G::BR> rb;
   rb.lo = zs;
   rb.hi = ze - 1;
-  if (tid == 0) {
+  if (tid == G::SVC) {
     abort_flag = 0;
     int e = tma_preflight(zsm, G::smem_bytes(), &tmx);
     if (!e) e = tma_preflight(zsm, G::smem_bytes(), &tmb);
@@ -702,129 +724,246 @@ __global__ void __launch_bounds__(ZNT, 2) k_zrestrict(const __grid_constant__ CU
       abort_flag = e;
       a.err[0] = (double)e;
     } else {
-      for (int q = 0; q < G::XR; ++q) mbar_init(&xbar[q], 1);
-      for (int q = 0; q < G::BR; ++q) mbar_init(&bbar[q], 1);
+      for (int q = 0; q < G::XR; ++q) {
+        mbar_init(&xfull[q], 1);
+        mbar_init(&xempty[q], G::TILE_WARPS);
+      }
+      for (int q = 0; q < G::BR; ++q) {
+        mbar_init(&bfull[q], 1);
+        mbar_init(&bempty[q], G::TILE_WARPS);
+      }
       fence_mbar_init();
     }
   }
   __syncthreads();
   if (abort_flag) return;
-  int xissued = rx.lo - 1, bissued = rb.lo - 1;  // thread 0
-  auto issue_x = [&](int p) {
-    if (!rx.has(p)) return;
-    const int q = rx.slot(p);
-    mbar_expect_tx(&xbar[q], (uint32_t)(G::XH * BOXW * sizeof(float)));
-    tma_plane(zsm + q * G::XS, &tmx, i0 - 4, j0 - 1, p, &xbar[q]);
-    xissued = p;
-  };
-  auto issue_b = [&](int p) {
-    if (!rb.has(p)) return;
-    const int q = rb.slot(p);
-    mbar_expect_tx(&bbar[q], (uint32_t)(ZY * ZX * sizeof(float)));
-    tma_plane(zsm + G::BOFF + q * G::BS, &tmb, i0, j0, p, &bbar[q]);
-    bissued = p;
-  };
-  // step t: residual of plane t (needs x of t-1, t, t+1)
-  const int t0 = zs, t1 = ze - 1;
-  const int xnext0 = zc ? t0 + 1 + PF : t0 + PF;
-  if (tid == 0) {
-    for (int p = rx.lo; p < xnext0 && p <= rx.hi; ++p) issue_x(p);
-    for (int p = rb.lo; p < t0 + PF && p <= rb.hi; ++p) issue_b(p);
+
+  if (warp == G::TILE_WARPS) {
+    // ---- producer: planes in the order the tile warps need them ----
+    if (lane == 0) {
+      bool ok = true;
+      int px = rx.lo, pb = rb.lo;
+      int xdone = rx.lo - 1, bdone = rb.lo - 1;  // issued planes
+      while (ok && (px <= rx.hi || pb <= rb.hi)) {
+        // x(p) is first needed one step before b(p) (coupled levels)
+        const bool take_x = px <= rx.hi && (pb > rb.hi || px <= pb + (zc ? 1 : 0));
+        if (take_x) {
+          const int q = rx.slot(px);
+          if (px - G::XR >= rx.lo) ok = mbar_wait(&xempty[q], rx.parity(px - G::XR));
+          if (ok) {
+            fence_proxy_async();
+            mbar_expect_tx(&xfull[q], (uint32_t)(G::XH * BOXW * sizeof(float)));
+            tma_plane(zsm + q * G::XS, &tmx, i0 - 4, j0 - 1, px, &xfull[q]);
+            xdone = px++;
+          }
+        } else {
+          const int q = rb.slot(pb);
+          if (pb - G::BR >= rb.lo) ok = mbar_wait(&bempty[q], rb.parity(pb - G::BR));
+          if (ok) {
+            fence_proxy_async();
+            mbar_expect_tx(&bfull[q], (uint32_t)(ZX * SY * sizeof(float)));
+            tma_plane(zsm + G::BOFF + q * G::BS, &tmb, i0, j0, pb, &bfull[q]);
+            bdone = pb++;
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        a.err[0] = 1.0;
+      }
+      // every issued copy lands before the CTA may exit (bounded waits)
+      for (int p = max(xdone - G::XR + 1, rx.lo); p <= xdone; ++p) mbar_wait(&xfull[rx.slot(p)], rx.parity(p));
+      for (int p = max(bdone - G::BR + 1, rb.lo); p <= bdone; ++p) mbar_wait(&bfull[rb.slot(p)], rb.parity(p));
+    }
+    __syncthreads();
+    return;
   }
-  int xwait = rx.lo - 1, bwait = rb.lo - 1;  // warp 0
-  const int tx = tid % ZX, ty = tid / ZX;
-  const int gi = i0 + tx;
-  const bool col_in = gi < nx;
-  const float nbx = (float)((gi > 0) + (gi < nx - 1));
+
+  // ---- tile warps ----
+  const int c4 = lane & 15, kr = 2 * warp + (lane >> 4);  // rows 2 kr, 2 kr + 1
+  const int gi = i0 + 4 * c4, gj0 = j0 + 2 * kr, gj1 = gj0 + 1;
+  const bool colin = gi < nx;
+  const bool act0 = colin && gj0 < ny, act1 = colin && gj1 < ny;
+  const int so0 = (2 * kr + 1) * BOXW + 4 + 4 * c4, so1 = so0 + BOXW;
+  const int sb0 = (2 * kr) * ZX + 4 * c4, sb1 = sb0 + ZX;
   const float cxu = L.wx * (float)L.sy * (float)L.sz;
   const float cyu = L.wy * (float)L.sx * (float)L.sz;
   const float czu = zc ? L.wz * (float)L.sx * (float)L.sy : 0.f;
   const float mmu = L.wm * (float)L.sx * (float)L.sy * (float)L.sz;
+  const bool fast = UNIFORM && i0 >= 1 && i0 + ZX + 1 <= nx && j0 >= 1 && j0 + SY + 1 <= ny;
   const int fx = a.fx, fy = a.fy, fz = a.fz;
-  const int CW = ZX >> fx, CH = ZY >> fy;
-  for (int t = t0; t <= t1; ++t) {
-    if (tid == 0) {
-      fence_proxy_async();
-      issue_x(zc ? t + 1 + PF : t + PF);
-      issue_b(t + PF);
+  const unsigned FULL = 0xffffffffu;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  bool failed = false;
+  int xw = rx.lo - 1, bw = rb.lo - 1;  // planes this warp has waited for
+  // (a failed wait is made warp-uniform, so the shuffles stay convergent)
+  auto need_x = [&](int p) {
+    for (int q = xw + 1; q <= min(p, rx.hi) && !failed; ++q) {
+      failed = !mbar_wait(&xfull[rx.slot(q)], rx.parity(q));
+      if (!failed) xw = q;
     }
-    const int ux = min(zc ? t + 1 : t, rx.hi), ub = min(t, rb.hi);
+    failed = __any_sync(FULL, failed);
+  };
+  auto need_b = [&](int p) {
+    for (int q = bw + 1; q <= min(p, rb.hi) && !failed; ++q) {
+      failed = !mbar_wait(&bfull[rb.slot(q)], rb.parity(q));
+      if (!failed) bw = q;
+    }
+    failed = __any_sync(FULL, failed);
+  };
+  auto release_x = [&](int p) {
+    __syncwarp();
+    if (lane == 0 && rx.has(p)) mbar_arrive(&xempty[rx.slot(p)]);
+  };
+  auto release_b = [&](int p) {
+    __syncwarp();
+    if (lane == 0 && rb.has(p)) mbar_arrive(&bempty[rb.slot(p)]);
+  };
+  // residual of one cell; sxn / syn: sums of its x / y neighbours
+  auto res = [&](auto fast_c, float bv, float xv, float sxn, float syn, float zm, float zp, float zmf,
+                 float zpf, float mz, int ci, int cj) -> float {
+    if constexpr (decltype(fast_c)::value) {
+      const float dg = 2.f * (cxu + cyu) + czu * (zmf + zpf) + mmu;
+      return bv + cxu * sxn + cyu * syn + czu * (zm + zp) - dg * xv;
+    }
+    float cx = cxu, cy = cyu, cz = czu, mm = mmu;
+    if (!UNIFORM) {
+      const float mx = mass_of(ci, nx, L.sx, L.lx), my = mass_of(cj, ny, L.sy, L.ly);
+      cx = L.wx * my * mz;
+      cy = L.wy * mx * mz;
+      cz = zc ? L.wz * mx * my : 0.f;
+      mm = L.wm * mx * my * mz;
+    }
+    const float nbx = (float)((ci > 0) + (ci < nx - 1));
+    const float nby = (float)((cj > 0) + (cj < ny - 1));
+    const float dg = cx * nbx + cy * nby + cz * (zmf + zpf) + mm;
+    return bv + cx * sxn + cy * syn + cz * (zmf * zm + zpf * zp) - dg * xv;
+  };
+  float4 acc0 = zero4, acc1 = zero4;  // first child plane's sums (z coarsened)
+  auto march = [&](auto fast_c) {
+    float4 xm0 = zero4, xm1 = zero4, xc0 = zero4, xc1 = zero4;
+    const int t0 = zs, t1 = ze - 1;
+    if (zc && t0 > 0) {
+      need_x(t0 - 1);
+      const int o = rx.slot(t0 - 1) * G::XS;
+      xm0 = lds4(o + so0);
+      xm1 = lds4(o + so1);
+      release_x(t0 - 1);
+    }
+    need_x(t0);
     {
-      // every warp waits for its planes itself
-      bool ok = true;
-      for (int p = xwait + 1; p <= ux && ok; ++p) {
-        ok = mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
-        if (ok) xwait = p;
-      }
-      for (int p = bwait + 1; p <= ub && ok; ++p) {
-        ok = mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
-        if (ok) bwait = p;
-      }
-      if (!ok) abort_flag = 1;
+      const int o = rx.slot(t0) * G::XS;
+      xc0 = lds4(o + so0);
+      xc1 = lds4(o + so1);
     }
-    const int p = t;
-    const int roff = G::ROFF + (t & 1) * ZX * ZY;  // residual buffer of this step
-    const int xop = rx.slot(p) * G::XS;
-    const bool hm = zc && p > 0, hp = zc && p < nz - 1;
-    const int xmo = hm ? rx.slot(p - 1) * G::XS : xop, xpo = hp ? rx.slot(p + 1) * G::XS : xop;
-    const int bop = G::BOFF + rb.slot(p) * G::BS;
-    const float zmf = hm ? 1.f : 0.f, zpf = hp ? 1.f : 0.f;
-    const float mz = mass_of(p, nz, L.sz, L.lz);
-    const float czm = czu * zmf, czp = czu * zpf;
-#pragma unroll
-    for (int k = 0; k < ZY / NTY; ++k) {
-      const int row = ty + NTY * k, gj = j0 + row;
-      float rv = 0.f;
-      if (col_in && gj < ny) {
-        const int so = (row + 1) * BOXW + 4 + tx;
-        float cx = cxu, cy = cyu, cz = czu, mm = mmu;
-        if (!UNIFORM) {
-          const float mx = mass_of(gi, nx, L.sx, L.lx), my = mass_of(gj, ny, L.sy, L.ly);
-          cx = L.wx * my * mz;
-          cy = L.wy * mx * mz;
-          cz = zc ? L.wz * mx * my : 0.f;
-          mm = L.wm * mx * my * mz;
-        }
-        const float nby = (float)((gj > 0) + (gj < ny - 1));
-        const float dg = cx * nbx + cy * nby + cz * (zmf + zpf) + mm;
-        const float *xc = zsm + xop + so;
-        float sacc = cx * (xc[-1] + xc[1]) + cy * (xc[-BOXW] + xc[BOXW]);
-        if (zc) sacc += (UNIFORM ? czm : cz * zmf) * zsm[xmo + so] + (UNIFORM ? czp : cz * zpf) * zsm[xpo + so];
-        rv = zsm[bop + row * ZX + tx] + sacc - dg * xc[0];  // b - A x
+    for (int t = t0; t <= t1 && !failed; ++t) {
+      const bool hm = zc && t > 0, hp = zc && t < nz - 1;
+      need_x(zc ? t + 1 : t);
+      need_b(t);
+      if (failed) break;
+      const int o = rx.slot(t) * G::XS, ob = G::BOFF + rb.slot(t) * G::BS;
+      float4 xn0 = zero4, xn1 = zero4;
+      if (hp) {
+        const int on = rx.slot(t + 1) * G::XS;
+        xn0 = lds4(on + so0);
+        xn1 = lds4(on + so1);
       }
-      zsm[roff + row * ZX + tx] = rv;
-    }
-    __syncthreads();
-    if (abort_flag) break;
-    const size_t cpl = (size_t)(p >> fz) * a.ncy;
-    for (int q = tid; q < CW * CH; q += ZNT) {
-      const int cr = q / CW, cc = q - cr * CW;
-      const float *r0 = zsm + roff + (cr << fy) * ZX + (cc << fx);
-      float sv = r0[0];
-      if (fx) sv += r0[1];
-      if (fy) {
-        sv += r0[ZX];
-        if (fx) sv += r0[ZX + 1];
+      const float4 xu = lds4(o + so0 - BOXW), xd = lds4(o + so1 + BOXW);
+      const float4 b0 = lds4(ob + sb0), b1 = lds4(ob + sb1);
+      // x-neighbours across the float4 edges
+      float l0 = __shfl_up_sync(FULL, xc0.w, 1, 16), l1 = __shfl_up_sync(FULL, xc1.w, 1, 16);
+      float r0 = __shfl_down_sync(FULL, xc0.x, 1, 16), r1 = __shfl_down_sync(FULL, xc1.x, 1, 16);
+      if (c4 == 0) {
+        l0 = zsm[o + so0 - 1];
+        l1 = zsm[o + so1 - 1];
       }
-      const int I = (i0 >> fx) + cc, J = (j0 >> fy) + cr;
-      if (fz && (p & 1) == 0 && p != nz - 1) {
-        zsm[G::AOFF + q] = sv;  // first child plane: keep for the second
+      if (c4 == 15) {
+        r0 = zsm[o + so0 + 4];
+        r1 = zsm[o + so1 + 4];
+      }
+      release_x(t);
+      release_b(t);
+      const float zmf = hm ? 1.f : 0.f, zpf = hp ? 1.f : 0.f;
+      const float mz = mass_of(t, nz, L.sz, L.lz);
+      float4 q0, q1;
+      q0.x = res(fast_c, b0.x, xc0.x, l0 + xc0.y, xu.x + xc1.x, xm0.x, xn0.x, zmf, zpf, mz, gi, gj0);
+      q0.y = res(fast_c, b0.y, xc0.y, xc0.x + xc0.z, xu.y + xc1.y, xm0.y, xn0.y, zmf, zpf, mz, gi + 1, gj0);
+      q0.z = res(fast_c, b0.z, xc0.z, xc0.y + xc0.w, xu.z + xc1.z, xm0.z, xn0.z, zmf, zpf, mz, gi + 2, gj0);
+      q0.w = res(fast_c, b0.w, xc0.w, xc0.z + r0, xu.w + xc1.w, xm0.w, xn0.w, zmf, zpf, mz, gi + 3, gj0);
+      q1.x = res(fast_c, b1.x, xc1.x, l1 + xc1.y, xc0.x + xd.x, xm1.x, xn1.x, zmf, zpf, mz, gi, gj1);
+      q1.y = res(fast_c, b1.y, xc1.y, xc1.x + xc1.z, xc0.y + xd.y, xm1.y, xn1.y, zmf, zpf, mz, gi + 1, gj1);
+      q1.z = res(fast_c, b1.z, xc1.z, xc1.y + xc1.w, xc0.z + xd.z, xm1.z, xn1.z, zmf, zpf, mz, gi + 2, gj1);
+      q1.w = res(fast_c, b1.w, xc1.w, xc1.z + r1, xc0.w + xd.w, xm1.w, xn1.w, zmf, zpf, mz, gi + 3, gj1);
+      if (!act0) q0 = zero4;
+      if (!act1) q1 = zero4;
+      // children of the coarse cells: x pairs in the float4, y pairs in the
+      // two rows, z pairs over two steps
+      float4 s0, s1;
+      if (fx) {
+        s0 = make_float4(q0.x + q0.y, q0.z + q0.w, 0.f, 0.f);
+        s1 = make_float4(q1.x + q1.y, q1.z + q1.w, 0.f, 0.f);
       } else {
-        if (fz && (p & 1) == 1) sv += zsm[G::AOFF + q];
-        if (I < a.ncx && J < a.ncy) a.bc[(cpl + J) * a.ncx + I] = sv;
+        s0 = q0;
+        s1 = q1;
+      }
+      if (fy) {
+        s0.x += s1.x;
+        s0.y += s1.y;
+        s0.z += s1.z;
+        s0.w += s1.w;
+      }
+      if (fz && (t & 1) == 0 && t != nz - 1) {
+        acc0 = s0;
+        acc1 = s1;
+      } else {
+        if (fz && (t & 1) == 1) {
+          s0.x += acc0.x;
+          s0.y += acc0.y;
+          s0.z += acc0.z;
+          s0.w += acc0.w;
+          s1.x += acc1.x;
+          s1.y += acc1.y;
+          s1.z += acc1.z;
+          s1.w += acc1.w;
+        }
+        float *cpl = a.bc + (size_t)(t >> fz) * a.ncy * a.ncx;
+        const int I = (i0 + 4 * c4) >> fx;
+        const int J0 = gj0 >> fy;
+        if (colin) {
+          if (fx) {
+            if (gj0 < ny) *reinterpret_cast<float2 *>(cpl + (size_t)J0 * a.ncx + I) = make_float2(s0.x, s0.y);
+            if (!fy && gj1 < ny)
+              *reinterpret_cast<float2 *>(cpl + (size_t)(J0 + 1) * a.ncx + I) = make_float2(s1.x, s1.y);
+          } else {
+            if (gj0 < ny) *reinterpret_cast<float4 *>(cpl + (size_t)J0 * a.ncx + I) = s0;
+            if (!fy && gj1 < ny) *reinterpret_cast<float4 *>(cpl + (size_t)(J0 + 1) * a.ncx + I) = s1;
+          }
+        }
+      }
+      xm0 = xc0;
+      xm1 = xc1;
+      xc0 = xn0;
+      xc1 = xn1;
+      if (!zc && t < t1) {
+        // uncoupled: the next plane's own rows are read in its own step
+        need_x(t + 1);
+        if (!failed) {
+          const int on = rx.slot(t + 1) * G::XS;
+          xc0 = lds4(on + so0);
+          xc1 = lds4(on + so1);
+        }
       }
     }
-    // The next issue targets x(t-5) / b(t-2): dead.  The next step writes the
-    // other residual buffer; this one is rewritten two steps on, after the
-    // next step's barrier.
+  };
+  if (fast)
+    march(std::true_type());
+  else
+    march(std::false_type());
+  if (failed) {
+    abort_flag = 1;
+    a.err[0] = 1.0;
   }
-  if (abort_flag) {
-    if (tid == 0) {
-      a.err[0] = 1.0;
-      for (int p = xwait + 1; p <= xissued; ++p) mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
-      for (int p = bwait + 1; p <= bissued; ++p) mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
-    }
-  }
+  __syncthreads();
 }
 
 // ===========================================================================
@@ -1264,17 +1403,17 @@ cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const ZSwee
   if (c) return run_zsweep_uc<Z, P, S, false, true>(mx, mb, a, grid, st);
   return run_zsweep_uc<Z, P, S, false, false>(mx, mb, a, grid, st);
 }
-template <bool U>
+template <bool U, bool C>
 cudaError_t run_zrestrict(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
                           dim3 grid, cudaStream_t st) {
   const size_t bytes = RestrictGeo::smem_bytes();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_zrestrict<U>, bytes);
+    cudaError_t e = set_smem(k_zrestrict<U, C>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zrestrict<U><<<grid, ZNT, bytes, st>>>(mx, mb, a);
+  k_zrestrict<U, C><<<grid, RestrictGeo::NT, bytes, st>>>(mx, mb, a);
   return cudaGetLastError();
 }
 
@@ -1321,16 +1460,20 @@ cudaError_t launch_zsweep(ZSweepArgs a, const float *xin, const float *b, bool z
 cudaError_t launch_zrestrict(ZSweepArgs a, const float *x, const float *b, cudaStream_t st) {
   const LevelDev &L = a.L;
   CUtensorMap mx, mb;
-  if (!make_map(&mx, x, L.nx, L.ny, L.nz, BOXW, ZY + 2)) return cudaErrorNotSupported;
-  if (!make_map(&mb, b, L.nx, L.ny, L.nz, ZX, ZY)) return cudaErrorNotSupported;
-  const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + ZY - 1) / ZY;
-  const bool coupled = (L.wz != 0.f) && (L.nz > 1);
-  a.zchunk = pick_zchunk(gx * gy, L.nz, coupled || a.fz, 3);
+  if (!make_map(&mx, x, L.nx, L.ny, L.nz, BOXW, RestrictGeo::XH)) return cudaErrorNotSupported;
+  if (!make_map(&mb, b, L.nx, L.ny, L.nz, ZX, SY)) return cudaErrorNotSupported;
+  if (((uintptr_t)a.bc & 15) != 0) return cudaErrorNotSupported;
+  const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
+  const bool coupled = level_coupled(L);
+  a.zchunk = pick_zchunk(gx * gy, L.nz, coupled || a.fz, 2);
   if (a.fz && (a.zchunk & 1)) ++a.zchunk;  // both children of a coarse plane in one chunk
   const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
   dim3 grid(gx, gy, gz);
-  if (level_uniform(L)) return run_zrestrict<true>(mx, mb, a, grid, st);
-  return run_zrestrict<false>(mx, mb, a, grid, st);
+  const bool u = level_uniform(L);
+  if (u && coupled) return run_zrestrict<true, true>(mx, mb, a, grid, st);
+  if (u) return run_zrestrict<true, false>(mx, mb, a, grid, st);
+  if (coupled) return run_zrestrict<false, true>(mx, mb, a, grid, st);
+  return run_zrestrict<false, false>(mx, mb, a, grid, st);
 }
 
 cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nblocks_out,
