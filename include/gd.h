@@ -131,8 +131,9 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
  * mean(I0).  w.alpha is ignored (AD has no screening term); needs
  * beta_x, beta_y >= 0, beta_z > 0.
  *   I0 (in), I1 (out): stack arrays; I1 must not alias I0.
- *   x0 (in, nullable): initial guess (default I0, Sec. 4.1 starts from the
- *     input); may alias I1.
+ *   x0 (in, nullable): initial guess (default zero: from I0 the residual
+ *     is the removed inter-slice variation, several times the right-hand
+ *     side on EM stacks); may alias I1.
  */
 int gd_diffuse_z(gd_stack *s, const float *I0, float *I1, gd_weights w, const gd_solve_ctl *ctl,
                  const float *x0, gd_report *rep);
@@ -143,7 +144,9 @@ int gd_diffuse_z(gd_stack *s, const float *I0, float *I1, gd_weights w, const gd
  * every slice; the slices are independent systems solved together.
  *   I0, I1 (in), I2 (out): stack arrays; I2 must alias neither input.
  *   alpha > 0: screening weight (the paper uses 0.01).
- *   x0 (in, nullable): initial guess (default I1); may alias I2.
+ *   x0 (in, nullable): initial guess (default I0, whose residual is
+ *     alpha (I1 - I0): small against the right-hand side when the screening
+ *     weight is small); may alias I2.
  */
 int gd_screened_poisson_slices(gd_stack *s, const float *I0, const float *I1, float *I2,
                                double alpha, const gd_solve_ctl *ctl, const float *x0,

@@ -1,7 +1,7 @@
 // gd_host.cu -- C ABI, multigrid planning and the solve driver (host code).
 //
 // Structure of one solve (gd_diffuse_z / gd_screened_poisson_slices):
-//   x  <- x0 (default: I0 for AD, I1 for SP), held as a float pair (hi, lo)
+//   x  <- x0 (default: 0 for AD, I0 for SP), held as a float pair (hi, lo)
 //   r  <- b - A x                    (outer pass, float-pair differences)
 //   repeat: e <- V(nu1,nu2)-cycle on A e = r from e = 0   (FP32 hierarchy)
 //           x <- x + e (+ mean shift for AD);  r <- b - A x;  ||r|| read back
@@ -820,8 +820,16 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   if (rep) rep->levels = (int)P.L.size();
 
   // initial iterate in `out`
-  const float *start = x0 ? x0 : (system == GD_SYSTEM_AD ? I0 : I1);
-  if (start != out) {
+  // Default start.  AD: zero (relative residual 1; starting from I0 leaves
+  // the removed inter-slice variation, several times the right-hand side,
+  // and costs a cycle).  SP: I0, whose residual alpha (I1 - I0) is a few
+  // thousandths of the right-hand side on EM stacks (from I1 about half of
+  // it remains).
+  const float *start = x0 ? x0 : (system == GD_SYSTEM_SP ? I0 : nullptr);
+  if (!start) {
+    ProfScope ps(s, P_COPY, (double)n * 4.0);
+    CK(launch_fill(out, n, 0.f, s->stream));
+  } else if (start != out) {
     ProfScope ps(s, P_COPY, (double)n * 8.0);
     CK(launch_copy(out, start, n, s->stream));
   }
@@ -900,8 +908,8 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
       break;
     }
   }
-  if (mean_fix && cycles == 0 && x0 != nullptr) {
-    // no cycle ran on a caller's initial guess: still move its mean to mean(I0)
+  if (mean_fix && cycles == 0) {
+    // no cycle ran: still move the start's mean to mean(I0)
     CK(launch_fill(F.x, n, 0.f, s->stream));
     CK(cudaMemsetAsync(s->scalars + S_E, 0, sizeof(double), s->stream));
     if ((st = update(F.x)) != GD_OK) return report(rep, st);

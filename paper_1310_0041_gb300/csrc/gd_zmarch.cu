@@ -1,11 +1,14 @@
 // gd_zmarch.cu -- TMA-pipelined 2.5D z-march kernels for sm_103a.
 //
-// A CTA owns a 64 x 16 column tile of one level and marches along z over a
-// chunk of planes.  Planes of each input array arrive in a shared-memory ring
-// by TMA (cp.async.bulk.tensor.3d, one elected thread, mbarrier completion),
-// PF planes ahead of their first use, so HBM latency is hidden without extra
-// threads.  Boxes start at x = i0 - 4 (16-byte aligned coordinates) and are
-// 72 floats wide; the tensor map zero-fills outside the array.
+// A CTA owns a column tile of one level (64 x 32 cells for the sweep and the
+// restriction, 64 x 16 for the outer pass) and marches along z over a chunk
+// of planes.  Planes of each input array arrive in a shared-memory ring by
+// TMA (cp.async.bulk.tensor.3d issued by one lane of a service warp, mbarrier
+// completion) a few planes ahead of their first use.  Boxes start at
+// x = i0 - 4 (16-byte aligned coordinates) and are 72 floats wide; the tensor
+// map zero-fills outside the array.  Tile threads own float4 groups of cells:
+// x-neighbours come from the neighbouring lanes (shuffles), y-neighbours from
+// shared memory, z-neighbours from the thread's own registers.
 //
 // k_zsweep: one red-black Gauss-Seidel sweep (Sec. 4.1 multi-colour
 //   relaxation) with optional fusions:
@@ -15,17 +18,18 @@
 //               stencil of Sec. 4.2);
 //     SUM       the block sums of the written iterate (mean fix of AD).
 //   Pipeline per step t: red of plane t on the tile + 1 ring, black of plane
-//   t-1 on the tile, stored from registers.  The ring recomputes the
-//   neighbouring CTA's red values exactly as it does, so the result is the
-//   textbook red-black sweep.
+//   t-1 on the tile, stored from registers; one CTA barrier per plane.  The
+//   ring recomputes the neighbouring CTA's red values exactly as it does, so
+//   the result is the textbook red-black sweep.
 //
 // k_zrestrict: residual r = b - A x and its down-sampling (sum over the
 //   children of each coarse cell, Sec. 4.1 / 4.2) into the next level's
-//   right-hand side.
+//   right-hand side.  Producer/consumer ring, no CTA barrier per plane.
 //
 // k_zouter: fine-level outer pass of the iterative refinement: x_new = x + e
 //   (+ mean shift) as a float pair, r = b - A x_new in double-float arithmetic
 //   with b assembled from I0 (and I1), and FP64 block partial sums.
+//   Producer/consumer ring, no CTA barrier per plane.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -38,10 +42,7 @@
 namespace {
 
 constexpr int ZX = 64;            // tile x extent
-constexpr int ZY = 16;            // tile y extent
-constexpr int ZNT = 256;          // threads per CTA
 constexpr int BOXW = ZX + 8;      // box width: tile + 4 on each side (16-byte aligned start)
-constexpr int PF = 2;             // planes in flight ahead of use
 constexpr uint32_t WAIT_LIMIT = 1u << 21;  // bounded mbarrier polling (at most ~1 s)
 
 __host__ __device__ constexpr int pad32(int n) { return (n + 31) & ~31; }  // 128-byte slots
@@ -987,248 +988,278 @@ __device__ __forceinline__ ff ff_add(ff a, ff b) {
   return quick_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
 }
 struct OuterGeo {
-  static constexpr int BH = ZY + 2;              // rows: tile + 1 halo
-  static constexpr int S = pad32(BH * BOXW);
-  static constexpr int XR = 3 + PF;              // x_new planes t-1..t+1 + in flight
-  static constexpr int ER = 3 + PF;              // corrections: same planes and lag as x
-  static constexpr int IR = 1 + PF;              // inputs: plane t + in flight
-  __host__ __device__ static constexpr size_t smem_bytes() {
-    return sizeof(float) * (size_t)S * (2 * XR + ER + 2 * IR) +
-           sizeof(uint64_t) * (2 * XR + ER + 2 * IR) + sizeof(double) * 32 + 16;
+  static constexpr int OY = 16;                  // tile rows
+  static constexpr int BH = OY + 2;              // box rows j0-1 .. j0+OY
+  static constexpr int S = pad32(BH * BOXW);     // floats per box
+  static constexpr int SI1 = ZX * OY;            // I1 box: the tile only
+  static constexpr int XR = 4;                   // x planes t, t+1 + 2 in flight
+  static constexpr int IR = 3;                   // input plane t + 2 in flight
+  static constexpr int TILE_WARPS = 8;
+  static constexpr int NT = 32 * (TILE_WARPS + 1);
+  static constexpr int SVC = 32 * TILE_WARPS;
+  // an x slot holds the high part, the low part (if read) and the correction
+  // (if added) of one plane; an input slot holds I0 (or b) and I1 (SP)
+  __host__ __device__ static constexpr int xstride(bool xl, bool e) { return S * (1 + xl + e); }
+  __host__ __device__ static constexpr int istride(bool sp) { return S + (sp ? SI1 : 0); }
+  __host__ __device__ static constexpr size_t smem_bytes(bool xl, bool e, bool sp) {
+    return sizeof(float) * (size_t)(XR * xstride(xl, e) + IR * istride(sp)) +
+           sizeof(uint64_t) * 2 * (XR + IR) + sizeof(double) * 32 + 16;
   }
 };
 
+// Outer pass of the iterative refinement on the fine level: x_new = x + e
+// (+ mean shift) as a float pair, the residual r = b - A x_new with b
+// assembled from I0 (and I1), and block sums (r^2, b^2, x, I0).  A tile
+// thread owns one float4 of the 64 x 16 tile; the updated values of its
+// neighbours' cells are recomputed from the shared-memory planes (rows above
+// and below, the row ends) or taken from the neighbouring lanes (shuffles)
+// and from its own registers (z), so no thread writes shared memory and the
+// planes stream through a producer/consumer ring without CTA barriers.
 template <int RHS, bool HAS_XL, bool HAS_E, bool ACCURATE>
-__global__ void __launch_bounds__(ZNT, 2) k_zouter(const __grid_constant__ CUtensorMap tmh,
-                                                const __grid_constant__ CUtensorMap tml,
-                                                const __grid_constant__ CUtensorMap tme,
-                                                const __grid_constant__ CUtensorMap tmi0,
-                                                const __grid_constant__ CUtensorMap tmi1,
-                                                const OuterArgs a, int zchunk, double *err) {
+__global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constant__ CUtensorMap tmh,
+                                                            const __grid_constant__ CUtensorMap tml,
+                                                            const __grid_constant__ CUtensorMap tme,
+                                                            const __grid_constant__ CUtensorMap tmi0,
+                                                            const __grid_constant__ CUtensorMap tmi1,
+                                                            const OuterArgs a, int zchunk, double *err) {
   using G = OuterGeo;
   constexpr int S = G::S;
-  float *hs = zsm;                                // XR slots: x_new high parts
-  float *ls = hs + G::XR * S;                     // XR slots: x_new low parts
-  float *es = ls + G::XR * S;                     // ER slots: corrections
-  float *i0s = es + G::ER * S;                    // IR slots: I0 (or explicit b)
-  float *i1s = i0s + G::IR * S;                   // IR slots: I1
-  uint64_t *hb = reinterpret_cast<uint64_t *>(i1s + G::IR * S);
-  uint64_t *lb = hb + G::XR;
-  uint64_t *eb = lb + G::XR;
-  uint64_t *ib0 = eb + G::ER;
-  uint64_t *ib1 = ib0 + G::IR;
-  double *dsh = reinterpret_cast<double *>(ib1 + G::IR);
-  __shared__ int abort_flag;
-
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * ZY;
-  const int zs = blockIdx.z * zchunk, ze = min(zs + zchunk, nz);
-  const bool zc = (a.bz != 0.f) && (nz > 1);
-  const size_t plane = (size_t)nx * ny;
-  const int t0 = zc ? zs - 1 : zs, t1 = ze - 1;
-  Ring<G::XR> rx;
-  rx.lo = zc ? max(zs - 1, 0) : zs;
-  rx.hi = zc ? min(ze, nz - 1) : ze - 1;
-  Ring<G::ER> re;  // same planes as x
-  re.lo = rx.lo;
-  re.hi = rx.hi;
-  Ring<G::IR> ri;
-  ri.lo = zs;
-  ri.hi = ze - 1;
   constexpr bool SP = RHS == RHS_SP;
+  constexpr int XST = G::xstride(HAS_XL, HAS_E), IST = G::istride(SP);
+  constexpr int LOFF = S, EOFF = S * (1 + (HAS_XL ? 1 : 0));  // within an x slot
+  constexpr int IBASE = G::XR * XST;
   // the low word of the float pair is carried only in exact passes (and read
   // whenever the caller passes one)
   constexpr bool USE_L = HAS_XL || (HAS_E && ACCURATE);
+  uint64_t *xfull = reinterpret_cast<uint64_t *>(zsm + IBASE + G::IR * IST);
+  uint64_t *ifull = xfull + G::XR;
+  uint64_t *xempty = ifull + G::IR;
+  uint64_t *iempty = xempty + G::XR;
+  double *dsh = reinterpret_cast<double *>(iempty + G::IR);
+  __shared__ int abort_flag;
+
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * G::OY;
+  const int zs = blockIdx.z * zchunk, ze = min(zs + zchunk, nz);
+  const bool zc = (a.bz != 0.f) && (nz > 1);
+  const size_t plane = (size_t)nx * ny;
+  PcRing<G::XR> rx;
+  rx.lo = zc ? max(zs - 1, 0) : zs;
+  rx.hi = zc ? min(ze, nz - 1) : ze - 1;
+  PcRing<G::IR> ri;
+  ri.lo = zs;
+  ri.hi = ze - 1;
   constexpr uint32_t BOXB = (uint32_t)(G::BH * BOXW * sizeof(float));
 
-  if (tid == 0) {
+  if (tid == G::SVC) {
     abort_flag = 0;
-    int e = tma_preflight(zsm, G::smem_bytes(), &tmh);
-    if (!e && HAS_XL) e = tma_preflight(zsm, G::smem_bytes(), &tml);
-    if (!e && HAS_E) e = tma_preflight(zsm, G::smem_bytes(), &tme);
-    if (!e) e = tma_preflight(zsm, G::smem_bytes(), &tmi0);
-    if (!e && SP) e = tma_preflight(zsm, G::smem_bytes(), &tmi1);
+    const size_t bytes = G::smem_bytes(HAS_XL, HAS_E, SP);
+    int e = tma_preflight(zsm, bytes, &tmh);
+    if (!e && HAS_XL) e = tma_preflight(zsm, bytes, &tml);
+    if (!e && HAS_E) e = tma_preflight(zsm, bytes, &tme);
+    if (!e) e = tma_preflight(zsm, bytes, &tmi0);
+    if (!e && SP) e = tma_preflight(zsm, bytes, &tmi1);
     if (e) {
       abort_flag = e;
       err[0] = (double)e;
     } else {
-      for (int s = 0; s < G::XR; ++s) { mbar_init(&hb[s], 1); mbar_init(&lb[s], 1); }
-      for (int s = 0; s < G::ER; ++s) mbar_init(&eb[s], 1);
-      for (int s = 0; s < G::IR; ++s) { mbar_init(&ib0[s], 1); mbar_init(&ib1[s], 1); }
+      for (int q = 0; q < G::XR; ++q) {
+        mbar_init(&xfull[q], 1);
+        mbar_init(&xempty[q], G::TILE_WARPS);
+      }
+      for (int q = 0; q < G::IR; ++q) {
+        mbar_init(&ifull[q], 1);
+        mbar_init(&iempty[q], G::TILE_WARPS);
+      }
       fence_mbar_init();
     }
   }
   __syncthreads();
   if (abort_flag) return;  // nothing issued yet
 
-  int xissued = rx.lo - 1, iissued = ri.lo - 1;  // meaningful in thread 0
-  auto issue_x = [&](int p) {
-    if (!rx.has(p)) return;
-    xissued = p;
-    const int s = rx.slot(p);
-    mbar_expect_tx(&hb[s], BOXB);
-    tma_plane(hs + s * S, &tmh, i0 - 4, j0 - 1, p, &hb[s]);
-    if (HAS_XL) {
-      mbar_expect_tx(&lb[s], BOXB);
-      tma_plane(ls + s * S, &tml, i0 - 4, j0 - 1, p, &lb[s]);
-    }
-    if (HAS_E) {
-      const int se = re.slot(p);
-      mbar_expect_tx(&eb[se], BOXB);
-      tma_plane(es + se * S, &tme, i0 - 4, j0 - 1, p, &eb[se]);
-    }
-  };
-  auto issue_i = [&](int p) {
-    if (!ri.has(p)) return;
-    iissued = p;
-    const int s = ri.slot(p);
-    mbar_expect_tx(&ib0[s], BOXB);
-    tma_plane(i0s + s * S, &tmi0, i0 - 4, j0 - 1, p, &ib0[s]);
-    if (SP) {
-      mbar_expect_tx(&ib1[s], BOXB);
-      tma_plane(i1s + s * S, &tmi1, i0 - 4, j0 - 1, p, &ib1[s]);
-    }
-  };
-  const int xnext0 = zc ? t0 + 1 + PF : t0 + PF;
-  if (tid == 0) {
-    for (int p = rx.lo; p < xnext0 && p <= rx.hi; ++p) issue_x(p);
-    for (int p = ri.lo; p < t0 + PF && p <= ri.hi; ++p) issue_i(p);
-  }
-  float shift = 0.f;
-  if (HAS_E && a.mean_fix)
-    shift = (float)((a.scalars[S_I0] - a.scalars[S_X] - a.scalars[S_E]) * a.inv_n);
-  int xready = rx.lo - 1, iready = ri.lo - 1;
-  auto ready_x = [&](int upto) {
-    upto = min(upto, rx.hi);
-    for (int p = xready + 1; p <= upto; ++p) {
-      const int s = rx.slot(p);
-      const uint32_t ph = rx.parity(p);
-      bool ok = mbar_wait(&hb[s], ph);
-      if (HAS_XL) ok = mbar_wait(&lb[s], ph) && ok;
-      if (HAS_E) ok = mbar_wait(&eb[re.slot(p)], re.parity(p)) && ok;
-      if (!ok) {
-        abort_flag = 1;
-        return;
-      }
-      float *Hs = hs + s * S, *Ls = ls + s * S;
-      const float *Es = es + re.slot(p) * S;
-      if (HAS_E || (USE_L && !HAS_XL)) {
-        for (int q = tid; q < G::BH * BOXW; q += ZNT) {
-          const float h = Hs[q];
-          const float l = HAS_XL ? Ls[q] : 0.f;
-          if (HAS_E && ACCURATE) {
-            const ff v = ff_add({h, l}, {__fadd_rn(Es[q], shift), 0.f});
-            Hs[q] = v.h;
-            Ls[q] = v.l;
-          } else if (HAS_E) {
-            Hs[q] = __fadd_rn(h, __fadd_rn(Es[q], shift));
-            if (USE_L) Ls[q] = l;
-          } else {
-            Ls[q] = 0.f;
-          }
-        }
-      }
-      xready = p;
-    }
-  };
-  auto ready_i = [&](int upto) {
-    upto = min(upto, ri.hi);
-    for (int p = iready + 1; p <= upto; ++p) {
-      bool ok = mbar_wait(&ib0[ri.slot(p)], ri.parity(p));
-      if (SP) ok = mbar_wait(&ib1[ri.slot(p)], ri.parity(p)) && ok;
-      if (!ok) {
-        abort_flag = 1;
-        return;
-      }
-      iready = p;
-    }
-  };
   // per-thread sums in FP32 (r^2, b^2, I0) and double-float (x); FP64 only
   // once per block
   float srr = 0.f, sbb = 0.f, si = 0.f, sxh = 0.f, sxl = 0.f;
-  auto add_x = [&](float v) {
-    const ff t = two_sum(sxh, v);
-    sxh = t.h;
-    sxl += t.l;
-  };
 
-  auto residual_plane = [&](int p) {
-    const int s = rx.slot(p);
-    const float *Hc = hs + s * S, *Lc = ls + s * S;
-    const bool hm = zc && p > 0, hp = zc && p < nz - 1;
-    const float *Hm = hm ? hs + rx.slot(p - 1) * S : Hc, *Lm = hm ? ls + rx.slot(p - 1) * S : Lc;
-    const float *Hp = hp ? hs + rx.slot(p + 1) * S : Hc, *Lp = hp ? ls + rx.slot(p + 1) * S : Lc;
-    const float *I0 = i0s + ri.slot(p) * S, *I1 = i1s + ri.slot(p) * S;
-#pragma unroll 1
-    for (int q = tid; q < ZX * ZY; q += ZNT) {
-      const int r = q >> 6, c = q & 63;
-      const int gi = i0 + c, gj = j0 + r;
-      if (gi >= nx || gj >= ny) continue;
-      const int o = (r + 1) * BOXW + 4 + c;
-      const bool w = gi > 0, e = gi < nx - 1, so = gj > 0, no = gj < ny - 1;
-      const float hc = Hc[o], lc = USE_L ? Lc[o] : 0.f;
-      // right-hand side: I0 differences are exact (integer-valued inputs)
+  if (warp == G::TILE_WARPS) {
+    // ---- producer: planes in the order the tile warps need them ----
+    if (lane == 0) {
+      bool ok = true;
+      int px = rx.lo, pi = ri.lo;
+      int xdone = rx.lo - 1, idone = ri.lo - 1;
+      while (ok && (px <= rx.hi || pi <= ri.hi)) {
+        const bool take_x = px <= rx.hi && (pi > ri.hi || px <= pi + (zc ? 1 : 0));
+        if (take_x) {
+          const int q = rx.slot(px);
+          if (px - G::XR >= rx.lo) ok = mbar_wait(&xempty[q], rx.parity(px - G::XR));
+          if (ok) {
+            fence_proxy_async();
+            float *xb = zsm + q * XST;
+            mbar_expect_tx(&xfull[q], BOXB * (1 + (HAS_XL ? 1 : 0) + (HAS_E ? 1 : 0)));
+            tma_plane(xb, &tmh, i0 - 4, j0 - 1, px, &xfull[q]);
+            if (HAS_XL) tma_plane(xb + LOFF, &tml, i0 - 4, j0 - 1, px, &xfull[q]);
+            if (HAS_E) tma_plane(xb + EOFF, &tme, i0 - 4, j0 - 1, px, &xfull[q]);
+            xdone = px++;
+          }
+        } else {
+          const int q = ri.slot(pi);
+          if (pi - G::IR >= ri.lo) ok = mbar_wait(&iempty[q], ri.parity(pi - G::IR));
+          if (ok) {
+            fence_proxy_async();
+            float *ib = zsm + IBASE + q * IST;
+            mbar_expect_tx(&ifull[q], BOXB + (SP ? (uint32_t)(G::SI1 * sizeof(float)) : 0u));
+            tma_plane(ib, &tmi0, i0 - 4, j0 - 1, pi, &ifull[q]);
+            if (SP) tma_plane(ib + S, &tmi1, i0, j0, pi, &ifull[q]);
+            idone = pi++;
+          }
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        err[0] = 1.0;
+      }
+      // every issued copy lands before the CTA may exit (bounded waits)
+      for (int p = max(xdone - G::XR + 1, rx.lo); p <= xdone; ++p) mbar_wait(&xfull[rx.slot(p)], rx.parity(p));
+      for (int p = max(idone - G::IR + 1, ri.lo); p <= idone; ++p) mbar_wait(&ifull[ri.slot(p)], ri.parity(p));
+    }
+  } else {
+    // ---- tile warps ----
+    const unsigned FULL = 0xffffffffu;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int c4 = lane & 15, r = 2 * warp + (lane >> 4);
+    const int gi = i0 + 4 * c4, gj = j0 + r;
+    const bool act = gi < nx && gj < ny;
+    const int so = (r + 1) * BOXW + 4 + 4 * c4;  // box row 0 is j0 - 1
+    const int si1 = r * ZX + 4 * c4;
+    float shift = 0.f;
+    if (HAS_E && a.mean_fix)
+      shift = (float)((a.scalars[S_I0] - a.scalars[S_X] - a.scalars[S_E]) * a.inv_n);
+    bool failed = false;
+    int xw = rx.lo - 1, iw = ri.lo - 1;
+    auto need_x = [&](int p) {
+      for (int q = xw + 1; q <= min(p, rx.hi) && !failed; ++q) {
+        failed = !mbar_wait(&xfull[rx.slot(q)], rx.parity(q));
+        if (!failed) xw = q;
+      }
+      failed = __any_sync(FULL, failed);
+    };
+    auto need_i = [&](int p) {
+      for (int q = iw + 1; q <= min(p, ri.hi) && !failed; ++q) {
+        failed = !mbar_wait(&ifull[ri.slot(q)], ri.parity(q));
+        if (!failed) iw = q;
+      }
+      failed = __any_sync(FULL, failed);
+    };
+    auto release_x = [&](int p) {
+      __syncwarp();
+      if (lane == 0 && rx.has(p)) mbar_arrive(&xempty[rx.slot(p)]);
+    };
+    auto release_i = [&](int p) {
+      __syncwarp();
+      if (lane == 0 && ri.has(p)) mbar_arrive(&iempty[ri.slot(p)]);
+    };
+    // the updated iterate (a float pair) at one cell / four cells of a slot
+    auto upd1 = [&](const float *xb, int off, float &h, float &l) {
+      h = xb[off];
+      l = HAS_XL ? xb[LOFF + off] : 0.f;
+      if (HAS_E) {
+        const float e = __fadd_rn(xb[EOFF + off], shift);
+        if (ACCURATE) {
+          const ff v = ff_add({h, l}, {e, 0.f});
+          h = v.h;
+          l = v.l;
+        } else {
+          h = __fadd_rn(h, e);
+        }
+      }
+      if (!USE_L) l = 0.f;
+    };
+    auto upd4 = [&](const float *xb, int off, float4 &h, float4 &l) {
+      h = *reinterpret_cast<const float4 *>(xb + off);
+      l = HAS_XL ? *reinterpret_cast<const float4 *>(xb + LOFF + off) : zero4;
+      if (HAS_E) {
+        const float4 e = *reinterpret_cast<const float4 *>(xb + EOFF + off);
+        float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+        const float ev[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float ee = __fadd_rn(ev[c], shift);
+          if (ACCURATE) {
+            const ff v = ff_add({hv[c], lv[c]}, {ee, 0.f});
+            hv[c] = v.h;
+            lv[c] = v.l;
+          } else {
+            hv[c] = __fadd_rn(hv[c], ee);
+          }
+        }
+        h = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        l = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      }
+      if (!USE_L) l = zero4;
+    };
+    auto add_x = [&](float v) {
+      const ff t = two_sum(sxh, v);
+      sxh = t.h;
+      sxl += t.l;
+    };
+    // residual at one cell from its value (hc, lc), its neighbours' values
+    // and presence flags (missing neighbours contribute no difference), the
+    // I0 values around it (gradient right-hand side) and I1
+    auto cell = [&](float hc, float lc, bool w, float hw, float lw, bool e, float he, float le, bool s,
+                    float hs, float ls, bool n, float hn, float ln, bool m, float hm, float lm, bool p,
+                    float hp, float lp, float ic, float iw_, float ie, float is, float in_, float i1,
+                    float &bh_out) -> float {
       float gx = 0.f, gy = 0.f, bh, bl = 0.f;
       if (RHS == RHS_EXPLICIT) {
-        bh = I0[o];
+        bh = ic;
       } else {
-        const float ic = I0[o];
-        if (w) gx += ic - I0[o - 1];
-        if (e) gx += ic - I0[o + 1];
-        if (so) gy += ic - I0[o - BOXW];
-        if (no) gy += ic - I0[o + BOXW];
-        si += ic;
+        if (w) gx += ic - iw_;
+        if (e) gx += ic - ie;
+        if (s) gy += ic - is;
+        if (n) gy += ic - in_;
       }
-      float rv, rr_h, rr_l;
+      float rv;
       if (!ACCURATE) {
         // FP32 differences of the float pair: error ~1e-7 of the local terms
         float dx = 0.f, dy = 0.f, dz = 0.f;
-        if (USE_L) {
-          if (w) dx += (hc - Hc[o - 1]) + (lc - Lc[o - 1]);
-          if (e) dx += (hc - Hc[o + 1]) + (lc - Lc[o + 1]);
-          if (so) dy += (hc - Hc[o - BOXW]) + (lc - Lc[o - BOXW]);
-          if (no) dy += (hc - Hc[o + BOXW]) + (lc - Lc[o + BOXW]);
-          if (hm) dz += (hc - Hm[o]) + (lc - Lm[o]);
-          if (hp) dz += (hc - Hp[o]) + (lc - Lp[o]);
-        } else {
-          if (w) dx += hc - Hc[o - 1];
-          if (e) dx += hc - Hc[o + 1];
-          if (so) dy += hc - Hc[o - BOXW];
-          if (no) dy += hc - Hc[o + BOXW];
-          if (hm) dz += hc - Hm[o];
-          if (hp) dz += hc - Hp[o];
-        }
+        if (w) dx += (hc - hw) + (lc - lw);
+        if (e) dx += (hc - he) + (lc - le);
+        if (s) dy += (hc - hs) + (lc - ls);
+        if (n) dy += (hc - hn) + (lc - ln);
+        if (m) dz += (hc - hm) + (lc - lm);
+        if (p) dz += (hc - hp) + (lc - lp);
         const float ax = a.bx * dx + a.by * dy + a.bz * dz + a.alpha * (hc + lc);
         if (RHS != RHS_EXPLICIT) {
           bh = a.rbx * gx + a.rby * gy;
-          if (SP) bh += a.ralpha * I1[o];
+          if (SP) bh += a.ralpha * i1;
         }
         rv = bh - ax;
-        rr_h = rv;
-        rr_l = 0.f;
       } else {
         // compensated evaluation: every rounding error of the hi parts is
         // captured by an error-free transformation and summed into `lo`
         float lo = 0.f;
-        auto axis = [&](bool has1, float h1, float l1, bool has2, float h2, float l2, float wh,
-                        float wl, float &ph) {
+        auto axis = [&](bool has1, float h1, float l1, bool has2, float h2, float l2, float wh, float wl) {
           float t1 = 0.f, t2 = 0.f, la = 0.f;
-          if (has1) { const ff d = two_sum(hc, -h1); t1 = d.h; la += d.l + (lc - l1); }
-          if (has2) { const ff d = two_sum(hc, -h2); t2 = d.h; la += d.l + (lc - l2); }
+          if (has1) {
+            const ff d = two_sum(hc, -h1);
+            t1 = d.h;
+            la += d.l + (lc - l1);
+          }
+          if (has2) {
+            const ff d = two_sum(hc, -h2);
+            t2 = d.h;
+            la += d.l + (lc - l2);
+          }
           const ff S2 = two_sum(t1, t2);
           la += S2.l;
           const float pp = S2.h * wh;
           lo += __fmaf_rn(S2.h, wh, -pp) + S2.h * wl + la * wh;
-          ph = pp;
+          return pp;
         };
-        float px, py, pz = 0.f;
-        auto lo_at = [&](const float *Ls, int oo) { return USE_L ? Ls[oo] : 0.f; };
-        axis(w, w ? Hc[o - 1] : 0.f, w ? lo_at(Lc, o - 1) : 0.f, e, e ? Hc[o + 1] : 0.f,
-             e ? lo_at(Lc, o + 1) : 0.f, a.bx, a.bx_lo, px);
-        axis(so, so ? Hc[o - BOXW] : 0.f, so ? lo_at(Lc, o - BOXW) : 0.f, no,
-             no ? Hc[o + BOXW] : 0.f, no ? lo_at(Lc, o + BOXW) : 0.f, a.by, a.by_lo, py);
-        if (zc) axis(hm, Hm[o], lo_at(Lm, o), hp, Hp[o], lo_at(Lp, o), a.bz, a.bz_lo, pz);
+        const float px = axis(w, hw, lw, e, he, le, a.bx, a.bx_lo);
+        const float py = axis(s, hs, ls, n, hn, ln, a.by, a.by_lo);
+        const float pz = zc ? axis(m, hm, lm, p, hp, lp, a.bz, a.bz_lo) : 0.f;
         const float pa = hc * a.alpha;
         lo += __fmaf_rn(hc, a.alpha, -pa) + hc * a.alpha_lo + lc * a.alpha;
         ff A = two_sum(px, py);
@@ -1237,14 +1268,12 @@ __global__ void __launch_bounds__(ZNT, 2) k_zouter(const __grid_constant__ CUten
         lo += A.l;
         A = two_sum(A.h, pa);
         lo += A.l;
-        // b as a pair
         if (RHS != RHS_EXPLICIT) {
           const float qx = gx * a.rbx, qy = gy * a.rby;
           bl = __fmaf_rn(gx, a.rbx, -qx) + gx * a.rbx_lo + __fmaf_rn(gy, a.rby, -qy) + gy * a.rby_lo;
           ff Bv = two_sum(qx, qy);
           bl += Bv.l;
           if (SP) {
-            const float i1 = I1[o];
             const float qa = i1 * a.ralpha;
             bl += __fmaf_rn(i1, a.ralpha, -qa) + i1 * a.ralpha_lo;
             Bv = two_sum(Bv.h, qa);
@@ -1253,51 +1282,107 @@ __global__ void __launch_bounds__(ZNT, 2) k_zouter(const __grid_constant__ CUten
           bh = Bv.h;
         }
         const ff Rv = two_sum(bh, -A.h);
-        rr_h = Rv.h;
-        rr_l = Rv.l + (bl - lo);
-        rv = rr_h + rr_l;
+        rv = Rv.h + (Rv.l + (bl - lo));
       }
-      const size_t g = (size_t)p * plane + (size_t)gj * nx + gi;
-      if (a.xh_out) a.xh_out[g] = hc;
-      if (USE_L && a.xl_out) a.xl_out[g] = lc;
-      if (a.r_out) a.r_out[g] = rv;
-      srr += rv * rv;
-      sbb += bh * bh;
-      add_x(hc);
-      sxl += lc;
-      (void)rr_h;
-      (void)rr_l;
-    }
-  };
+      bh_out = bh;
+      return rv;
+    };
 
-  for (int t = t0; t <= t1; ++t) {
-    if (tid == 0) {
-      fence_proxy_async();
-      issue_x(zc ? t + 1 + PF : t + PF);
-      issue_i(t + PF);
-    }
-    ready_x(zc ? t + 1 : t);
-    ready_i(t);
-    __syncthreads();
-    if (abort_flag) break;
-    if (t >= zs) residual_plane(t);
-    __syncthreads();
-  }
-  if (abort_flag) {
-    if (tid == 0) {
+    // The plane loop, specialised for tiles whose cells all have their four
+    // in-plane neighbours inside the domain (presence flags constant).
+    const bool fast = i0 >= 1 && i0 + ZX + 1 <= nx && j0 >= 1 && j0 + G::OY + 1 <= ny;
+    auto march = [&](auto fast_c) {
+      constexpr bool F = decltype(fast_c)::value;
+      const bool w0 = F || gi > 0, e3 = F || gi + 3 < nx - 1, sn = F || gj > 0, nn = F || gj < ny - 1;
+      float4 hm4 = zero4, lm4 = zero4, hc4 = zero4, lc4 = zero4;  // planes t-1, t (own cells)
+      const int t0 = zs, t1 = ze - 1;
+      if (zc && t0 > 0) {
+        need_x(t0 - 1);
+        upd4(zsm + rx.slot(t0 - 1) * XST, so, hm4, lm4);
+        release_x(t0 - 1);
+      }
+      need_x(t0);
+      if (!failed) upd4(zsm + rx.slot(t0) * XST, so, hc4, lc4);
+      for (int t = t0; t <= t1 && !failed; ++t) {
+        const bool hm = zc && t > 0, hp = zc && t < nz - 1;
+        float4 hp4 = zero4, lp4 = zero4;
+        if (hp) {
+          need_x(t + 1);
+          if (failed) break;
+          upd4(zsm + rx.slot(t + 1) * XST, so, hp4, lp4);
+        }
+        need_i(t);
+        if (failed) break;
+        const float *xb = zsm + rx.slot(t) * XST;
+        const float *ib = zsm + IBASE + ri.slot(t) * IST;
+        float4 hu, lu, hd, ld;
+        upd4(xb, so - BOXW, hu, lu);
+        upd4(xb, so + BOXW, hd, ld);
+        // x-neighbours across the float4 edges: the neighbouring lane's cells,
+        // or the shared-memory planes at the tile's ends
+        float hw = __shfl_up_sync(FULL, hc4.w, 1, 16), lw = __shfl_up_sync(FULL, lc4.w, 1, 16);
+        float he = __shfl_down_sync(FULL, hc4.x, 1, 16), le = __shfl_down_sync(FULL, lc4.x, 1, 16);
+        if (c4 == 0) upd1(xb, so - 1, hw, lw);
+        if (c4 == 15) upd1(xb, so + 4, he, le);
+        const float4 ic = *reinterpret_cast<const float4 *>(ib + so);
+        float4 iu = zero4, id = zero4;
+        float iw_ = 0.f, ie_ = 0.f;
+        if (RHS != RHS_EXPLICIT) {
+          iu = *reinterpret_cast<const float4 *>(ib + so - BOXW);
+          id = *reinterpret_cast<const float4 *>(ib + so + BOXW);
+          iw_ = __shfl_up_sync(FULL, ic.w, 1, 16);
+          ie_ = __shfl_down_sync(FULL, ic.x, 1, 16);
+          if (c4 == 0) iw_ = ib[so - 1];
+          if (c4 == 15) ie_ = ib[so + 4];
+        }
+        const float4 i1 = SP ? *reinterpret_cast<const float4 *>(ib + S + si1) : zero4;
+        release_x(t);
+        release_i(t);
+        if (act) {
+          float rv[4], bh[4];
+          rv[0] = cell(hc4.x, lc4.x, w0, hw, lw, true, hc4.y, lc4.y, sn, hu.x, lu.x, nn, hd.x, ld.x, hm,
+                       hm4.x, lm4.x, hp, hp4.x, lp4.x, ic.x, iw_, ic.y, iu.x, id.x, i1.x, bh[0]);
+          rv[1] = cell(hc4.y, lc4.y, true, hc4.x, lc4.x, true, hc4.z, lc4.z, sn, hu.y, lu.y, nn, hd.y, ld.y,
+                       hm, hm4.y, lm4.y, hp, hp4.y, lp4.y, ic.y, ic.x, ic.z, iu.y, id.y, i1.y, bh[1]);
+          rv[2] = cell(hc4.z, lc4.z, true, hc4.y, lc4.y, true, hc4.w, lc4.w, sn, hu.z, lu.z, nn, hd.z, ld.z,
+                       hm, hm4.z, lm4.z, hp, hp4.z, lp4.z, ic.z, ic.y, ic.w, iu.z, id.z, i1.z, bh[2]);
+          rv[3] = cell(hc4.w, lc4.w, true, hc4.z, lc4.z, e3, he, le, sn, hu.w, lu.w, nn, hd.w, ld.w, hm,
+                       hm4.w, lm4.w, hp, hp4.w, lp4.w, ic.w, ic.z, ie_, iu.w, id.w, i1.w, bh[3]);
+          const size_t g = (size_t)t * plane + (size_t)gj * nx + gi;
+          if (a.xh_out) *reinterpret_cast<float4 *>(a.xh_out + g) = hc4;
+          if (USE_L && a.xl_out) *reinterpret_cast<float4 *>(a.xl_out + g) = lc4;
+          if (a.r_out) *reinterpret_cast<float4 *>(a.r_out + g) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+  #pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            srr += rv[c] * rv[c];
+            sbb += bh[c] * bh[c];
+          }
+          add_x((hc4.x + hc4.y) + (hc4.z + hc4.w));
+          sxl += (lc4.x + lc4.y) + (lc4.z + lc4.w);
+          if (RHS != RHS_EXPLICIT) si += (ic.x + ic.y) + (ic.z + ic.w);
+        }
+        hm4 = hc4;
+        lm4 = lc4;
+        hc4 = hp4;
+        lc4 = lp4;
+        if (!zc && t < t1) {
+          // uncoupled: the next plane's own cells are read in its own step
+          need_x(t + 1);
+          if (!failed) upd4(zsm + rx.slot(t + 1) * XST, so, hc4, lc4);
+        }
+      }
+    };
+    if (fast)
+      march(std::true_type());
+    else
+      march(std::false_type());
+    if (failed) {
+      abort_flag = 1;
       err[0] = 1.0;
-      for (int p = xready + 1; p <= xissued; ++p) {
-        mbar_wait(&hb[rx.slot(p)], rx.parity(p));
-        if (HAS_XL) mbar_wait(&lb[rx.slot(p)], rx.parity(p));
-        if (HAS_E) mbar_wait(&eb[re.slot(p)], re.parity(p));
-      }
-      for (int p = iready + 1; p <= iissued; ++p) {
-        mbar_wait(&ib0[ri.slot(p)], ri.parity(p));
-        if (SP) mbar_wait(&ib1[ri.slot(p)], ri.parity(p));
-      }
     }
-    return;
   }
+  __syncthreads();
+  if (abort_flag) return;
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   double v;
   v = block_sum((double)srr, dsh);
@@ -1420,14 +1505,14 @@ cudaError_t run_zrestrict(const CUtensorMap &mx, const CUtensorMap &mb, const ZS
 template <int RHS, bool XL, bool E, bool ACC>
 cudaError_t run_zouter(const CUtensorMap *m, const OuterArgs &a, int zchunk, double *err, dim3 grid,
                        cudaStream_t st) {
-  const size_t bytes = OuterGeo::smem_bytes();
+  const size_t bytes = OuterGeo::smem_bytes(XL, E, RHS == RHS_SP);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = set_smem(k_zouter<RHS, XL, E, ACC>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zouter<RHS, XL, E, ACC><<<grid, ZNT, bytes, st>>>(m[0], m[1], m[2], m[3], m[4], a, zchunk, err);
+  k_zouter<RHS, XL, E, ACC><<<grid, OuterGeo::NT, bytes, st>>>(m[0], m[1], m[2], m[3], m[4], a, zchunk, err);
   return cudaGetLastError();
 }
 
@@ -1479,7 +1564,7 @@ cudaError_t launch_zrestrict(ZSweepArgs a, const float *x, const float *b, cudaS
 cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nblocks_out,
                           cudaStream_t st) {
   if ((a.nx & 3) != 0) return cudaErrorNotSupported;
-  const int rows = ZY + 2;
+  const int rows = OuterGeo::BH;
   CUtensorMap m[5];
   std::memset(m, 0, sizeof m);
   const float *rhs0 = rhs_mode == RHS_EXPLICIT ? a.b : a.I0;
@@ -1487,9 +1572,11 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nb
   if (a.xl_in && !make_map(&m[1], a.xl_in, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
   if (a.e && !make_map(&m[2], a.e, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
   if (!make_map(&m[3], rhs0, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
-  if (rhs_mode == RHS_SP && !make_map(&m[4], a.I1, a.nx, a.ny, a.nz, BOXW, rows))
+  if (rhs_mode == RHS_SP && !make_map(&m[4], a.I1, a.nx, a.ny, a.nz, ZX, OuterGeo::OY))
     return cudaErrorNotSupported;
-  const int gx = (a.nx + ZX - 1) / ZX, gy = (a.ny + ZY - 1) / ZY;
+  if (((uintptr_t)a.xh_out & 15) || ((uintptr_t)a.xl_out & 15) || ((uintptr_t)a.r_out & 15))
+    return cudaErrorNotSupported;
+  const int gx = (a.nx + ZX - 1) / ZX, gy = (a.ny + OuterGeo::OY - 1) / OuterGeo::OY;
   const bool coupled = (a.bz != 0.f) && (a.nz > 1);
   const int zchunk = pick_zchunk(gx * gy, a.nz, coupled, 2);
   const int gz = (a.nz + zchunk - 1) / zchunk;
@@ -1514,6 +1601,6 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nb
 }
 
 int zouter_max_blocks(int nx, int ny, int nz) {
-  const int gx = (nx + ZX - 1) / ZX, gy = (ny + ZY - 1) / ZY;
+  const int gx = (nx + ZX - 1) / ZX, gy = (ny + OuterGeo::OY - 1) / OuterGeo::OY;
   return gx * gy * nz;
 }

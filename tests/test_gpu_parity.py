@@ -195,10 +195,15 @@ def test_ragged_sizes(torch, shape):
 def test_z_constant_stack_is_a_fixed_point(torch):
     sl = stack_u8(80, 48, 1, seed=12)
     I0 = np.repeat(sl, 9, axis=0)
-    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-6)
+    # started from I0: b - A I0 = -bz Kz I0 = 0, converged before any cycle
+    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-6, x0=dev(torch, I0))
     assert rep["status"] == gd.GD_OK
-    assert rep["cycles"] == 0  # b - A I0 = -bz Kz I0 = 0: converged at the start
+    assert rep["cycles"] == 0
     np.testing.assert_array_equal(got, I0)
+    # from the default zero start the cycles reach the same fixed point
+    got, rep = ad_gpu(torch, I0, 10.0, tol=1e-7)
+    assert rep["status"] == gd.GD_OK and rep["cycles"] > 0
+    np.testing.assert_allclose(got, I0, atol=1e-3)
 
 
 def test_slice_constant_stack(torch):
@@ -311,14 +316,15 @@ def test_tma_pipeline_matches_plain_kernels(torch, shape, monkeypatch):
     a2, r2, b2, s2 = out["plain"]
     # the TMA path's early outer passes keep only the high word of the iterate
     # (plain FP32 while the residual is above 1e-4); the plain kernels always
-    # keep both words, so below 1e-4 the histories agree only in rate
+    # keep both words, so below 1e-4 the histories differ by rounding and are
+    # compared by their rates: every cycle there still gains a factor 4
     for h1, h2 in ((r1["history"], r2["history"]), (s1["history"], s2["history"])):
         assert len(h1) == len(h2)
-        for u, v in zip(h1, h2):
+        for k, (u, v) in enumerate(zip(h1, h2)):
             if max(u, v) > 1e-4:
                 assert abs(u - v) <= 0.02 * max(u, v), (h1, h2)
             else:
-                assert max(u, v) <= 1.5 * min(u, v) + 1e-10, (h1, h2)
+                assert u <= 0.25 * h1[k - 1] and v <= 0.25 * h2[k - 1], (h1, h2)
     assert np.abs(a1 - a2).max() < 1e-3
     assert np.abs(b1 - b2).max() < 1e-3
 
