@@ -42,16 +42,19 @@ TOL_SP = 1e-7   # SP: alpha = 0.01 makes the slice-smooth error ~100x the residu
 SEED = 2
 WORKLOAD = "gd_ad_then_sp_1024x1024x128"
 
-# DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum per launch, divided by the voxels of that launch), valid
-# only while the kernel source is the one it was taken from.
+# DRAM traffic of the dominant kernel class from one ncu capture: the ratio of
+# dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic bytes over the
+# four fine-level sweeps of one AD V-cycle (zero start, plain, prolongation,
+# plain) of the 1024 x 512 x 64 case (bench.py --ncu-case); the traffic of a
+# full-size launch is that ratio times its algorithmic bytes.  Valid only while
+# the kernel source is the one it was taken from.
 NCU_TRAFFIC = {
-    # "rb_sweep_fine": {"bytes_per_voxel": ..., "src_sha256": "..."},
+    "rb_sweep_fine": {"dram_over_alg": 1430.3 / 1543.6, "src_sha256": "26e52adc929a9617b761165168624ec61cbb64b5aebd44e50d218d0716dede3e"},
 }
 
 
 def kernel_src_sha() -> str:
-    p = os.path.join(ROOT, "paper_1310_0041_gb300", "csrc", "gd_kernels.cu")
+    p = os.path.join(ROOT, "paper_1310_0041_gb300", "csrc", "gd_zmarch.cu")
     with open(p, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()
 
@@ -318,7 +321,7 @@ def run_gpu(args):
             tr = NCU_TRAFFIC.get(name)
             traffic = None
             if tr and tr.get("src_sha256") == kernel_src_sha():
-                traffic = tr["bytes_per_voxel"] * (by / nl) / tr["alg_bytes_per_voxel"]
+                traffic = tr["dram_over_alg"] * (by / nl)
             roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic, "launches": nl, "avg_launch_ms": ms / nl,
