@@ -288,6 +288,37 @@ def run_gpu(args):
     voxels = NX * NY * NZ
     value = world * voxels * args.steps / (ms_max * 1e-3)
 
+    # the mixed-precision mode (bfloat16 levels, float32 arithmetic, the same
+    # float-pair refinement and tolerances), timed the same way
+    sm = gd.gd_stack_create(NX, NY, NZ, prec=gd.GD_PREC_MIXED, stream=stream.cuda_stream)
+    mreps = []
+
+    def mstep():
+        r1 = gd.gd_diffuse_z(sm, I0, I1, w_ad, ctl)
+        r2 = gd.gd_screened_poisson_slices(sm, I0, I1, I2, ALPHA, ctl_sp)
+        mreps.append((r1, r2))
+
+    for _ in range(max(args.warmup, 1)):
+        mstep()
+    mreps.clear()
+    torch.cuda.synchronize()
+    barrier(world)
+    e0.record(stream)
+    for _ in range(args.steps):
+        mstep()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    mms = reduce_max(e0.elapsed_time(e1), world, dev)
+    gd.gd_destroy(sm)
+    m1, m2 = mreps[-1]
+    mixed = {"value": world * voxels * args.steps / (mms * 1e-3), "unit": UNIT,
+             "ms_per_step": mms / args.steps,
+             "storage": "bfloat16 multigrid levels (coarsest float32), float32 arithmetic, "
+                        "float-pair outer refinement",
+             "ad_cycles": m1["cycles"], "ad_rel_residual": m1["rel_residual"],
+             "sp_cycles": m2["cycles"], "sp_rel_residual": m2["rel_residual"]}
+
     # end to end through the C ABI with pinned host buffers: H2D of the input
     # (once per solve) and D2H of the result inside the timed region
     I0p = torch.from_numpy(I0h.astype(np.float32)).pin_memory()
@@ -346,6 +377,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * voxels * 4,
                     "d2h_bytes_per_step": voxels * 4},
             "gpu_launches": launches,
+            "mixed": mixed,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

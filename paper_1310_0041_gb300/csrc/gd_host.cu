@@ -42,8 +42,11 @@ const char *kProfNames[P_NUM] = {"rb_sweep_fine", "rb_sweep_coarse", "residual_r
 struct Level {
   LevelDev d;
   int fx = 0, fy = 0, fz = 0;  // axes coarsened from this level to the next
+  // the level's arrays: float32, or bfloat16 (esz = 2) in the mixed mode, where
+  // the buffers hold n halves
   float *x = nullptr, *b = nullptr, *t = nullptr;
   size_t n = 0;
+  int esz = 4;
 };
 
 struct ProfRec {
@@ -73,6 +76,8 @@ struct Plan {
   int batch_z = 0;
   double w[4] = {0, 0, 0, 0};  // alpha, bx, by, bz
   int cxy = 16;
+  int prec = GD_PREC_FP32;     // requested storage (the cache key)
+  bool half = false;           // levels above the coarsest hold bfloat16
   std::vector<Level> L;
   float *Vx = nullptr, *Vy = nullptr, *Vz = nullptr, *Dinv = nullptr;
   std::vector<std::unique_ptr<VGraph>> graphs;
@@ -317,14 +322,14 @@ void axis_eig(int n, int sfac, int last, std::vector<float> &V, std::vector<doub
 // When the strongest axis can no longer be halved the level is the coarsest.
 // Coarse stiffness w_d is halved per coarsening of axis d (6-point stencil
 // re-discretised at the coarse spacing); masses are the children counts.
-int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cxy);
+int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cxy, int prec);
 
 // Makes the plan for these weights current: from the cache, else built (the
 // least recently used plan is freed when the cache is full).
-int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
+int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy, int prec = GD_PREC_FP32) {
   s->cur = nullptr;
   for (auto &p : s->plans)
-    if (p->valid && p->batch_z == batch_z && p->cxy == cxy &&
+    if (p->valid && p->batch_z == batch_z && p->cxy == cxy && p->prec == prec &&
         std::memcmp(p->w, w, sizeof(p->w)) == 0) {
       p->last_use = ++s->use_clock;
       s->cur = p.get();
@@ -345,7 +350,7 @@ int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
   if (!s->f_b && (st = dalloc(s, &s->f_b, n)) != GD_OK) return st;
   if (!s->f_t && (st = dalloc(s, &s->f_t, n)) != GD_OK) return st;
   std::unique_ptr<Plan> P(new Plan);
-  if ((st = plan_build_into(s, *P, w, batch_z, cxy)) != GD_OK) {
+  if ((st = plan_build_into(s, *P, w, batch_z, cxy, prec)) != GD_OK) {
     plan_free(s, *P);
     return st;
   }
@@ -355,8 +360,9 @@ int plan_build(gd_stack *s, const double w[4], int batch_z, int cxy) {
   return GD_OK;
 }
 
-int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cxy) {
+int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cxy, int prec) {
   P.batch_z = batch_z;
+  P.prec = prec;
   P.cxy = cxy;
   std::memcpy(P.w, w, sizeof(P.w));
   Level l0;
@@ -395,10 +401,19 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
                    (float)wd[0], (float)wd[1], (float)wd[2], (float)w[0]};
     P.L.push_back(C);
   }
+  // Mixed precision (the paper's 16-bit storage of intermediate solutions
+  // and constraints, Sec. 4.1 "Disk I/O"): every level but the coarsest
+  // stores its correction, constraints and sweep array as bfloat16, when all
+  // of them meet TMA's row alignment (nx % 8); arithmetic stays float32 and
+  // the coarsest solve float32.
+  P.half = prec == GD_PREC_MIXED && !s->no_tma && P.L.size() > 1;
+  for (size_t li = 0; li + 1 < P.L.size() && P.half; ++li)
+    P.half = zmarch_usable(P.L[li].d, 2);
   // workspace
   for (size_t li = 0; li < P.L.size(); ++li) {
     Level &l = P.L[li];
     l.n = (size_t)l.d.nx * l.d.ny * l.d.nz;
+    l.esz = (P.half && li + 1 < P.L.size()) ? 2 : 4;
     if (li == 0) {
       l.x = s->f_x;
       l.b = s->f_b;
@@ -406,9 +421,10 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
       continue;
     }
     int st;
-    if ((st = dalloc(s, &l.x, l.n)) != GD_OK) return st;
-    if ((st = dalloc(s, &l.b, l.n)) != GD_OK) return st;
-    if ((st = dalloc(s, &l.t, l.n)) != GD_OK) return st;
+    const size_t nf = l.esz == 2 ? (l.n + 1) / 2 : l.n;  // floats holding the level's values
+    if ((st = dalloc(s, &l.x, nf)) != GD_OK) return st;
+    if ((st = dalloc(s, &l.b, nf)) != GD_OK) return st;
+    if ((st = dalloc(s, &l.t, nf)) != GD_OK) return st;
   }
   // coarsest-level fast diagonalisation data
   const LevelDev &c = P.L.back().d;
@@ -478,14 +494,19 @@ int sweep(gd_stack *s, int li, bool zero_in, bool prolong, bool restrict_, bool 
     a.fz = l.fz;
     a.bc = C->b;
   }
-  const bool tma = !s->no_tma && zmarch_usable(l.d);
+  const bool tma = !s->no_tma && zmarch_usable(l.d, l.esz);
+  const int esz_c = C ? C->esz : 4;
+  if (!tma && l.esz != 4) {
+    set_err(s, "a bfloat16 level needs the TMA kernels");
+    return GD_ERR_UNSUPPORTED;
+  }
   bool swept = false;
   if (tma) {
     cudaError_t e;
     {
       ProfScope ps(s, fine ? P_SWEEP_FINE : P_SWEEP_COARSE,
-                   (double)l.n * (zero_in ? 8.0 : 12.0) + (prolong ? 4.0 * (double)C->n : 0.0));
-      e = launch_zsweep(a, l.x, l.b, zero_in, prolong, sum_e, &nb, s->stream);
+                   (double)l.n * l.esz * (zero_in ? 2.0 : 3.0) + (prolong ? (double)esz_c * C->n : 0.0));
+      e = launch_zsweep(a, l.x, l.b, zero_in, prolong, sum_e, l.esz, esz_c, &nb, s->stream);
       if (e == cudaErrorNotSupported) {
         s->launches -= 1;
         ps.bytes = 0;
@@ -510,8 +531,8 @@ int sweep(gd_stack *s, int li, bool zero_in, bool prolong, bool restrict_, bool 
     // residual of the relaxed iterate (now in l.t) down-sampled into C->b
     cudaError_t e = cudaErrorNotSupported;
     if (tma) {
-      ProfScope ps(s, P_RESTRICT, (double)l.n * 8.0 + (double)C->n * 4.0);
-      e = launch_zrestrict(a, l.t, l.b, s->stream);
+      ProfScope ps(s, P_RESTRICT, (double)l.n * 2.0 * l.esz + (double)C->n * esz_c);
+      e = launch_zrestrict(a, l.t, l.b, l.esz, esz_c, s->stream);
       if (e == cudaErrorNotSupported) {
         s->launches -= 1;
         ps.bytes = 0;
@@ -650,7 +671,11 @@ int vcycle_run(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
   return GD_OK;
 }
 
-int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] */) {
+// One outer pass.  esz_e: element size of the correction read and the
+// residual written (the fine level's storage).  With h_out the reduced sums
+// are read back, and *rmax_out (if given) gets max |r|.
+int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] */, int esz_e = 4,
+               float *rmax_out = nullptr) {
   a.nx = s->nx;
   a.ny = s->ny;
   a.nz = s->nz;
@@ -663,15 +688,20 @@ int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] 
   if ((st = ensure_partials(s, sms * 8 + 64)) != GD_OK) return st;
   if ((st = ensure_partials(s, zouter_max_blocks(s->nx, s->ny, s->nz))) != GD_OK) return st;
   a.partials = s->partials;
-  double bytes = 4.0 * (1 + (a.xl_in ? 1 : 0) + (a.e ? 1 : 0) + (a.xh_out ? 1 : 0) +
-                        (a.xl_out ? 1 : 0) + (a.r_out ? 1 : 0) + (rhs_mode == RHS_SP ? 2 : 1)) *
+  if (a.e_scale == 0.f) a.e_scale = 1.f;
+  if (a.r_scale == 0.f) a.r_scale = 1.f;
+  a.rmax = reinterpret_cast<unsigned *>(s->scalars + S_RMAX);
+  CK(cudaMemsetAsync(s->scalars + S_RMAX, 0, sizeof(double), s->stream));
+  double bytes = (4.0 * (1 + (a.xl_in ? 1 : 0) + (a.xh_out ? 1 : 0) + (a.xl_out ? 1 : 0) +
+                         (rhs_mode == RHS_SP ? 2 : 1)) +
+                  (double)esz_e * ((a.e ? 1 : 0) + (a.r_out ? 1 : 0))) *
                  (double)n;
   int nb = 0;
   {
     ProfScope ps(s, P_OUTER, bytes);
     cudaError_t e = s->no_tma ? cudaErrorNotSupported
-                              : launch_zouter(a, rhs_mode, s->scalars + S_ERR, &nb, s->stream);
-    if (e == cudaErrorNotSupported) {
+                              : launch_zouter(a, rhs_mode, esz_e, s->scalars + S_ERR, &nb, s->stream);
+    if (e == cudaErrorNotSupported && esz_e == 4) {
       cudaGetLastError();
       e = launch_outer(a, rhs_mode, &nb, s->stream);
     }
@@ -690,6 +720,11 @@ int outer_pass(gd_stack *s, OuterArgs a, int rhs_mode, double *h_out /* [S_NUM] 
     CK(cudaStreamSynchronize(s->stream));
     if (!s->replayed.empty()) prof_collect_graphs(s);
     std::memcpy(h_out, s->h_scalars, S_NUM * sizeof(double));
+    if (rmax_out) {
+      unsigned u;
+      std::memcpy(&u, s->h_scalars + S_RMAX, sizeof u);
+      std::memcpy(rmax_out, &u, sizeof u);
+    }
     if (s->h_scalars[S_ERR] != 0.0) {
       const int code = (int)s->h_scalars[S_ERR];
       if (code == 1) {
@@ -812,7 +847,8 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   if ((st = resolve(s, outh, x0h == outh, 2, &out)) != GD_OK) return report(rep, st);
   if (x0h && x0h != outh && (st = resolve(s, x0h, true, 3, &x0)) != GD_OK) return report(rep, st);
   if (x0h == outh) x0 = out;
-  if ((st = plan_build(s, w, system == GD_SYSTEM_SP, ctl.coarsest_xy)) != GD_OK) return report(rep, st);
+  if ((st = plan_build(s, w, system == GD_SYSTEM_SP, ctl.coarsest_xy, s->prec)) != GD_OK)
+    return report(rep, st);
   Plan &P = *s->cur;
   if (!s->xh2 && (st = dalloc(s, &s->xh2, n)) != GD_OK) return report(rep, st);
   if (!s->xl1 && (st = dalloc(s, &s->xl1, n)) != GD_OK) return report(rep, st);
@@ -844,12 +880,21 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   const int rhs = system == GD_SYSTEM_SP ? RHS_SP : RHS_AD;
   const int mean_fix = system == GD_SYSTEM_AD;
   Level &F = P.L[0];
+  const int esz = F.esz;  // storage of the correction solve (4, or 2 when mixed)
+
+  double h[S_NUM];
+  // bfloat16 storage keeps float32's exponent range: no scaling is needed
+  // (the scale hooks of the outer pass stay at 1)
+  auto run_pass = [&](OuterArgs &pa) -> int {
+    pa.e_scale = 1.f;
+    pa.r_scale = 1.f;
+    return outer_pass(s, pa, rhs, h, esz);
+  };
 
   // initial residual
-  double h[S_NUM];
   a.xh_in = out;
   a.r_out = F.b;
-  if ((st = outer_pass(s, a, rhs, h)) != GD_OK) return report(rep, st);
+  if ((st = run_pass(a)) != GD_OK) return report(rep, st);
   const double bnorm = std::sqrt(h[S_BB]);
   const double denom = bnorm > 0.0 ? bnorm : 1.0;
   double rel = std::sqrt(h[S_RR]) / denom;
@@ -882,7 +927,7 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
     a.xh_out = H[1 - c];
     a.xl_out = exact ? Lo[1 - c] : nullptr;
     a.r_out = F.b;
-    int r = outer_pass(s, a, rhs, h);
+    int r = run_pass(a);
     c = 1 - c;
     if (exact) lo_zero = false;
     return r;
@@ -910,7 +955,7 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   }
   if (mean_fix && cycles == 0) {
     // no cycle ran: still move the start's mean to mean(I0)
-    CK(launch_fill(F.x, n, 0.f, s->stream));
+    CK(cudaMemsetAsync(F.x, 0, n * esz, s->stream));
     CK(cudaMemsetAsync(s->scalars + S_E, 0, sizeof(double), s->stream));
     if ((st = update(F.x)) != GD_OK) return report(rep, st);
     rel = std::sqrt(h[S_RR]) / denom;
@@ -981,7 +1026,7 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
   if ((double)nx * ny * nz > 9.0e18 / 64) return GD_ERR_INVALID_ARG;
   if (bc != GD_BC_NEUMANN) return GD_ERR_UNSUPPORTED;
   if (disc != GD_DISC_CONSTANT) return disc == GD_DISC_HYBRID || disc == GD_DISC_LINEAR ? GD_ERR_UNSUPPORTED : GD_ERR_INVALID_ARG;
-  if (prec != GD_PREC_FP32) return prec == GD_PREC_MIXED ? GD_ERR_UNSUPPORTED : GD_ERR_INVALID_ARG;
+  if (prec != GD_PREC_FP32 && prec != GD_PREC_MIXED) return GD_ERR_INVALID_ARG;
   gd_stack *s = new (std::nothrow) gd_stack();
   if (!s) return GD_ERR_OOM;
   s->nx = nx;

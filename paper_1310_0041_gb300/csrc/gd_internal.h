@@ -29,7 +29,10 @@ enum {
   S_E = 4,    // sum of the correction e
   S_NUM = 5
 };
-// scalars[S_ERR] is set to 1 by a kernel whose bounded wait gave up
+// scalars[S_RMAX] holds max |r| of the last outer pass (float bits in its
+// first word); scalars[S_ERR] is set to 1 by a kernel whose bounded wait gave
+// up
+constexpr int S_RMAX = 6;
 constexpr int S_ERR = 7;
 
 enum RhsMode { RHS_EXPLICIT = 0, RHS_AD = 1, RHS_SP = 2 };
@@ -47,9 +50,11 @@ struct OuterArgs {
   const float *I0, *I1;         // inputs (RHS_AD / RHS_SP)
   const float *xh_in;           // iterate, high part
   const float *xl_in;           // iterate, low part (nullable: zero)
-  const float *e;               // correction to add (nullable: none)
+  const void *e;                // correction to add (nullable: none); stored / e_scale
   float *xh_out, *xl_out;       // new iterate (nullable: not written)
-  float *r_out;                 // residual (nullable: not written)
+  void *r_out;                  // residual (nullable: not written); stored * r_scale
+  float e_scale, r_scale;       // 1 for float32 storage; powers of two for float16
+  unsigned *rmax;               // nullable: atomic max of |r| (float bits)
   const double *scalars;        // reduced sums of the previous passes (mean fix)
   int mean_fix;                 // AD: shift the update so that sum x = sum I0
   int accurate;                 // residual by error-free transformations (else plain FP32)
@@ -60,11 +65,11 @@ struct OuterArgs {
 // Arguments of the TMA z-march sweep (gd_zmarch.cu).
 struct ZSweepArgs {
   LevelDev L;
-  float *xout;          // relaxed iterate (a different array from the input)
-  const float *xc;      // prolongation: coarse correction (next level's x)
+  void *xout;           // relaxed iterate (a different array from the input)
+  const void *xc;       // prolongation: coarse correction (next level's x)
   int ncx, ncy;         // next level's x, y sizes (prolongation / restriction)
   int fx, fy, fz;       // axes coarsened from this level to the next
-  float *bc;            // restriction: next level's right-hand side
+  void *bc;             // restriction: next level's right-hand side
   int zchunk;           // set by the launcher
   double *partials;     // SUM: per-block sums of the output, slot S_E
   double *err;          // set to 1 when a bounded wait gives up
@@ -73,12 +78,16 @@ struct ZSweepArgs {
 // TMA z-march launchers (gd_zmarch.cu); cudaErrorNotSupported when the arrays
 // do not meet TMA's alignment rules (nx % 4, 16-byte base) -- the caller then
 // uses the plain kernels.
-bool zmarch_usable(const LevelDev &L);
-cudaError_t launch_zsweep(ZSweepArgs a, const float *xin, const float *b, bool zero_in, bool prolong,
-                          bool sum, int *nblocks_out, cudaStream_t st);
+// esz: bytes per element of a level's arrays (4: float32, 2: float16); esz_c
+// the same for the next coarser level
+bool zmarch_usable(const LevelDev &L, int esz);
+cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zero_in, bool prolong,
+                          bool sum, int esz, int esz_c, int *nblocks_out, cudaStream_t st);
 // residual of (x, b) on level a.L summed into the next level's b (a.bc)
-cudaError_t launch_zrestrict(ZSweepArgs a, const float *x, const float *b, cudaStream_t st);
-cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nblocks_out,
+cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz, int esz_c,
+                             cudaStream_t st);
+// esz_e: element size of the correction e read and the residual r written
+cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, int esz_e, double *err, int *nblocks_out,
                           cudaStream_t st);
 int zouter_max_blocks(int nx, int ny, int nz);
 

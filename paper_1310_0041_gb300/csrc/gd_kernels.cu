@@ -306,7 +306,10 @@ __global__ void __launch_bounds__(NT) k_outer(OuterArgs a) {
   const size_t total = pl * nz;
   float shift = 0.f;
   if (HAS_E && a.mean_fix)
-    shift = (float)((a.scalars[S_I0] - a.scalars[S_X] - a.scalars[S_E]) * a.inv_n);
+    shift = (float)((a.scalars[S_I0] - a.scalars[S_X] - a.scalars[S_E] * (double)a.e_scale) * a.inv_n);
+  // float32 storage only (the plain kernels serve float32 hierarchies)
+  const float *ev = static_cast<const float *>(a.e);
+  float *rout = static_cast<float *>(a.r_out);
   const ff Wx = {a.bx, a.bx_lo}, Wy = {a.by, a.by_lo}, Wz = {a.bz, a.bz_lo};
   const ff Wa = {a.alpha, a.alpha_lo};
   const ff Rx = {a.rbx, a.rbx_lo}, Ry = {a.rby, a.rby_lo}, Ra = {a.ralpha, a.ralpha_lo};
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(NT) k_outer(OuterArgs a) {
   auto xnew = [&](size_t q) -> ff {
     const float xh = __ldg(a.xh_in + q);
     const float xl = HAS_XL ? __ldg(a.xl_in + q) : 0.f;
-    if (HAS_E) return ff_add({xh, xl}, {__fadd_rn(__ldg(a.e + q), shift), 0.f});
+    if (HAS_E) return ff_add({xh, xl}, {__fadd_rn(__ldg(ev + q) * a.e_scale, shift), 0.f});
     return {xh, xl};
   };
   for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < total;
@@ -355,7 +358,7 @@ __global__ void __launch_bounds__(NT) k_outer(OuterArgs a) {
     const float r = __fadd_rn(rr.h, rr.l);
     if (a.xh_out) a.xh_out[p] = xc.h;
     if (a.xl_out) a.xl_out[p] = xc.l;
-    if (a.r_out) a.r_out[p] = r;
+    if (rout) rout[p] = r * a.r_scale;
     const double rd = (double)rr.h + (double)rr.l;
     const double bd = (double)bv.h + (double)bv.l;
     srr += rd * rd;

@@ -32,6 +32,7 @@
 //   Producer/consumer ring, no CTA barrier per plane.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 
 #include <cstdint>
 #include <cstring>
@@ -75,7 +76,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   }
   return false;
 }
-__device__ __forceinline__ void tma_plane(float *dst, const CUtensorMap *map, int x, int y, int z,
+__device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map, int x, int y, int z,
                                           uint64_t *bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -138,15 +139,73 @@ struct Ring {
 // ===========================================================================
 // red-black sweep
 // ===========================================================================
-// Dynamic shared memory of the z-march kernels, addressed with 32-bit float
-// offsets (slots are multiples of 32 floats, i.e. 128 bytes).
+// Dynamic shared memory of the z-march kernels, addressed with 32-bit element
+// offsets (slots are multiples of 128 bytes).
 extern __shared__ __align__(128) float zsm[];
+
+// ---- storage types ----
+// The hierarchy's arrays are float32, or float16 in the mixed-precision mode
+// (arithmetic is float32 either way).  A TMA box must start on a 16-byte
+// boundary: boxes start 4 floats / 8 halves left of the tile and are 72 / 80
+// elements wide.  Four consecutive cells are one float4 / one 8-byte pair of
+// half2.
+template <typename T>
+struct St;
+template <>
+struct St<float> {
+  static constexpr int W = 72, OFF = 4;
+  __device__ static __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+  __device__ static __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+  __device__ static __forceinline__ float ld1(const float *p) { return *p; }
+  __device__ static __forceinline__ void st1(float *p, float v) { *p = v; }
+  __device__ static __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+  __device__ static __forceinline__ float2 ldg2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+  __device__ static __forceinline__ void stg2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <>
+struct St<__nv_bfloat16> {
+  static constexpr int W = 80, OFF = 8;
+  __device__ static __forceinline__ float4 cvt(uint2 u) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+  }
+  __device__ static __forceinline__ uint2 pack(float4 v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const unsigned *>(&a), *reinterpret_cast<const unsigned *>(&b));
+  }
+  __device__ static __forceinline__ float4 ld4(const __nv_bfloat16 *p) { return cvt(*reinterpret_cast<const uint2 *>(p)); }
+  __device__ static __forceinline__ void st4(__nv_bfloat16 *p, float4 v) { *reinterpret_cast<uint2 *>(p) = pack(v); }
+  __device__ static __forceinline__ float ld1(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+  __device__ static __forceinline__ void st1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+  __device__ static __forceinline__ float4 ldg4(const __nv_bfloat16 *p) {
+    return cvt(__ldg(reinterpret_cast<const uint2 *>(p)));
+  }
+  __device__ static __forceinline__ float2 ldg2(const __nv_bfloat16 *p) {
+    const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+  }
+  __device__ static __forceinline__ void stg2(__nv_bfloat16 *p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+  }
+};
+// the 16-bit storage type of the mixed mode
+using half_t = __nv_bfloat16;
+// slot sizes are multiples of 128 bytes
+template <typename T>
+__host__ __device__ constexpr int pad128(int n) {
+  return (n + (int)(128 / sizeof(T)) - 1) / (int)(128 / sizeof(T)) * (int)(128 / sizeof(T));
+}
+
+
 
 // Sweep tiles are 64 x 32: eight tile warps (two float4 cells per thread)
 // and one service warp (TMA issue, mbarrier polling, the red ring).
 constexpr int SY = 32;  // sweep tile rows
 
+template <typename T>
 struct SweepGeo {
+  static constexpr int W = St<T>::W, OFF = St<T>::OFF;
   static constexpr int H = 2;                    // x box halo rows
   static constexpr int XH = SY + 2 * H;          // x box rows j0-2 .. j0+SY+1
   static constexpr int BH = SY + 2 * (H - 1);    // b box rows j0-1 .. j0+SY
@@ -157,10 +216,10 @@ struct SweepGeo {
   static constexpr int XR = 6;                   // needs PFS + 4
   static constexpr int BR = 4;                   // needs PFS + 2 (power of two)
   static_assert(XR >= PFS + 4 && BR >= PFS + 2, "ring depth");
-  static constexpr int XS = pad32(XH * BOXW);    // floats per x slot
-  static constexpr int BS = pad32(BH * BOXW);
+  static constexpr int XS = pad128<T>(XH * W);   // elements per x slot
+  static constexpr int BS = pad128<T>(BH * W);
   static constexpr int BOFF = XR * XS;           // b slots
-  static constexpr int MOFF = BOFF + BR * BS;    // mbarriers
+  static constexpr int MOFF = BOFF + BR * BS;    // mbarriers (element offset)
   static constexpr int TILE_WARPS = 8;
   static constexpr int NT = 32 * (TILE_WARPS + 1);  // + the service warp
   static constexpr int SVC = 32 * TILE_WARPS;       // first thread of the service warp
@@ -170,12 +229,9 @@ struct SweepGeo {
   static constexpr int RING_IT = NRING / 32;
   static_assert(NRING % 32 == 0, "ring cells per lane");
   __host__ __device__ static constexpr size_t smem_bytes() {
-    return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + sizeof(double) * 32 + 16;
+    return sizeof(T) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + sizeof(double) * 32 + 16;
   }
 };
-
-__device__ __forceinline__ float4 lds4(int off) { return *reinterpret_cast<const float4 *>(zsm + off); }
-__device__ __forceinline__ void sts4(int off, float4 v) { *reinterpret_cast<float4 *>(zsm + off) = v; }
 
 // Thread layout of the tile: a tile thread owns two float4 cells, rows r and
 // r + 16 of one column of four, where warp w's half-warps take rows
@@ -184,16 +240,21 @@ __device__ __forceinline__ void sts4(int off, float4 v) { *reinterpret_cast<floa
 // are the same thread's (its previous plane in registers, older planes and b
 // from the shared-memory rings), so one CTA barrier per plane orders all the
 // in-plane exchanges.
-template <bool ZERO_IN, bool PROLONG, bool SUM, bool UNIFORM, bool COUPLED>
-__global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
-                                                            const __grid_constant__ CUtensorMap tmb,
-                                                            const ZSweepArgs a) {
-  using G = SweepGeo;
+template <typename T, typename TC, bool ZERO_IN, bool PROLONG, bool SUM, bool UNIFORM, bool COUPLED>
+__global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
+                                                               const __grid_constant__ CUtensorMap tmb,
+                                                               const ZSweepArgs a) {
+  using G = SweepGeo<T>;
+  using S = St<T>;
   constexpr int H = G::H;
   constexpr int PFS = G::PFS;
   constexpr int XS = G::XS;
+  constexpr int W = G::W, OFF = G::OFF;
   constexpr bool zc = COUPLED;  // the launcher passes wz != 0 && nz > 1
-  uint64_t *xbar = reinterpret_cast<uint64_t *>(zsm + G::MOFF);
+  T *sm = reinterpret_cast<T *>(zsm);
+  auto lds4 = [&](int off) { return S::ld4(sm + off); };
+  auto sts4 = [&](int off, float4 v) { S::st4(sm + off, v); };
+  uint64_t *xbar = reinterpret_cast<uint64_t *>(sm + G::MOFF);
   uint64_t *bbar = xbar + G::XR;
   double *dsh = reinterpret_cast<double *>(bbar + G::BR);
   __shared__ int abort_flag;
@@ -243,15 +304,15 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
   auto issue_x = [&](int p) {
     if (ZERO_IN || !rx.has(p)) return;
     const int q = rx.slot(p);
-    mbar_expect_tx(&xbar[q], (uint32_t)(G::XH * BOXW * sizeof(float)));
-    tma_plane(zsm + q * XS, &tmx, i0 - 4, j0 - H, p, &xbar[q]);
+    mbar_expect_tx(&xbar[q], (uint32_t)(G::XH * W * sizeof(T)));
+    tma_plane(sm + q * XS, &tmx, i0 - OFF, j0 - H, p, &xbar[q]);
     xissued = p;
   };
   auto issue_b = [&](int p) {
     if (!rb.has(p)) return;
     const int q = rb.slot(p);
-    mbar_expect_tx(&bbar[q], (uint32_t)(G::BH * BOXW * sizeof(float)));
-    tma_plane(zsm + G::BOFF + q * G::BS, &tmb, i0 - 4, j0 - (H - 1), p, &bbar[q]);
+    mbar_expect_tx(&bbar[q], (uint32_t)(G::BH * W * sizeof(T)));
+    tma_plane(sm + G::BOFF + q * G::BS, &tmb, i0 - OFF, j0 - (H - 1), p, &bbar[q]);
     bissued = p;
   };
   // x plane issued at step t, and the last x plane a step reads or corrects
@@ -335,7 +396,7 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
   const int gi = i0 + 4 * c4, gj0 = j0 + r0, gj1 = gj0 + 16;
   const bool act0 = !svc && gi < nx && gj0 < ny;  // nx % 4 == 0: all four cells or none
   const bool act1 = !svc && gi < nx && gj1 < ny;
-  const int so0 = (r0 + H) * BOXW + 4 + 4 * c4, so1 = so0 + 16 * BOXW;
+  const int so0 = (r0 + H) * W + OFF + 4 * c4, so1 = so0 + 16 * W;
   const int go0 = gj0 * nx + gi, go1 = go0 + 16 * nx;  // in-plane offsets
 
   // ---- service warp: red ring cell m of this lane for colour class P ----
@@ -360,34 +421,34 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
     }
     ci = i0 + col;
     cj = j0 + row;
-    off = (ci >= 0 && ci < nx && cj >= 0 && cj < ny) ? (row + H) * BOXW + 4 + col : -1;
+    off = (ci >= 0 && ci < nx && cj >= 0 && cj < ny) ? (row + H) * W + OFF + col : -1;
   };
 
   // ---- prolongation by replication: every float4 of the x box inside the
   // domain gets the coarse value of each of its cells (with x coarsened the
   // four cells take two coarse values; nx % 4 == 0 keeps both loads aligned)
-  constexpr int PQ = G::XH * (BOXW / 4);
+  constexpr int PQ = G::XH * (W / 4);
   constexpr int PMAX = PROLONG ? (PQ + G::NT - 1) / G::NT : 1;
   int corrected = rx.lo - 1;  // planes that hold the coarse correction
   auto correct_upto = [&](int u) {
     for (int p = corrected + 1; p <= min(u, rx.hi); ++p) {
       const int xop = xo(p);
-      const float *xcp = a.xc + (size_t)(p >> a.fz) * a.ncy * a.ncx;
+      const TC *xcp = reinterpret_cast<const TC *>(a.xc) + (size_t)(p >> a.fz) * a.ncy * a.ncx;
 #pragma unroll
       for (int m = 0; m < PMAX; ++m) {
         const int q = tid + m * G::NT;
-        const int rr = q / (BOXW / 4), cq = q - rr * (BOXW / 4);
-        const int gci = i0 - 4 + 4 * cq, gcj = j0 - H + rr;
+        const int rr = q / (W / 4), cq = q - rr * (W / 4);
+        const int gci = i0 - OFF + 4 * cq, gcj = j0 - H + rr;
         if (q < PQ && gci >= 0 && gci < nx && gcj >= 0 && gcj < ny) {
           const int pc = (gcj >> a.fy) * a.ncx + (gci >> a.fx);
           float4 c;
           if (a.fx) {
-            const float2 c2 = __ldg(reinterpret_cast<const float2 *>(xcp + pc));
+            const float2 c2 = St<TC>::ldg2(xcp + pc);
             c = make_float4(c2.x, c2.x, c2.y, c2.y);
           } else {
-            c = __ldg(reinterpret_cast<const float4 *>(xcp + pc));
+            c = St<TC>::ldg4(xcp + pc);
           }
-          const int so = xop + rr * BOXW + 4 * cq;
+          const int so = xop + rr * W + 4 * cq;
           float4 v = lds4(so);
           v.x += c.x;
           v.y += c.y;
@@ -473,7 +534,7 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
       float4 cc0 = cp0, cc1 = cp1, bv0 = zero4, bv1 = zero4;
       if (do_red) {
         const PlaneK k = plane_k(t);
-        const int bs = bo(t) - BOXW;  // b rows start one row below x rows
+        const int bs = bo(t) - W;  // b rows start one row below x rows
         if (!svc) {
           bv0 = lds4(bs + so0);
           bv1 = lds4(bs + so1);
@@ -481,11 +542,11 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
           float4 xc1 = zero4, xu1 = zero4, xd1 = zero4, xp1 = zero4, xm1 = zero4;
           if (!ZERO_IN) {
             xc0 = lds4(xs_t + so0);
-            xu0 = lds4(xs_t + so0 - BOXW);
-            xd0 = lds4(xs_t + so0 + BOXW);
+            xu0 = lds4(xs_t + so0 - W);
+            xd0 = lds4(xs_t + so0 + W);
             xc1 = lds4(xs_t + so1);
-            xu1 = lds4(xs_t + so1 - BOXW);
-            xd1 = lds4(xs_t + so1 + BOXW);
+            xu1 = lds4(xs_t + so1 - W);
+            xd1 = lds4(xs_t + so1 + W);
             if (zc) {
               if (k.zpf != 0.f) {
                 xp0 = lds4(xs_p + so0);
@@ -508,8 +569,8 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
               e0 = __shfl_up_sync(FULL, xc0.w, 1, 16);
               e1 = __shfl_up_sync(FULL, xc1.w, 1, 16);
               if (c4 == 0) {
-                e0 = zsm[xs_t + so0 - 1];
-                e1 = zsm[xs_t + so1 - 1];
+                e0 = S::ld1(sm + xs_t + so0 - 1);
+                e1 = S::ld1(sm + xs_t + so1 - 1);
               }
             }
             red2(std::true_type(), k, xc0, xu0, xd0, xm0, xp0, bv0, e0, gj0, cc0);
@@ -520,8 +581,8 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
               e0 = __shfl_down_sync(FULL, xc0.x, 1, 16);
               e1 = __shfl_down_sync(FULL, xc1.x, 1, 16);
               if (c4 == 15) {
-                e0 = zsm[xs_t + so0 + 4];
-                e1 = zsm[xs_t + so1 + 4];
+                e0 = S::ld1(sm + xs_t + so0 + 4);
+                e1 = S::ld1(sm + xs_t + so1 + 4);
               }
             }
             red2(std::false_type(), k, xc0, xu0, xd0, xm0, xp0, bv0, e0, gj0, cc0);
@@ -538,17 +599,18 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
             int off, ci, cj;
             ring_cell(m, t & 1, off, ci, cj);
             if (off >= 0) {
-              const float bq = zsm[bs + off];
+              const float bq = S::ld1(sm + bs + off);
               float v;
               if (ZERO_IN) {
                 v = gs(fast_c, red0, k, bq, 0.f, 0.f, 0.f, 0.f, ci, cj);
               } else {
-                const float *xq = zsm + xs_t + off;
-                const float zm = (zc && k.zmf != 0.f) ? zsm[xs_m + off] : 0.f;
-                const float zp = (zc && k.zpf != 0.f) ? zsm[xs_p + off] : 0.f;
-                v = gs(fast_c, red0, k, bq, xq[-1] + xq[1], xq[-BOXW] + xq[BOXW], zm, zp, ci, cj);
+                const T *xq = sm + xs_t + off;
+                const float zm = (zc && k.zmf != 0.f) ? S::ld1(sm + xs_m + off) : 0.f;
+                const float zp = (zc && k.zpf != 0.f) ? S::ld1(sm + xs_p + off) : 0.f;
+                v = gs(fast_c, red0, k, bq, S::ld1(xq - 1) + S::ld1(xq + 1),
+                       S::ld1(xq - W) + S::ld1(xq + W), zm, zp, ci, cj);
               }
-              zsm[xs_t + off] = v;
+              S::st1(sm + xs_t + off, v);
             }
           }
         }
@@ -569,10 +631,10 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
           const PlaneK k = plane_k(pb);
           const int xob = zc ? xs_m : xs_t;
           const float4 yc0 = zc ? cp0 : cc0, yc1 = zc ? cp1 : cc1;  // plane pb after red
-          const int bsb = bo(pb) - BOXW;
+          const int bsb = bo(pb) - W;
           const float4 yb0 = lds4(bsb + so0), yb1 = lds4(bsb + so1);  // b(pb)
-          const float4 yu0 = lds4(xob + so0 - BOXW), yd0 = lds4(xob + so0 + BOXW);
-          const float4 yu1 = lds4(xob + so1 - BOXW), yd1 = lds4(xob + so1 + BOXW);
+          const float4 yu0 = lds4(xob + so0 - W), yd0 = lds4(xob + so0 + W);
+          const float4 yu1 = lds4(xob + so1 - W), yd1 = lds4(xob + so1 + W);
           // red cells of plane pb - 1 (z-neighbours below; coupled case)
           float4 ym0 = zero4, ym1 = zero4;
           if (zc && k.zmf != 0.f) {
@@ -584,8 +646,8 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
             float e0 = __shfl_up_sync(FULL, yc0.w, 1, 16);
             float e1 = __shfl_up_sync(FULL, yc1.w, 1, 16);
             if (c4 == 0) {
-              e0 = zsm[xob + so0 - 1];
-              e1 = zsm[xob + so1 - 1];
+              e0 = S::ld1(sm + xob + so0 - 1);
+              e1 = S::ld1(sm + xob + so1 - 1);
             }
             black2(std::true_type(), k, yc0, yu0, yd0, ym0, cc0, yb0, e0, gj0, f0);
             black2(std::true_type(), k, yc1, yu1, yd1, ym1, cc1, yb1, e1, gj1, f1);
@@ -593,19 +655,19 @@ __global__ void __launch_bounds__(SweepGeo::NT, 2) k_zsweep(const __grid_constan
             float e0 = __shfl_down_sync(FULL, yc0.x, 1, 16);
             float e1 = __shfl_down_sync(FULL, yc1.x, 1, 16);
             if (c4 == 15) {
-              e0 = zsm[xob + so0 + 4];
-              e1 = zsm[xob + so1 + 4];
+              e0 = S::ld1(sm + xob + so0 + 4);
+              e1 = S::ld1(sm + xob + so1 + 4);
             }
             black2(std::false_type(), k, yc0, yu0, yd0, ym0, cc0, yb0, e0, gj0, f0);
             black2(std::false_type(), k, yc1, yu1, yd1, ym1, cc1, yb1, e1, gj1, f1);
           }
-          float *xo_pb = a.xout + (size_t)pb * plane;
+          T *xo_pb = reinterpret_cast<T *>(a.xout) + (size_t)pb * plane;
           if (act0) {
-            *reinterpret_cast<float4 *>(xo_pb + go0) = f0;
+            S::st4(xo_pb + go0, f0);
             if (SUM) acc(f0);
           }
           if (act1) {
-            *reinterpret_cast<float4 *>(xo_pb + go1) = f1;
+            S::st4(xo_pb + go1, f1);
             if (SUM) acc(f1);
           }
         }
@@ -675,11 +737,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
 }
 
+template <typename T>
 struct RestrictGeo {
+  static constexpr int W = St<T>::W, OFF = St<T>::OFF;
   static constexpr int XH = SY + 2;              // x box rows j0-1 .. j0+SY
   static constexpr int XR = 6;                   // x planes t, t+1 + 4 in flight
   static constexpr int BR = 4;                   // b plane t + 3 in flight
-  static constexpr int XS = pad32(XH * BOXW);
+  static constexpr int XS = pad128<T>(XH * W);
   static constexpr int BS = ZX * SY;             // b box: the tile only
   static constexpr int BOFF = XR * XS;
   static constexpr int MOFF = BOFF + BR * BS;
@@ -687,7 +751,7 @@ struct RestrictGeo {
   static constexpr int NT = 32 * (TILE_WARPS + 1);
   static constexpr int SVC = 32 * TILE_WARPS;
   __host__ __device__ static constexpr size_t smem_bytes() {
-    return sizeof(float) * (size_t)MOFF + sizeof(uint64_t) * 2 * (XR + BR) + 16;
+    return sizeof(T) * (size_t)MOFF + sizeof(uint64_t) * 2 * (XR + BR) + 16;
   }
 };
 
@@ -695,13 +759,17 @@ struct RestrictGeo {
 // level's right-hand side.  A tile thread owns rows 2k and 2k + 1 of one
 // column of four cells, so the children of a coarse cell in x and y are its
 // own; children in z are two consecutive planes of the march.
-template <bool UNIFORM, bool COUPLED>
-__global__ void __launch_bounds__(RestrictGeo::NT, 2) k_zrestrict(const __grid_constant__ CUtensorMap tmx,
-                                                                 const __grid_constant__ CUtensorMap tmb,
-                                                                 const ZSweepArgs a) {
-  using G = RestrictGeo;
+template <typename T, typename TC, bool UNIFORM, bool COUPLED>
+__global__ void __launch_bounds__(RestrictGeo<T>::NT, 2) k_zrestrict(const __grid_constant__ CUtensorMap tmx,
+                                                                    const __grid_constant__ CUtensorMap tmb,
+                                                                    const ZSweepArgs a) {
+  using G = RestrictGeo<T>;
+  using S = St<T>;
+  constexpr int W = G::W, OFF = G::OFF;
   constexpr bool zc = COUPLED;
-  uint64_t *xfull = reinterpret_cast<uint64_t *>(zsm + G::MOFF);
+  T *sm = reinterpret_cast<T *>(zsm);
+  auto lds4 = [&](int off) { return S::ld4(sm + off); };
+  uint64_t *xfull = reinterpret_cast<uint64_t *>(sm + G::MOFF);
   uint64_t *bfull = xfull + G::XR;
   uint64_t *xempty = bfull + G::BR;
   uint64_t *bempty = xempty + G::XR;
@@ -753,8 +821,8 @@ __global__ void __launch_bounds__(RestrictGeo::NT, 2) k_zrestrict(const __grid_c
           if (px - G::XR >= rx.lo) ok = mbar_wait(&xempty[q], rx.parity(px - G::XR));
           if (ok) {
             fence_proxy_async();
-            mbar_expect_tx(&xfull[q], (uint32_t)(G::XH * BOXW * sizeof(float)));
-            tma_plane(zsm + q * G::XS, &tmx, i0 - 4, j0 - 1, px, &xfull[q]);
+            mbar_expect_tx(&xfull[q], (uint32_t)(G::XH * W * sizeof(T)));
+            tma_plane(sm + q * G::XS, &tmx, i0 - OFF, j0 - 1, px, &xfull[q]);
             xdone = px++;
           }
         } else {
@@ -762,8 +830,8 @@ __global__ void __launch_bounds__(RestrictGeo::NT, 2) k_zrestrict(const __grid_c
           if (pb - G::BR >= rb.lo) ok = mbar_wait(&bempty[q], rb.parity(pb - G::BR));
           if (ok) {
             fence_proxy_async();
-            mbar_expect_tx(&bfull[q], (uint32_t)(ZX * SY * sizeof(float)));
-            tma_plane(zsm + G::BOFF + q * G::BS, &tmb, i0, j0, pb, &bfull[q]);
+            mbar_expect_tx(&bfull[q], (uint32_t)(ZX * SY * sizeof(T)));
+            tma_plane(sm + G::BOFF + q * G::BS, &tmb, i0, j0, pb, &bfull[q]);
             bdone = pb++;
           }
         }
@@ -785,7 +853,7 @@ __global__ void __launch_bounds__(RestrictGeo::NT, 2) k_zrestrict(const __grid_c
   const int gi = i0 + 4 * c4, gj0 = j0 + 2 * kr, gj1 = gj0 + 1;
   const bool colin = gi < nx;
   const bool act0 = colin && gj0 < ny, act1 = colin && gj1 < ny;
-  const int so0 = (2 * kr + 1) * BOXW + 4 + 4 * c4, so1 = so0 + BOXW;
+  const int so0 = (2 * kr + 1) * W + OFF + 4 * c4, so1 = so0 + W;
   const int sb0 = (2 * kr) * ZX + 4 * c4, sb1 = sb0 + ZX;
   const float cxu = L.wx * (float)L.sy * (float)L.sz;
   const float cyu = L.wy * (float)L.sx * (float)L.sz;
@@ -869,18 +937,18 @@ __global__ void __launch_bounds__(RestrictGeo::NT, 2) k_zrestrict(const __grid_c
         xn0 = lds4(on + so0);
         xn1 = lds4(on + so1);
       }
-      const float4 xu = lds4(o + so0 - BOXW), xd = lds4(o + so1 + BOXW);
+      const float4 xu = lds4(o + so0 - W), xd = lds4(o + so1 + W);
       const float4 b0 = lds4(ob + sb0), b1 = lds4(ob + sb1);
       // x-neighbours across the float4 edges
       float l0 = __shfl_up_sync(FULL, xc0.w, 1, 16), l1 = __shfl_up_sync(FULL, xc1.w, 1, 16);
       float r0 = __shfl_down_sync(FULL, xc0.x, 1, 16), r1 = __shfl_down_sync(FULL, xc1.x, 1, 16);
       if (c4 == 0) {
-        l0 = zsm[o + so0 - 1];
-        l1 = zsm[o + so1 - 1];
+        l0 = S::ld1(sm + o + so0 - 1);
+        l1 = S::ld1(sm + o + so1 - 1);
       }
       if (c4 == 15) {
-        r0 = zsm[o + so0 + 4];
-        r1 = zsm[o + so1 + 4];
+        r0 = S::ld1(sm + o + so0 + 4);
+        r1 = S::ld1(sm + o + so1 + 4);
       }
       release_x(t);
       release_b(t);
@@ -927,17 +995,16 @@ __global__ void __launch_bounds__(RestrictGeo::NT, 2) k_zrestrict(const __grid_c
           s1.z += acc1.z;
           s1.w += acc1.w;
         }
-        float *cpl = a.bc + (size_t)(t >> fz) * a.ncy * a.ncx;
+        TC *cpl = reinterpret_cast<TC *>(a.bc) + (size_t)(t >> fz) * a.ncy * a.ncx;
         const int I = (i0 + 4 * c4) >> fx;
         const int J0 = gj0 >> fy;
         if (colin) {
           if (fx) {
-            if (gj0 < ny) *reinterpret_cast<float2 *>(cpl + (size_t)J0 * a.ncx + I) = make_float2(s0.x, s0.y);
-            if (!fy && gj1 < ny)
-              *reinterpret_cast<float2 *>(cpl + (size_t)(J0 + 1) * a.ncx + I) = make_float2(s1.x, s1.y);
+            if (gj0 < ny) St<TC>::stg2(cpl + (size_t)J0 * a.ncx + I, make_float2(s0.x, s0.y));
+            if (!fy && gj1 < ny) St<TC>::stg2(cpl + (size_t)(J0 + 1) * a.ncx + I, make_float2(s1.x, s1.y));
           } else {
-            if (gj0 < ny) *reinterpret_cast<float4 *>(cpl + (size_t)J0 * a.ncx + I) = s0;
-            if (!fy && gj1 < ny) *reinterpret_cast<float4 *>(cpl + (size_t)(J0 + 1) * a.ncx + I) = s1;
+            if (gj0 < ny) St<TC>::st4(cpl + (size_t)J0 * a.ncx + I, s0);
+            if (!fy && gj1 < ny) St<TC>::st4(cpl + (size_t)(J0 + 1) * a.ncx + I, s1);
           }
         }
       }
@@ -997,12 +1064,18 @@ struct OuterGeo {
   static constexpr int TILE_WARPS = 8;
   static constexpr int NT = 32 * (TILE_WARPS + 1);
   static constexpr int SVC = 32 * TILE_WARPS;
-  // an x slot holds the high part, the low part (if read) and the correction
-  // (if added) of one plane; an input slot holds I0 (or b) and I1 (SP)
-  __host__ __device__ static constexpr int xstride(bool xl, bool e) { return S * (1 + xl + e); }
-  __host__ __device__ static constexpr int istride(bool sp) { return S + (sp ? SI1 : 0); }
-  __host__ __device__ static constexpr size_t smem_bytes(bool xl, bool e, bool sp) {
-    return sizeof(float) * (size_t)(XR * xstride(xl, e) + IR * istride(sp)) +
+  // An x slot holds the high part, the low part (if read) and the correction
+  // (if added, float32 or float16: esz bytes per element, its own box width)
+  // of one plane; an input slot holds I0 (or b) and I1 (SP).  Sizes in bytes.
+  __host__ __device__ static constexpr int ebytes(int esz) {
+    return esz == 2 ? 2 * pad128<half_t>(BH * St<half_t>::W) : 4 * S;
+  }
+  __host__ __device__ static constexpr int xstride(bool xl, bool e, int esz) {
+    return 4 * S * (1 + xl) + (e ? ebytes(esz) : 0);
+  }
+  __host__ __device__ static constexpr int istride(bool sp) { return 4 * (S + (sp ? SI1 : 0)); }
+  __host__ __device__ static constexpr size_t smem_bytes(bool xl, bool e, bool sp, int esz) {
+    return (size_t)(XR * xstride(xl, e, esz) + IR * istride(sp)) +
            sizeof(uint64_t) * 2 * (XR + IR) + sizeof(double) * 32 + 16;
   }
 };
@@ -1015,7 +1088,7 @@ struct OuterGeo {
 // and below, the row ends) or taken from the neighbouring lanes (shuffles)
 // and from its own registers (z), so no thread writes shared memory and the
 // planes stream through a producer/consumer ring without CTA barriers.
-template <int RHS, bool HAS_XL, bool HAS_E, bool ACCURATE>
+template <typename TE, int RHS, bool HAS_XL, bool HAS_E, bool ACCURATE>
 __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constant__ CUtensorMap tmh,
                                                             const __grid_constant__ CUtensorMap tml,
                                                             const __grid_constant__ CUtensorMap tme,
@@ -1025,13 +1098,18 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
   using G = OuterGeo;
   constexpr int S = G::S;
   constexpr bool SP = RHS == RHS_SP;
-  constexpr int XST = G::xstride(HAS_XL, HAS_E), IST = G::istride(SP);
-  constexpr int LOFF = S, EOFF = S * (1 + (HAS_XL ? 1 : 0));  // within an x slot
-  constexpr int IBASE = G::XR * XST;
+  constexpr int ESZ = (int)sizeof(TE);
+  constexpr int XSTB = G::xstride(HAS_XL, HAS_E, ESZ), ISTB = G::istride(SP);  // bytes
+  constexpr int LOFF = S;                                 // floats, within an x slot
+  constexpr int EOFFB = 4 * S * (1 + (HAS_XL ? 1 : 0));  // bytes, within an x slot
+  constexpr int WE = St<TE>::W, OFFE = St<TE>::OFF;
+  char *const smb = reinterpret_cast<char *>(zsm);
+  auto xslot = [&](int q) { return reinterpret_cast<float *>(smb + q * XSTB); };
+  auto islot = [&](int q) { return reinterpret_cast<float *>(smb + G::XR * XSTB + q * ISTB); };
   // the low word of the float pair is carried only in exact passes (and read
   // whenever the caller passes one)
   constexpr bool USE_L = HAS_XL || (HAS_E && ACCURATE);
-  uint64_t *xfull = reinterpret_cast<uint64_t *>(zsm + IBASE + G::IR * IST);
+  uint64_t *xfull = reinterpret_cast<uint64_t *>(smb + G::XR * XSTB + G::IR * ISTB);
   uint64_t *ifull = xfull + G::XR;
   uint64_t *xempty = ifull + G::IR;
   uint64_t *iempty = xempty + G::XR;
@@ -1054,7 +1132,7 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
 
   if (tid == G::SVC) {
     abort_flag = 0;
-    const size_t bytes = G::smem_bytes(HAS_XL, HAS_E, SP);
+    const size_t bytes = G::smem_bytes(HAS_XL, HAS_E, SP, ESZ);
     int e = tma_preflight(zsm, bytes, &tmh);
     if (!e && HAS_XL) e = tma_preflight(zsm, bytes, &tml);
     if (!e && HAS_E) e = tma_preflight(zsm, bytes, &tme);
@@ -1081,6 +1159,7 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
   // per-thread sums in FP32 (r^2, b^2, I0) and double-float (x); FP64 only
   // once per block
   float srr = 0.f, sbb = 0.f, si = 0.f, sxh = 0.f, sxl = 0.f;
+  float rmx = 0.f;  // max |r| (for the scale of a float16 residual)
 
   if (warp == G::TILE_WARPS) {
     // ---- producer: planes in the order the tile warps need them ----
@@ -1095,11 +1174,12 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
           if (px - G::XR >= rx.lo) ok = mbar_wait(&xempty[q], rx.parity(px - G::XR));
           if (ok) {
             fence_proxy_async();
-            float *xb = zsm + q * XST;
-            mbar_expect_tx(&xfull[q], BOXB * (1 + (HAS_XL ? 1 : 0) + (HAS_E ? 1 : 0)));
+            float *xb = xslot(q);
+            mbar_expect_tx(&xfull[q], BOXB * (1 + (HAS_XL ? 1 : 0)) +
+                                          (HAS_E ? (uint32_t)(G::BH * WE * ESZ) : 0u));
             tma_plane(xb, &tmh, i0 - 4, j0 - 1, px, &xfull[q]);
             if (HAS_XL) tma_plane(xb + LOFF, &tml, i0 - 4, j0 - 1, px, &xfull[q]);
-            if (HAS_E) tma_plane(xb + EOFF, &tme, i0 - 4, j0 - 1, px, &xfull[q]);
+            if (HAS_E) tma_plane(smb + q * XSTB + EOFFB, &tme, i0 - OFFE, j0 - 1, px, &xfull[q]);
             xdone = px++;
           }
         } else {
@@ -1107,7 +1187,7 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
           if (pi - G::IR >= ri.lo) ok = mbar_wait(&iempty[q], ri.parity(pi - G::IR));
           if (ok) {
             fence_proxy_async();
-            float *ib = zsm + IBASE + q * IST;
+            float *ib = islot(q);
             mbar_expect_tx(&ifull[q], BOXB + (SP ? (uint32_t)(G::SI1 * sizeof(float)) : 0u));
             tma_plane(ib, &tmi0, i0 - 4, j0 - 1, pi, &ifull[q]);
             if (SP) tma_plane(ib + S, &tmi1, i0, j0, pi, &ifull[q]);
@@ -1134,7 +1214,8 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
     const int si1 = r * ZX + 4 * c4;
     float shift = 0.f;
     if (HAS_E && a.mean_fix)
-      shift = (float)((a.scalars[S_I0] - a.scalars[S_X] - a.scalars[S_E]) * a.inv_n);
+      shift = (float)((a.scalars[S_I0] - a.scalars[S_X] - a.scalars[S_E] * (double)a.e_scale) * a.inv_n);
+    const float esc = a.e_scale;
     bool failed = false;
     int xw = rx.lo - 1, iw = ri.lo - 1;
     auto need_x = [&](int p) {
@@ -1159,12 +1240,16 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
       __syncwarp();
       if (lane == 0 && ri.has(p)) mbar_arrive(&iempty[ri.slot(p)]);
     };
-    // the updated iterate (a float pair) at one cell / four cells of a slot
-    auto upd1 = [&](const float *xb, int off, float &h, float &l) {
+    // the updated iterate (a float pair) at one cell / four cells of x slot
+    // q; rr is the box row, col the column relative to the tile
+    auto upd1 = [&](int q, int rr, int col, float &h, float &l) {
+      const float *xb = xslot(q);
+      const int off = rr * BOXW + 4 + col;
       h = xb[off];
       l = HAS_XL ? xb[LOFF + off] : 0.f;
       if (HAS_E) {
-        const float e = __fadd_rn(xb[EOFF + off], shift);
+        const TE *eb = reinterpret_cast<const TE *>(smb + q * XSTB + EOFFB);
+        const float e = __fadd_rn(St<TE>::ld1(eb + rr * WE + OFFE + col) * esc, shift);
         if (ACCURATE) {
           const ff v = ff_add({h, l}, {e, 0.f});
           h = v.h;
@@ -1175,16 +1260,19 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
       }
       if (!USE_L) l = 0.f;
     };
-    auto upd4 = [&](const float *xb, int off, float4 &h, float4 &l) {
+    auto upd4 = [&](int q, int rr, int col, float4 &h, float4 &l) {
+      const float *xb = xslot(q);
+      const int off = rr * BOXW + 4 + col;
       h = *reinterpret_cast<const float4 *>(xb + off);
       l = HAS_XL ? *reinterpret_cast<const float4 *>(xb + LOFF + off) : zero4;
       if (HAS_E) {
-        const float4 e = *reinterpret_cast<const float4 *>(xb + EOFF + off);
+        const TE *eb = reinterpret_cast<const TE *>(smb + q * XSTB + EOFFB);
+        const float4 e = St<TE>::ld4(eb + rr * WE + OFFE + col);
         float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
         const float ev[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-          const float ee = __fadd_rn(ev[c], shift);
+          const float ee = __fadd_rn(ev[c] * esc, shift);
           if (ACCURATE) {
             const ff v = ff_add({hv[c], lv[c]}, {ee, 0.f});
             hv[c] = v.h;
@@ -1298,32 +1386,32 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
       const int t0 = zs, t1 = ze - 1;
       if (zc && t0 > 0) {
         need_x(t0 - 1);
-        upd4(zsm + rx.slot(t0 - 1) * XST, so, hm4, lm4);
+        upd4(rx.slot(t0 - 1), r + 1, 4 * c4, hm4, lm4);
         release_x(t0 - 1);
       }
       need_x(t0);
-      if (!failed) upd4(zsm + rx.slot(t0) * XST, so, hc4, lc4);
+      if (!failed) upd4(rx.slot(t0), r + 1, 4 * c4, hc4, lc4);
       for (int t = t0; t <= t1 && !failed; ++t) {
         const bool hm = zc && t > 0, hp = zc && t < nz - 1;
         float4 hp4 = zero4, lp4 = zero4;
         if (hp) {
           need_x(t + 1);
           if (failed) break;
-          upd4(zsm + rx.slot(t + 1) * XST, so, hp4, lp4);
+          upd4(rx.slot(t + 1), r + 1, 4 * c4, hp4, lp4);
         }
         need_i(t);
         if (failed) break;
-        const float *xb = zsm + rx.slot(t) * XST;
-        const float *ib = zsm + IBASE + ri.slot(t) * IST;
+        const int qx = rx.slot(t);
+        const float *ib = islot(ri.slot(t));
         float4 hu, lu, hd, ld;
-        upd4(xb, so - BOXW, hu, lu);
-        upd4(xb, so + BOXW, hd, ld);
+        upd4(qx, r, 4 * c4, hu, lu);
+        upd4(qx, r + 2, 4 * c4, hd, ld);
         // x-neighbours across the float4 edges: the neighbouring lane's cells,
         // or the shared-memory planes at the tile's ends
         float hw = __shfl_up_sync(FULL, hc4.w, 1, 16), lw = __shfl_up_sync(FULL, lc4.w, 1, 16);
         float he = __shfl_down_sync(FULL, hc4.x, 1, 16), le = __shfl_down_sync(FULL, lc4.x, 1, 16);
-        if (c4 == 0) upd1(xb, so - 1, hw, lw);
-        if (c4 == 15) upd1(xb, so + 4, he, le);
+        if (c4 == 0) upd1(qx, r + 1, -1, hw, lw);
+        if (c4 == 15) upd1(qx, r + 1, 4 * c4 + 4, he, le);
         const float4 ic = *reinterpret_cast<const float4 *>(ib + so);
         float4 iu = zero4, id = zero4;
         float iw_ = 0.f, ie_ = 0.f;
@@ -1351,7 +1439,10 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
           const size_t g = (size_t)t * plane + (size_t)gj * nx + gi;
           if (a.xh_out) *reinterpret_cast<float4 *>(a.xh_out + g) = hc4;
           if (USE_L && a.xl_out) *reinterpret_cast<float4 *>(a.xl_out + g) = lc4;
-          if (a.r_out) *reinterpret_cast<float4 *>(a.r_out + g) = make_float4(rv[0], rv[1], rv[2], rv[3]);
+          if (a.r_out)
+            St<TE>::st4(reinterpret_cast<TE *>(a.r_out) + g,
+                        make_float4(rv[0] * a.r_scale, rv[1] * a.r_scale, rv[2] * a.r_scale, rv[3] * a.r_scale));
+          rmx = fmaxf(rmx, fmaxf(fmaxf(fabsf(rv[0]), fabsf(rv[1])), fmaxf(fabsf(rv[2]), fabsf(rv[3]))));
   #pragma unroll
           for (int c = 0; c < 4; ++c) {
             srr += rv[c] * rv[c];
@@ -1368,7 +1459,7 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
         if (!zc && t < t1) {
           // uncoupled: the next plane's own cells are read in its own step
           need_x(t + 1);
-          if (!failed) upd4(zsm + rx.slot(t + 1) * XST, so, hc4, lc4);
+          if (!failed) upd4(rx.slot(t + 1), r + 1, 4 * c4, hc4, lc4);
         }
       }
     };
@@ -1383,6 +1474,11 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
   }
   __syncthreads();
   if (abort_flag) return;
+  if (a.rmax) {
+    for (int o = 16; o > 0; o >>= 1) rmx = fmaxf(rmx, __shfl_xor_sync(0xffffffffu, rmx, o));
+    // non-negative floats order as their bit patterns
+    if (lane == 0 && rmx > 0.f) atomicMax(a.rmax, __float_as_uint(rmx));
+  }
   const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   double v;
   v = block_sum((double)srr, dsh);
@@ -1418,19 +1514,24 @@ bool encoder() {
   return g_encode_state == 1;
 }
 
-// 3D map over a float32 [nz][ny][nx] array with a (width x rows x 1) box.
-bool make_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int width, int rows) {
+// 3D map over a float32 / float16 (esz = 4 / 2 bytes) [nz][ny][nx] array with a
+// (width x rows x 1) box; rows must be 16-byte multiples (TMA strides).
+bool make_map(CUtensorMap *m, const void *base, int nx, int ny, int nz, int width, int rows, int esz) {
   if (!encoder() || !base) return false;
-  if (((uintptr_t)base & 15) != 0 || (nx & 3) != 0) return false;
+  if (((uintptr_t)base & 15) != 0 || ((size_t)nx * esz) % 16 != 0) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * esz, (cuuint64_t)nx * ny * esz};
   const cuuint32_t box[3] = {(cuuint32_t)width, (cuuint32_t)rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  return g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides,
-                  box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+  return g_encode(m, esz == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                  const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+bool make_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int width, int rows) {
+  return make_map(m, static_cast<const void *>(base), nx, ny, nz, width, rows, 4);
+}
+int box_w(int esz) { return esz == 2 ? St<half_t>::W : St<float>::W; }
 
 int sm_count() {
   static int n = 0;
@@ -1464,89 +1565,129 @@ int pick_zchunk(int tiles, int nz, bool coupled, int ctas_per_sm) {
   return zc;
 }
 
-template <bool Z, bool P, bool S, bool U, bool C>
+template <typename T, typename TC, bool Z, bool P, bool S, bool U, bool C>
 cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
                           dim3 grid, cudaStream_t st) {
-  const size_t bytes = SweepGeo::smem_bytes();
+  const size_t bytes = SweepGeo<T>::smem_bytes();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_zsweep<Z, P, S, U, C>, bytes);
+    cudaError_t e = set_smem(k_zsweep<T, TC, Z, P, S, U, C>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zsweep<Z, P, S, U, C><<<grid, SweepGeo::NT, bytes, st>>>(mx, mb, a);
+  k_zsweep<T, TC, Z, P, S, U, C><<<grid, SweepGeo<T>::NT, bytes, st>>>(mx, mb, a);
   return cudaGetLastError();
 }
 bool level_uniform(const LevelDev &L) { return L.sx == L.lx && L.sy == L.ly && L.sz == L.lz; }
 bool level_coupled(const LevelDev &L) { return L.wz != 0.f && L.nz > 1; }
-template <bool Z, bool P, bool S>
+template <typename T, typename TC, bool Z, bool P, bool S>
 cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a, dim3 grid,
                        cudaStream_t st) {
   const bool u = level_uniform(a.L), c = level_coupled(a.L);
-  if (u && c) return run_zsweep_uc<Z, P, S, true, true>(mx, mb, a, grid, st);
-  if (u) return run_zsweep_uc<Z, P, S, true, false>(mx, mb, a, grid, st);
-  if (c) return run_zsweep_uc<Z, P, S, false, true>(mx, mb, a, grid, st);
-  return run_zsweep_uc<Z, P, S, false, false>(mx, mb, a, grid, st);
+  if (u && c) return run_zsweep_uc<T, TC, Z, P, S, true, true>(mx, mb, a, grid, st);
+  if (u) return run_zsweep_uc<T, TC, Z, P, S, true, false>(mx, mb, a, grid, st);
+  if (c) return run_zsweep_uc<T, TC, Z, P, S, false, true>(mx, mb, a, grid, st);
+  return run_zsweep_uc<T, TC, Z, P, S, false, false>(mx, mb, a, grid, st);
 }
-template <bool U, bool C>
+// the five sweep variants of a V-cycle; the coarse type matters only with
+// the prolongation
+template <typename T, typename TC>
+cudaError_t run_zsweep_variant(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
+                               bool zero_in, bool prolong, bool sum, dim3 grid, cudaStream_t st) {
+  if (zero_in && !prolong && !sum) return run_zsweep<T, T, true, false, false>(mx, mb, a, grid, st);
+  if (!zero_in && prolong && !sum) return run_zsweep<T, TC, false, true, false>(mx, mb, a, grid, st);
+  if (!zero_in && prolong && sum) return run_zsweep<T, TC, false, true, true>(mx, mb, a, grid, st);
+  if (!zero_in && !prolong && !sum) return run_zsweep<T, T, false, false, false>(mx, mb, a, grid, st);
+  if (!zero_in && !prolong && sum) return run_zsweep<T, T, false, false, true>(mx, mb, a, grid, st);
+  return cudaErrorNotSupported;
+}
+template <typename T, typename TC, bool U, bool C>
 cudaError_t run_zrestrict(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
                           dim3 grid, cudaStream_t st) {
-  const size_t bytes = RestrictGeo::smem_bytes();
+  const size_t bytes = RestrictGeo<T>::smem_bytes();
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_zrestrict<U, C>, bytes);
+    cudaError_t e = set_smem(k_zrestrict<T, TC, U, C>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zrestrict<U, C><<<grid, RestrictGeo::NT, bytes, st>>>(mx, mb, a);
+  k_zrestrict<T, TC, U, C><<<grid, RestrictGeo<T>::NT, bytes, st>>>(mx, mb, a);
   return cudaGetLastError();
 }
+template <typename T, typename TC>
+cudaError_t run_zrestrict_t(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
+                            dim3 grid, cudaStream_t st) {
+  const bool u = level_uniform(a.L), c = level_coupled(a.L);
+  if (u && c) return run_zrestrict<T, TC, true, true>(mx, mb, a, grid, st);
+  if (u) return run_zrestrict<T, TC, true, false>(mx, mb, a, grid, st);
+  if (c) return run_zrestrict<T, TC, false, true>(mx, mb, a, grid, st);
+  return run_zrestrict<T, TC, false, false>(mx, mb, a, grid, st);
+}
 
-template <int RHS, bool XL, bool E, bool ACC>
+template <typename TE, int RHS, bool XL, bool E, bool ACC>
 cudaError_t run_zouter(const CUtensorMap *m, const OuterArgs &a, int zchunk, double *err, dim3 grid,
                        cudaStream_t st) {
-  const size_t bytes = OuterGeo::smem_bytes(XL, E, RHS == RHS_SP);
+  const size_t bytes = OuterGeo::smem_bytes(XL, E, RHS == RHS_SP, (int)sizeof(TE));
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = set_smem(k_zouter<RHS, XL, E, ACC>, bytes);
+    cudaError_t e = set_smem(k_zouter<TE, RHS, XL, E, ACC>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zouter<RHS, XL, E, ACC><<<grid, OuterGeo::NT, bytes, st>>>(m[0], m[1], m[2], m[3], m[4], a, zchunk, err);
+  k_zouter<TE, RHS, XL, E, ACC><<<grid, OuterGeo::NT, bytes, st>>>(m[0], m[1], m[2], m[3], m[4], a, zchunk,
+                                                                    err);
   return cudaGetLastError();
+}
+template <typename TE>
+cudaError_t run_zouter_t(const CUtensorMap *m, const OuterArgs &a, int rhs_mode, int zchunk, double *err,
+                         dim3 grid, cudaStream_t st) {
+  const bool xl = a.xl_in != nullptr, e = a.e != nullptr;
+#define GD_ZO2(R, ACC)                                                                 \
+  if (xl && e) return run_zouter<TE, R, true, true, ACC>(m, a, zchunk, err, grid, st);  \
+  if (xl) return run_zouter<TE, R, true, false, ACC>(m, a, zchunk, err, grid, st);      \
+  if (e) return run_zouter<TE, R, false, true, ACC>(m, a, zchunk, err, grid, st);       \
+  return run_zouter<TE, R, false, false, ACC>(m, a, zchunk, err, grid, st);
+#define GD_ZO(R)    \
+  if (a.accurate) { \
+    GD_ZO2(R, true) \
+  } else {          \
+    GD_ZO2(R, false) \
+  }
+  if (rhs_mode == RHS_EXPLICIT) { GD_ZO(RHS_EXPLICIT) }
+  if (rhs_mode == RHS_AD) { GD_ZO(RHS_AD) }
+  GD_ZO(RHS_SP)
+#undef GD_ZO
+#undef GD_ZO2
 }
 
 }  // namespace
 
-bool zmarch_usable(const LevelDev &L) { return encoder() && (L.nx & 3) == 0; }
+bool zmarch_usable(const LevelDev &L, int esz) { return encoder() && ((size_t)L.nx * esz) % 16 == 0; }
 
-cudaError_t launch_zsweep(ZSweepArgs a, const float *xin, const float *b, bool zero_in, bool prolong,
-                          bool sum, int *nblocks_out, cudaStream_t st) {
+cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zero_in, bool prolong,
+                          bool sum, int esz, int esz_c, int *nblocks_out, cudaStream_t st) {
   const LevelDev &L = a.L;
-  const int rows_x = SweepGeo::XH, rows_b = SweepGeo::BH;
+  const int rows_x = SweepGeo<float>::XH, rows_b = SweepGeo<float>::BH;
   CUtensorMap mx, mb;
   std::memset(&mx, 0, sizeof mx);
-  if (!make_map(&mx, zero_in ? b : xin, L.nx, L.ny, L.nz, BOXW, rows_x)) return cudaErrorNotSupported;
-  if (!make_map(&mb, b, L.nx, L.ny, L.nz, BOXW, rows_b)) return cudaErrorNotSupported;
+  if (!make_map(&mx, zero_in ? b : xin, L.nx, L.ny, L.nz, box_w(esz), rows_x, esz)) return cudaErrorNotSupported;
+  if (!make_map(&mb, b, L.nx, L.ny, L.nz, box_w(esz), rows_b, esz)) return cudaErrorNotSupported;
   if (((uintptr_t)a.xout & 15) != 0) return cudaErrorNotSupported;
   const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
   a.zchunk = pick_zchunk(gx * gy, L.nz, level_coupled(L), 2);
   const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
   if (nblocks_out) *nblocks_out = gx * gy * gz;
   dim3 grid(gx, gy, gz);
-  if (zero_in && !prolong && !sum) return run_zsweep<true, false, false>(mx, mb, a, grid, st);
-  if (!zero_in && prolong && !sum) return run_zsweep<false, true, false>(mx, mb, a, grid, st);
-  if (!zero_in && prolong && sum) return run_zsweep<false, true, true>(mx, mb, a, grid, st);
-  if (!zero_in && !prolong && !sum) return run_zsweep<false, false, false>(mx, mb, a, grid, st);
-  if (!zero_in && !prolong && sum) return run_zsweep<false, false, true>(mx, mb, a, grid, st);
-  return cudaErrorNotSupported;
+  if (esz == 4) return run_zsweep_variant<float, float>(mx, mb, a, zero_in, prolong, sum, grid, st);
+  if (esz_c == 2 || !prolong) return run_zsweep_variant<half_t, half_t>(mx, mb, a, zero_in, prolong, sum, grid, st);
+  return run_zsweep_variant<half_t, float>(mx, mb, a, zero_in, prolong, sum, grid, st);
 }
 
-cudaError_t launch_zrestrict(ZSweepArgs a, const float *x, const float *b, cudaStream_t st) {
+cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz, int esz_c, cudaStream_t st) {
   const LevelDev &L = a.L;
   CUtensorMap mx, mb;
-  if (!make_map(&mx, x, L.nx, L.ny, L.nz, BOXW, RestrictGeo::XH)) return cudaErrorNotSupported;
-  if (!make_map(&mb, b, L.nx, L.ny, L.nz, ZX, SY)) return cudaErrorNotSupported;
+  if (!make_map(&mx, x, L.nx, L.ny, L.nz, box_w(esz), RestrictGeo<float>::XH, esz)) return cudaErrorNotSupported;
+  if (!make_map(&mb, b, L.nx, L.ny, L.nz, ZX, SY, esz)) return cudaErrorNotSupported;
   if (((uintptr_t)a.bc & 15) != 0) return cudaErrorNotSupported;
   const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
   const bool coupled = level_coupled(L);
@@ -1554,23 +1695,21 @@ cudaError_t launch_zrestrict(ZSweepArgs a, const float *x, const float *b, cudaS
   if (a.fz && (a.zchunk & 1)) ++a.zchunk;  // both children of a coarse plane in one chunk
   const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
   dim3 grid(gx, gy, gz);
-  const bool u = level_uniform(L);
-  if (u && coupled) return run_zrestrict<true, true>(mx, mb, a, grid, st);
-  if (u) return run_zrestrict<true, false>(mx, mb, a, grid, st);
-  if (coupled) return run_zrestrict<false, true>(mx, mb, a, grid, st);
-  return run_zrestrict<false, false>(mx, mb, a, grid, st);
+  if (esz == 4) return run_zrestrict_t<float, float>(mx, mb, a, grid, st);
+  if (esz_c == 2) return run_zrestrict_t<half_t, half_t>(mx, mb, a, grid, st);
+  return run_zrestrict_t<half_t, float>(mx, mb, a, grid, st);
 }
 
-cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nblocks_out,
+cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, int esz_e, double *err, int *nblocks_out,
                           cudaStream_t st) {
-  if ((a.nx & 3) != 0) return cudaErrorNotSupported;
+  if ((a.nx & 3) != 0 || ((size_t)a.nx * esz_e) % 16 != 0) return cudaErrorNotSupported;
   const int rows = OuterGeo::BH;
   CUtensorMap m[5];
   std::memset(m, 0, sizeof m);
   const float *rhs0 = rhs_mode == RHS_EXPLICIT ? a.b : a.I0;
   if (!make_map(&m[0], a.xh_in, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
   if (a.xl_in && !make_map(&m[1], a.xl_in, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
-  if (a.e && !make_map(&m[2], a.e, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
+  if (a.e && !make_map(&m[2], a.e, a.nx, a.ny, a.nz, box_w(esz_e), rows, esz_e)) return cudaErrorNotSupported;
   if (!make_map(&m[3], rhs0, a.nx, a.ny, a.nz, BOXW, rows)) return cudaErrorNotSupported;
   if (rhs_mode == RHS_SP && !make_map(&m[4], a.I1, a.nx, a.ny, a.nz, ZX, OuterGeo::OY))
     return cudaErrorNotSupported;
@@ -1582,22 +1721,8 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, double *err, int *nb
   const int gz = (a.nz + zchunk - 1) / zchunk;
   if (nblocks_out) *nblocks_out = gx * gy * gz;
   dim3 grid(gx, gy, gz);
-  const bool xl = a.xl_in != nullptr, e = a.e != nullptr;
-#define GD_ZO2(R, ACC)                                                          \
-  if (xl && e) return run_zouter<R, true, true, ACC>(m, a, zchunk, err, grid, st);  \
-  if (xl) return run_zouter<R, true, false, ACC>(m, a, zchunk, err, grid, st);      \
-  if (e) return run_zouter<R, false, true, ACC>(m, a, zchunk, err, grid, st);       \
-  return run_zouter<R, false, false, ACC>(m, a, zchunk, err, grid, st);
-#define GD_ZO(R)                \
-  if (a.accurate) {             \
-    GD_ZO2(R, true)             \
-  } else {                      \
-    GD_ZO2(R, false)            \
-  }
-  if (rhs_mode == RHS_EXPLICIT) { GD_ZO(RHS_EXPLICIT) }
-  if (rhs_mode == RHS_AD) { GD_ZO(RHS_AD) }
-  GD_ZO(RHS_SP)
-#undef GD_ZO
+  if (esz_e == 2) return run_zouter_t<half_t>(m, a, rhs_mode, zchunk, err, grid, st);
+  return run_zouter_t<float>(m, a, rhs_mode, zchunk, err, grid, st);
 }
 
 int zouter_max_blocks(int nx, int ny, int nz) {
