@@ -1302,22 +1302,21 @@ __global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constan
       if (RHS == RHS_EXPLICIT) {
         bh = ic;
       } else {
-        if (w) gx += ic - iw_;
-        if (e) gx += ic - ie;
-        if (s) gy += ic - is;
-        if (n) gy += ic - in_;
+        gx = (w ? ic - iw_ : 0.f) + (e ? ic - ie : 0.f);
+        gy = (s ? ic - is : 0.f) + (n ? ic - in_ : 0.f);
       }
       float rv;
       if (!ACCURATE) {
         // FP32 differences of the float pair: error ~1e-7 of the local terms
-        float dx = 0.f, dy = 0.f, dz = 0.f;
-        if (w) dx += (hc - hw) + (lc - lw);
-        if (e) dx += (hc - he) + (lc - le);
-        if (s) dy += (hc - hs) + (lc - ls);
-        if (n) dy += (hc - hn) + (lc - ln);
-        if (m) dz += (hc - hm) + (lc - lm);
-        if (p) dz += (hc - hp) + (lc - lp);
-        const float ax = a.bx * dx + a.by * dy + a.bz * dz + a.alpha * (hc + lc);
+        // (the low words enter only when the pair is carried)
+        auto d = [&](bool has, float h, float l) -> float {
+          if (!has) return 0.f;
+          return USE_L ? (hc - h) + (lc - l) : hc - h;
+        };
+        const float dx = d(w, hw, lw) + d(e, he, le);
+        const float dy = d(s, hs, ls) + d(n, hn, ln);
+        const float dz = d(m, hm, lm) + d(p, hp, lp);
+        const float ax = a.bx * dx + a.by * dy + a.bz * dz + a.alpha * (USE_L ? hc + lc : hc);
         if (RHS != RHS_EXPLICIT) {
           bh = a.rbx * gx + a.rby * gy;
           if (SP) bh += a.ralpha * i1;
