@@ -162,6 +162,32 @@ int gd_screened_poisson_slices(gd_stack *s, const float *I0, const float *I1, fl
                                gd_report *rep);
 
 /*
+ * gd_screened_poisson -- the general system of Sec. 4 with an explicit
+ * right-hand side: (alpha + bx Kx + by Ky + bz Kz) x = b, solved like the two
+ * steps above (float-pair refinement over float32 V(nu1,nu2)-cycles) to
+ * ||b - A x|| <= rel_tol ||b||.  Needs alpha > 0 (the system is then
+ * nonsingular) and beta_* >= 0; beta_z == 0 makes the slices independent.
+ *   b (in), x (out): stack arrays; x must not alias b.
+ *   x0 (in, nullable): initial guess (default zero); may alias x.
+ */
+int gd_screened_poisson(gd_stack *s, gd_weights w, const float *b, float *x, const gd_solve_ctl *ctl,
+                        const float *x0, gd_report *rep);
+
+/*
+ * gd_npr_rhs -- right-hand side of the NPR gradient filter of Sec. 7 (after
+ * Bhat et al. 2010, Sec. 6.2): b = alpha I0 - div(W V) with the target
+ * gradients V = lambda (1 - exp(-|grad I0|^2 / (2 sigma^2))) grad I0, for
+ * gd_screened_poisson with the same weights (the paper's video example:
+ * alpha = 0.001, W = Diag(1, 1, 0.1), lambda = 1.25, sigma = 5).
+ * Gradients are forward differences on voxel faces, none leaving the
+ * domain; the face p -> p + e_d is modulated by the norm of the
+ * forward-difference vector at its lower voxel p.
+ *   I0 (in), b (out): stack arrays (device or host), b must not alias I0.
+ *   w: alpha and the gradient weights W; sigma > 0.
+ */
+int gd_npr_rhs(gd_stack *s, const float *I0, float *b, gd_weights w, double lambda, double sigma);
+
+/*
  * gd_vcycle -- ncycles plain float32 V-cycles (Sec. 4.1) on A x = b with an
  * explicit right-hand side, A = alpha + bx Kx + by Ky + bz Kz (Sec. 4 general
  * form).  system: GD_SYSTEM_AD (3D coupling, needs bz > 0) or GD_SYSTEM_SP

@@ -33,7 +33,7 @@ GD_HISTORY = 64
 EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_vcycle",
            "gd_destroy", "gd_residual", "gd_smooth", "gd_profile_enable", "gd_profile_reset",
            "gd_profile_query", "gd_launch_count", "gd_status_string", "gd_last_error",
-           "gd_version", "gd_smooth_noalloc")
+           "gd_version", "gd_smooth_noalloc", "gd_screened_poisson", "gd_npr_rhs")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -107,6 +107,9 @@ def lib():
                 "gd_last_error": (ctypes.c_char_p, [P]),
                 "gd_version": (I, []),
                 "gd_smooth_noalloc": (I, [I, I, I, GdWeights, P, P, I, P]),
+                "gd_screened_poisson": (I, [P, GdWeights, P, P, ctypes.POINTER(GdSolveCtl), P,
+                                            ctypes.POINTER(GdReport)]),
+                "gd_npr_rhs": (I, [P, P, P, GdWeights, D, D]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -240,6 +243,26 @@ def gd_screened_poisson_slices(s: Stack, I0, I1, I2, alpha: float,
     if raise_on_error:
         _check(st, s, ok=(GD_OK, GD_ERR_NOT_CONVERGED))
     return rep.to_dict()
+
+
+def gd_screened_poisson(s: Stack, w, b, x, ctl: Optional[GdSolveCtl] = None, x0=None,
+                        raise_on_error: bool = True) -> dict:
+    """(alpha + bx Kx + by Ky + bz Kz) x = b; w = (alpha, bx, by, bz)."""
+    rep = GdReport()
+    st = lib().gd_screened_poisson(s.handle, _weights(w), _ptr(b, s.n, "b"), _ptr(x, s.n, "x"),
+                                   ctypes.byref(ctl) if ctl is not None else None,
+                                   _ptr(x0, s.n, "x0"), ctypes.byref(rep))
+    if raise_on_error:
+        _check(st, s, ok=(GD_OK, GD_ERR_NOT_CONVERGED))
+    return rep.to_dict()
+
+
+def gd_npr_rhs(s: Stack, I0, b, w, lam: float, sigma: float) -> int:
+    """b = alpha I0 - div(W V) of the NPR filter; w = (alpha, wx, wy, wz)."""
+    st = lib().gd_npr_rhs(s.handle, _ptr(I0, s.n, "I0"), _ptr(b, s.n, "b"), _weights(w),
+                          float(lam), float(sigma))
+    _check(st, s)
+    return st
 
 
 def gd_vcycle(s: Stack, system: int, w, b, x, ncycles: int, raise_on_error: bool = True) -> dict:

@@ -49,6 +49,9 @@ struct Level {
   int esz = 4;
 };
 
+// internal system id of the general screened Poisson solve (explicit b)
+constexpr int SYS_GENERIC = 2;
+
 struct ProfRec {
   int cls;
   cudaEvent_t a, b;
@@ -844,10 +847,12 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   const bool out_host = !is_device_ptr(outh);
   if ((st = resolve(s, I0h, true, 0, &I0)) != GD_OK) return report(rep, st);
   if (system == GD_SYSTEM_SP && (st = resolve(s, I1h, true, 1, &I1)) != GD_OK) return report(rep, st);
+  const bool generic = system == SYS_GENERIC;  // I0 holds the explicit right-hand side
   if ((st = resolve(s, outh, x0h == outh, 2, &out)) != GD_OK) return report(rep, st);
   if (x0h && x0h != outh && (st = resolve(s, x0h, true, 3, &x0)) != GD_OK) return report(rep, st);
   if (x0h == outh) x0 = out;
-  if ((st = plan_build(s, w, system == GD_SYSTEM_SP, ctl.coarsest_xy, s->prec)) != GD_OK)
+  const bool uncoupled = system == GD_SYSTEM_SP || (generic && w[3] == 0.0);
+  if ((st = plan_build(s, w, uncoupled, ctl.coarsest_xy, s->prec)) != GD_OK)
     return report(rep, st);
   Plan &P = *s->cur;
   if (!s->xh2 && (st = dalloc(s, &s->xh2, n)) != GD_OK) return report(rep, st);
@@ -873,11 +878,14 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
   std::memset(&a, 0, sizeof a);
   if (system == GD_SYSTEM_SP)
     set_weights(a, w[1], w[2], 0.0, w[0], 1.0, 1.0, w[0]);
+  else if (generic)
+    set_weights(a, w[1], w[2], w[3], w[0], 0.0, 0.0, 0.0);
   else
     set_weights(a, w[1], w[2], w[3], 0.0, w[1], w[2], 0.0);
   a.I0 = I0;
   a.I1 = I1;
-  const int rhs = system == GD_SYSTEM_SP ? RHS_SP : RHS_AD;
+  a.b = generic ? I0 : nullptr;
+  const int rhs = generic ? RHS_EXPLICIT : (system == GD_SYSTEM_SP ? RHS_SP : RHS_AD);
   const int mean_fix = system == GD_SYSTEM_AD;
   Level &F = P.L[0];
   const int esz = F.esz;  // storage of the correction solve (4, or 2 when mixed)
@@ -1101,6 +1109,44 @@ int gd_screened_poisson_slices(gd_stack *s, const float *I0, const float *I1, fl
   }
   double wv[4] = {alpha, 1.0, 1.0, 0.0};
   return solve(s, GD_SYSTEM_SP, I0, I1, I2, wv, ctl, x0, rep);
+}
+
+int gd_screened_poisson(gd_stack *s, gd_weights w, const float *b, float *x, const gd_solve_ctl *ctl,
+                        const float *x0, gd_report *rep) {
+  rep_init(rep);
+  if (!s || !b || !x) return report(rep, GD_ERR_INVALID_ARG);
+  if (x == b) {
+    set_err(s, "x must not alias b");
+    return report(rep, GD_ERR_INVALID_ARG);
+  }
+  if (!weights_ok(w) || !(w.alpha > 0.0)) {
+    set_err(s, "the general solve needs finite weights >= 0 and alpha > 0");
+    return report(rep, GD_ERR_INVALID_ARG);
+  }
+  double wv[4] = {w.alpha, w.beta_x, w.beta_y, w.beta_z};
+  return solve(s, SYS_GENERIC, b, nullptr, x, wv, ctl, x0, rep);
+}
+
+int gd_npr_rhs(gd_stack *s, const float *I0h, float *bh, gd_weights w, double lambda, double sigma) {
+  if (!s || !I0h || !bh || I0h == bh || !weights_ok(w) || !std::isfinite(lambda) ||
+      !std::isfinite(sigma) || !(sigma > 0.0))
+    return GD_ERR_INVALID_ARG;
+  int st;
+  if ((st = ensure_common(s)) != GD_OK) return st;
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  float *I0 = nullptr, *b = nullptr;
+  const bool b_host = !is_device_ptr(bh);
+  if ((st = resolve(s, I0h, true, 0, &I0)) != GD_OK) return st;
+  if ((st = resolve(s, bh, false, 2, &b)) != GD_OK) return st;
+  {
+    ProfScope ps(s, P_COPY, (double)n * 8.0);
+    CK(launch_npr_rhs(I0, b, s->nx, s->ny, s->nz, w.alpha, w.beta_x, w.beta_y, w.beta_z, lambda, sigma,
+                      s->stream));
+  }
+  if (b_host) CK(cudaMemcpyAsync(bh, b, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->prof_on) prof_collect(s);
+  return GD_OK;
 }
 
 int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh, int ncycles,

@@ -109,6 +109,9 @@ cudaError_t launch_fdm(int nx, int ny, int nz, const float *Vx, const float *Vy,
                        cudaStream_t st);
 cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st);
 cudaError_t launch_copy(float *dst, const float *src, size_t n, cudaStream_t st);
+// b = alpha I0 - div(W V) of the NPR gradient filter (gd_kernels.cu)
+cudaError_t launch_npr_rhs(const float *I0, float *b, int nx, int ny, int nz, double alpha, double wx,
+                           double wy, double wz, double lam, double sigma, cudaStream_t st);
 
 // Host: symmetric eigen-decomposition (cyclic Jacobi), FP64, row-major a[n*n].
 // On return w holds the eigenvalues and v (row-major, column k = eigenvector k).

@@ -81,3 +81,27 @@ def test_binding_marshalling_rejects_wrong_dtype(lib):
     with pytest.raises(ValueError):
         gd._ptr(np.zeros(7, np.float32), 8, "x")
     assert gd._ptr(None) is None
+
+
+def test_general_solve_and_npr_validation_without_gpu(lib):
+    """Argument checks of gd_screened_poisson / gd_npr_rhs return before any
+    CUDA call."""
+    h = ctypes.c_void_p()
+    assert lib.gd_stack_create(ctypes.byref(h), 8, 8, 8, 0, 0, 0, None) == gd.GD_OK
+    s = gd.Stack(h, 8, 8, 8)
+    try:
+        buf = (ctypes.c_float * 512)()
+        buf2 = (ctypes.c_float * 512)()
+        rep = gd.GdReport()
+        p, q = ctypes.cast(buf, ctypes.c_void_p), ctypes.cast(buf2, ctypes.c_void_p)
+        # alpha must be > 0
+        assert lib.gd_screened_poisson(s.handle, gd.GdWeights(0.0, 1, 1, 1), p, q, None, None,
+                                       ctypes.byref(rep)) == gd.GD_ERR_INVALID_ARG
+        # x aliasing b
+        assert lib.gd_screened_poisson(s.handle, gd.GdWeights(0.1, 1, 1, 1), p, p, None, None,
+                                       ctypes.byref(rep)) == gd.GD_ERR_INVALID_ARG
+        # sigma must be > 0, b must not alias I0
+        assert lib.gd_npr_rhs(s.handle, p, q, gd.GdWeights(0.001, 1, 1, 0.1), 1.25, 0.0) == gd.GD_ERR_INVALID_ARG
+        assert lib.gd_npr_rhs(s.handle, p, p, gd.GdWeights(0.001, 1, 1, 0.1), 1.25, 5.0) == gd.GD_ERR_INVALID_ARG
+    finally:
+        gd.gd_destroy(s)
