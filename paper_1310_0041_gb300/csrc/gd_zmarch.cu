@@ -199,8 +199,8 @@ __host__ __device__ constexpr int pad128(int n) {
 
 
 
-// Sweep tiles are 64 x 32: eight tile warps (two float4 cells per thread)
-// and one service warp (TMA issue, mbarrier polling, the red ring).
+// Sweep tiles are 64 x 32: eight tile warps (two float4 cells per thread),
+// a service warp (TMA issue, mbarrier polling) and a ring warp (the red ring).
 constexpr int SY = 32;  // sweep tile rows
 
 template <typename T>
@@ -221,10 +221,11 @@ struct SweepGeo {
   static constexpr int BOFF = XR * XS;           // b slots
   static constexpr int MOFF = BOFF + BR * BS;    // mbarriers (element offset)
   static constexpr int TILE_WARPS = 8;
-  static constexpr int NT = 32 * (TILE_WARPS + 1);  // + the service warp
+  static constexpr int NT = 32 * (TILE_WARPS + 2);  // + the service and ring warps
   static constexpr int SVC = 32 * TILE_WARPS;       // first thread of the service warp
   // red ring cells of one colour: the in-plane neighbours of tile cells that
-  // lie outside the tile (corners are nobody's neighbour)
+  // lie outside the tile (corners are nobody's neighbour), relaxed by the
+  // ring warp while the service warp issues copies and polls
   static constexpr int NRING = ZX + SY;          // (2 ZX + 2 SY) / 2
   static constexpr int RING_IT = NRING / 32;
   static_assert(NRING % 32 == 0, "ring cells per lane");
@@ -262,7 +263,9 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
   const LevelDev &L = a.L;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool tile = warp < G::TILE_WARPS;
   const bool svc = warp == G::TILE_WARPS;
+  const bool rwarp = warp == G::TILE_WARPS + 1;
   const int i0 = blockIdx.x * ZX, j0 = blockIdx.y * SY;
   const int zs = blockIdx.z * a.zchunk, ze = min(zs + a.zchunk, nz);
   const int t0 = zc ? zs - 1 : zs;
@@ -394,12 +397,12 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
   const int c4 = lane & 15;
   const int r0 = 4 * ((warp & 7) >> 1) + (warp & 1) + 2 * (lane >> 4);
   const int gi = i0 + 4 * c4, gj0 = j0 + r0, gj1 = gj0 + 16;
-  const bool act0 = !svc && gi < nx && gj0 < ny;  // nx % 4 == 0: all four cells or none
-  const bool act1 = !svc && gi < nx && gj1 < ny;
+  const bool act0 = tile && gi < nx && gj0 < ny;  // nx % 4 == 0: all four cells or none
+  const bool act1 = tile && gi < nx && gj1 < ny;
   const int so0 = (r0 + H) * W + OFF + 4 * c4, so1 = so0 + 16 * W;
   const int go0 = gj0 * nx + gi, go1 = go0 + 16 * nx;  // in-plane offsets
 
-  // ---- service warp: red ring cell m of this lane for colour class P ----
+  // ---- ring warp: red ring cell m of this lane for colour class P ----
   // Class P holds the cells with (col + row) & 1 = P (i0 + j0 even), so the
   // red ring of plane t is class t & 1.  Decoded on the fly (no registers
   // held across the loop); off < 0 marks a cell outside the domain.
@@ -535,7 +538,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
       if (do_red) {
         const PlaneK k = plane_k(t);
         const int bs = bo(t) - W;  // b rows start one row below x rows
-        if (!svc) {
+        if (tile) {
           bv0 = lds4(bs + so0);
           bv1 = lds4(bs + so1);
           float4 xc0 = zero4, xu0 = zero4, xd0 = zero4, xp0 = zero4, xm0 = zero4;
@@ -592,7 +595,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
           else cc0 = zero4;
           if (act1) sts4(xs_t + so1, cc1);
           else cc1 = zero4;
-        } else {
+        } else if (rwarp) {
           // red ring cells of plane t
 #pragma unroll
           for (int m = 0; m < G::RING_IT; ++m) {
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
 
       // ---- black pass of plane pb = t - lagb ----
       const int pb = t - lagb;
-      if (!svc) {
+      if (tile) {
         if (pb >= blk_lo && pb <= blk_hi) {
           const PlaneK k = plane_k(pb);
           const int xob = zc ? xs_m : xs_t;
