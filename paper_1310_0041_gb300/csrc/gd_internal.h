@@ -71,6 +71,7 @@ struct ZSweepArgs {
   int fx, fy, fz;       // axes coarsened from this level to the next
   void *bc;             // restriction: next level's right-hand side
   int zchunk;           // set by the launcher
+  int cpf;              // set by the launcher: prolongation prefetches the coarse level
   double *partials;     // SUM: per-block sums of the output, slot S_E
   double *err;          // set to 1 when a bounded wait gives up
 };

@@ -84,6 +84,12 @@ __device__ __forceinline__ void tma_plane(void *dst, const CUtensorMap *map, int
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(su32(bar))
       : "memory");
 }
+// L2 prefetch of one box of a tensor (no shared memory, no completion)
+__device__ __forceinline__ void prefetch_plane(const CUtensorMap *map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map),
+               "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -244,6 +250,7 @@ struct SweepGeo {
 template <typename T, typename TC, bool ZERO_IN, bool PROLONG, bool SUM, bool UNIFORM, bool COUPLED>
 __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
                                                                const __grid_constant__ CUtensorMap tmb,
+                                                               const __grid_constant__ CUtensorMap tmc,
                                                                const ZSweepArgs a) {
   using G = SweepGeo<T>;
   using S = St<T>;
@@ -285,6 +292,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
     abort_flag = 0;
     int e = tma_preflight(zsm, G::smem_bytes(), &tmx);
     if (!e) e = tma_preflight(zsm, G::smem_bytes(), &tmb);
+    if (!e && PROLONG && a.cpf) e = tma_preflight(zsm, G::smem_bytes(), &tmc);
     if (e) {
       abort_flag = e;
       a.err[0] = (double)e;
@@ -526,6 +534,14 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
         fence_proxy_async();
         issue_x(x_issue_at(t));
         issue_b(t + PFS);
+        // prolongation: warm L2 with the coarse box the correction of a
+        // plane two steps on reads (its loads then hit L2)
+        if (PROLONG) {
+          const int pn = (zc ? t + 2 : t + 1) + 2;
+          constexpr int AC = 16 / (int)sizeof(TC);  // TMA x alignment in coarse elements
+          if (a.cpf && pn <= rx.hi)
+            prefetch_plane(&tmc, a.fx ? (i0 >> 1) - AC : i0 - OFF, (j0 - H) >> a.fy, pn >> a.fz);
+        }
       }
       const int xs_p = (xs_t == (G::XR - 1) * XS) ? 0 : xs_t + XS;   // plane t + 1
       const int xs_m = (xs_t == 0) ? (G::XR - 1) * XS : xs_t - XS;   // plane t - 1
@@ -1568,8 +1584,8 @@ int pick_zchunk(int tiles, int nz, bool coupled, int ctas_per_sm) {
 }
 
 template <typename T, typename TC, bool Z, bool P, bool S, bool U, bool C>
-cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
-                          dim3 grid, cudaStream_t st) {
+cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc,
+                          const ZSweepArgs &a, dim3 grid, cudaStream_t st) {
   const size_t bytes = SweepGeo<T>::smem_bytes();
   static bool attr = false;
   if (!attr) {
@@ -1577,30 +1593,31 @@ cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const ZS
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_zsweep<T, TC, Z, P, S, U, C><<<grid, SweepGeo<T>::NT, bytes, st>>>(mx, mb, a);
+  k_zsweep<T, TC, Z, P, S, U, C><<<grid, SweepGeo<T>::NT, bytes, st>>>(mx, mb, mc, a);
   return cudaGetLastError();
 }
 bool level_uniform(const LevelDev &L) { return L.sx == L.lx && L.sy == L.ly && L.sz == L.lz; }
 bool level_coupled(const LevelDev &L) { return L.wz != 0.f && L.nz > 1; }
 template <typename T, typename TC, bool Z, bool P, bool S>
-cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a, dim3 grid,
-                       cudaStream_t st) {
+cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc,
+                       const ZSweepArgs &a, dim3 grid, cudaStream_t st) {
   const bool u = level_uniform(a.L), c = level_coupled(a.L);
-  if (u && c) return run_zsweep_uc<T, TC, Z, P, S, true, true>(mx, mb, a, grid, st);
-  if (u) return run_zsweep_uc<T, TC, Z, P, S, true, false>(mx, mb, a, grid, st);
-  if (c) return run_zsweep_uc<T, TC, Z, P, S, false, true>(mx, mb, a, grid, st);
-  return run_zsweep_uc<T, TC, Z, P, S, false, false>(mx, mb, a, grid, st);
+  if (u && c) return run_zsweep_uc<T, TC, Z, P, S, true, true>(mx, mb, mc, a, grid, st);
+  if (u) return run_zsweep_uc<T, TC, Z, P, S, true, false>(mx, mb, mc, a, grid, st);
+  if (c) return run_zsweep_uc<T, TC, Z, P, S, false, true>(mx, mb, mc, a, grid, st);
+  return run_zsweep_uc<T, TC, Z, P, S, false, false>(mx, mb, mc, a, grid, st);
 }
 // the five sweep variants of a V-cycle; the coarse type matters only with
 // the prolongation
 template <typename T, typename TC>
-cudaError_t run_zsweep_variant(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
-                               bool zero_in, bool prolong, bool sum, dim3 grid, cudaStream_t st) {
-  if (zero_in && !prolong && !sum) return run_zsweep<T, T, true, false, false>(mx, mb, a, grid, st);
-  if (!zero_in && prolong && !sum) return run_zsweep<T, TC, false, true, false>(mx, mb, a, grid, st);
-  if (!zero_in && prolong && sum) return run_zsweep<T, TC, false, true, true>(mx, mb, a, grid, st);
-  if (!zero_in && !prolong && !sum) return run_zsweep<T, T, false, false, false>(mx, mb, a, grid, st);
-  if (!zero_in && !prolong && sum) return run_zsweep<T, T, false, false, true>(mx, mb, a, grid, st);
+cudaError_t run_zsweep_variant(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc,
+                               const ZSweepArgs &a, bool zero_in, bool prolong, bool sum, dim3 grid,
+                               cudaStream_t st) {
+  if (zero_in && !prolong && !sum) return run_zsweep<T, T, true, false, false>(mx, mb, mc, a, grid, st);
+  if (!zero_in && prolong && !sum) return run_zsweep<T, TC, false, true, false>(mx, mb, mc, a, grid, st);
+  if (!zero_in && prolong && sum) return run_zsweep<T, TC, false, true, true>(mx, mb, mc, a, grid, st);
+  if (!zero_in && !prolong && !sum) return run_zsweep<T, T, false, false, false>(mx, mb, mc, a, grid, st);
+  if (!zero_in && !prolong && sum) return run_zsweep<T, T, false, false, true>(mx, mb, mc, a, grid, st);
   return cudaErrorNotSupported;
 }
 template <typename T, typename TC, bool U, bool C>
@@ -1680,9 +1697,22 @@ cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zer
   const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
   if (nblocks_out) *nblocks_out = gx * gy * gz;
   dim3 grid(gx, gy, gz);
-  if (esz == 4) return run_zsweep_variant<float, float>(mx, mb, a, zero_in, prolong, sum, grid, st);
-  if (esz_c == 2 || !prolong) return run_zsweep_variant<half_t, half_t>(mx, mb, a, zero_in, prolong, sum, grid, st);
-  return run_zsweep_variant<half_t, float>(mx, mb, a, zero_in, prolong, sum, grid, st);
+  // prolongation: a map over the coarse level for the L2 prefetch of the
+  // boxes the correction reads (x: 32 coarse cells + alignment margins when
+  // x is coarsened, else the fine box; y: the 36 fine box rows)
+  CUtensorMap mc = mx;
+  a.cpf = 0;
+  if (prolong) {
+    const int ac = 16 / esz_c, ncz = a.fz ? (L.nz + 1) / 2 : L.nz;
+    const int cw = a.fx ? 32 + 2 * ac : box_w(esz), ch = a.fy ? rows_x / 2 : rows_x;
+    // (a coarse level whose rows break TMA's alignment is simply not prefetched)
+    a.cpf = make_map(&mc, a.xc, a.ncx, a.ncy, ncz, cw, ch, esz_c) ? 1 : 0;
+    if (!a.cpf) mc = mx;
+  }
+  if (esz == 4) return run_zsweep_variant<float, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
+  if (esz_c == 2 || !prolong)
+    return run_zsweep_variant<half_t, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
+  return run_zsweep_variant<half_t, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
 }
 
 cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz, int esz_c, cudaStream_t st) {
