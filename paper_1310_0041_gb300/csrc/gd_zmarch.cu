@@ -1108,7 +1108,7 @@ struct OuterGeo {
 // and from its own registers (z), so no thread writes shared memory and the
 // planes stream through a producer/consumer ring without CTA barriers.
 template <typename TE, int RHS, bool HAS_XL, bool HAS_E, bool ACCURATE>
-__global__ void __launch_bounds__(OuterGeo::NT, 2) k_zouter(const __grid_constant__ CUtensorMap tmh,
+__global__ void __launch_bounds__(OuterGeo::NT, ACCURATE ? 2 : 3) k_zouter(const __grid_constant__ CUtensorMap tmh,
                                                             const __grid_constant__ CUtensorMap tml,
                                                             const __grid_constant__ CUtensorMap tme,
                                                             const __grid_constant__ CUtensorMap tmi0,
