@@ -54,7 +54,7 @@ NPR_TOL = 1e-8
 # full-size launch is that ratio times its algorithmic bytes.  Valid only while
 # the kernel source is the one it was taken from.
 NCU_TRAFFIC = {
-    "rb_sweep_fine": {"dram_over_alg": 1430.3 / 1543.6, "src_sha256": "26e52adc929a9617b761165168624ec61cbb64b5aebd44e50d218d0716dede3e"},
+    "rb_sweep_fine": {"dram_over_alg": 1429.7 / 1543.6, "src_sha256": "33525bcd7a41689c53539a47a8fda5f828702b2dcf9b175d22e3d83f8ac490f0"},
 }
 
 
@@ -98,7 +98,7 @@ def barrier(world: int):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -113,13 +113,17 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
             return
         self.th = threading.Thread(target=self._read, daemon=True)
         self.th.start()
+        # the timed region starts once the sampler is producing rows
+        t0 = time.perf_counter()
+        while not self.rows and time.perf_counter() - t0 < 3.0:
+            time.sleep(0.02)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -271,8 +275,6 @@ def run_gpu(args):
     barrier(world)
     clocks = ClockSampler(local if world > 1 else 0)
     clocks.start()
-    gd.gd_profile_reset(s)
-    gd.gd_profile_enable(s, True)
     launches0 = gd.gd_launch_count(s)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -286,6 +288,15 @@ def run_gpu(args):
     barrier(world)
     ms_local = e0.elapsed_time(e1)
     launches = gd.gd_launch_count(s) - launches0
+    # per-kernel durations: the same K steps again with a CUDA event pair
+    # around every launch (event nodes in the captured V-cycles); the events
+    # stretch the step, so this pass gives the kernel figures, not the value
+    reps.clear()
+    gd.gd_profile_reset(s)
+    gd.gd_profile_enable(s, True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
     gd.gd_profile_enable(s, False)
     prof = gd.gd_profile_all(s)
     clk = clocks.stop()
@@ -415,6 +426,8 @@ def run_gpu(args):
                        "alpha": ALPHA, "rel_tol": TOL, "rel_tol_sp": TOL_SP, "cycle": "V(2,2)", "coarsest_xy": 16,
                        "precision": "fp32 kernels, float-pair fine iterate",
                        "l2": "inputs larger than L2 (537 MB per array), no flush",
+                       "kernel_timing": "a second pass of the same steps with a CUDA event pair "
+                                        "around every launch",
                        "parallelism": "replicas" if world > 1 else "single"},
             "solver": {"ad_cycles": r1["cycles"], "ad_rel_residual": r1["rel_residual"],
                        "ad_levels": r1["levels"], "sp_cycles": r2["cycles"],
@@ -459,7 +472,7 @@ def run_ncu_case(args):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
