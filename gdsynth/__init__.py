@@ -103,3 +103,56 @@ def sp_pair(n: int, seed: int):
     i0 = em_stack(n, n, 1, seed=seed)[0]
     i1 = em_stack(n, n, 1, seed=seed, photo_seed=seed * 2 + 7, noise_sigma=0.0)[0]
     return i0, i1
+
+
+# ---------------------------------------------------------------------------
+# batches of independent slices of different sizes
+# ---------------------------------------------------------------------------
+def batch_sides(n: int, lo: int = 256, hi: int = 4096, seed: int = 0) -> list:
+    """``n`` integer slice sides, log-uniform in ``[lo, hi]``."""
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(np.log(lo), np.log(hi + 1.0), n)
+    return [int(v) for v in np.clip(np.floor(np.exp(u)), lo, hi)]
+
+
+def batch_alphas(n: int, lo: float = 0.001, hi: float = 0.1, seed: int = 0) -> list:
+    """``n`` screening weights, uniform in ``[lo, hi)``."""
+    rng = np.random.default_rng(seed + 7919)
+    return [float(v) for v in rng.uniform(lo, hi, n)]
+
+
+def batch_slices(nx, ny, seed: int = 0):
+    """(I0, I1) lists of float32 ``[ny_s][nx_s]`` slices.  Every slice is a
+    crop, at a seeded offset, of one synthetic EM slice as large as the
+    largest (so a batch costs one slice's generation); I1 is the crop with a
+    fresh per-slice gain ~U(0.85, 1.15), offset ~U(-15, 15) and a linear ramp
+    of amplitude ~U(-10, 10) across the slice, standing in for the output of
+    a previous step."""
+    W, H = max(nx), max(ny)
+    master = em_stack(W, H, 1, seed=seed, ncells=default_cells(W, H))[0].astype(np.float32)
+    rng = np.random.default_rng(seed + 104729)
+    I0s, I1s = [], []
+    for a, b in zip(nx, ny):
+        x0 = int(rng.integers(0, W - a + 1))
+        y0 = int(rng.integers(0, H - b + 1))
+        i0 = np.ascontiguousarray(master[y0:y0 + b, x0:x0 + a])
+        g, o, r = rng.uniform(0.85, 1.15), rng.uniform(-15, 15), rng.uniform(-10, 10)
+        ramp = np.linspace(-r, r, a, dtype=np.float32)[None, :] if a > 1 else np.zeros((1, 1), np.float32)
+        i1 = np.clip(g * i0 + o + ramp, 0.0, 255.0).astype(np.float32)
+        I0s.append(i0)
+        I1s.append(np.ascontiguousarray(i1))
+    return I0s, I1s
+
+
+def pack(slices) -> np.ndarray:
+    """Concatenates 2D slices (x fastest) into one float32 array."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(s, np.float32).ravel() for s in slices]))
+
+
+def unpack(flat, nx, ny) -> list:
+    """Splits a packed array into ``[ny_s][nx_s]`` slices (views)."""
+    out, o = [], 0
+    for a, b in zip(nx, ny):
+        out.append(np.asarray(flat[o:o + a * b]).reshape(b, a))
+        o += a * b
+    return out

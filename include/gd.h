@@ -254,6 +254,65 @@ int gd_profile_query(gd_stack *s, int k, char *name, int name_len, long long *la
 int gd_smooth_noalloc(int nx, int ny, int nz, gd_weights w, const float *b, float *x, int nsweeps,
                       void *cuda_stream);
 
+/*
+ * ---- Batched screened Poisson on slices of different sizes ----
+ *
+ * The screened Poisson step of Sec. 3.1 (Eq. screened_poisson), solved on
+ * independent 2D slices: slice s (nx_s x ny_s cells, weight alpha_s > 0)
+ * solves (alpha_s + Kx + Ky) I2 = alpha_s I1 + (Kx + Ky) I0 with the 6-point
+ * "Constant" stencil of Sec. 4.2 (Neumann boundary).  The slices decouple
+ * (the step has no z term), so one multigrid V-cycle (Sec. 4.1) runs over
+ * all of them at once: each slice has its own 2D hierarchy (the stack
+ * solver's coarsening rule), every kernel is one launch over the tiles of
+ * all slices at a depth, each slice's coarsest level is solved exactly, and
+ * the cycle is replayed from a CUDA graph.
+ *
+ * Array layout: one packed float32 array per quantity; slice s occupies
+ * elements [off_s, off_s + nx_s ny_s), x fastest, off_s = sum over t < s of
+ * nx_t ny_t (gd_batch_offset).  Device pointers are used in place; host
+ * pointers are staged through buffers the batch allocates on first use.
+ */
+typedef struct gd_batch gd_batch;
+
+/*
+ * gd_batch_create -- plans the hierarchies and allocates the packed levels.
+ *   nslices >= 1; nx[s], ny[s] in [1, 2^20]; alpha[s] finite and > 0 (the
+ *     arrays are copied);
+ *   coarsest_xy: an axis is not halved below this many cells (0 means 16);
+ *   stream: a cudaStream_t (NULL: the legacy default stream).
+ * GD_ERR_UNSUPPORTED if a slice's coarsest level would hold more than 4096
+ * cells (aspect ratios above about 256:1); GD_ERR_OOM on allocation failure.
+ * On failure *out is NULL and gd_batch_last_error(NULL) holds the reason.
+ */
+int gd_batch_create(gd_batch **out, int nslices, const int *nx, const int *ny, const double *alpha,
+                    int coarsest_xy, void *stream);
+
+/*
+ * gd_batch_screened_poisson -- V(nu1, nu2) cycles until every slice's
+ * relative residual ||b_s - A_s x_s|| / ||b_s|| is <= ctl->rel_tol, or
+ * ctl->max_cycles cycles.  The iterate is float32 (its rounding bounds the
+ * attainable relative residual near 1e-6); nu1 + nu2 must be even;
+ * ctl->coarsest_xy must be 0 or the batch's.
+ *   I0, I1 (in), I2 (out): packed arrays of gd_batch_voxels() floats;
+ *   x0 (in, nullable): initial guess (default I0);
+ *   rep (out, nullable): status, cycles, levels (deepest hierarchy),
+ *     rel_residual (max over slices), rhs_norm (over all slices), history
+ *     (max relative residual before cycle 1 and after each cycle);
+ *   slice_rel (out, nullable): [nslices] final relative residual per slice.
+ * Returns GD_ERR_NOT_CONVERGED (I2 still written) when the tolerance is not
+ * met, GD_ERR_DIVERGED when a residual is not finite.
+ */
+int gd_batch_screened_poisson(gd_batch *b, const float *I0, const float *I1, float *I2,
+                              const gd_solve_ctl *ctl, const float *x0, gd_report *rep,
+                              double *slice_rel);
+
+long long gd_batch_voxels(const gd_batch *b);            /* total cells, -1 for NULL */
+long long gd_batch_offset(const gd_batch *b, int slice); /* off_s, -1 if out of range */
+int gd_batch_levels(const gd_batch *b);                  /* depth of the deepest hierarchy */
+long long gd_batch_launch_count(const gd_batch *b);      /* kernel launches since creation */
+const char *gd_batch_last_error(const gd_batch *b);
+int gd_batch_destroy(gd_batch *b);
+
 /* Number of kernel launches the stack has enqueued since creation. */
 long long gd_launch_count(gd_stack *s);
 

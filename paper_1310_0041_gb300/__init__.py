@@ -33,7 +33,9 @@ GD_HISTORY = 64
 EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_vcycle",
            "gd_destroy", "gd_residual", "gd_smooth", "gd_profile_enable", "gd_profile_reset",
            "gd_profile_query", "gd_launch_count", "gd_status_string", "gd_last_error",
-           "gd_version", "gd_smooth_noalloc", "gd_screened_poisson", "gd_npr_rhs")
+           "gd_version", "gd_smooth_noalloc", "gd_screened_poisson", "gd_npr_rhs",
+           "gd_batch_create", "gd_batch_screened_poisson", "gd_batch_voxels", "gd_batch_offset",
+           "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -110,6 +112,16 @@ def lib():
                 "gd_screened_poisson": (I, [P, GdWeights, P, P, ctypes.POINTER(GdSolveCtl), P,
                                             ctypes.POINTER(GdReport)]),
                 "gd_npr_rhs": (I, [P, P, P, GdWeights, D, D]),
+                "gd_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                        ctypes.POINTER(D), I, P]),
+                "gd_batch_screened_poisson": (I, [P, P, P, P, ctypes.POINTER(GdSolveCtl), P,
+                                                  ctypes.POINTER(GdReport), ctypes.POINTER(D)]),
+                "gd_batch_voxels": (ctypes.c_longlong, [P]),
+                "gd_batch_offset": (ctypes.c_longlong, [P, I]),
+                "gd_batch_levels": (I, [P]),
+                "gd_batch_launch_count": (ctypes.c_longlong, [P]),
+                "gd_batch_last_error": (ctypes.c_char_p, [P]),
+                "gd_batch_destroy": (I, [P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -332,6 +344,86 @@ def gd_launch_count(s: Stack) -> int:
 
 def gd_status_string(st: int) -> str:
     return lib().gd_status_string(st).decode()
+
+
+class Batch:
+    """Handle returned by gd_batch_create (holds the opaque gd_batch*)."""
+
+    def __init__(self, handle, nx, ny, alpha):
+        self.handle = handle
+        self.nx, self.ny, self.alpha = list(nx), list(ny), list(alpha)
+        self.ns = len(self.nx)
+        self.n = sum(a * b for a, b in zip(self.nx, self.ny))
+
+    def __repr__(self):
+        return "Batch(%d slices, %d cells)" % (self.ns, self.n)
+
+    @property
+    def last_error(self) -> str:
+        return gd_batch_last_error(self)
+
+
+def gd_batch_create(nx, ny, alpha, coarsest_xy: int = 0, stream=None) -> Batch:
+    """Plans the batch of slices nx[s] x ny[s] with screening weights alpha[s]."""
+    nx, ny, alpha = [int(v) for v in nx], [int(v) for v in ny], [float(v) for v in alpha]
+    ns = len(nx)
+    if len(ny) != ns or len(alpha) != ns:
+        raise ValueError("nx, ny and alpha must have the same length")
+    if stream is None:
+        stream = _default_stream()
+    h = ctypes.c_void_p()
+    st = lib().gd_batch_create(ctypes.byref(h), ns, (ctypes.c_int * ns)(*nx), (ctypes.c_int * ns)(*ny),
+                               (ctypes.c_double * ns)(*alpha), int(coarsest_xy),
+                               ctypes.c_void_p(stream) if stream else None)
+    if st != GD_OK:
+        raise GdError(st, gd_batch_last_error(None))
+    return Batch(h, nx, ny, alpha)
+
+
+def gd_batch_screened_poisson(b: Batch, I0, I1, I2, ctl: Optional[GdSolveCtl] = None, x0=None,
+                              raise_on_error: bool = True, slice_rel: bool = False) -> dict:
+    """Packed arrays of b.n floats; returns the report (+ 'slice_rel' if asked)."""
+    rep = GdReport()
+    sr = (ctypes.c_double * b.ns)() if slice_rel else None
+    st = lib().gd_batch_screened_poisson(b.handle, _ptr(I0, b.n, "I0"), _ptr(I1, b.n, "I1"),
+                                         _ptr(I2, b.n, "I2"),
+                                         ctypes.byref(ctl) if ctl is not None else None,
+                                         _ptr(x0, b.n, "x0"), ctypes.byref(rep), sr)
+    if raise_on_error and st not in (GD_OK, GD_ERR_NOT_CONVERGED):
+        raise GdError(st, gd_batch_last_error(b))
+    out = rep.to_dict()
+    if slice_rel:
+        out["slice_rel"] = list(sr)
+    return out
+
+
+def gd_batch_voxels(b: Batch) -> int:
+    return lib().gd_batch_voxels(b.handle)
+
+
+def gd_batch_offset(b: Batch, s: int) -> int:
+    return lib().gd_batch_offset(b.handle, s)
+
+
+def gd_batch_levels(b: Batch) -> int:
+    return lib().gd_batch_levels(b.handle)
+
+
+def gd_batch_launch_count(b: Batch) -> int:
+    return lib().gd_batch_launch_count(b.handle)
+
+
+def gd_batch_last_error(b: Optional[Batch]) -> str:
+    r = lib().gd_batch_last_error(b.handle if b is not None else None)
+    return r.decode() if r else ""
+
+
+def gd_batch_destroy(b: Batch) -> int:
+    if b is None or b.handle is None:
+        return GD_OK
+    st = lib().gd_batch_destroy(b.handle)
+    b.handle = None
+    return st
 
 
 def gd_last_error(s: Optional[Stack]) -> str:

@@ -47,3 +47,24 @@ void jacobi_eigen(int n, double *a, double *w, double *v) {
   }
   for (int i = 0; i < n; ++i) w[i] = a[i * n + i];
 }
+
+// Generalised eigen-decomposition of (K_n, M) with K_n the 1D Neumann
+// Laplacian and M = diag(children counts): V^T M V = I, V^T K V = diag(lam).
+void axis_eig(int n, int sfac, int last, std::vector<float> &V, std::vector<double> &lam) {
+  std::vector<double> m(n), a((size_t)n * n, 0.0), v((size_t)n * n), w(n);
+  for (int i = 0; i < n; ++i) m[i] = (i == n - 1) ? last : sfac;
+  for (int i = 0; i + 1 < n; ++i) {  // K_n = sum over edges of e e^T, e = u_i - u_{i+1}
+    a[i * n + i] += 1.0;
+    a[(i + 1) * n + i + 1] += 1.0;
+    a[i * n + i + 1] -= 1.0;
+    a[(i + 1) * n + i] -= 1.0;
+  }
+  for (int i = 0; i < n; ++i)  // C = M^{-1/2} K M^{-1/2}
+    for (int j = 0; j < n; ++j) a[i * n + j] /= std::sqrt(m[i] * m[j]);
+  jacobi_eigen(n, a.data(), w.data(), v.data());
+  V.assign((size_t)n * n, 0.f);
+  lam.assign(n, 0.0);
+  for (int k = 0; k < n; ++k) lam[k] = w[k] < 0 ? 0.0 : w[k];
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) V[(size_t)i * n + k] = (float)(v[i * n + k] / std::sqrt(m[i]));
+}

@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 // One multigrid level.  The operator is the Kronecker form
 //   A = wx Kx (x) My (x) Mz + wy Mx (x) Ky (x) Mz + wz Mx (x) My (x) Kz + wm Mx (x) My (x) Mz
 // where K_n is the 1D Neumann Laplacian and M_d = diag(children counts of the
@@ -117,3 +119,7 @@ cudaError_t launch_npr_rhs(const float *I0, float *b, int nx, int ny, int nz, do
 // Host: symmetric eigen-decomposition (cyclic Jacobi), FP64, row-major a[n*n].
 // On return w holds the eigenvalues and v (row-major, column k = eigenvector k).
 void jacobi_eigen(int n, double *a, double *w, double *v);
+// Host: generalised eigen-decomposition of (K_n, M) with K_n the 1D Neumann
+// Laplacian and M = diag(sfac, ..., sfac, last): V (row-major, n x n, column
+// k = eigenvector k) with V^T M V = I and V^T K V = diag(lam).
+void axis_eig(int n, int sfac, int last, std::vector<float> &V, std::vector<double> &lam);

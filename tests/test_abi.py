@@ -105,3 +105,28 @@ def test_general_solve_and_npr_validation_without_gpu(lib):
         assert lib.gd_npr_rhs(s.handle, p, p, gd.GdWeights(0.001, 1, 1, 0.1), 1.25, 5.0) == gd.GD_ERR_INVALID_ARG
     finally:
         gd.gd_destroy(s)
+
+
+def test_batch_validation_without_gpu(lib):
+    # argument checks return before any CUDA call
+    for nx, ny, al in (([10], [10], [0.0]), ([10], [10], [-1.0]), ([0], [5], [0.01]),
+                       ([5], [1 << 21], [0.01]), ([4, 4], [4, 4], [0.01, float("nan")])):
+        with pytest.raises(gd.GdError) as ei:
+            gd.gd_batch_create(nx, ny, al)
+        assert ei.value.status == gd.GD_ERR_INVALID_ARG
+        assert gd.gd_batch_last_error(None)
+    with pytest.raises(gd.GdError) as ei:
+        gd.gd_batch_create([10], [10], [0.01], coarsest_xy=1)
+    assert ei.value.status == gd.GD_ERR_INVALID_ARG
+    # a slice whose coarsest level exceeds the batched direct solve (planned on
+    # the host before any allocation)
+    with pytest.raises(gd.GdError) as ei:
+        gd.gd_batch_create([64, 20], [64, 100000], [0.01, 0.01])
+    assert ei.value.status == gd.GD_ERR_UNSUPPORTED
+    assert "coarsest level" in gd.gd_batch_last_error(None)
+    # NULL handles
+    assert lib.gd_batch_voxels(None) == -1
+    assert lib.gd_batch_offset(None, 0) == -1
+    assert lib.gd_batch_destroy(None) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_batch_screened_poisson(None, None, None, None, None, None, None, None) == \
+        gd.GD_ERR_INVALID_ARG

@@ -38,3 +38,23 @@ def test_noise_off_and_photo_seed():
     i0, i1 = gdsynth.sp_pair(64, 21)
     assert i0.shape == (64, 64) and i1.shape == (64, 64)
     assert not np.array_equal(i0, i1)
+
+
+def test_batch_inputs():
+    sides = gdsynth.batch_sides(512, 256, 4096, seed=1)
+    assert len(sides) == 512 and min(sides) >= 256 and max(sides) <= 4096
+    # log-uniform: the median is near the geometric mean 1024 of the bounds
+    assert 700 < sorted(sides)[256] < 1500
+    al = gdsynth.batch_alphas(512, seed=1)
+    assert min(al) >= 0.001 and max(al) < 0.1
+    nx, ny = [5, 1, 70], [3, 9, 2]
+    I0s, I1s = gdsynth.batch_slices(nx, ny, seed=4)
+    assert [a.shape for a in I0s] == [(3, 5), (9, 1), (2, 70)]
+    assert all(a.dtype == np.float32 and b.dtype == np.float32 for a, b in zip(I0s, I1s))
+    flat = gdsynth.pack(I0s)
+    assert flat.size == 15 + 9 + 140
+    back = gdsynth.unpack(flat, nx, ny)
+    assert all(np.array_equal(a, b) for a, b in zip(I0s, back))
+    # seeded
+    J0s, _ = gdsynth.batch_slices(nx, ny, seed=4)
+    assert all(np.array_equal(a, b) for a, b in zip(I0s, J0s))
