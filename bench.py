@@ -46,6 +46,9 @@ NPR_NX, NPR_NY, NPR_NZ = 1920, 1080, 742
 NPR_W = (0.001, 1.0, 1.0, 0.1)   # alpha, W = Diag(1, 1, 0.1)
 NPR_LAMBDA, NPR_SIGMA = 1.25, 5.0
 NPR_TOL = 1e-8
+# batched screened Poisson on independent slices of different sizes
+BATCH_N, BATCH_LO, BATCH_HI = 512, 256, 4096
+BATCH_TOL = 1e-7
 
 # DRAM traffic of the dominant kernel class from one ncu capture: the ratio of
 # dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic bytes over the
@@ -379,6 +382,53 @@ def run_gpu(args):
         del V0, Vb, Vx
         torch.cuda.empty_cache()
 
+    # Batched screened Poisson on 512 independent slices, square, sides
+    # log-uniform in [256, 4096], alpha ~ U(0.001, 0.1) per slice; every
+    # slice to 1e-7 relative residual, timed like the main workload.
+    batch = None
+    if not args.no_batch:
+        bseed = SEED + 200 + rank
+        sides = gdsynth.batch_sides(BATCH_N, BATCH_LO, BATCH_HI, seed=bseed)
+        bal = gdsynth.batch_alphas(BATCH_N, seed=bseed)
+        B0s, B1s = gdsynth.batch_slices(sides, sides, seed=bseed)
+        BI0 = torch.from_numpy(gdsynth.pack(B0s)).to(dev)
+        BI1 = torch.from_numpy(gdsynth.pack(B1s)).to(dev)
+        del B0s, B1s
+        BO = torch.empty_like(BI0)
+        bh = gd.gd_batch_create(sides, sides, bal, stream=stream.cuda_stream)
+        bctl = gd.solve_ctl(40, BATCH_TOL, 2, 2, 16)
+        breps = []
+        for _ in range(max(1, min(args.warmup, 2))):
+            breps.append(gd.gd_batch_screened_poisson(bh, BI0, BI1, BO, bctl))
+        breps.clear()
+        bsteps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        barrier(world)
+        bl0 = gd.gd_batch_launch_count(bh)
+        e0.record(stream)
+        for _ in range(bsteps):
+            breps.append(gd.gd_batch_screened_poisson(bh, BI0, BI1, BO, bctl))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        bms = reduce_max(e0.elapsed_time(e1), world, dev)
+        blaunch = gd.gd_batch_launch_count(bh) - bl0
+        per_cycle, per_solve = gd.gd_batch_traffic(bh, 2, 2)
+        bvox = int(BI0.numel())
+        rb_ = breps[-1]
+        alg = per_solve + rb_["cycles"] * per_cycle
+        batch = {"workload": "sp_batch_%d_slices_%d_to_%d" % (BATCH_N, BATCH_LO, BATCH_HI),
+                 "value": world * bvox * bsteps / (bms * 1e-3), "unit": UNIT,
+                 "ms_per_step": bms / bsteps, "steps": bsteps, "voxels": bvox, "slices": BATCH_N,
+                 "params": {"alpha": [0.001, 0.1], "rel_tol": BATCH_TOL, "x0": "I0",
+                            "tolerance_per": "slice"},
+                 "cycles": rb_["cycles"], "rel_residual_max": rb_["rel_residual"],
+                 "levels": rb_["levels"], "gpu_launches": blaunch,
+                 "alg_bytes_per_step": alg, "achieved_GBps": alg / (bms / bsteps * 1e-3) / 1e9}
+        gd.gd_batch_destroy(bh)
+        del BI0, BI1, BO
+        torch.cuda.empty_cache()
+
     # end to end through the C ABI with pinned host buffers: H2D of the input
     # (once per solve) and D2H of the result inside the timed region
     I0p = torch.from_numpy(I0h.astype(np.float32)).pin_memory()
@@ -417,6 +467,8 @@ def run_gpu(args):
                     "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                     "traffic": traffic, "launches": nl, "avg_launch_ms": ms / nl,
                     "alg_bytes_per_launch": by / nl}
+        if batch is not None:
+            batch["frac_of_hbm"] = batch["achieved_GBps"] / peak
         r1, r2 = reps[-1]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -441,6 +493,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "mixed": mixed,
             "npr": npr,
+            "batch": batch,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -469,6 +522,31 @@ def run_ncu_case(args):
     return 0 if rep["status"] in (0, 5) else 1
 
 
+def run_ncu_batch(args):
+    """One batched solve of the 512-slice workload (for ncu launch lists; not
+    a benchmark): sides log-uniform in [256, 4096], to 1e-7 per slice."""
+    import torch
+    import gdsynth
+    import paper_1310_0041_gb300 as gd
+    gd.build()
+    bseed = SEED + 200
+    sides = gdsynth.batch_sides(BATCH_N, BATCH_LO, BATCH_HI, seed=bseed)
+    bal = gdsynth.batch_alphas(BATCH_N, seed=bseed)
+    B0s, B1s = gdsynth.batch_slices(sides, sides, seed=bseed)
+    BI0 = torch.from_numpy(gdsynth.pack(B0s)).cuda()
+    BI1 = torch.from_numpy(gdsynth.pack(B1s)).cuda()
+    del B0s, B1s
+    BO = torch.empty_like(BI0)
+    bh = gd.gd_batch_create(sides, sides, bal)
+    rep = gd.gd_batch_screened_poisson(bh, BI0, BI1, BO, gd.solve_ctl(40, BATCH_TOL, 2, 2, 16),
+                                       raise_on_error=False)
+    torch.cuda.synchronize()
+    gd.gd_batch_destroy(bh)
+    print(json.dumps({"ncu_batch": "sp_batch_%d_slices" % BATCH_N, "status": rep["status"],
+                      "cycles": rep["cycles"], "voxels": int(BI0.numel())}))
+    return 0 if rep["status"] == 0 else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,11 +555,16 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-npr", action="store_true", help="skip the NPR filter measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-slices measurement")
+    ap.add_argument("--ncu-batch", action="store_true",
+                    help="one solve of the 512-slice batch for ncu launch lists (no timing)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case instead of the benchmark")
     args = ap.parse_args(argv)
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.ncu_batch:
+        return run_ncu_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -309,6 +309,10 @@ int gd_batch_screened_poisson(gd_batch *b, const float *I0, const float *I1, flo
 long long gd_batch_voxels(const gd_batch *b);            /* total cells, -1 for NULL */
 long long gd_batch_offset(const gd_batch *b, int slice); /* off_s, -1 if out of range */
 int gd_batch_levels(const gd_batch *b);                  /* depth of the deepest hierarchy */
+/* Algorithmic device-memory bytes of one V(nu1, nu2) cycle with its outer
+ * pass, and of the once-per-solve passes (input, first outer pass, output):
+ * each pass's arrays read and written once. */
+int gd_batch_traffic(const gd_batch *b, int nu1, int nu2, double *per_cycle, double *per_solve);
 long long gd_batch_launch_count(const gd_batch *b);      /* kernel launches since creation */
 const char *gd_batch_last_error(const gd_batch *b);
 int gd_batch_destroy(gd_batch *b);

@@ -35,7 +35,8 @@ EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_
            "gd_profile_query", "gd_launch_count", "gd_status_string", "gd_last_error",
            "gd_version", "gd_smooth_noalloc", "gd_screened_poisson", "gd_npr_rhs",
            "gd_batch_create", "gd_batch_screened_poisson", "gd_batch_voxels", "gd_batch_offset",
-           "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy")
+           "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy",
+           "gd_batch_traffic")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -119,6 +120,7 @@ def lib():
                 "gd_batch_voxels": (ctypes.c_longlong, [P]),
                 "gd_batch_offset": (ctypes.c_longlong, [P, I]),
                 "gd_batch_levels": (I, [P]),
+                "gd_batch_traffic": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
                 "gd_batch_launch_count": (ctypes.c_longlong, [P]),
                 "gd_batch_last_error": (ctypes.c_char_p, [P]),
                 "gd_batch_destroy": (I, [P]),
@@ -407,6 +409,15 @@ def gd_batch_offset(b: Batch, s: int) -> int:
 
 def gd_batch_levels(b: Batch) -> int:
     return lib().gd_batch_levels(b.handle)
+
+
+def gd_batch_traffic(b: Batch, nu1: int = 2, nu2: int = 2) -> tuple:
+    """(bytes per V-cycle with its outer pass, bytes of the once-per-solve passes)."""
+    pc, ps = ctypes.c_double(), ctypes.c_double()
+    st = lib().gd_batch_traffic(b.handle, nu1, nu2, ctypes.byref(pc), ctypes.byref(ps))
+    if st != GD_OK:
+        raise GdError(st, gd_batch_last_error(b))
+    return pc.value, ps.value
 
 
 def gd_batch_launch_count(b: Batch) -> int:

@@ -37,34 +37,45 @@ namespace {
 // ---------------------------------------------------------------------------
 // device side
 // ---------------------------------------------------------------------------
-constexpr int BX = 64, BY = 32;  // tile (cells)
-constexpr int BNT = 256;         // threads per CTA
-constexpr int XW = BX + 4, XH = BY + 4;  // x box: two-cell halo (the red ring and its neighbours)
-constexpr int BW = BX + 2, BH = BY + 2;  // b box: one-cell halo (the red ring)
+// Internal layout: every slice level is stored with a row pitch rounded up
+// to 4 floats (rows and slices 16-byte aligned); the padding cells hold 0.
+//
+// The level kernels are row marches by one warp over a strip of 128 columns:
+// lane l holds the float4 of columns x0 - 4 + 4 l, lanes 1..30 own the 120
+// columns x0 .. x0 + 119 and lanes 0 and 31 carry the halo (their cells are
+// computed, never stored).  The warp walks down a chunk of rows keeping the
+// previous rows in registers: no shared memory, no CTA barrier.
+constexpr int BNT = 256;  // threads per CTA
+constexpr int WPB = BNT / 32;
+constexpr int SW = 120;   // owned columns of a strip
+constexpr int CH = 64;    // rows of a chunk (even)
+constexpr int TX = 64, TY = 32;  // tiles of the element-wise kernels
 constexpr int kBMaxLev = 24;
 constexpr int kFdmMaxCells = 4096;
+constexpr unsigned FULL = 0xffffffffu;
 
 // One slice at one level.  The level operator is the Kronecker form of the
 // stack solver restricted to a slice:
 //   A = wx Kx (x) My + wy Mx (x) Ky + wm Mx (x) My,
 // M = diag(children counts, s inside and l for the last cell of an axis).
 struct BEntry {
-  long long off;   // first element of the slice in this level's packed buffer
+  long long off;   // first element of the slice in this level's buffer
   long long coff;  // the same in the next level's buffer (-1: coarsest level)
-  int nx, ny;
+  long long uoff;  // level 0: first element of the slice in the caller's packed arrays
+  int nx, ny, pitch;
   int sx, sy, lx, ly;
-  int cnx, cny, fx, fy;  // next level's sizes and the axes halved to reach it
+  int cnx, cny, cpitch, fx, fy;  // next level and the axes halved to reach it
   float wx, wy, wm;
   int slice;
 };
 
 struct BCoarse {  // coarsest level of one slice
   int lev;        // its depth
-  int nx, ny;
+  int nx, ny, pitch;
   int vx, vy;     // offsets of Vx, Vy in the V table
   int lx, ly;     // offsets of the eigenvalues in the lambda table
   float wx, wy, wm;
-  long long off;  // first element in the level's packed buffer
+  long long off;  // first element in the level's buffer
 };
 
 struct BLevelPtrs {
@@ -72,183 +83,226 @@ struct BLevelPtrs {
   float *x[kBMaxLev];
 };
 
-__device__ __forceinline__ bool inside(const BEntry &e, int i, int j) {
-  return i >= 0 && i < e.nx && j >= 0 && j < e.ny;
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+__device__ __forceinline__ float cmp(const float4 &v, int c) {
+  return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set(float4 &v, int c, float a) {
+  if (c == 0) v.x = a;
+  else if (c == 1) v.y = a;
+  else if (c == 2) v.z = a;
+  else v.w = a;
 }
 
-// Couplings and diagonal of cell (i, j): cx to each x-neighbour, cy to each
-// y-neighbour; neighbours outside the slice are absent (Neumann).
-__device__ __forceinline__ void coef(const BEntry &e, int i, int j, float &cx, float &cy, float &dg) {
-  const float mx = (i == e.nx - 1) ? (float)e.lx : (float)e.sx;
-  const float my = (j == e.ny - 1) ? (float)e.ly : (float)e.sy;
-  cx = e.wx * my;
-  cy = e.wy * mx;
-  const float nbx = (float)((i > 0) + (i < e.nx - 1));
-  const float nby = (float)((j > 0) + (j < e.ny - 1));
-  dg = cx * nbx + cy * nby + e.wm * mx * my;
+// The lane's four columns: inside flags, masses along x and x-neighbour counts.
+struct Cols {
+  int gi;     // first column
+  bool mem;   // the float4 lies inside the row pitch
+  bool own;   // and the lane owns it (lanes 1..30)
+  bool in[4];
+  float mx[4], nbx[4];
+  __device__ __forceinline__ Cols(const BEntry &e, int x0, int lane) {
+    gi = x0 - 4 + 4 * lane;
+    mem = gi >= 0 && gi < e.pitch;
+    own = mem && lane >= 1 && lane <= 30;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = gi + c;
+      in[c] = i >= 0 && i < e.nx;
+      mx[c] = (i == e.nx - 1) ? (float)e.lx : (float)e.sx;
+      nbx[c] = (float)((i > 0) + (i < e.nx - 1));
+    }
+  }
+  __device__ __forceinline__ float4 mask(float4 v) const {
+    return make_float4(in[0] ? v.x : 0.f, in[1] ? v.y : 0.f, in[2] ? v.z : 0.f, in[3] ? v.w : 0.f);
+  }
+};
+
+// Couplings of row t: cx to each x-neighbour; per cell cy = wy mx and the
+// diagonal cx nbx + cy nby + wm mx my.
+struct RowK {
+  float cx, my, nby;
+  __device__ __forceinline__ RowK(const BEntry &e, int t) {
+    my = (t == e.ny - 1) ? (float)e.ly : (float)e.sy;
+    cx = e.wx * my;
+    nby = (float)((t > 0) + (t < e.ny - 1));
+  }
+};
+
+// Gauss-Seidel value of cell c of a row: (b + cx (l + r) + cy (u + d)) / diag.
+__device__ __forceinline__ float relax(const BEntry &e, const Cols &C, const RowK &k, int c, float bv,
+                                       float lr, float ud) {
+  const float cy = e.wy * C.mx[c];
+  const float dg = k.cx * C.nbx[c] + cy * k.nby + e.wm * C.mx[c] * k.my;
+  return __fdividef(bv + k.cx * lr + cy * ud, dg);
 }
 
-// Fills two shared-memory boxes (h1 x w1 and h2 x w2, row-major) with
-// get1(r, c) and get2(r, c): every global load of the thread is issued
-// before the first shared-memory store, so one round trip covers both.
-template <int H1, int W1, int H2, int W2, typename G1, typename G2>
-__device__ __forceinline__ void load_boxes(float *d1, G1 get1, float *d2, G2 get2) {
-  constexpr int N1 = (H1 * W1 + BNT - 1) / BNT, N2 = (H2 * W2 + BNT - 1) / BNT;
-  float v1[N1], v2[N2 > 0 ? N2 : 1];
-#pragma unroll
-  for (int k = 0; k < N1; ++k) {
-    const int q = threadIdx.x + k * BNT;
-    v1[k] = (q < H1 * W1) ? get1(q / W1, q % W1) : 0.f;
-  }
-#pragma unroll
-  for (int k = 0; k < N2; ++k) {
-    const int q = threadIdx.x + k * BNT;
-    v2[k] = (q < H2 * W2) ? get2(q / W2, q % W2) : 0.f;
-  }
-#pragma unroll
-  for (int k = 0; k < N1; ++k) {
-    const int q = threadIdx.x + k * BNT;
-    if (q < H1 * W1) d1[q] = v1[k];
-  }
-#pragma unroll
-  for (int k = 0; k < N2; ++k) {
-    const int q = threadIdx.x + k * BNT;
-    if (q < H2 * W2) d2[q] = v2[k];
-  }
+// Residual b - A x at cell c of a row.
+__device__ __forceinline__ float resid(const BEntry &e, const Cols &C, const RowK &k, int c, float bv,
+                                       float xv, float lr, float ud) {
+  const float cy = e.wy * C.mx[c];
+  const float dg = k.cx * C.nbx[c] + cy * k.nby + e.wm * C.mx[c] * k.my;
+  return bv - (dg * xv - k.cx * lr - cy * ud);
 }
 
-// One red-black Gauss-Seidel sweep of every tile of the work list, xin ->
-// xout.  Red cells are (i + j) even.  A tile relaxes its red cells and the red
-// ring around it (whose values the tile's black cells read), then its black
-// cells; a red value depends only on black values of the input, so the ring
-// values a CTA computes are the ones the neighbouring tile writes.
+// One red-black Gauss-Seidel sweep, xin -> xout, over the strip items
+// (entry, x0, ys, ye).  Red cells are (i + j) even.  At step t the warp
+// relaxes the red cells of row t (from the old black values of rows t-1,
+// t, t+1) and then the black cells of row t-1 (from the new red values of
+// rows t-2, t-1, t), which completes row t-1.  Rows ys-1 and ye get their
+// red pass only (the chunk's halo rows); a red value depends only on old
+// black values, so neighbouring chunks and strips compute the same ones.
+// ZERO_IN: the input is 0.  PROLONG: the input is xin plus the next level's
+// value of each cell's parent (piecewise-constant prolongation).
 template <bool ZERO_IN, bool PROLONG>
 __global__ void __launch_bounds__(BNT) k_bsweep(const BEntry *__restrict__ E, const int4 *__restrict__ items,
                                                 int nitems, const float *__restrict__ xin,
                                                 const float *__restrict__ b, float *__restrict__ xout,
                                                 const float *__restrict__ xc) {
-  __shared__ float xs[XH][XW];
-  __shared__ float bs[BH][BW];
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * WPB;
+  for (int it = blockIdx.x * WPB + (threadIdx.x >> 5); it < nitems; it += nw) {
     const int4 w = items[it];
     const BEntry e = E[w.x];
-    const int i0 = w.y, j0 = w.z;
-    load_boxes<XH, XW, BH, BW>(
-        &xs[0][0],
-        [&](int r, int c) {
-          const int gi = i0 - 2 + c, gj = j0 - 2 + r;
-          float v = 0.f;
-          if (inside(e, gi, gj)) {
-            if (!ZERO_IN) v = xin[e.off + (long long)gj * e.nx + gi];
-            if (PROLONG) v += xc[e.coff + (long long)(gj >> e.fy) * e.cnx + (gi >> e.fx)];
-          }
-          return v;
-        },
-        &bs[0][0],
-        [&](int r, int c) {
-          const int gi = i0 - 1 + c, gj = j0 - 1 + r;
-          return inside(e, gi, gj) ? b[e.off + (long long)gj * e.nx + gi] : 0.f;
-        });
-    __syncthreads();
-    // red cells of the tile and its ring: rows j0-1 .. j0+BY, BW/2 per row
-    for (int q = threadIdx.x; q < BH * (BW / 2); q += BNT) {
-      const int r = q / (BW / 2), k = q - r * (BW / 2);
-      const int gj = j0 - 1 + r;
-      const int gi = i0 - 1 + ((i0 - 1 + gj) & 1) + 2 * k;
-      if (inside(e, gi, gj)) {
-        const int xr = r + 1, xq = gi - i0 + 2;
-        float cx, cy, dg;
-        coef(e, gi, gj, cx, cy, dg);
-        const float s = bs[r][gi - i0 + 1] + cx * (xs[xr][xq - 1] + xs[xr][xq + 1]) +
-                        cy * (xs[xr - 1][xq] + xs[xr + 1][xq]);
-        xs[xr][xq] = __fdividef(s, dg);
+    const int ys = w.z, ye = w.w, ny = e.ny;
+    const Cols C(e, w.y, lane);
+    const long long rb = e.off + C.gi;
+    // raw rows of x and their parents' values (PROLONG); the sum is formed
+    // when a row enters the window, so the loads of a row stay in flight
+    // for a step
+    auto ldx = [&](int t) -> float4 {
+      return (!ZERO_IN && t >= 0 && t < ny && C.mem) ? ld4(xin + rb + (long long)t * e.pitch) : f4(0.f);
+    };
+    auto ldc = [&](int t) -> float4 {
+      if (!PROLONG || t < 0 || t >= ny || !C.mem) return f4(0.f);
+      const float *cp = xc + e.coff + (long long)(t >> e.fy) * e.cpitch;
+      if (e.fx) {
+        const float2 c = ld2(cp + (C.gi >> 1));
+        return make_float4(c.x, c.x, c.y, c.y);
       }
-    }
-    __syncthreads();
-    // black cells of the tile: BX/2 per row
-    for (int q = threadIdx.x; q < BY * (BX / 2); q += BNT) {
-      const int r = q / (BX / 2), k = q - r * (BX / 2);
-      const int gj = j0 + r;
-      const int gi = i0 + (((i0 + gj) & 1) ^ 1) + 2 * k;
-      if (inside(e, gi, gj)) {
-        const int xr = r + 2, xq = gi - i0 + 2;
-        float cx, cy, dg;
-        coef(e, gi, gj, cx, cy, dg);
-        const float s = bs[r + 1][gi - i0 + 1] + cx * (xs[xr][xq - 1] + xs[xr][xq + 1]) +
-                        cy * (xs[xr - 1][xq] + xs[xr + 1][xq]);
-        xs[xr][xq] = __fdividef(s, dg);
+      return ld4(cp + C.gi);
+    };
+    auto corr = [&](float4 v, float4 c) -> float4 {
+      if (!PROLONG) return v;
+      return C.mask(make_float4(v.x + c.x, v.y + c.y, v.z + c.z, v.w + c.w));
+    };
+    auto ldb = [&](int t) -> float4 {
+      return (t >= 0 && t < ny && C.mem) ? ld4(b + rb + (long long)t * e.pitch) : f4(0.f);
+    };
+    float4 xm2 = f4(0.f), xm1 = corr(ldx(ys - 2), ldc(ys - 2)), xcur = corr(ldx(ys - 1), ldc(ys - 1));
+    float4 xp1 = corr(ldx(ys), ldc(ys)), xp2 = ldx(ys + 1), cp2 = ldc(ys + 1);
+    float4 bm1 = f4(0.f), b0 = ldb(ys - 1), bp1 = ldb(ys);
+    for (int t = ys - 1; t <= ye; ++t) {
+      // row t + 3 reuses its parents' row when the pair's first row had it
+      const float4 xn = ldx(t + 3), bn = ldb(t + 2);
+      const float4 cn = (PROLONG && e.fy && ((t + 3) & 1) && t + 3 < ny) ? cp2 : ldc(t + 3);
+      // red cells of row t
+      float4 xr = xcur;
+      if (t >= 0 && t < ny) {
+        const RowK k(e, t);
+        const float lw = __shfl_up_sync(FULL, xcur.w, 1), rx = __shfl_down_sync(FULL, xcur.x, 1);
+        if ((t & 1) == 0) {
+          xr.x = relax(e, C, k, 0, b0.x, lw + xcur.y, xm1.x + xp1.x);
+          xr.z = relax(e, C, k, 2, b0.z, xcur.y + xcur.w, xm1.z + xp1.z);
+        } else {
+          xr.y = relax(e, C, k, 1, b0.y, xcur.x + xcur.z, xm1.y + xp1.y);
+          xr.w = relax(e, C, k, 3, b0.w, xcur.z + rx, xm1.w + xp1.w);
+        }
+        xr = C.mask(xr);
       }
+      // black cells of row t - 1, which is then complete
+      const int j = t - 1;
+      float4 xb = xm1;
+      if (j >= ys && j < ye) {
+        const RowK k(e, j);
+        const float lw = __shfl_up_sync(FULL, xm1.w, 1), rx = __shfl_down_sync(FULL, xm1.x, 1);
+        if ((j & 1) != 0) {
+          xb.x = relax(e, C, k, 0, bm1.x, lw + xm1.y, xm2.x + xr.x);
+          xb.z = relax(e, C, k, 2, bm1.z, xm1.y + xm1.w, xm2.z + xr.z);
+        } else {
+          xb.y = relax(e, C, k, 1, bm1.y, xm1.x + xm1.z, xm2.y + xr.y);
+          xb.w = relax(e, C, k, 3, bm1.w, xm1.z + rx, xm2.w + xr.w);
+        }
+        xb = C.mask(xb);
+        if (C.own) st4(xout + rb + (long long)j * e.pitch, xb);
+      }
+      xm2 = xb;
+      xm1 = xr;
+      xcur = xp1;
+      xp1 = corr(xp2, cp2);
+      xp2 = xn;
+      cp2 = cn;
+      bm1 = b0;
+      b0 = bp1;
+      bp1 = bn;
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < BY * BX; q += BNT) {
-      const int r = q / BX, c = q - r * BX;
-      const int gi = i0 + c, gj = j0 + r;
-      if (inside(e, gi, gj)) xout[e.off + (long long)gj * e.nx + gi] = xs[r + 2][c + 2];
-    }
-    __syncthreads();  // the next item reuses the boxes
   }
 }
 
-// Residual r = b - A x of a tile into rs (0 outside the slice); xs holds the
-// x box with a one-cell halo.
-__device__ __forceinline__ void tile_residual(float (*xs)[BW], float (*rs)[BX], const BEntry &e, int i0,
-                                              int j0, const float *__restrict__ b) {
-  for (int q = threadIdx.x; q < BY * BX; q += BNT) {
-    const int r = q / BX, c = q - r * BX;
-    const int gi = i0 + c, gj = j0 + r;
-    float v = 0.f;
-    if (inside(e, gi, gj)) {
-      float cx, cy, dg;
-      coef(e, gi, gj, cx, cy, dg);
-      const float ax = dg * xs[r + 1][c + 1] - cx * (xs[r + 1][c] + xs[r + 1][c + 2]) -
-                       cy * (xs[r][c + 1] + xs[r + 2][c + 1]);
-      v = b[e.off + (long long)gj * e.nx + gi] - ax;
-    }
-    rs[r][c] = v;
-  }
-}
-
-__device__ __forceinline__ void load_xbox1(float (*xs)[BW], const BEntry &e, int i0, int j0,
-                                           const float *__restrict__ x) {
-  auto get = [&](int r, int c) {
-    const int gi = i0 - 1 + c, gj = j0 - 1 + r;
-    return inside(e, gi, gj) ? x[e.off + (long long)gj * e.nx + gi] : 0.f;
-  };
-  load_boxes<BH, BW, 0, 1>(&xs[0][0], get, &xs[0][0], get);
-}
-
-// Residual of the tile summed over each coarse cell's children into the next
+// Residual of x summed over each coarse cell's children into the next
 // level's right-hand side (restriction = transpose of the prolongation).
-// Tiles start at even cells, so a coarse cell's children share one tile.
+// Chunks start at even rows and strips at even columns, so a coarse cell's
+// children lie in one lane's float4 and one chunk.
 __global__ void __launch_bounds__(BNT) k_brestrict(const BEntry *__restrict__ E, const int4 *__restrict__ items,
                                                    int nitems, const float *__restrict__ x,
                                                    const float *__restrict__ b, float *__restrict__ bc) {
-  __shared__ float xs[BH][BW];
-  __shared__ float rs[BY][BX];
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * WPB;
+  for (int it = blockIdx.x * WPB + (threadIdx.x >> 5); it < nitems; it += nw) {
     const int4 w = items[it];
     const BEntry e = E[w.x];
-    const int i0 = w.y, j0 = w.z;
-    load_xbox1(xs, e, i0, j0, x);
-    __syncthreads();
-    tile_residual(xs, rs, e, i0, j0, b);
-    __syncthreads();
-    const int cw = BX >> e.fx, ch = BY >> e.fy;
-    for (int q = threadIdx.x; q < cw * ch; q += BNT) {
-      const int cr = q / cw, cc = q - cr * cw;
-      const int ci = (i0 >> e.fx) + cc, cj = (j0 >> e.fy) + cr;
-      if (ci < e.cnx && cj < e.cny) {
-        float s = 0.f;
-        for (int dy = 0; dy <= e.fy; ++dy)
-          for (int dx = 0; dx <= e.fx; ++dx) s += rs[(cr << e.fy) + dy][(cc << e.fx) + dx];
-        bc[e.coff + (long long)cj * e.cnx + ci] = s;
+    const int ys = w.z, ye = w.w, ny = e.ny;
+    const Cols C(e, w.y, lane);
+    const long long rb = e.off + C.gi;
+    auto ldx = [&](int t) -> float4 {
+      return (t >= 0 && t < ny && C.mem) ? ld4(x + rb + (long long)t * e.pitch) : f4(0.f);
+    };
+    auto ldb = [&](int t) -> float4 {
+      return (t >= 0 && t < ny && C.mem) ? ld4(b + rb + (long long)t * e.pitch) : f4(0.f);
+    };
+    float4 xm = ldx(ys - 1), xcur = ldx(ys), xp = ldx(ys + 1), xpp = ldx(ys + 2);
+    float4 b0 = ldb(ys), bp = ldb(ys + 1);
+    float4 acc = f4(0.f);
+    for (int t = ys; t < ye; ++t) {
+      const float4 xn = ldx(t + 3), bn = ldb(t + 2);
+      const RowK k(e, t);
+      const float lw = __shfl_up_sync(FULL, xcur.w, 1), rx = __shfl_down_sync(FULL, xcur.x, 1);
+      float4 r;
+      r.x = resid(e, C, k, 0, b0.x, xcur.x, lw + xcur.y, xm.x + xp.x);
+      r.y = resid(e, C, k, 1, b0.y, xcur.y, xcur.x + xcur.z, xm.y + xp.y);
+      r.z = resid(e, C, k, 2, b0.z, xcur.z, xcur.y + xcur.w, xm.z + xp.z);
+      r.w = resid(e, C, k, 3, b0.w, xcur.w, xcur.z + rx, xm.w + xp.w);
+      r = C.mask(r);
+      const bool first = e.fy && (t & 1) == 0;
+      acc.x += r.x;
+      acc.y += r.y;
+      acc.z += r.z;
+      acc.w += r.w;
+      if (!first || t == ny - 1) {
+        if (C.own) {
+          float *cp = bc + e.coff + (long long)(t >> e.fy) * e.cpitch;
+          if (e.fx)
+            st2(cp + (C.gi >> 1), make_float2(acc.x + acc.y, acc.z + acc.w));
+          else
+            st4(cp + C.gi, acc);
+        }
+        acc = f4(0.f);
       }
+      xm = xcur;
+      xcur = xp;
+      xp = xpp;
+      xpp = xn;
+      b0 = bp;
+      bp = bn;
     }
-    __syncthreads();
   }
 }
 
-// Error-free transformations (Knuth's TwoSum): s + e == a + b exactly.
+// Error-free transformation (Knuth's TwoSum): s + e == a + b exactly.
 struct ff {
   float h, l;
 };
@@ -260,155 +314,169 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
 }
 
 // The outer pass of the float-pair refinement at the fine level (unit
-// masses and stiffness, A = alpha + Kx + Ky): (h, l) <- (h, l) + e
-// (ADD_E; input pair -> output pair, never in place, since neighbouring
-// tiles read this tile's cells), then r = bf - A (h + l) with every rounding
-// error of the high parts captured, written as the correction's right-hand
-// side, and the per-slice sums of r^2 and bf^2 (FP64 slots acc[2 s],
-// acc[2 s + 1]; each thread sums its few cells in FP32, the block in FP64).
+// masses and stiffness, A = alpha + Kx + Ky): (h, l) <- (h, l) + e (ADD_E;
+// from the input pair to the output pair, never in place, since
+// neighbouring strips read this strip's cells), then r = bf - A (h + l) with
+// every rounding error of the high parts captured, written as the
+// correction's right-hand side, and the per-slice sums of r^2 and bf^2 (FP64
+// slots acc[2 s], acc[2 s + 1]; lanes sum in FP32, the warp in FP64).
 template <bool ADD_E>
 __global__ void __launch_bounds__(BNT) k_bouter(const BEntry *__restrict__ E, const int4 *__restrict__ items,
                                                 int nitems, const float *__restrict__ bf,
                                                 const float *__restrict__ hin, const float *__restrict__ lin,
-                                                const float *__restrict__ e, float *__restrict__ hout,
+                                                const float *__restrict__ ein, float *__restrict__ hout,
                                                 float *__restrict__ lout, float *__restrict__ r,
                                                 double *__restrict__ acc) {
-  __shared__ float hs[BH][BW];
-  __shared__ float ls[BH][BW];
-  __shared__ double red[2][BNT / 32];
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int nw = gridDim.x * WPB;
+  for (int it = blockIdx.x * WPB + (threadIdx.x >> 5); it < nitems; it += nw) {
     const int4 w = items[it];
-    const BEntry en = E[w.x];
-    const int i0 = w.y, j0 = w.z, nx = en.nx;
-    {
-      constexpr int N = (BH * BW + BNT - 1) / BNT;
-      float hv[N], lv[N], ev[N];
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const int q = threadIdx.x + k * BNT;
-        const int rr = q / BW, c = q - rr * BW;
-        const int gi = i0 - 1 + c, gj = j0 - 1 + rr;
-        hv[k] = lv[k] = ev[k] = 0.f;
-        if (q < BH * BW && inside(en, gi, gj)) {
-          const long long o = en.off + (long long)gj * nx + gi;
-          hv[k] = hin[o];
-          lv[k] = lin[o];
-          if (ADD_E) ev[k] = e[o];
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        const int q = threadIdx.x + k * BNT;
-        if (q < BH * BW) {
-          float h = hv[k], l = lv[k];
-          if (ADD_E) {
-            const ff a = two_sum(h, ev[k]);
-            const ff v = two_sum(a.h, __fadd_rn(a.l, l));
-            h = v.h;
-            l = v.l;
-          }
-          (&hs[0][0])[q] = h;
-          (&ls[0][0])[q] = l;
-        }
-      }
-    }
-    __syncthreads();
-    float s_rr = 0.f, s_bb = 0.f;
-    const float alpha = en.wm;
-    for (int q = threadIdx.x; q < BY * BX; q += BNT) {
-      const int rr = q / BX, c = q - rr * BX;
-      const int gi = i0 + c, gj = j0 + rr;
-      if (!inside(en, gi, gj)) continue;
-      const long long o = en.off + (long long)gj * nx + gi;
-      const float hc = hs[rr + 1][c + 1], lc = ls[rr + 1][c + 1];
+    const BEntry e = E[w.x];
+    const int ys = w.z, ye = w.w, ny = e.ny;
+    const Cols C(e, w.y, lane);
+    const long long rb = e.off + C.gi;
+    const float alpha = e.wm;
+    // the updated pair of row t (0 outside)
+    auto ldp = [&](int t, float4 &h, float4 &l) {
+      h = l = f4(0.f);
+      if (t < 0 || t >= ny || !C.mem) return;
+      const long long o = rb + (long long)t * e.pitch;
+      h = ld4(hin + o);
+      l = ld4(lin + o);
       if (ADD_E) {
-        hout[o] = hc;
-        lout[o] = lc;
-      } else if (hout != hin) {
-        hout[o] = hc;
-        lout[o] = lc;
+        const float4 d = ld4(ein + o);
+        float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+        const float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const ff a = two_sum(hv[c], dv[c]);
+          const ff s = two_sum(a.h, __fadd_rn(a.l, lv[c]));
+          hv[c] = s.h;
+          lv[c] = s.l;
+        }
+        h = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        l = make_float4(lv[0], lv[1], lv[2], lv[3]);
       }
-      const float bv = bf[o];
-      float hi = bv, lo = 0.f;
-      auto sub = [&](float v) {
-        const ff t = two_sum(hi, -v);
-        hi = t.h;
-        lo += t.l;
-      };
-      auto nb = [&](bool has, float hn, float ln) {
-        if (!has) return;
-        const ff d = two_sum(hc, -hn);
-        sub(d.h);
-        lo -= d.l + (lc - ln);
-      };
-      nb(gi > 0, hs[rr + 1][c], ls[rr + 1][c]);
-      nb(gi < nx - 1, hs[rr + 1][c + 2], ls[rr + 1][c + 2]);
-      nb(gj > 0, hs[rr][c + 1], ls[rr][c + 1]);
-      nb(gj < en.ny - 1, hs[rr + 2][c + 1], ls[rr + 2][c + 1]);
-      const float pa = alpha * hc;
-      sub(pa);
-      lo -= __fmaf_rn(alpha, hc, -pa) + alpha * lc;
-      const float rv = hi + lo;
-      r[o] = rv;
-      s_rr = fmaf(rv, rv, s_rr);
-      s_bb = fmaf(bv, bv, s_bb);
+    };
+    auto ldb = [&](int t) -> float4 {
+      return (t >= 0 && t < ny && C.mem) ? ld4(bf + rb + (long long)t * e.pitch) : f4(0.f);
+    };
+    float4 hm, lm, hc, lc, hp, lp;
+    ldp(ys - 1, hm, lm);
+    ldp(ys, hc, lc);
+    ldp(ys + 1, hp, lp);
+    float4 b0 = ldb(ys);
+    float s_rr = 0.f, s_bb = 0.f;
+    for (int t = ys; t < ye; ++t) {
+      float4 hn, ln;
+      ldp(t + 2, hn, ln);
+      const float4 bn = ldb(t + 1);
+      const float hlw = __shfl_up_sync(FULL, hc.w, 1), llw = __shfl_up_sync(FULL, lc.w, 1);
+      const float hrx = __shfl_down_sync(FULL, hc.x, 1), lrx = __shfl_down_sync(FULL, lc.x, 1);
+      const float hcv[4] = {hc.x, hc.y, hc.z, hc.w}, lcv[4] = {lc.x, lc.y, lc.z, lc.w};
+      const float hmv[4] = {hm.x, hm.y, hm.z, hm.w}, lmv[4] = {lm.x, lm.y, lm.z, lm.w};
+      const float hpv[4] = {hp.x, hp.y, hp.z, hp.w}, lpv[4] = {lp.x, lp.y, lp.z, lp.w};
+      const float bv4[4] = {b0.x, b0.y, b0.z, b0.w};
+      float rv4[4];
+      const bool up = t > 0, dn = t < ny - 1;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int i = C.gi + c;
+        const float hcc = hcv[c], lcc = lcv[c];
+        float hi = bv4[c], lo = 0.f;
+        auto sub = [&](float v) {
+          const ff s = two_sum(hi, -v);
+          hi = s.h;
+          lo += s.l;
+        };
+        auto nb = [&](bool has, float hn_, float ln_) {
+          if (!has) return;
+          const ff d = two_sum(hcc, -hn_);
+          sub(d.h);
+          lo -= d.l + (lcc - ln_);
+        };
+        nb(i > 0, c == 0 ? hlw : hcv[c - 1], c == 0 ? llw : lcv[c - 1]);
+        nb(i < e.nx - 1, c == 3 ? hrx : hcv[c + 1], c == 3 ? lrx : lcv[c + 1]);
+        nb(up, hmv[c], lmv[c]);
+        nb(dn, hpv[c], lpv[c]);
+        const float pa = alpha * hcc;
+        sub(pa);
+        lo -= __fmaf_rn(alpha, hcc, -pa) + alpha * lcc;
+        const float rr = (C.in[c] && C.own) ? hi + lo : 0.f;
+        rv4[c] = rr;
+        s_rr = fmaf(rr, rr, s_rr);
+        if (C.in[c] && C.own) s_bb = fmaf(bv4[c], bv4[c], s_bb);
+      }
+      if (C.own) {
+        const long long o = rb + (long long)t * e.pitch;
+        st4(r + o, make_float4(rv4[0], rv4[1], rv4[2], rv4[3]));
+        st4(hout + o, C.mask(hc));
+        st4(lout + o, C.mask(lc));
+      }
+      hm = hc;
+      lm = lc;
+      hc = hp;
+      lc = lp;
+      hp = hn;
+      lp = ln;
+      b0 = bn;
     }
     double drr = s_rr, dbb = s_bb;
     for (int o = 16; o > 0; o >>= 1) {
-      drr += __shfl_down_sync(0xffffffffu, drr, o);
-      dbb += __shfl_down_sync(0xffffffffu, dbb, o);
+      drr += __shfl_down_sync(FULL, drr, o);
+      dbb += __shfl_down_sync(FULL, dbb, o);
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) {
-      red[0][warp] = drr;
-      red[1][warp] = dbb;
+      atomicAdd(&acc[2 * e.slice], drr);
+      atomicAdd(&acc[2 * e.slice + 1], dbb);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double a0 = 0.0, a1 = 0.0;
-      for (int k = 0; k < BNT / 32; ++k) {
-        a0 += red[0][k];
-        a1 += red[1][k];
-      }
-      atomicAdd(&acc[2 * en.slice], a0);
-      atomicAdd(&acc[2 * en.slice + 1], a1);
-    }
-    __syncthreads();
   }
 }
 
-// I2 = h + l rounded to float32
-__global__ void k_bfinal(float *__restrict__ out, const float *__restrict__ h, const float *__restrict__ l,
-                         long long n) {
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x)
-    out[q] = __fadd_rn(h[q], l[q]);
-}
-
 // Fine right-hand side b = alpha I1 + (Kx + Ky) I0 and the initial float
-// pair (x0 or I0, 0).
+// pair (x0 or I0, 0), from the caller's packed arrays to the internal
+// layout; one 64 x 32 tile per item (entry, i0, j0).
 __global__ void __launch_bounds__(BNT) k_brhs(const BEntry *__restrict__ E, const int4 *__restrict__ items,
                                               int nitems, const float *__restrict__ I0,
                                               const float *__restrict__ I1, const float *__restrict__ x0,
-                                              float *__restrict__ b, float *__restrict__ x,
+                                              float *__restrict__ b, float *__restrict__ xh,
                                               float *__restrict__ xl) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 w = items[it];
     const BEntry e = E[w.x];
-    const int i0 = w.y, j0 = w.z;
-    for (int q = threadIdx.x; q < BY * BX; q += BNT) {
-      const int r = q / BX, c = q - r * BX;
-      const int gi = i0 + c, gj = j0 + r;
-      if (!inside(e, gi, gj)) continue;
-      const long long o = e.off + (long long)gj * e.nx + gi;
-      const float c0 = I0[o];
+    const int i0 = w.y, j0 = w.z, nx = e.nx;
+    for (int q = threadIdx.x; q < TX * TY; q += BNT) {
+      const int gi = i0 + (q % TX), gj = j0 + q / TX;
+      if (gi >= nx || gj >= e.ny) continue;
+      const long long u = e.uoff + (long long)gj * nx + gi;
+      const long long o = e.off + (long long)gj * e.pitch + gi;
+      const float c0 = I0[u];
       float k = 0.f;
-      if (gi > 0) k += c0 - I0[o - 1];
-      if (gi < e.nx - 1) k += c0 - I0[o + 1];
-      if (gj > 0) k += c0 - I0[o - e.nx];
-      if (gj < e.ny - 1) k += c0 - I0[o + e.nx];
-      b[o] = fmaf(e.wm, I1[o], k);
-      x[o] = x0 ? x0[o] : c0;
+      if (gi > 0) k += c0 - I0[u - 1];
+      if (gi < nx - 1) k += c0 - I0[u + 1];
+      if (gj > 0) k += c0 - I0[u - nx];
+      if (gj < e.ny - 1) k += c0 - I0[u + nx];
+      b[o] = fmaf(e.wm, I1[u], k);
+      xh[o] = x0 ? x0[u] : c0;
       xl[o] = 0.f;
+    }
+  }
+}
+
+// I2 = h + l rounded to float32, from the internal layout to the caller's
+// packed array.
+__global__ void __launch_bounds__(BNT) k_bfinal(const BEntry *__restrict__ E, const int4 *__restrict__ items,
+                                                int nitems, const float *__restrict__ h,
+                                                const float *__restrict__ l, float *__restrict__ out) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 w = items[it];
+    const BEntry e = E[w.x];
+    const int i0 = w.y, j0 = w.z;
+    for (int q = threadIdx.x; q < TX * TY; q += BNT) {
+      const int gi = i0 + (q % TX), gj = j0 + q / TX;
+      if (gi >= e.nx || gj >= e.ny) continue;
+      const long long o = e.off + (long long)gj * e.pitch + gi;
+      out[e.uoff + (long long)gj * e.nx + gi] = __fadd_rn(h[o], l[o]);
     }
   }
 }
@@ -426,7 +494,7 @@ __global__ void __launch_bounds__(BNT) k_bfdm(const BCoarse *__restrict__ C, int
     const float *Vx = V + c.vx, *Vy = V + c.vy;
     const float *bl = P.b[c.lev] + c.off;
     float *xl = P.x[c.lev] + c.off;
-    for (int q = threadIdx.x; q < n; q += BNT) B[q] = bl[q];
+    for (int q = threadIdx.x; q < n; q += BNT) B[q] = bl[(q / nx) * c.pitch + q % nx];
     __syncthreads();
     // T[j][k] = sum_i B[j][i] Vx[i][k]
     for (int q = threadIdx.x; q < n; q += BNT) {
@@ -457,7 +525,7 @@ __global__ void __launch_bounds__(BNT) k_bfdm(const BCoarse *__restrict__ C, int
       const int j = q / nx, i = q - j * nx;
       float a = 0.f;
       for (int k = 0; k < nx; ++k) a = fmaf(Vx[i * nx + k], T[j * nx + k], a);
-      xl[q] = a;
+      xl[j * c.pitch + i] = a;
     }
     __syncthreads();
   }
@@ -484,10 +552,12 @@ struct gd_batch {
     float *x = nullptr, *t = nullptr, *b = nullptr;
     BEntry *E = nullptr;            // device
     int ne = 0;
-    int4 *items = nullptr;          // tiles of the entries that have a next level
+    int4 *items = nullptr;          // strips of the entries that have a next level
     int nitems = 0;
-    int4 *items_all = nullptr;      // tiles of every entry (level 0 only)
-    int nitems_all = 0;
+    int4 *strips_all = nullptr;     // level 0: strips of every entry (outer pass)
+    int nstrips_all = 0;
+    int4 *tiles_all = nullptr;      // level 0: 64 x 32 tiles of every entry (input / output)
+    int ntiles_all = 0;
   };
   std::vector<Lev> L;
   BCoarse *C = nullptr;  // device, one per slice
@@ -504,7 +574,8 @@ struct gd_batch {
   int g_nu1 = -1, g_nu2 = -1;
   long long launches = 0;
   long long g_launches = 0;
-  int occ_sweep = 1, occ_aux = 1;
+  int occ_sweep = 1, occ_aux = 1, occ_tile = 1;
+  std::vector<long long> lev_fine_cells, lev_coarse_cells;  // algorithmic traffic per level
   std::string err;
 };
 
@@ -553,7 +624,8 @@ void batch_free(gd_batch *B) {
     cudaFree(l.b);
     cudaFree(l.E);
     cudaFree(l.items);
-    cudaFree(l.items_all);
+    cudaFree(l.strips_all);
+    cudaFree(l.tiles_all);
   }
   cudaFree(B->C);
   cudaFree(B->V);
@@ -618,13 +690,24 @@ std::vector<SliceLevel> slice_levels(int nx, int ny, double alpha, int cxy) {
 }
 
 void tiles_of(int e, int nx, int ny, std::vector<int4> &out) {
-  for (int j0 = 0; j0 < ny; j0 += BY)
-    for (int i0 = 0; i0 < nx; i0 += BX) out.push_back(make_int4(e, i0, j0, 0));
+  for (int j0 = 0; j0 < ny; j0 += TY)
+    for (int i0 = 0; i0 < nx; i0 += TX) out.push_back(make_int4(e, i0, j0, 0));
 }
 
-int grid_for(gd_batch *B, int nitems, int occ) {
+// strips of 120 columns by chunks of CH rows, row-chunk major so that
+// neighbouring warps take neighbouring strips (shared halos in L2)
+void strips_of(int e, int nx, int ny, std::vector<int4> &out) {
+  for (int ys = 0; ys < ny; ys += CH)
+    for (int x0 = 0; x0 < nx; x0 += SW) out.push_back(make_int4(e, x0, ys, std::min(ys + CH, ny)));
+}
+
+int pitch_of(int nx) { return (nx + 3) & ~3; }
+
+// CTAs for a launch over n items: one item per CTA (tile kernels) or per warp
+int grid_for(gd_batch *B, int nitems, int occ, bool warp_items = true) {
+  const int need = warp_items ? (nitems + WPB - 1) / WPB : nitems;
   const int g = B->sm_count * std::max(occ, 1);
-  return std::max(1, std::min(nitems, g));
+  return std::max(1, std::min(need, g));
 }
 
 // One V(nu1, nu2) cycle on the correction equation A e = r: r in L[0].b,
@@ -688,12 +771,12 @@ int outer_pass(gd_batch *B, bool add_e) {
   gd_batch::Lev &f = B->L[0];
   const int a = B->cur, o = 1 - B->cur;
   BCK(cudaMemsetAsync(B->acc, 0, 2 * B->ns * sizeof(double), B->stream));
-  const int g = grid_for(B, f.nitems_all, B->occ_aux);
+  const int g = grid_for(B, f.nstrips_all, B->occ_aux);
   if (add_e)
-    k_bouter<true><<<g, BNT, 0, B->stream>>>(f.E, f.items_all, f.nitems_all, B->bf, B->ph[a], B->pl[a], f.x,
-                                             B->ph[o], B->pl[o], f.b, B->acc);
+    k_bouter<true><<<g, BNT, 0, B->stream>>>(f.E, f.strips_all, f.nstrips_all, B->bf, B->ph[a], B->pl[a],
+                                             f.x, B->ph[o], B->pl[o], f.b, B->acc);
   else
-    k_bouter<false><<<g, BNT, 0, B->stream>>>(f.E, f.items_all, f.nitems_all, B->bf, B->ph[a], B->pl[a],
+    k_bouter<false><<<g, BNT, 0, B->stream>>>(f.E, f.strips_all, f.nstrips_all, B->bf, B->ph[a], B->pl[a],
                                               nullptr, B->ph[o], B->pl[o], f.b, B->acc);
   ++B->launches;
   BCK(cudaGetLastError());
@@ -786,8 +869,10 @@ int batch_build(gd_batch *B) {
       std::memset(&e, 0, sizeof e);
       e.off = o;
       e.coff = -1;
+      e.uoff = B->off[s];
       e.nx = v.nx;
       e.ny = v.ny;
+      e.pitch = pitch_of(v.nx);
       e.sx = v.sx;
       e.sy = v.sy;
       e.lx = v.lx;
@@ -800,7 +885,7 @@ int batch_build(gd_batch *B) {
       e.slice = s;
       eidx[s].push_back((int)E[l].size());
       E[l].push_back(e);
-      o += (long long)v.nx * v.ny;
+      o += (long long)e.pitch * v.ny;
     }
     B->L[l].n = o;
   }
@@ -811,36 +896,59 @@ int batch_build(gd_batch *B) {
       e.coff = c.off;
       e.cnx = c.nx;
       e.cny = c.ny;
+      e.cpitch = c.pitch;
     }
   // work lists and buffers
   int st;
   for (int l = 0; l < D; ++l) {
     gd_batch::Lev &v = B->L[l];
-    std::vector<int4> it, all;
+    std::vector<int4> it, sa, ta;
     for (int k = 0; k < (int)E[l].size(); ++k) {
       const BEntry &e = E[l][k];
-      if (e.coff >= 0) tiles_of(k, e.nx, e.ny, it);
-      if (l == 0) tiles_of(k, e.nx, e.ny, all);
+      if (e.coff >= 0) strips_of(k, e.nx, e.ny, it);
+      if (l == 0) {
+        strips_of(k, e.nx, e.ny, sa);
+        tiles_of(k, e.nx, e.ny, ta);
+      }
     }
+    long long fc = 0, cc = 0;
+    for (const BEntry &e : E[l])
+      if (e.coff >= 0) {
+        fc += (long long)e.pitch * e.ny;
+        cc += (long long)e.cpitch * e.cny;
+      }
+    B->lev_fine_cells.push_back(fc);
+    B->lev_coarse_cells.push_back(cc);
     v.ne = (int)E[l].size();
     v.nitems = (int)it.size();
-    v.nitems_all = (int)all.size();
+    v.nstrips_all = (int)sa.size();
+    v.ntiles_all = (int)ta.size();
     if ((st = balloc(B, &v.x, (size_t)v.n)) != GD_OK) return st;
     if ((st = balloc(B, &v.b, (size_t)v.n)) != GD_OK) return st;
     if (v.nitems > 0 && (st = balloc(B, &v.t, (size_t)v.n)) != GD_OK) return st;
+    // padding cells hold 0 from here on: every kernel writes 0 there
+    BCK(cudaMemset(v.x, 0, (size_t)v.n * sizeof(float)));
+    BCK(cudaMemset(v.b, 0, (size_t)v.n * sizeof(float)));
+    if (v.t) BCK(cudaMemset(v.t, 0, (size_t)v.n * sizeof(float)));
     if ((st = balloc(B, &v.E, E[l].size())) != GD_OK) return st;
     if ((st = balloc(B, &v.items, it.size())) != GD_OK) return st;
-    if ((st = balloc(B, &v.items_all, all.size())) != GD_OK) return st;
+    if ((st = balloc(B, &v.strips_all, sa.size())) != GD_OK) return st;
+    if ((st = balloc(B, &v.tiles_all, ta.size())) != GD_OK) return st;
     BCK(cudaMemcpy(v.E, E[l].data(), E[l].size() * sizeof(BEntry), cudaMemcpyHostToDevice));
     if (!it.empty()) BCK(cudaMemcpy(v.items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    if (!all.empty())
-      BCK(cudaMemcpy(v.items_all, all.data(), all.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!sa.empty())
+      BCK(cudaMemcpy(v.strips_all, sa.data(), sa.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!ta.empty())
+      BCK(cudaMemcpy(v.tiles_all, ta.data(), ta.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
   const size_t n0 = (size_t)B->L[0].n;
   if ((st = balloc(B, &B->bf, n0)) != GD_OK) return st;
+  BCK(cudaMemset(B->bf, 0, n0 * sizeof(float)));
   for (int k = 0; k < 2; ++k) {
     if ((st = balloc(B, &B->ph[k], n0)) != GD_OK) return st;
     if ((st = balloc(B, &B->pl[k], n0)) != GD_OK) return st;
+    BCK(cudaMemset(B->ph[k], 0, n0 * sizeof(float)));
+    BCK(cudaMemset(B->pl[k], 0, n0 * sizeof(float)));
   }
   // coarsest levels: eigen-decompositions shared by equal (n, s, l) axes
   std::map<std::tuple<int, int, int>, std::pair<int, int>> cache;  // -> (V offset, lambda offset)
@@ -865,7 +973,7 @@ int batch_build(gd_batch *B) {
     const BEntry &e = E[l][eidx[s][l]];
     const auto ax = axis(v.nx, v.sx, v.lx);
     const auto ay = axis(v.ny, v.sy, v.ly);
-    C[s] = BCoarse{l, v.nx, v.ny, ax.first, ay.first, ax.second, ay.second,
+    C[s] = BCoarse{l, v.nx, v.ny, e.pitch, ax.first, ay.first, ax.second, ay.second,
                    (float)v.wx, (float)v.wy, (float)v.wm, e.off};
   }
   if ((st = balloc(B, &B->C, C.size())) != GD_OK) return st;
@@ -888,6 +996,7 @@ int batch_build(gd_batch *B) {
   BCK(cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, dev));
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_sweep, k_bsweep<false, true>, BNT, 0));
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_aux, k_bouter<true>, BNT, 0));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_tile, k_brhs, BNT, 0));
   return GD_OK;
 }
 
@@ -957,6 +1066,30 @@ long long gd_batch_offset(const gd_batch *b, int slice) {
 
 int gd_batch_levels(const gd_batch *b) { return b ? b->depth_max : -1; }
 
+int gd_batch_traffic(const gd_batch *b, int nu1, int nu2, double *per_cycle, double *per_solve) {
+  if (!b || nu1 < 1 || nu2 < 1) return GD_ERR_INVALID_ARG;
+  // cells (padded rows) of the entries of each level that have a next level,
+  // and of their next levels
+  double cyc = 0.0;
+  for (size_t l = 0; l < b->L.size(); ++l) {
+    const double nf = (double)b->lev_fine_cells[l], nc = (double)b->lev_coarse_cells[l];
+    if (nf == 0.0) continue;
+    // pre-sweeps: the first from zero reads b and writes x (8 B), the others
+    // read x and b and write x (12 B); post-sweeps likewise, the first adding
+    // the parents (4 B per coarse cell); restriction reads x and b and writes
+    // the coarse b
+    cyc += nf * (8.0 + 12.0 * (nu1 - 1)) + nf * 12.0 * nu2 + 4.0 * nc;
+    cyc += nf * 8.0 + 4.0 * nc;
+  }
+  const double n0 = (double)b->L[0].n;
+  cyc += 28.0 * n0;  // outer pass: reads bf, h, l, e; writes h, l, r
+  if (per_cycle) *per_cycle = cyc;
+  // right-hand side (reads I0, I1; writes bf, h, l), first outer pass
+  // (reads bf, h, l; writes h, l, r), output (reads h, l; writes I2)
+  if (per_solve) *per_solve = 20.0 * (double)b->nvox + 24.0 * n0 + 12.0 * n0;
+  return GD_OK;
+}
+
 long long gd_batch_launch_count(const gd_batch *b) { return b ? b->launches : -1; }
 
 const char *gd_batch_last_error(const gd_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
@@ -1004,8 +1137,8 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
   }
   gd_batch::Lev &f = B->L[0];
   B->cur = 0;
-  k_brhs<<<grid_for(B, f.nitems_all, B->occ_aux), BNT, 0, B->stream>>>(f.E, f.items_all, f.nitems_all, dv[0],
-                                                                       dv[1], dv[2], B->bf, B->ph[0], B->pl[0]);
+  k_brhs<<<grid_for(B, f.ntiles_all, B->occ_tile, false), BNT, 0, B->stream>>>(
+      f.E, f.tiles_all, f.ntiles_all, dv[0], dv[1], dv[2], B->bf, B->ph[0], B->pl[0]);
   ++B->launches;
   BCK(cudaGetLastError());
   int st = outer_pass(B, false);
@@ -1046,7 +1179,8 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
     }
     out = B->stage[3];
   }
-  k_bfinal<<<B->sm_count * 8, 256, 0, B->stream>>>(out, B->ph[B->cur], B->pl[B->cur], (long long)n);
+  k_bfinal<<<grid_for(B, f.ntiles_all, B->occ_tile, false), BNT, 0, B->stream>>>(
+      f.E, f.tiles_all, f.ntiles_all, B->ph[B->cur], B->pl[B->cur], out);
   ++B->launches;
   BCK(cudaGetLastError());
   if (out != I2) BCK(cudaMemcpyAsync(I2, out, n * sizeof(float), cudaMemcpyDeviceToHost, B->stream));
