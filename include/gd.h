@@ -306,6 +306,14 @@ int gd_batch_screened_poisson(gd_batch *b, const float *I0, const float *I1, flo
                               const gd_solve_ctl *ctl, const float *x0, gd_report *rep,
                               double *slice_rel);
 
+/*
+ * gd_batch_tune -- picks the rows per work item of the batch's kernels (32,
+ * 64, 128 or 256; 64 until tuned) by timing two V(2,2) cycles with each, and
+ * keeps the fastest.  Overwrites the batch's internal buffers only; call it
+ * between solves.  chunk_out (nullable) receives the choice.
+ */
+int gd_batch_tune(gd_batch *b, int *chunk_out);
+
 long long gd_batch_voxels(const gd_batch *b);            /* total cells, -1 for NULL */
 long long gd_batch_offset(const gd_batch *b, int slice); /* off_s, -1 if out of range */
 int gd_batch_levels(const gd_batch *b);                  /* depth of the deepest hierarchy */

@@ -48,7 +48,7 @@ namespace {
 constexpr int BNT = 256;  // threads per CTA
 constexpr int WPB = BNT / 32;
 constexpr int SW = 120;   // owned columns of a strip
-constexpr int CH = 64;    // rows of a chunk (even)
+constexpr int CH = 64;    // default rows of a chunk (even; gd_batch_tune picks another)
 constexpr int TX = 64, TY = 32;  // tiles of the element-wise kernels
 constexpr int kBMaxLev = 24;
 constexpr int kFdmMaxCells = 4096;
@@ -576,6 +576,8 @@ struct gd_batch {
   long long g_launches = 0;
   int occ_sweep = 1, occ_aux = 1, occ_tile = 1;
   std::vector<long long> lev_fine_cells, lev_coarse_cells;  // algorithmic traffic per level
+  std::vector<std::vector<BEntry>> Eh;  // host copies of the entries, per level
+  int chunk = CH;                       // rows per work item of the row marches
   std::string err;
 };
 
@@ -694,11 +696,11 @@ void tiles_of(int e, int nx, int ny, std::vector<int4> &out) {
     for (int i0 = 0; i0 < nx; i0 += TX) out.push_back(make_int4(e, i0, j0, 0));
 }
 
-// strips of 120 columns by chunks of CH rows, row-chunk major so that
-// neighbouring warps take neighbouring strips (shared halos in L2)
-void strips_of(int e, int nx, int ny, std::vector<int4> &out) {
-  for (int ys = 0; ys < ny; ys += CH)
-    for (int x0 = 0; x0 < nx; x0 += SW) out.push_back(make_int4(e, x0, ys, std::min(ys + CH, ny)));
+// strips of 120 columns by chunks of `ch` rows (even), row-chunk major so
+// that neighbouring warps take neighbouring strips (shared halos in L2)
+void strips_of(int e, int nx, int ny, int ch, std::vector<int4> &out) {
+  for (int ys = 0; ys < ny; ys += ch)
+    for (int x0 = 0; x0 < nx; x0 += SW) out.push_back(make_int4(e, x0, ys, std::min(ys + ch, ny)));
 }
 
 int pitch_of(int nx) { return (nx + 3) & ~3; }
@@ -836,6 +838,37 @@ int ensure_graph(gd_batch *B, int nu1, int nu2) {
   return GD_OK;
 }
 
+// (Re)builds the row-march work lists for chunks of `ch` rows.
+int build_lists(gd_batch *B, int ch) {
+  int st;
+  for (size_t l = 0; l < B->L.size(); ++l) {
+    gd_batch::Lev &v = B->L[l];
+    std::vector<int4> it, sa;
+    for (int k = 0; k < (int)B->Eh[l].size(); ++k) {
+      const BEntry &e = B->Eh[l][k];
+      if (e.coff >= 0) strips_of(k, e.nx, e.ny, ch, it);
+      if (l == 0) strips_of(k, e.nx, e.ny, ch, sa);
+    }
+    cudaFree(v.items);
+    cudaFree(v.strips_all);
+    v.items = v.strips_all = nullptr;
+    v.nitems = (int)it.size();
+    v.nstrips_all = (int)sa.size();
+    if ((st = balloc(B, &v.items, it.size())) != GD_OK) return st;
+    if ((st = balloc(B, &v.strips_all, sa.size())) != GD_OK) return st;
+    if (!it.empty()) BCK(cudaMemcpy(v.items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!sa.empty())
+      BCK(cudaMemcpy(v.strips_all, sa.data(), sa.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  }
+  B->chunk = ch;
+  if (B->gexec) {  // the graph holds the old lists
+    cudaGraphExecDestroy(B->gexec);
+    B->gexec = nullptr;
+    B->g_nu1 = B->g_nu2 = -1;
+  }
+  return GD_OK;
+}
+
 int batch_build(gd_batch *B) {
   const int ns = B->ns;
   std::vector<std::vector<SliceLevel>> H(ns);
@@ -902,15 +935,8 @@ int batch_build(gd_batch *B) {
   int st;
   for (int l = 0; l < D; ++l) {
     gd_batch::Lev &v = B->L[l];
-    std::vector<int4> it, sa, ta;
-    for (int k = 0; k < (int)E[l].size(); ++k) {
-      const BEntry &e = E[l][k];
-      if (e.coff >= 0) strips_of(k, e.nx, e.ny, it);
-      if (l == 0) {
-        strips_of(k, e.nx, e.ny, sa);
-        tiles_of(k, e.nx, e.ny, ta);
-      }
-    }
+    std::vector<int4> ta;
+    for (int k = 0; k < (int)E[l].size() && l == 0; ++k) tiles_of(k, E[l][k].nx, E[l][k].ny, ta);
     long long fc = 0, cc = 0;
     for (const BEntry &e : E[l])
       if (e.coff >= 0) {
@@ -920,27 +946,22 @@ int batch_build(gd_batch *B) {
     B->lev_fine_cells.push_back(fc);
     B->lev_coarse_cells.push_back(cc);
     v.ne = (int)E[l].size();
-    v.nitems = (int)it.size();
-    v.nstrips_all = (int)sa.size();
     v.ntiles_all = (int)ta.size();
     if ((st = balloc(B, &v.x, (size_t)v.n)) != GD_OK) return st;
     if ((st = balloc(B, &v.b, (size_t)v.n)) != GD_OK) return st;
-    if (v.nitems > 0 && (st = balloc(B, &v.t, (size_t)v.n)) != GD_OK) return st;
+    if (fc > 0 && (st = balloc(B, &v.t, (size_t)v.n)) != GD_OK) return st;
     // padding cells hold 0 from here on: every kernel writes 0 there
     BCK(cudaMemset(v.x, 0, (size_t)v.n * sizeof(float)));
     BCK(cudaMemset(v.b, 0, (size_t)v.n * sizeof(float)));
     if (v.t) BCK(cudaMemset(v.t, 0, (size_t)v.n * sizeof(float)));
     if ((st = balloc(B, &v.E, E[l].size())) != GD_OK) return st;
-    if ((st = balloc(B, &v.items, it.size())) != GD_OK) return st;
-    if ((st = balloc(B, &v.strips_all, sa.size())) != GD_OK) return st;
     if ((st = balloc(B, &v.tiles_all, ta.size())) != GD_OK) return st;
     BCK(cudaMemcpy(v.E, E[l].data(), E[l].size() * sizeof(BEntry), cudaMemcpyHostToDevice));
-    if (!it.empty()) BCK(cudaMemcpy(v.items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    if (!sa.empty())
-      BCK(cudaMemcpy(v.strips_all, sa.data(), sa.size() * sizeof(int4), cudaMemcpyHostToDevice));
     if (!ta.empty())
       BCK(cudaMemcpy(v.tiles_all, ta.data(), ta.size() * sizeof(int4), cudaMemcpyHostToDevice));
   }
+  B->Eh = E;
+  if ((st = build_lists(B, CH)) != GD_OK) return st;
   const size_t n0 = (size_t)B->L[0].n;
   if ((st = balloc(B, &B->bf, n0)) != GD_OK) return st;
   BCK(cudaMemset(B->bf, 0, n0 * sizeof(float)));
@@ -1192,6 +1213,44 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
     rep->rho_per_cycle = (cycles > 0 && rel0 > 0.0) ? std::pow(rel / rel0, 1.0 / cycles) : NAN;
   }
   return status;
+}
+
+int gd_batch_tune(gd_batch *B, int *chunk_out) {
+  if (!B) return GD_ERR_INVALID_ARG;
+  // every candidate runs the same V(2, 2) cycle on whatever the buffers
+  // hold (the timing does not depend on the values); the next solve starts
+  // from its own right-hand side
+  static const int cand[] = {32, 64, 128, 256};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  BCK(cudaEventCreate(&e0));
+  BCK(cudaEventCreate(&e1));
+  int best = B->chunk;
+  float best_ms = 0.f;
+  int st = GD_OK;
+  for (int c : cand) {
+    if ((st = build_lists(B, c)) != GD_OK) break;
+    if ((st = bvcycle(B, 2, 2, B->stream)) != GD_OK) break;  // warm-up
+    cudaEventRecord(e0, B->stream);
+    for (int r = 0; r < 2 && st == GD_OK; ++r) st = bvcycle(B, 2, 2, B->stream);
+    cudaEventRecord(e1, B->stream);
+    if (st != GD_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      bset_err(B, "tuning run failed: %s", cudaGetErrorString(cudaGetLastError()));
+      st = GD_ERR_CUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (best_ms == 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == GD_OK) st = build_lists(B, best);
+  if (chunk_out) *chunk_out = B->chunk;
+  return st;
 }
 
 int gd_batch_destroy(gd_batch *b) {

@@ -139,3 +139,23 @@ def test_batch_full_size_512_slices(torch):
     order = np.argsort(sides)
     sample = [int(order[0]), int(order[n // 2]), int(order[-1]), int(np.argmin(al))]
     check_slices(outs, I0s, I1s, al, idx=sample)
+
+
+def test_batch_tuning_keeps_results_bitwise(torch):
+    # the work decomposition (rows per item) changes no cell's arithmetic:
+    # a red value depends only on old black values wherever it is computed
+    nx, ny, al, I0s, I1s = ragged_case(24)
+    ctl = gd.solve_ctl(40, 1e-7)
+    b = gd.gd_batch_create(nx, ny, al)
+    try:
+        I0 = torch.from_numpy(gdsynth.pack(I0s)).cuda()
+        I1 = torch.from_numpy(gdsynth.pack(I1s)).cuda()
+        o1, o2 = torch.empty_like(I0), torch.empty_like(I0)
+        r1 = gd.gd_batch_screened_poisson(b, I0, I1, o1, ctl)
+        chunk = gd.gd_batch_tune(b)
+        assert chunk in (32, 64, 128, 256)
+        r2 = gd.gd_batch_screened_poisson(b, I0, I1, o2, ctl)
+    finally:
+        gd.gd_batch_destroy(b)
+    assert r1["cycles"] == r2["cycles"]
+    assert torch.equal(o1, o2)
