@@ -382,6 +382,43 @@ def run_gpu(args):
         del V0, Vb, Vx
         torch.cuda.empty_cache()
 
+    # The Hybrid discretisation (Sec. 4.2: 6-point fine operator, first-order
+    # B-spline transfers, Galerkin 27-point coarse operators) on the same
+    # stack and tolerances.
+    hybrid = None
+    if not args.no_hybrid:
+        sh = gd.gd_stack_create(NX, NY, NZ, disc=gd.GD_DISC_HYBRID, stream=stream.cuda_stream)
+        hreps = []
+
+        def hstep():
+            h1 = gd.gd_diffuse_z(sh, I0, I1, w_ad, ctl)
+            h2 = gd.gd_screened_poisson_slices(sh, I0, I1, I2, ALPHA, ctl_sp)
+            hreps.append((h1, h2))
+
+        for _ in range(max(1, min(args.warmup, 2))):
+            hstep()
+        hreps.clear()
+        hsteps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(hsteps):
+            hstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        hms = reduce_max(e0.elapsed_time(e1), world, dev)
+        gd.gd_destroy(sh)
+        h1, h2 = hreps[-1]
+        hybrid = {"value": world * voxels * hsteps / (hms * 1e-3), "unit": UNIT,
+                  "ms_per_step": hms / hsteps, "steps": hsteps,
+                  "discretisation": "hybrid: 6-point fine, B-spline transfers, Galerkin 27-point coarse",
+                  "ad_cycles": h1["cycles"], "ad_rho_per_cycle": h1["rho_per_cycle"],
+                  "ad_rel_residual": h1["rel_residual"], "sp_cycles": h2["cycles"],
+                  "sp_rho_per_cycle": h2["rho_per_cycle"], "sp_rel_residual": h2["rel_residual"],
+                  "constant_ad_rho_per_cycle": reps[-1][0]["rho_per_cycle"],
+                  "constant_sp_rho_per_cycle": reps[-1][1]["rho_per_cycle"]}
+
     # Batched screened Poisson on 512 independent slices, square, sides
     # log-uniform in [256, 4096], alpha ~ U(0.001, 0.1) per slice; every
     # slice to 1e-7 relative residual, timed like the main workload.
@@ -525,6 +562,7 @@ def run_gpu(args):
             "mixed": mixed,
             "npr": npr,
             "batch": batch,
+            "hybrid": hybrid,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -587,6 +625,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-npr", action="store_true", help="skip the NPR filter measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-slices measurement")
+    ap.add_argument("--no-hybrid", action="store_true", help="skip the Hybrid discretisation measurement")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="one solve of the 512-slice batch for ncu launch lists (no timing)")
     ap.add_argument("--ncu-case", action="store_true",

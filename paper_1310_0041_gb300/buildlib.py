@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgd.so")
-SOURCES = ["gd_kernels.cu", "gd_zmarch.cu", "gd_host.cu", "gd_batch.cu", "gd_eig.cpp"]
+SOURCES = ["gd_kernels.cu", "gd_zmarch.cu", "gd_host.cu", "gd_batch.cu", "gd_hybrid.cu", "gd_eig.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

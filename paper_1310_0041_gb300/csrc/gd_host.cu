@@ -47,6 +47,9 @@ struct Level {
   float *x = nullptr, *b = nullptr, *t = nullptr;
   size_t n = 0;
   int esz = 4;
+  // Hybrid discretisation: the level's per-axis Galerkin factors
+  float *hf = nullptr;
+  HLevelDev hd{};
 };
 
 // internal system id of the general screened Poisson solve (explicit b)
@@ -273,6 +276,7 @@ void plan_free(gd_stack *s, Plan &P) {
     dfree(P.L[li].b);
     dfree(P.L[li].t);
   }
+  for (auto &l : P.L) dfree(l.hf);
   P.L.clear();
   dfree(P.Vx);
   dfree(P.Vy);
@@ -408,20 +412,83 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
     if ((st = dalloc(s, &l.b, nf)) != GD_OK) return st;
     if ((st = dalloc(s, &l.t, nf)) != GD_OK) return st;
   }
+  // Hybrid: per-axis Galerkin factors (K_d, M_d) of every level, from the
+  // fine (1D Neumann Laplacian, identity) through P^T . P along halved axes
+  const bool hybrid = s->disc == GD_DISC_HYBRID;
+  std::vector<double> HK[3], HM[3];
+  if (hybrid) {
+    const int n0[3] = {s->nx, s->ny, s->nz};
+    for (int a = 0; a < 3; ++a) {
+      const int n = n0[a];
+      HK[a].assign((size_t)n * 3, 0.0);
+      HM[a].assign((size_t)n * 3, 0.0);
+      for (int i = 0; i < n; ++i) {
+        if (i > 0) {
+          HK[a][(size_t)i * 3 + 0] = -1.0;
+          HK[a][(size_t)i * 3 + 1] += 1.0;
+        }
+        if (i < n - 1) {
+          HK[a][(size_t)i * 3 + 2] = -1.0;
+          HK[a][(size_t)i * 3 + 1] += 1.0;
+        }
+        HM[a][(size_t)i * 3 + 1] = 1.0;
+      }
+    }
+    for (size_t li = 0; li < P.L.size(); ++li) {
+      Level &l = P.L[li];
+      if (li > 0) {
+        const Level &f = P.L[li - 1];
+        const int fl[3] = {f.fx, f.fy, f.fz}, nf[3] = {f.d.nx, f.d.ny, f.d.nz};
+        for (int a = 0; a < 3; ++a)
+          if (fl[a]) {
+            std::vector<double> t;
+            galerkin_tri(nf[a], HK[a], t);
+            HK[a].swap(t);
+            galerkin_tri(nf[a], HM[a], t);
+            HM[a].swap(t);
+          }
+      }
+      const int nn[3] = {l.d.nx, l.d.ny, l.d.nz};
+      std::vector<float> h;
+      for (int a = 0; a < 3; ++a) {
+        for (int q = 0; q < 3 * nn[a]; ++q) h.push_back((float)HK[a][q]);
+        for (int q = 0; q < 3 * nn[a]; ++q) h.push_back((float)HM[a][q]);
+      }
+      int st;
+      if ((st = dalloc(s, &l.hf, h.size())) != GD_OK) return st;
+      CK(cudaMemcpyAsync(l.hf, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+      const float *b0 = l.hf;
+      l.hd = HLevelDev{l.d.nx, l.d.ny, l.d.nz, (float)w[1], (float)w[2], batch_z ? 0.f : (float)w[3],
+                       (float)w[0], b0, b0 + 3 * nn[0], b0 + 6 * nn[0], b0 + 6 * nn[0] + 3 * nn[1],
+                       b0 + 6 * nn[0] + 6 * nn[1], b0 + 6 * nn[0] + 6 * nn[1] + 3 * nn[2]};
+    }
+  }
   // coarsest-level fast diagonalisation data
   const LevelDev &c = P.L.back().d;
   std::vector<float> Vx, Vy, Vz;
   std::vector<double> lx, ly, lz;
-  axis_eig(c.nx, c.sx, c.lx, Vx, lx);
-  axis_eig(c.ny, c.sy, c.ly, Vy, ly);
+  double cw[4] = {c.wm, c.wx, c.wy, c.wz};
+  if (hybrid) {
+    axis_eig_tri(c.nx, HK[0], HM[0], Vx, lx);
+    axis_eig_tri(c.ny, HK[1], HM[1], Vy, ly);
+    if (!batch_z) axis_eig_tri(c.nz, HK[2], HM[2], Vz, lz);
+    cw[0] = w[0];
+    cw[1] = w[1];
+    cw[2] = w[2];
+    cw[3] = batch_z ? 0.0 : w[3];
+  } else {
+    axis_eig(c.nx, c.sx, c.lx, Vx, lx);
+    axis_eig(c.ny, c.sy, c.ly, Vy, ly);
+    if (!batch_z) axis_eig(c.nz, c.sz, c.lz, Vz, lz);
+  }
   const int dz = batch_z ? 1 : c.nz;
-  if (!batch_z) axis_eig(c.nz, c.sz, c.lz, Vz, lz);
   std::vector<double> D((size_t)c.nx * c.ny * dz);
   double dmax = 0.0;
   for (int k = 0; k < dz; ++k)
     for (int j = 0; j < c.ny; ++j)
       for (int i = 0; i < c.nx; ++i) {
-        double v = c.wx * lx[i] + c.wy * ly[j] + (batch_z ? 0.0 : c.wz * lz[k]) + c.wm;
+        double v = cw[1] * lx[i] + cw[2] * ly[j] + (batch_z ? 0.0 : cw[3] * lz[k]) + cw[0];
         D[((size_t)k * c.ny + j) * c.nx + i] = v;
         dmax = std::fmax(dmax, std::fabs(v));
       }
@@ -547,11 +614,72 @@ int coarsest_solve(gd_stack *s, Level &l) {
   return GD_OK;
 }
 
+// One V(nu1, nu2) cycle of the Hybrid discretisation: red-black sweeps of
+// the 6-point fine level, eight-colour sweeps of the 27-point Galerkin
+// levels, first-order B-spline transfers as separate passes.
+int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
+  std::vector<Level> &L = s->cur->L;
+  const int nl = (int)L.size();
+  int st;
+  if (nl == 1) {
+    if ((st = coarsest_solve(s, L[0])) != GD_OK) return st;
+    if (sum_e && (st = sweep(s, 0, false, false, false, true)) != GD_OK) return st;
+    return GD_OK;
+  }
+  auto gs = [&](Level &v) -> int {
+    ProfScope ps(s, P_SWEEP_COARSE, (double)v.n * 12.0);
+    CK(launch_h_gs(v.hd, v.x, v.b, s->stream));
+    s->launches += 7;  // eight colour launches
+    return GD_OK;
+  };
+  for (int l = 0; l < nl - 1; ++l) {
+    Level &v = L[l], &c = L[l + 1];
+    if (l == 0) {
+      for (int k = 0; k < nu1; ++k)
+        if ((st = sweep(s, 0, zero_init && k == 0, false, false, false)) != GD_OK) return st;
+    } else {
+      {
+        ProfScope ps(s, P_SWEEP_COARSE, (double)v.n * 4.0);
+        CK(launch_fill(v.x, v.n, 0.f, s->stream));
+      }
+      for (int k = 0; k < nu1; ++k)
+        if ((st = gs(v)) != GD_OK) return st;
+    }
+    {
+      ProfScope ps(s, P_RESTRICT, (double)v.n * 12.0);
+      CK(launch_h_resid(v.hd, l == 0, v.x, v.b, v.t, s->stream));
+    }
+    {
+      ProfScope ps(s, P_RESTRICT, (double)v.n * 4.0 + (double)c.n * 4.0);
+      CK(launch_h_restrict(v.d.nx, v.d.ny, v.d.nz, v.fx, v.fy, v.fz, c.d.nx, c.d.ny, c.d.nz, v.t, c.b,
+                           s->stream));
+    }
+  }
+  if ((st = coarsest_solve(s, L[nl - 1])) != GD_OK) return st;
+  for (int l = nl - 2; l >= 0; --l) {
+    Level &v = L[l], &c = L[l + 1];
+    {
+      ProfScope ps(s, P_PROLONG, (double)v.n * 8.0 + (double)c.n * 4.0);
+      CK(launch_h_prolong(v.d.nx, v.d.ny, v.d.nz, v.fx, v.fy, v.fz, c.d.nx, c.d.ny, c.d.nz, c.x, v.x,
+                          s->stream));
+    }
+    if (l == 0) {
+      for (int k = 0; k < nu2; ++k)
+        if ((st = sweep(s, 0, false, false, false, sum_e && k == nu2 - 1)) != GD_OK) return st;
+    } else {
+      for (int k = 0; k < nu2; ++k)
+        if ((st = gs(v)) != GD_OK) return st;
+    }
+  }
+  return GD_OK;
+}
+
 // One V(nu1,nu2) cycle on level 0's (x, b).  zero_init: level 0's x starts at
 // zero (correction form).  sum_e: the last fine sweep also sums its output
 // into scalars[S_E].  The last pre-sweep of a level carries the residual and
 // its down-sampling; the first post-sweep carries the up-sampled correction.
 int vcycle(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
+  if (s->disc == GD_DISC_HYBRID) return vcycle_hybrid(s, nu1, nu2, zero_init, sum_e);
   std::vector<Level> &L = s->cur->L;
   const int nl = (int)L.size();
   int st;
@@ -1012,8 +1140,10 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
   if (nx < 2 || ny < 2 || nz < 1) return GD_ERR_INVALID_ARG;
   if ((double)nx * ny * nz > 9.0e18 / 64) return GD_ERR_INVALID_ARG;
   if (bc != GD_BC_NEUMANN) return GD_ERR_UNSUPPORTED;
-  if (disc != GD_DISC_CONSTANT) return disc == GD_DISC_HYBRID || disc == GD_DISC_LINEAR ? GD_ERR_UNSUPPORTED : GD_ERR_INVALID_ARG;
+  if (disc != GD_DISC_CONSTANT && disc != GD_DISC_HYBRID)
+    return disc == GD_DISC_LINEAR ? GD_ERR_UNSUPPORTED : GD_ERR_INVALID_ARG;
   if (prec != GD_PREC_FP32 && prec != GD_PREC_MIXED) return GD_ERR_INVALID_ARG;
+  if (disc == GD_DISC_HYBRID && prec != GD_PREC_FP32) return GD_ERR_UNSUPPORTED;
   gd_stack *s = new (std::nothrow) gd_stack();
   if (!s) return GD_ERR_OOM;
   s->nx = nx;

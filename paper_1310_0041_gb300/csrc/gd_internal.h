@@ -116,6 +116,33 @@ cudaError_t launch_copy(float *dst, const float *src, size_t n, cudaStream_t st)
 cudaError_t launch_npr_rhs(const float *I0, float *b, int nx, int ny, int nz, double alpha, double wx,
                            double wy, double wz, double lam, double sigma, cudaStream_t st);
 
+// A level of the Hybrid discretisation (gd_hybrid.cu): the Kronecker form
+// of the fine operator with per-axis tridiagonal factors, 3 floats per index
+// (sub-diagonal, diagonal, super-diagonal), and the fine weights.
+struct HLevelDev {
+  int nx, ny, nz;
+  float wx, wy, wz, wm;
+  const float *kx, *mx, *ky, *my, *kz, *mz;
+};
+// eight-colour Gauss-Seidel sweep of a 27-point level, in place
+cudaError_t launch_h_gs(const HLevelDev &L, float *x, const float *b, cudaStream_t st);
+// r = b - A x (six: the fine 6-point operator, factors unused)
+cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const float *b, float *r,
+                           cudaStream_t st);
+// bc = P^T r and x += P e with the first-order B-spline transfers along the
+// halved axes (fx, fy, fz)
+cudaError_t launch_h_restrict(int nx, int ny, int nz, int fx, int fy, int fz, int cnx, int cny, int cnz,
+                              const float *r, float *bc, cudaStream_t st);
+cudaError_t launch_h_prolong(int nx, int ny, int nz, int fx, int fy, int fz, int cnx, int cny, int cnz,
+                             const float *e, float *x, cudaStream_t st);
+// Host: the per-axis Galerkin product T_c = P^T T P of a tridiagonal T (n x 3)
+// with the first-order B-spline prolongation from nc = ceil(n / 2) cells.
+void galerkin_tri(int n, const std::vector<double> &T, std::vector<double> &Tc);
+// Host: generalised eigen-decomposition of tridiagonal (K, M) (n x 3 each, M
+// symmetric positive definite): V^T M V = I, V^T K V = diag(lam).
+void axis_eig_tri(int n, const std::vector<double> &K, const std::vector<double> &M, std::vector<float> &V,
+                  std::vector<double> &lam);
+
 // Host: symmetric eigen-decomposition (cyclic Jacobi), FP64, row-major a[n*n].
 // On return w holds the eigenvalues and v (row-major, column k = eigenvector k).
 void jacobi_eigen(int n, double *a, double *w, double *v);
