@@ -419,6 +419,36 @@ def run_gpu(args):
                   "constant_ad_rho_per_cycle": reps[-1][0]["rho_per_cycle"],
                   "constant_sp_rho_per_cycle": reps[-1][1]["rho_per_cycle"]}
 
+    # The Linear discretisation (Sec. 4.2, trilinear finite elements: a
+    # 27-point fine operator, FP64 residuals) on the same stack.
+    linear = None
+    if not args.no_hybrid:
+        sl = gd.gd_stack_create(NX, NY, NZ, disc=gd.GD_DISC_LINEAR, stream=stream.cuda_stream)
+        lreps = []
+
+        def lstep():
+            l1 = gd.gd_diffuse_z(sl, I0, I1, w_ad, ctl)
+            l2 = gd.gd_screened_poisson_slices(sl, I0, I1, I2, ALPHA, ctl_sp)
+            lreps.append((l1, l2))
+
+        lstep()
+        lreps.clear()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        lstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        lms = reduce_max(e0.elapsed_time(e1), world, dev)
+        gd.gd_destroy(sl)
+        l1, l2 = lreps[-1]
+        linear = {"value": world * voxels / (lms * 1e-3), "unit": UNIT, "ms_per_step": lms, "steps": 1,
+                  "discretisation": "linear: trilinear elements, 27-point fine operator",
+                  "ad_cycles": l1["cycles"], "ad_rho_per_cycle": l1["rho_per_cycle"],
+                  "ad_rel_residual": l1["rel_residual"], "sp_cycles": l2["cycles"],
+                  "sp_rho_per_cycle": l2["rho_per_cycle"], "sp_rel_residual": l2["rel_residual"]}
+
     # Batched screened Poisson on 512 independent slices, square, sides
     # log-uniform in [256, 4096], alpha ~ U(0.001, 0.1) per slice; every
     # slice to 1e-7 relative residual, timed like the main workload.
@@ -563,6 +593,7 @@ def run_gpu(args):
             "npr": npr,
             "batch": batch,
             "hybrid": hybrid,
+            "linear": linear,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -625,7 +656,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-npr", action="store_true", help="skip the NPR filter measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-slices measurement")
-    ap.add_argument("--no-hybrid", action="store_true", help="skip the Hybrid discretisation measurement")
+    ap.add_argument("--no-hybrid", action="store_true",
+                    help="skip the Hybrid and Linear discretisation measurements")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="one solve of the 512-slice batch for ncu launch lists (no timing)")
     ap.add_argument("--ncu-case", action="store_true",

@@ -112,7 +112,21 @@ typedef struct {
  * weights keep the same coarsening plan).
  *   nx, ny >= 2, nz >= 1:  stack size (voxels) -- Sec. 3.1, slices along z
  *   bc:   GD_BC_NEUMANN only (others: GD_ERR_UNSUPPORTED)
- *   disc: GD_DISC_CONSTANT only (Sec. 4.2; others: GD_ERR_UNSUPPORTED)
+ *   disc: the discretisation of Sec. 4.2:
+ *         GD_DISC_CONSTANT -- 6-point operator, piecewise-constant transfers,
+ *           re-discretised 6-point coarse operators (the fast path);
+ *         GD_DISC_HYBRID -- the same 6-point fine operator (same answers),
+ *           first-order B-spline transfers (1/2, 1, 1/2) and Galerkin
+ *           27-point coarse operators, eight-colour Gauss-Seidel on them;
+ *         GD_DISC_LINEAR -- trilinear finite elements: the fine operator is
+ *           27-point (1D stiffness K_n and P1 mass (1/6) tridiag(1, [2, 4,
+ *           ..., 4, 2], 1) per axis; an axis of one node, and z for the
+ *           per-slice step, keep mass 1), the right-hand sides are the same
+ *           operators applied to I0 and I1, the residual of the float-pair
+ *           iterate is evaluated in FP64; B-spline transfers, Galerkin
+ *           levels.  gd_vcycle, gd_residual and gd_smooth evaluate the
+ *           6-point operator and return GD_ERR_UNSUPPORTED on such a stack.
+ *         Hybrid and Linear need prec = GD_PREC_FP32 (else GD_ERR_UNSUPPORTED).
  *   prec: GD_PREC_FP32, or GD_PREC_MIXED: the correction solves of
  *         gd_diffuse_z / gd_screened_poisson_slices store every multigrid level
  *         but the coarsest (corrections, constraints, sweep arrays) as

@@ -105,6 +105,7 @@ struct gd_stack {
   float *f_x = nullptr, *f_b = nullptr, *f_t = nullptr;  // fine-level workspace
   // fine-level outer iterate buffers (second float pair, low parts)
   float *xh2 = nullptr, *xl1 = nullptr, *xl2 = nullptr;
+  float *lbh = nullptr;  // Linear discretisation: high part of the right-hand side
   double *partials = nullptr;
   int partials_cap = 0;  // blocks
   double *scalars = nullptr;
@@ -414,7 +415,11 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
   }
   // Hybrid: per-axis Galerkin factors (K_d, M_d) of every level, from the
   // fine (1D Neumann Laplacian, identity) through P^T . P along halved axes
-  const bool hybrid = s->disc == GD_DISC_HYBRID;
+  // Linear: the fine mass factors are the P1 mass (1/6) tridiag(1, [2, 4,
+  // ..., 4, 2], 1) (an axis of one node, or the z axis of independent
+  // slices, keeps M = I)
+  const bool hybrid = s->disc != GD_DISC_CONSTANT;
+  const bool p1 = s->disc == GD_DISC_LINEAR;
   std::vector<double> HK[3], HM[3];
   if (hybrid) {
     const int n0[3] = {s->nx, s->ny, s->nz};
@@ -433,6 +438,12 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
         }
         HM[a][(size_t)i * 3 + 1] = 1.0;
       }
+      if (p1 && n > 1 && !(a == 2 && batch_z))
+        for (int i = 0; i < n; ++i) {
+          HM[a][(size_t)i * 3 + 0] = i > 0 ? 1.0 / 6.0 : 0.0;
+          HM[a][(size_t)i * 3 + 2] = i < n - 1 ? 1.0 / 6.0 : 0.0;
+          HM[a][(size_t)i * 3 + 1] = (i > 0 ? 2.0 / 6.0 : 0.0) + (i < n - 1 ? 2.0 / 6.0 : 0.0);
+        }
     }
     for (size_t li = 0; li < P.L.size(); ++li) {
       Level &l = P.L[li];
@@ -620,10 +631,11 @@ int coarsest_solve(gd_stack *s, Level &l) {
 int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
   std::vector<Level> &L = s->cur->L;
   const int nl = (int)L.size();
+  const bool six0 = s->disc == GD_DISC_HYBRID;  // the fine level is 6-point (Hybrid) or 27-point (Linear)
   int st;
   if (nl == 1) {
     if ((st = coarsest_solve(s, L[0])) != GD_OK) return st;
-    if (sum_e && (st = sweep(s, 0, false, false, false, true)) != GD_OK) return st;
+    if (six0 && sum_e && (st = sweep(s, 0, false, false, false, true)) != GD_OK) return st;
     return GD_OK;
   }
   auto gs = [&](Level &v) -> int {
@@ -634,11 +646,11 @@ int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
   };
   for (int l = 0; l < nl - 1; ++l) {
     Level &v = L[l], &c = L[l + 1];
-    if (l == 0) {
+    if (l == 0 && six0) {
       for (int k = 0; k < nu1; ++k)
         if ((st = sweep(s, 0, zero_init && k == 0, false, false, false)) != GD_OK) return st;
     } else {
-      {
+      if (l > 0 || zero_init) {
         ProfScope ps(s, P_SWEEP_COARSE, (double)v.n * 4.0);
         CK(launch_fill(v.x, v.n, 0.f, s->stream));
       }
@@ -647,7 +659,7 @@ int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
     }
     {
       ProfScope ps(s, P_RESTRICT, (double)v.n * 12.0);
-      CK(launch_h_resid(v.hd, l == 0, v.x, v.b, v.t, s->stream));
+      CK(launch_h_resid(v.hd, l == 0 && six0, v.x, v.b, v.t, s->stream));
     }
     {
       ProfScope ps(s, P_RESTRICT, (double)v.n * 4.0 + (double)c.n * 4.0);
@@ -663,7 +675,7 @@ int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
       CK(launch_h_prolong(v.d.nx, v.d.ny, v.d.nz, v.fx, v.fy, v.fz, c.d.nx, c.d.ny, c.d.nz, c.x, v.x,
                           s->stream));
     }
-    if (l == 0) {
+    if (l == 0 && six0) {
       for (int k = 0; k < nu2; ++k)
         if ((st = sweep(s, 0, false, false, false, sum_e && k == nu2 - 1)) != GD_OK) return st;
     } else {
@@ -679,7 +691,7 @@ int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
 // into scalars[S_E].  The last pre-sweep of a level carries the residual and
 // its down-sampling; the first post-sweep carries the up-sampled correction.
 int vcycle(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
-  if (s->disc == GD_DISC_HYBRID) return vcycle_hybrid(s, nu1, nu2, zero_init, sum_e);
+  if (s->disc != GD_DISC_CONSTANT) return vcycle_hybrid(s, nu1, nu2, zero_init, sum_e);
   std::vector<Level> &L = s->cur->L;
   const int nl = (int)L.size();
   int st;
@@ -941,8 +953,157 @@ void rep_init(gd_report *rep) {
 }
 
 // Solve one of the two systems with iterative refinement on the float pair.
+// The Linear discretisation's driver: the right-hand side once as an FP64
+// float pair, then V-cycles on the correction with the float-pair iterate
+// updated and its residual evaluated in FP64 after each; AD keeps the plain
+// sum of I0 by a constant shift of the output (the constant is A's null
+// space, so the shift changes no residual).
+int solve_linear(gd_stack *s, int system, const float *I0h, const float *I1h, float *outh, double w[4],
+                 const gd_solve_ctl *ctl_in, const float *x0h, gd_report *rep) {
+  rep_init(rep);
+  gd_solve_ctl ctl;
+  int st = check_ctl(s, ctl_in, &ctl);
+  if (st != GD_OK) return report(rep, st);
+  if ((st = ensure_common(s)) != GD_OK) return report(rep, st);
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  float *I0 = nullptr, *I1 = nullptr, *out = nullptr, *x0 = nullptr;
+  const bool out_host = !is_device_ptr(outh);
+  if ((st = resolve(s, I0h, true, 0, &I0)) != GD_OK) return report(rep, st);
+  if (system == GD_SYSTEM_SP && (st = resolve(s, I1h, true, 1, &I1)) != GD_OK) return report(rep, st);
+  const bool generic = system == SYS_GENERIC;
+  if ((st = resolve(s, outh, false, 2, &out)) != GD_OK) return report(rep, st);
+  if (x0h && (st = resolve(s, x0h, true, 3, &x0)) != GD_OK) return report(rep, st);
+  const bool uncoupled = system == GD_SYSTEM_SP || (generic && w[3] == 0.0);
+  if ((st = plan_build(s, w, uncoupled, ctl.coarsest_xy, GD_PREC_FP32)) != GD_OK) return report(rep, st);
+  Plan &P = *s->cur;
+  Level &F = P.L[0];
+  if (rep) rep->levels = (int)P.L.size();
+  // float pair of the iterate (xh2, xl1) and of the right-hand side (xl2, out)
+  if (!s->xh2 && (st = dalloc(s, &s->xh2, n)) != GD_OK) return report(rep, st);
+  if (!s->xl1 && (st = dalloc(s, &s->xl1, n)) != GD_OK) return report(rep, st);
+  if (!s->xl2 && (st = dalloc(s, &s->xl2, n)) != GD_OK) return report(rep, st);
+  if (!s->lbh && (st = dalloc(s, &s->lbh, n)) != GD_OK) return report(rep, st);
+  float *xh = s->xh2, *xl = s->xl1, *bh = s->lbh, *bl = s->xl2;
+  LinW lw;
+  if (system == GD_SYSTEM_SP)
+    lw = LinW{w[1], w[2], 0.0, w[0], 1.0, 1.0, w[0]};
+  else if (generic)
+    lw = LinW{w[1], w[2], uncoupled ? 0.0 : w[3], w[0], 0.0, 0.0, 0.0};
+  else
+    lw = LinW{w[1], w[2], w[3], 0.0, w[1], w[2], 0.0};
+  const HLevelDev &L0 = F.hd;
+  const int mean_fix = system == GD_SYSTEM_AD;
+  int nb = 0;
+  {
+    ProfScope ps(s, P_OUTER, (double)n * 16.0);
+    if (generic) {
+      CK(launch_copy(bh, I0, n, s->stream));
+      CK(launch_fill(bl, n, 0.f, s->stream));
+    } else {
+      CK(launch_l_rhs(L0, lw, I0, I1, bh, bl, s->stream));
+    }
+  }
+  {
+    ProfScope ps(s, P_COPY, (double)n * 8.0);
+    const float *start = x0 ? x0 : (system == GD_SYSTEM_SP ? I0 : nullptr);
+    if (start)
+      CK(launch_copy(xh, start, n, s->stream));
+    else
+      CK(launch_fill(xh, n, 0.f, s->stream));
+    CK(launch_fill(xl, n, 0.f, s->stream));
+  }
+  if ((st = ensure_partials(s, linear_grid((long long)n) + 8)) != GD_OK) return report(rep, st);
+  double sum_i0 = 0.0;
+  auto reduce_read = [&](int lo, int hi, double *outv) -> int {
+    CK(launch_reduce(s->partials, nb, s->scalars, lo, hi, 0, s->stream));
+    CK(cudaMemcpyAsync(s->h_scalars, s->scalars, 8 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int k = lo; k < hi; ++k) outv[k] = s->h_scalars[k];
+    return GD_OK;
+  };
+  double hs[S_NUM] = {0, 0, 0, 0, 0};
+  if (mean_fix) {
+    CK(launch_l_sum((long long)n, I0, s->partials, S_I0, &nb, s->stream));
+    if ((st = reduce_read(S_I0, S_I0 + 1, hs)) != GD_OK) return report(rep, st);
+    sum_i0 = hs[S_I0];
+  }
+  auto residual = [&](double *rel_out, double *bnorm_out) -> int {
+    {
+      ProfScope ps(s, P_OUTER, (double)n * 20.0);
+      CK(launch_l_resid(L0, lw, bh, bl, xh, xl, F.b, s->partials, &nb, s->stream));
+    }
+    int r = reduce_read(S_RR, S_BB + 1, hs);
+    if (r != GD_OK) return r;
+    *bnorm_out = std::sqrt(hs[S_BB]);
+    *rel_out = std::sqrt(hs[S_RR]) / (*bnorm_out > 0.0 ? *bnorm_out : 1.0);
+    return GD_OK;
+  };
+  double rel = 0.0, bnorm = 0.0;
+  if ((st = residual(&rel, &bnorm)) != GD_OK) return report(rep, st);
+  const double rel0 = rel;
+  if (rep) {
+    rep->rhs_norm = bnorm;
+    rep->history[0] = rel;
+  }
+  int cycles = 0, status = GD_OK;
+  std::vector<double> hist(1, rel);
+  double sum_x = 0.0;
+  bool have_sum_x = false;
+  while (!(rel <= ctl.rel_tol)) {
+    if (cycles >= ctl.max_cycles) {
+      status = GD_ERR_NOT_CONVERGED;
+      break;
+    }
+    if ((st = vcycle_run(s, ctl.nu1, ctl.nu2, true, false)) != GD_OK) return report(rep, st);
+    {
+      ProfScope ps(s, P_OUTER, (double)n * 20.0);
+      CK(launch_l_update((long long)n, F.x, xh, xl, s->partials, &nb, s->stream));
+    }
+    if (mean_fix) {
+      if ((st = reduce_read(S_X, S_X + 1, hs)) != GD_OK) return report(rep, st);
+      sum_x = hs[S_X];
+      have_sum_x = true;
+    }
+    if ((st = residual(&rel, &bnorm)) != GD_OK) return report(rep, st);
+    ++cycles;
+    hist.push_back(rel);
+    if (rep && cycles < GD_HISTORY) rep->history[cycles] = rel;
+    if (!std::isfinite(rel) || rel > 1e3 * std::fmax(rel0, 1e-300)) {
+      status = GD_ERR_DIVERGED;
+      break;
+    }
+    if (cycles >= 4 && rel > 0.7 * hist[cycles - 3] && rel > ctl.rel_tol) {
+      status = GD_ERR_NOT_CONVERGED;
+      break;
+    }
+  }
+  double shift = 0.0;
+  if (mean_fix) {
+    if (!have_sum_x) {
+      CK(launch_l_sum((long long)n, xh, s->partials, S_X, &nb, s->stream));
+      if ((st = reduce_read(S_X, S_X + 1, hs)) != GD_OK) return report(rep, st);
+      sum_x = hs[S_X];  // the low words are zero before the first update
+    }
+    shift = (sum_i0 - sum_x) / (double)n;
+  }
+  {
+    ProfScope ps(s, P_COPY, (double)n * 12.0);
+    CK(launch_l_final((long long)n, xh, xl, shift, out, s->stream));
+  }
+  if (rep) {
+    rep->cycles = cycles;
+    rep->rel_residual = rel;
+    rep->rho_per_cycle = cycles > 0 && rel0 > 0 ? std::pow(rel / rel0, 1.0 / cycles) : NAN;
+  }
+  if (out_host) CK(cudaMemcpyAsync(outh, out, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->prof_on) prof_collect(s);
+  return report(rep, status);
+}
+
 int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *outh, double w[4],
           const gd_solve_ctl *ctl_in, const float *x0h, gd_report *rep) {
+  if (s->disc == GD_DISC_LINEAR) return solve_linear(s, system, I0h, I1h, outh, w, ctl_in, x0h, rep);
   rep_init(rep);
   gd_solve_ctl ctl;
   int st = check_ctl(s, ctl_in, &ctl);
@@ -1140,10 +1301,9 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
   if (nx < 2 || ny < 2 || nz < 1) return GD_ERR_INVALID_ARG;
   if ((double)nx * ny * nz > 9.0e18 / 64) return GD_ERR_INVALID_ARG;
   if (bc != GD_BC_NEUMANN) return GD_ERR_UNSUPPORTED;
-  if (disc != GD_DISC_CONSTANT && disc != GD_DISC_HYBRID)
-    return disc == GD_DISC_LINEAR ? GD_ERR_UNSUPPORTED : GD_ERR_INVALID_ARG;
+  if (disc != GD_DISC_CONSTANT && disc != GD_DISC_HYBRID && disc != GD_DISC_LINEAR) return GD_ERR_INVALID_ARG;
   if (prec != GD_PREC_FP32 && prec != GD_PREC_MIXED) return GD_ERR_INVALID_ARG;
-  if (disc == GD_DISC_HYBRID && prec != GD_PREC_FP32) return GD_ERR_UNSUPPORTED;
+  if (disc != GD_DISC_CONSTANT && prec != GD_PREC_FP32) return GD_ERR_UNSUPPORTED;
   gd_stack *s = new (std::nothrow) gd_stack();
   if (!s) return GD_ERR_OOM;
   s->nx = nx;
@@ -1174,6 +1334,7 @@ int gd_destroy(gd_stack *s) {
   dfree(s->xh2);
   dfree(s->xl1);
   dfree(s->xl2);
+  dfree(s->lbh);
   for (auto &p : s->stage) dfree(p);
   if (s->partials) cudaFree(s->partials);
   if (s->scalars) cudaFree(s->scalars);
@@ -1263,6 +1424,11 @@ int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh,
   rep_init(rep);
   if (!s || !bh || !xh || ncycles < 0 || bh == xh) return report(rep, GD_ERR_INVALID_ARG);
   if (!weights_ok(w)) return report(rep, GD_ERR_INVALID_ARG);
+  if (s->disc == GD_DISC_LINEAR) {
+    set_err(s, "gd_vcycle evaluates the 6-point fine operator; the Linear discretisation solves "
+               "through gd_diffuse_z / gd_screened_poisson_slices / gd_screened_poisson");
+    return report(rep, GD_ERR_UNSUPPORTED);
+  }
   if (system == GD_SYSTEM_AD) {
     if (!(w.beta_z > 0.0)) return report(rep, GD_ERR_INVALID_ARG);
   } else if (system == GD_SYSTEM_SP) {
@@ -1332,6 +1498,10 @@ int gd_residual(gd_stack *s, int system, gd_weights w, const float *I0h, const f
   if (system != GD_SYSTEM_AD && system != GD_SYSTEM_SP) return GD_ERR_INVALID_ARG;
   if (system == GD_SYSTEM_SP && (!I1h || !(w.alpha > 0.0))) return GD_ERR_INVALID_ARG;
   if (!weights_ok(w)) return GD_ERR_INVALID_ARG;
+  if (s->disc == GD_DISC_LINEAR) {
+    set_err(s, "gd_residual evaluates the 6-point operator, not the Linear discretisation's");
+    return GD_ERR_UNSUPPORTED;
+  }
   int st;
   if ((st = ensure_common(s)) != GD_OK) return st;
   float *I0 = nullptr, *I1 = nullptr, *x = nullptr;
@@ -1358,6 +1528,10 @@ int gd_residual(gd_stack *s, int system, gd_weights w, const float *I0h, const f
 
 int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps) {
   if (!s || !bh || !xh || nsweeps < 0 || bh == xh || !weights_ok(w)) return GD_ERR_INVALID_ARG;
+  if (s->disc == GD_DISC_LINEAR) {
+    set_err(s, "gd_smooth relaxes the 6-point operator, not the Linear discretisation's");
+    return GD_ERR_UNSUPPORTED;
+  }
   int st;
   if ((st = ensure_common(s)) != GD_OK) return st;
   const size_t n = (size_t)s->nx * s->ny * s->nz;

@@ -267,3 +267,186 @@ cudaError_t launch_h_prolong(int nx, int ny, int nz, int fx, int fy, int fz, int
   k_h_prolong<<<grid_of((long long)nx * ny * nz), HNT, 0, st>>>(nx, ny, nz, fx, fy, fz, cnx, cny, cnz, e, x);
   return cudaGetLastError();
 }
+
+// ===========================================================================
+// The "Linear" discretisation (Sec. 4.2): the same Kronecker form with the
+// fine factors K_n and the P1 mass (1/6) tridiag(1, [2, 4, ..., 4, 2], 1), so
+// the fine operator is 27-point too.  Its outer pass evaluates the
+// right-hand side once and the residual of the float-pair iterate in FP64
+// (the 27 coefficients nearly cancel on smooth data; FP32 sums would lose
+// ~1e-5 of the right-hand side).
+// ===========================================================================
+namespace {
+
+// sum over the 27-point neighbourhood of coef(a, b, c) * v, in FP64, for the
+// operator with weights (wx, wy, wz, wm) over Kx(x)My(x)Mz etc.
+template <bool ZC, typename V>
+__device__ __forceinline__ double kron_sum(const HLevelDev &L, double wx, double wy, double wz, double wm, int i,
+                                           int j, int k, V val) {
+  const float *kx = L.kx + 3 * i, *mx = L.mx + 3 * i;
+  const float *ky = L.ky + 3 * j, *my = L.my + 3 * j;
+  const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
+  double acc = 0.0;
+  const int c0 = ZC ? -1 : 0, c1 = ZC ? 1 : 0;
+  for (int c = c0; c <= c1; ++c) {
+    const int kk = k + c;
+    if (kk < 0 || kk >= L.nz) continue;
+    const double mzc = mz[c + 1], kzc = ZC ? (double)kz[c + 1] : 0.0;
+    for (int b = -1; b <= 1; ++b) {
+      const int jj = j + b;
+      if (jj < 0 || jj >= L.ny) continue;
+      const double myb = my[b + 1], kyb = ky[b + 1];
+      const double cm = myb * (wz * kzc + wm * mzc) + wy * kyb * mzc;  // multiplies mx
+      const double ck = wx * myb * mzc;                                  // multiplies kx
+      for (int a = -1; a <= 1; ++a) {
+        const int ii = i + a;
+        if (ii < 0 || ii >= L.nx) continue;
+        const double cf = (double)mx[a + 1] * cm + (double)kx[a + 1] * ck;
+        if (cf != 0.0) acc = fma(cf, val(((long long)kk * L.ny + jj) * L.nx + ii), acc);
+      }
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ void block_sums(double a, double b, double *partials, int sa, int sb) {
+  __shared__ double red[2][HNT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][warp] = a;
+    red[1][warp] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < HNT / 32; ++w) {
+      s0 += red[0][w];
+      s1 += red[1][w];
+    }
+    if (sa >= 0) partials[(size_t)blockIdx.x * S_NUM + sa] = s0;
+    if (sb >= 0) partials[(size_t)blockIdx.x * S_NUM + sb] = s1;
+  }
+}
+
+// b = (gx Kx(x)My(x)Mz + gy Mx(x)Ky(x)Mz) I0 + gm (Mx(x)My(x)Mz) I1, as a float pair
+template <bool ZC>
+__global__ void __launch_bounds__(HNT) k_l_rhs(HLevelDev L, LinW w, const float *__restrict__ I0,
+                                               const float *__restrict__ I1, float *__restrict__ bh,
+                                               float *__restrict__ bl) {
+  const long long n = (long long)L.nx * L.ny * L.nz;
+  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
+    const int i = (int)(q % L.nx);
+    const long long t = q / L.nx;
+    const int j = (int)(t % L.ny), k = (int)(t / L.ny);
+    double v = kron_sum<ZC>(L, w.gx, w.gy, 0.0, 0.0, i, j, k, [&](long long o) { return (double)I0[o]; });
+    if (w.gm != 0.0)
+      v += kron_sum<ZC>(L, 0.0, 0.0, 0.0, w.gm, i, j, k, [&](long long o) { return (double)I1[o]; });
+    const float hv = (float)v;
+    bh[q] = hv;
+    bl[q] = (float)(v - (double)hv);
+  }
+}
+
+// r = b - A (h + l) in FP64 (stored as float), and the block sums of r^2
+// (slot S_RR) and b^2 (slot S_BB)
+template <bool ZC>
+__global__ void __launch_bounds__(HNT) k_l_resid(HLevelDev L, LinW w, const float *__restrict__ bh,
+                                                 const float *__restrict__ bl, const float *__restrict__ h,
+                                                 const float *__restrict__ l, float *__restrict__ r,
+                                                 double *__restrict__ partials) {
+  const long long n = (long long)L.nx * L.ny * L.nz;
+  double srr = 0.0, sbb = 0.0;
+  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
+    const int i = (int)(q % L.nx);
+    const long long t = q / L.nx;
+    const int j = (int)(t % L.ny), k = (int)(t / L.ny);
+    const double ax = kron_sum<ZC>(L, w.ax, w.ay, w.az, w.am, i, j, k,
+                                   [&](long long o) { return (double)h[o] + (double)l[o]; });
+    const double b = (double)bh[q] + (double)bl[q];
+    const double rv = b - ax;
+    if (r) r[q] = (float)rv;
+    srr += rv * rv;
+    sbb += b * b;
+  }
+  block_sums(srr, sbb, partials, S_RR, S_BB);
+}
+
+// (h, l) += e exactly in FP64 and rounded back to a float pair; block sums
+// of the new iterate (slot S_X)
+__global__ void __launch_bounds__(HNT) k_l_update(long long n, const float *__restrict__ e, float *__restrict__ h,
+                                                  float *__restrict__ l, double *__restrict__ partials) {
+  double sx = 0.0;
+  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
+    const double v = (double)h[q] + (double)l[q] + (double)e[q];
+    const float hv = (float)v;
+    h[q] = hv;
+    l[q] = (float)(v - (double)hv);
+    sx += v;
+  }
+  block_sums(sx, 0.0, partials, S_X, -1);
+}
+
+// block sums of an array (slot)
+__global__ void __launch_bounds__(HNT) k_l_sum(long long n, const float *__restrict__ a, double *__restrict__ partials,
+                                               int slot) {
+  double s = 0.0;
+  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) s += a[q];
+  block_sums(s, 0.0, partials, slot, -1);
+}
+
+// out = h + l + shift, rounded to float
+__global__ void __launch_bounds__(HNT) k_l_final(long long n, const float *__restrict__ h, const float *__restrict__ l,
+                                                 double shift, float *__restrict__ out) {
+  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT)
+    out[q] = (float)((double)h[q] + (double)l[q] + shift);
+}
+
+}  // namespace
+
+int linear_grid(long long n) { return grid_of(n); }
+
+cudaError_t launch_l_rhs(const HLevelDev &L, const LinW &w, const float *I0, const float *I1, float *bh, float *bl,
+                         cudaStream_t st) {
+  const long long n = (long long)L.nx * L.ny * L.nz;
+  if (L.wz != 0.f && L.nz > 1)
+    k_l_rhs<true><<<grid_of(n), HNT, 0, st>>>(L, w, I0, I1, bh, bl);
+  else
+    k_l_rhs<false><<<grid_of(n), HNT, 0, st>>>(L, w, I0, I1, bh, bl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l_resid(const HLevelDev &L, const LinW &w, const float *bh, const float *bl, const float *h,
+                           const float *l, float *r, double *partials, int *nblocks, cudaStream_t st) {
+  const long long n = (long long)L.nx * L.ny * L.nz;
+  const int g = grid_of(n);
+  if (nblocks) *nblocks = g;
+  if (L.wz != 0.f && L.nz > 1)
+    k_l_resid<true><<<g, HNT, 0, st>>>(L, w, bh, bl, h, l, r, partials);
+  else
+    k_l_resid<false><<<g, HNT, 0, st>>>(L, w, bh, bl, h, l, r, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l_update(long long n, const float *e, float *h, float *l, double *partials, int *nblocks,
+                            cudaStream_t st) {
+  const int g = grid_of(n);
+  if (nblocks) *nblocks = g;
+  k_l_update<<<g, HNT, 0, st>>>(n, e, h, l, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l_sum(long long n, const float *a, double *partials, int slot, int *nblocks, cudaStream_t st) {
+  const int g = grid_of(n);
+  if (nblocks) *nblocks = g;
+  k_l_sum<<<g, HNT, 0, st>>>(n, a, partials, slot);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l_final(long long n, const float *h, const float *l, double shift, float *out, cudaStream_t st) {
+  k_l_final<<<grid_of(n), HNT, 0, st>>>(n, h, l, shift, out);
+  return cudaGetLastError();
+}

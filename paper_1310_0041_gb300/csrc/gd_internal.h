@@ -135,6 +135,25 @@ cudaError_t launch_h_restrict(int nx, int ny, int nz, int fx, int fy, int fz, in
                               const float *r, float *bc, cudaStream_t st);
 cudaError_t launch_h_prolong(int nx, int ny, int nz, int fx, int fy, int fz, int cnx, int cny, int cnz,
                              const float *e, float *x, cudaStream_t st);
+// Weights of the Linear discretisation's fine operator (ax Kx(x)My(x)Mz +
+// ay Mx(x)Ky(x)Mz + az Mx(x)My(x)Kz + am Mx(x)My(x)Mz) and right-hand side
+// (gx Kx(x)My(x)Mz I0 + gy Mx(x)Ky(x)Mz I0 + gm Mx(x)My(x)Mz I1).
+struct LinW {
+  double ax, ay, az, am;
+  double gx, gy, gm;
+};
+cudaError_t launch_l_rhs(const HLevelDev &L, const LinW &w, const float *I0, const float *I1, float *bh, float *bl,
+                         cudaStream_t st);
+// r = b - A (h + l) (r nullable) with FP64 sums of r^2, b^2 per block (S_RR, S_BB)
+cudaError_t launch_l_resid(const HLevelDev &L, const LinW &w, const float *bh, const float *bl, const float *h,
+                           const float *l, float *r, double *partials, int *nblocks, cudaStream_t st);
+// (h, l) += e with per-block sums of the new iterate (S_X)
+cudaError_t launch_l_update(long long n, const float *e, float *h, float *l, double *partials, int *nblocks,
+                            cudaStream_t st);
+cudaError_t launch_l_sum(long long n, const float *a, double *partials, int slot, int *nblocks, cudaStream_t st);
+cudaError_t launch_l_final(long long n, const float *h, const float *l, double shift, float *out, cudaStream_t st);
+int linear_grid(long long n);
+
 // Host: the per-axis Galerkin product T_c = P^T T P of a tridiagonal T (n x 3)
 // with the first-order B-spline prolongation from nc = ceil(n / 2) cells.
 void galerkin_tri(int n, const std::vector<double> &T, std::vector<double> &Tc);

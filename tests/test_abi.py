@@ -48,9 +48,10 @@ def test_create_validation_without_gpu(lib):
     assert f(ctypes.byref(h), 1, 8, 8, 0, 0, 0, None) == gd.GD_ERR_INVALID_ARG
     assert f(ctypes.byref(h), 8, 8, 0, 0, 0, 0, None) == gd.GD_ERR_INVALID_ARG
     assert f(ctypes.byref(h), 8, 8, 8, 1, 0, 0, None) == gd.GD_ERR_UNSUPPORTED
-    assert f(ctypes.byref(h), 8, 8, 8, 0, gd.GD_DISC_LINEAR, 0, None) == gd.GD_ERR_UNSUPPORTED
-    # the Hybrid discretisation runs in float32 only
-    assert f(ctypes.byref(h), 8, 8, 8, 0, gd.GD_DISC_HYBRID, gd.GD_PREC_MIXED, None) == gd.GD_ERR_UNSUPPORTED
+    # the Hybrid and Linear discretisations run in float32 only
+    for disc in (gd.GD_DISC_HYBRID, gd.GD_DISC_LINEAR):
+        assert f(ctypes.byref(h), 8, 8, 8, 0, disc, gd.GD_PREC_MIXED, None) == gd.GD_ERR_UNSUPPORTED
+    assert f(ctypes.byref(h), 8, 8, 8, 0, 3, 0, None) == gd.GD_ERR_INVALID_ARG
     assert f(ctypes.byref(h), 8, 8, 8, 0, 0, 7, None) == gd.GD_ERR_INVALID_ARG
     assert f(ctypes.byref(h), 8, 8, 8, 0, 0, 0, None) == gd.GD_OK
     s = gd.Stack(h, 8, 8, 8)
