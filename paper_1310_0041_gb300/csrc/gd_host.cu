@@ -86,6 +86,10 @@ struct Plan {
   bool half = false;           // levels above the coarsest hold bfloat16
   std::vector<Level> L;
   float *Vx = nullptr, *Vy = nullptr, *Vz = nullptr, *Dinv = nullptr;
+  // Linear: the fine factors scaled to integers (mass factors times lscale)
+  float *lfac = nullptr;
+  HLevelDev ls{};
+  double lscale[3] = {1.0, 1.0, 1.0};
   std::vector<std::unique_ptr<VGraph>> graphs;
   unsigned long long last_use = 0;
 };
@@ -278,6 +282,7 @@ void plan_free(gd_stack *s, Plan &P) {
     dfree(P.L[li].t);
   }
   for (auto &l : P.L) dfree(l.hf);
+  dfree(P.lfac);
   P.L.clear();
   dfree(P.Vx);
   dfree(P.Vy);
@@ -473,6 +478,27 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
       l.hd = HLevelDev{l.d.nx, l.d.ny, l.d.nz, (float)w[1], (float)w[2], batch_z ? 0.f : (float)w[3],
                        (float)w[0], b0, b0 + 3 * nn[0], b0 + 6 * nn[0], b0 + 6 * nn[0] + 3 * nn[1],
                        b0 + 6 * nn[0] + 6 * nn[1], b0 + 6 * nn[0] + 6 * nn[1] + 3 * nn[2]};
+      if (li == 0 && p1) {
+        // integer-scaled fine factors for the compensated outer pass
+        std::vector<float> g;
+        for (int a = 0; a < 3; ++a) {
+          const bool mass_p1 = nn[a] > 1 && !(a == 2 && batch_z);
+          P.lscale[a] = mass_p1 ? 6.0 : 1.0;
+          for (int q = 0; q < 3 * nn[a]; ++q) g.push_back((float)HK[a][q]);
+          for (int q = 0; q < 3 * nn[a]; ++q) g.push_back((float)std::nearbyint(HM[a][q] * P.lscale[a]));
+        }
+        if ((st = dalloc(s, &P.lfac, g.size())) != GD_OK) return st;
+        CK(cudaMemcpyAsync(P.lfac, g.data(), g.size() * 4, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        const float *c0 = P.lfac;
+        P.ls = l.hd;
+        P.ls.kx = c0;
+        P.ls.mx = c0 + 3 * nn[0];
+        P.ls.ky = c0 + 6 * nn[0];
+        P.ls.my = c0 + 6 * nn[0] + 3 * nn[1];
+        P.ls.kz = c0 + 6 * nn[0] + 6 * nn[1];
+        P.ls.mz = c0 + 6 * nn[0] + 6 * nn[1] + 3 * nn[2];
+      }
     }
   }
   // coarsest-level fast diagonalisation data
@@ -991,7 +1017,19 @@ int solve_linear(gd_stack *s, int system, const float *I0h, const float *I1h, fl
     lw = LinW{w[1], w[2], uncoupled ? 0.0 : w[3], w[0], 0.0, 0.0, 0.0};
   else
     lw = LinW{w[1], w[2], w[3], 0.0, w[1], w[2], 0.0};
-  const HLevelDev &L0 = F.hd;
+  const HLevelDev &L0 = P.ls;
+  {
+    // the kernels sum over the integer-scaled factors: divide each weight by
+    // the scales of the mass factors in its term
+    const double sx = P.lscale[0], sy = P.lscale[1], sz = P.lscale[2];
+    lw.ax /= sy * sz;
+    lw.ay /= sx * sz;
+    lw.az /= sx * sy;
+    lw.am /= sx * sy * sz;
+    lw.gx /= sy * sz;
+    lw.gy /= sx * sz;
+    lw.gm /= sx * sy * sz;
+  }
   const int mean_fix = system == GD_SYSTEM_AD;
   int nb = 0;
   {

@@ -272,42 +272,11 @@ cudaError_t launch_h_prolong(int nx, int ny, int nz, int fx, int fy, int fz, int
 // The "Linear" discretisation (Sec. 4.2): the same Kronecker form with the
 // fine factors K_n and the P1 mass (1/6) tridiag(1, [2, 4, ..., 4, 2], 1), so
 // the fine operator is 27-point too.  Its outer pass evaluates the
-// right-hand side once and the residual of the float-pair iterate in FP64
-// (the 27 coefficients nearly cancel on smooth data; FP32 sums would lose
-// ~1e-5 of the right-hand side).
+// right-hand side once and the residual of the float-pair iterate with
+// compensated sums (the 27 coefficients nearly cancel on smooth data; plain
+// FP32 sums would lose ~1e-5 of the right-hand side, and FP64 is slow here).
 // ===========================================================================
 namespace {
-
-// sum over the 27-point neighbourhood of coef(a, b, c) * v, in FP64, for the
-// operator with weights (wx, wy, wz, wm) over Kx(x)My(x)Mz etc.
-template <bool ZC, typename V>
-__device__ __forceinline__ double kron_sum(const HLevelDev &L, double wx, double wy, double wz, double wm, int i,
-                                           int j, int k, V val) {
-  const float *kx = L.kx + 3 * i, *mx = L.mx + 3 * i;
-  const float *ky = L.ky + 3 * j, *my = L.my + 3 * j;
-  const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
-  double acc = 0.0;
-  const int c0 = ZC ? -1 : 0, c1 = ZC ? 1 : 0;
-  for (int c = c0; c <= c1; ++c) {
-    const int kk = k + c;
-    if (kk < 0 || kk >= L.nz) continue;
-    const double mzc = mz[c + 1], kzc = ZC ? (double)kz[c + 1] : 0.0;
-    for (int b = -1; b <= 1; ++b) {
-      const int jj = j + b;
-      if (jj < 0 || jj >= L.ny) continue;
-      const double myb = my[b + 1], kyb = ky[b + 1];
-      const double cm = myb * (wz * kzc + wm * mzc) + wy * kyb * mzc;  // multiplies mx
-      const double ck = wx * myb * mzc;                                  // multiplies kx
-      for (int a = -1; a <= 1; ++a) {
-        const int ii = i + a;
-        if (ii < 0 || ii >= L.nx) continue;
-        const double cf = (double)mx[a + 1] * cm + (double)kx[a + 1] * ck;
-        if (cf != 0.0) acc = fma(cf, val(((long long)kk * L.ny + jj) * L.nx + ii), acc);
-      }
-    }
-  }
-  return acc;
-}
 
 __device__ __forceinline__ void block_sums(double a, double b, double *partials, int sa, int sb) {
   __shared__ double red[2][HNT / 32];
@@ -332,7 +301,64 @@ __device__ __forceinline__ void block_sums(double a, double b, double *partials,
   }
 }
 
-// b = (gx Kx(x)My(x)Mz + gy Mx(x)Ky(x)Mz) I0 + gm (Mx(x)My(x)Mz) I1, as a float pair
+// Integer-weighted neighbourhood sums, compensated.  With the fine factors
+// scaled to integers (K_n as is, the P1 mass times 6), every product of
+// three factor entries is a small integer, exact in FP32; each term p (h + l)
+// enters a float pair by TwoProd and TwoSum, so the four sums
+//   S_kx = sum (Kx My Mz) x, S_ky = sum (Mx Ky Mz) x,
+//   S_kz = sum (Mx My Kz) x, S_m = sum (Mx My Mz) x
+// come out exact to ~1e-12 of their terms, and the operator is their
+// weighted sum, formed in FP64 (a few operations per cell).
+struct Sums {
+  float h[4], l[4];
+};
+__device__ __forceinline__ void acc_term(float P, float xh, float xl, float &sh, float &sl) {
+  if (P == 0.f) return;
+  const float p = P * xh;
+  const float e = fmaf(P, xh, -p);
+  const float s = sh + p;
+  const float bb = s - sh;
+  const float err = (sh - (s - bb)) + (p - bb);
+  sh = s;
+  sl += err + e + P * xl;
+}
+template <bool ZC, typename V>
+__device__ __forceinline__ Sums kron_sums(const HLevelDev &L, bool want_kz, bool want_m, int i, int j, int k,
+                                          V val) {
+  Sums S;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) S.h[q] = S.l[q] = 0.f;
+  const float *kx = L.kx + 3 * i, *mx = L.mx + 3 * i;
+  const float *ky = L.ky + 3 * j, *my = L.my + 3 * j;
+  const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
+  const int c0 = ZC ? -1 : 0, c1 = ZC ? 1 : 0;
+  for (int c = c0; c <= c1; ++c) {
+    const int kk = k + c;
+    if (kk < 0 || kk >= L.nz) continue;
+    const float mzc = mz[c + 1], kzc = ZC ? kz[c + 1] : 0.f;
+    for (int b = -1; b <= 1; ++b) {
+      const int jj = j + b;
+      if (jj < 0 || jj >= L.ny) continue;
+      const float myb = my[b + 1], kyb = ky[b + 1];
+      for (int a = -1; a <= 1; ++a) {
+        const int ii = i + a;
+        if (ii < 0 || ii >= L.nx) continue;
+        float xh, xl;
+        val(((long long)kk * L.ny + jj) * L.nx + ii, xh, xl);
+        const float mxa = mx[a + 1], kxa = kx[a + 1];
+        acc_term(kxa * myb * mzc, xh, xl, S.h[0], S.l[0]);
+        acc_term(mxa * kyb * mzc, xh, xl, S.h[1], S.l[1]);
+        if (want_kz) acc_term(mxa * myb * kzc, xh, xl, S.h[2], S.l[2]);
+        if (want_m) acc_term(mxa * myb * mzc, xh, xl, S.h[3], S.l[3]);
+      }
+    }
+  }
+  return S;
+}
+__device__ __forceinline__ double sum_of(const Sums &S, int q) { return (double)S.h[q] + (double)S.l[q]; }
+
+// b = gx' S_kx(I0) + gy' S_ky(I0) + gm' S_m(I1) (weights already divided by
+// the factor scales), stored as a float pair
 template <bool ZC>
 __global__ void __launch_bounds__(HNT) k_l_rhs(HLevelDev L, LinW w, const float *__restrict__ I0,
                                                const float *__restrict__ I1, float *__restrict__ bh,
@@ -342,30 +368,45 @@ __global__ void __launch_bounds__(HNT) k_l_rhs(HLevelDev L, LinW w, const float 
     const int i = (int)(q % L.nx);
     const long long t = q / L.nx;
     const int j = (int)(t % L.ny), k = (int)(t / L.ny);
-    double v = kron_sum<ZC>(L, w.gx, w.gy, 0.0, 0.0, i, j, k, [&](long long o) { return (double)I0[o]; });
-    if (w.gm != 0.0)
-      v += kron_sum<ZC>(L, 0.0, 0.0, 0.0, w.gm, i, j, k, [&](long long o) { return (double)I1[o]; });
+    const Sums S0 = kron_sums<ZC>(L, false, false, i, j, k, [&](long long o, float &h, float &l) {
+      h = I0[o];
+      l = 0.f;
+    });
+    double v = w.gx * sum_of(S0, 0) + w.gy * sum_of(S0, 1);
+    if (w.gm != 0.0) {
+      const Sums S1 = kron_sums<ZC>(L, false, true, i, j, k, [&](long long o, float &h, float &l) {
+        h = I1[o];
+        l = 0.f;
+      });
+      v += w.gm * sum_of(S1, 3);
+    }
     const float hv = (float)v;
     bh[q] = hv;
     bl[q] = (float)(v - (double)hv);
   }
 }
 
-// r = b - A (h + l) in FP64 (stored as float), and the block sums of r^2
-// (slot S_RR) and b^2 (slot S_BB)
+// r = b - A (h + l) from the compensated sums (stored as float), and the
+// block sums of r^2 (slot S_RR) and b^2 (slot S_BB)
 template <bool ZC>
 __global__ void __launch_bounds__(HNT) k_l_resid(HLevelDev L, LinW w, const float *__restrict__ bh,
                                                  const float *__restrict__ bl, const float *__restrict__ h,
                                                  const float *__restrict__ l, float *__restrict__ r,
                                                  double *__restrict__ partials) {
   const long long n = (long long)L.nx * L.ny * L.nz;
+  const bool want_kz = w.az != 0.0, want_m = w.am != 0.0;
   double srr = 0.0, sbb = 0.0;
   for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
     const int i = (int)(q % L.nx);
     const long long t = q / L.nx;
     const int j = (int)(t % L.ny), k = (int)(t / L.ny);
-    const double ax = kron_sum<ZC>(L, w.ax, w.ay, w.az, w.am, i, j, k,
-                                   [&](long long o) { return (double)h[o] + (double)l[o]; });
+    const Sums S = kron_sums<ZC>(L, want_kz, want_m, i, j, k, [&](long long o, float &xh, float &xl) {
+      xh = h[o];
+      xl = l[o];
+    });
+    double ax = w.ax * sum_of(S, 0) + w.ay * sum_of(S, 1);
+    if (want_kz) ax += w.az * sum_of(S, 2);
+    if (want_m) ax += w.am * sum_of(S, 3);
     const double b = (double)bh[q] + (double)bl[q];
     const double rv = b - ax;
     if (r) r[q] = (float)rv;

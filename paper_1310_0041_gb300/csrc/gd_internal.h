@@ -137,7 +137,9 @@ cudaError_t launch_h_prolong(int nx, int ny, int nz, int fx, int fy, int fz, int
                              const float *e, float *x, cudaStream_t st);
 // Weights of the Linear discretisation's fine operator (ax Kx(x)My(x)Mz +
 // ay Mx(x)Ky(x)Mz + az Mx(x)My(x)Kz + am Mx(x)My(x)Mz) and right-hand side
-// (gx Kx(x)My(x)Mz I0 + gy Mx(x)Ky(x)Mz I0 + gm Mx(x)My(x)Mz I1).
+// (gx Kx(x)My(x)Mz I0 + gy Mx(x)Ky(x)Mz I0 + gm Mx(x)My(x)Mz I1), given for
+// the integer-scaled fine factors the kernels take (each weight divided by
+// the scales of the mass factors in its term).
 struct LinW {
   double ax, ay, az, am;
   double gx, gy, gm;
