@@ -478,6 +478,53 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
       l.hd = HLevelDev{l.d.nx, l.d.ny, l.d.nz, (float)w[1], (float)w[2], batch_z ? 0.f : (float)w[3],
                        (float)w[0], b0, b0 + 3 * nn[0], b0 + 6 * nn[0], b0 + 6 * nn[0] + 3 * nn[1],
                        b0 + 6 * nn[0] + 6 * nn[1], b0 + 6 * nn[0] + 6 * nn[1] + 3 * nn[2]};
+      // uniform interior rows and their 27 coefficients (same float formula
+      // as the kernels' general path)
+      {
+        const int fz = !batch_z && l.d.nz > 1 ? 1 : 0;
+        for (int a = 0; a < 3; ++a) {
+          const int n = nn[a], mid = n / 2;
+          int lo = 1, hi = n - 2;
+          auto same = [&](int r) {
+            for (int d = 0; d < 3; ++d)
+              if ((float)HK[a][(size_t)r * 3 + d] != (float)HK[a][(size_t)mid * 3 + d] ||
+                  (float)HM[a][(size_t)r * 3 + d] != (float)HM[a][(size_t)mid * 3 + d])
+                return false;
+            return true;
+          };
+          if (n < 3) {
+            lo = 1;
+            hi = 0;
+          } else {
+            lo = mid;
+            hi = mid;
+            while (lo - 1 >= 1 && same(lo - 1)) --lo;
+            while (hi + 1 <= n - 2 && same(hi + 1)) ++hi;
+          }
+          l.hd.ilo[a] = lo;
+          l.hd.ihi[a] = hi;
+        }
+        if (!fz) {
+          l.hd.ilo[2] = 0;
+          l.hd.ihi[2] = l.d.nz - 1;
+        }
+        const int mx_ = nn[0] / 2, my_ = nn[1] / 2, mz_ = nn[2] / 2;
+        for (int c = -1; c <= 1; ++c)
+          for (int b = -1; b <= 1; ++b)
+            for (int a = -1; a <= 1; ++a) {
+              float v = 0.f;
+              if (fz || c == 0) {
+                const float mzc = (float)HM[2][(size_t)mz_ * 3 + c + 1];  // (the z diagonal when uncoupled)
+                const float kzc = fz ? (float)HK[2][(size_t)mz_ * 3 + c + 1] : 0.f;
+                const float zterm = l.hd.wz * kzc + l.hd.wm * mzc;
+                const float myb = (float)HM[1][(size_t)my_ * 3 + b + 1], kyb = (float)HK[1][(size_t)my_ * 3 + b + 1];
+                const float yz = myb * zterm + l.hd.wy * kyb * mzc;
+                const float xz = l.hd.wx * myb * mzc;
+                v = (float)HM[0][(size_t)mx_ * 3 + a + 1] * yz + (float)HK[0][(size_t)mx_ * 3 + a + 1] * xz;
+              }
+              l.hd.cst[(c + 1) * 9 + (b + 1) * 3 + (a + 1)] = v;
+            }
+      }
       if (li == 0 && p1) {
         // integer-scaled fine factors for the compensated outer pass
         std::vector<float> g;

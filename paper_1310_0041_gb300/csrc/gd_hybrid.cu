@@ -48,6 +48,24 @@ __device__ __forceinline__ void apply_off(const HLevelDev &L, const float *__res
     dg = cnt + L.wm;
     return;
   }
+  if (i >= L.ilo[0] && i <= L.ihi[0] && j >= L.ilo[1] && j <= L.ihi[1] &&
+      (!ZC || (k >= L.ilo[2] && k <= L.ihi[2]))) {
+    // interior: constant coefficients, every neighbour exists
+    const int c0 = ZC ? -1 : 0, c1 = ZC ? 1 : 0;
+#pragma unroll
+    for (int c = c0; c <= c1; ++c)
+#pragma unroll
+      for (int b = -1; b <= 1; ++b) {
+        const float *xr = x + cell(L, i, j + b, k + c);
+#pragma unroll
+        for (int a = -1; a <= 1; ++a) {
+          if (a == 0 && b == 0 && c == 0) continue;
+          off = fmaf(L.cst[(c + 1) * 9 + (b + 1) * 3 + (a + 1)], xr[a], off);
+        }
+      }
+    dg = L.cst[13];
+    return;
+  }
   const float *kx = L.kx + 3 * i, *mx = L.mx + 3 * i;
   const float *ky = L.ky + 3 * j, *my = L.my + 3 * j;
   const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;

@@ -123,6 +123,11 @@ struct HLevelDev {
   int nx, ny, nz;
   float wx, wy, wz, wm;
   const float *kx, *mx, *ky, *my, *kz, *mz;
+  // cells whose factor rows along every axis equal the uniform interior rows
+  // (index range [ilo, ihi] per axis, empty when ilo > ihi) share the 27
+  // coefficients cst[(c+1)*9 + (b+1)*3 + (a+1)] of offset (a, b, c)
+  int ilo[3], ihi[3];
+  float cst[27];
 };
 // eight-colour Gauss-Seidel sweep of a 27-point level, in place
 cudaError_t launch_h_gs(const HLevelDev &L, float *x, const float *b, cudaStream_t st);
