@@ -188,6 +188,24 @@ int gd_screened_poisson(gd_stack *s, gd_weights w, const float *b, float *x, con
                         const float *x0, gd_report *rep);
 
 /*
+ * gd_ad_then_sp -- the paper's two steps in one call (Sec. 3.1: AD, then SP
+ * on the result): gd_diffuse_z(I0 -> I1) followed by
+ * gd_screened_poisson_slices(I0, I1 -> I2), with I0 copied to the device once
+ * (when it is a host array) and I1 kept on the device.
+ *   I0 (in), I2 (out): stack arrays (device or host), distinct;
+ *   w_ad: the AD weights (as gd_diffuse_z); alpha > 0: the SP weight;
+ *   ctl_ad, ctl_sp (nullable): the two solves' controls;
+ *   I1 (out, nullable): receives the AD result when given (device arrays
+ *     are used in place of the stack's buffer);
+ *   rep_ad, rep_sp (nullable): the two reports.
+ * Returns the first error, else GD_ERR_NOT_CONVERGED if either solve
+ * stopped short of its tolerance, else GD_OK.
+ */
+int gd_ad_then_sp(gd_stack *s, const float *I0, float *I2, gd_weights w_ad, double alpha,
+                  const gd_solve_ctl *ctl_ad, const gd_solve_ctl *ctl_sp, float *I1, gd_report *rep_ad,
+                  gd_report *rep_sp);
+
+/*
  * gd_npr_rhs -- right-hand side of the NPR gradient filter of Sec. 7 (after
  * Bhat et al. 2010, Sec. 6.2): b = alpha I0 - div(W V) with the target
  * gradients V = lambda (1 - exp(-|grad I0|^2 / (2 sigma^2))) grad I0, for

@@ -36,7 +36,7 @@ EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_
            "gd_version", "gd_smooth_noalloc", "gd_screened_poisson", "gd_npr_rhs",
            "gd_batch_create", "gd_batch_screened_poisson", "gd_batch_voxels", "gd_batch_offset",
            "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy",
-           "gd_batch_traffic", "gd_batch_tune")
+           "gd_batch_traffic", "gd_batch_tune", "gd_ad_then_sp")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -113,6 +113,9 @@ def lib():
                 "gd_screened_poisson": (I, [P, GdWeights, P, P, ctypes.POINTER(GdSolveCtl), P,
                                             ctypes.POINTER(GdReport)]),
                 "gd_npr_rhs": (I, [P, P, P, GdWeights, D, D]),
+                "gd_ad_then_sp": (I, [P, P, P, GdWeights, D, ctypes.POINTER(GdSolveCtl),
+                                      ctypes.POINTER(GdSolveCtl), P, ctypes.POINTER(GdReport),
+                                      ctypes.POINTER(GdReport)]),
                 "gd_batch_create": (I, [ctypes.POINTER(P), I, ctypes.POINTER(I), ctypes.POINTER(I),
                                         ctypes.POINTER(D), I, P]),
                 "gd_batch_screened_poisson": (I, [P, P, P, P, ctypes.POINTER(GdSolveCtl), P,
@@ -270,6 +273,19 @@ def gd_screened_poisson(s: Stack, w, b, x, ctl: Optional[GdSolveCtl] = None, x0=
     if raise_on_error:
         _check(st, s, ok=(GD_OK, GD_ERR_NOT_CONVERGED))
     return rep.to_dict()
+
+
+def gd_ad_then_sp(s: Stack, I0, I2, w_ad, alpha: float, ctl_ad: Optional[GdSolveCtl] = None,
+                  ctl_sp: Optional[GdSolveCtl] = None, I1=None, raise_on_error: bool = True) -> tuple:
+    """AD then SP in one call (I0 uploaded once); returns the two reports."""
+    ra, rs = GdReport(), GdReport()
+    st = lib().gd_ad_then_sp(s.handle, _ptr(I0, s.n, "I0"), _ptr(I2, s.n, "I2"), _weights(w_ad),
+                             float(alpha), ctypes.byref(ctl_ad) if ctl_ad is not None else None,
+                             ctypes.byref(ctl_sp) if ctl_sp is not None else None,
+                             _ptr(I1, s.n, "I1"), ctypes.byref(ra), ctypes.byref(rs))
+    if raise_on_error:
+        _check(st, s, ok=(GD_OK, GD_ERR_NOT_CONVERGED))
+    return ra.to_dict(), rs.to_dict()
 
 
 def gd_npr_rhs(s: Stack, I0, b, w, lam: float, sigma: float) -> int:

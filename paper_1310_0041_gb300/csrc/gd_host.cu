@@ -110,6 +110,7 @@ struct gd_stack {
   // fine-level outer iterate buffers (second float pair, low parts)
   float *xh2 = nullptr, *xl1 = nullptr, *xl2 = nullptr;
   float *lbh = nullptr;  // Linear discretisation: high part of the right-hand side
+  float *i1 = nullptr;   // gd_ad_then_sp: the intermediate I1 on the device
   double *partials = nullptr;
   int partials_cap = 0;  // blocks
   double *scalars = nullptr;
@@ -1420,6 +1421,7 @@ int gd_destroy(gd_stack *s) {
   dfree(s->xl1);
   dfree(s->xl2);
   dfree(s->lbh);
+  dfree(s->i1);
   for (auto &p : s->stage) dfree(p);
   if (s->partials) cudaFree(s->partials);
   if (s->scalars) cudaFree(s->scalars);
@@ -1464,6 +1466,48 @@ int gd_screened_poisson_slices(gd_stack *s, const float *I0, const float *I1, fl
   }
   double wv[4] = {alpha, 1.0, 1.0, 0.0};
   return solve(s, GD_SYSTEM_SP, I0, I1, I2, wv, ctl, x0, rep);
+}
+
+int gd_ad_then_sp(gd_stack *s, const float *I0h, float *I2h, gd_weights w_ad, double alpha,
+                  const gd_solve_ctl *ctl_ad, const gd_solve_ctl *ctl_sp, float *I1h, gd_report *rep_ad,
+                  gd_report *rep_sp) {
+  rep_init(rep_ad);
+  rep_init(rep_sp);
+  if (!s || !I0h || !I2h || I0h == I2h || (I1h && (I1h == I0h || I1h == I2h))) {
+    if (s) set_err(s, "gd_ad_then_sp needs I0 and I2 (and the optional I1) as distinct arrays");
+    report(rep_ad, GD_ERR_INVALID_ARG);
+    return report(rep_sp, GD_ERR_INVALID_ARG);
+  }
+  if (!std::isfinite(alpha) || !(alpha > 0.0)) {
+    set_err(s, "SP needs a finite alpha > 0");
+    report(rep_ad, GD_ERR_INVALID_ARG);
+    return report(rep_sp, GD_ERR_INVALID_ARG);
+  }
+  int st = ensure_common(s);
+  if (st != GD_OK) return report(rep_sp, report(rep_ad, st));
+  const size_t n = (size_t)s->nx * s->ny * s->nz;
+  // I0 on the device once (host arrays are staged here, so both solves find
+  // a device pointer and copy nothing); I1 stays on the device
+  float *I0 = nullptr;
+  if ((st = resolve(s, I0h, true, 0, &I0)) != GD_OK) return report(rep_sp, report(rep_ad, st));
+  float *I1 = nullptr;
+  const bool i1_dev = I1h && is_device_ptr(I1h);
+  if (i1_dev) {
+    I1 = I1h;
+  } else {
+    if (!s->i1 && (st = dalloc(s, &s->i1, n)) != GD_OK) return report(rep_sp, report(rep_ad, st));
+    I1 = s->i1;
+  }
+  st = gd_diffuse_z(s, I0, I1, w_ad, ctl_ad, nullptr, rep_ad);
+  if (st != GD_OK && st != GD_ERR_NOT_CONVERGED) return report(rep_sp, st);
+  const int st_ad = st;
+  st = gd_screened_poisson_slices(s, I0, I1, I2h, alpha, ctl_sp, nullptr, rep_sp);
+  if (st != GD_OK && st != GD_ERR_NOT_CONVERGED) return st;
+  if (I1h && !i1_dev) {
+    CK(cudaMemcpyAsync(I1h, I1, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  return st != GD_OK ? st : st_ad;
 }
 
 int gd_screened_poisson(gd_stack *s, gd_weights w, const float *b, float *x, const gd_solve_ctl *ctl,
