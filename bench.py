@@ -622,15 +622,17 @@ def run_ncu_case(args):
 
 
 def run_ncu_batch(args):
-    """One batched solve of the 512-slice workload (for ncu launch lists; not
-    a benchmark): sides log-uniform in [256, 4096], to 1e-7 per slice."""
+    """One batched solve of the batch workload (for ncu captures; not a
+    benchmark): sides log-uniform in [256, 4096], to 1e-7 per slice; 512
+    slices unless --ncu-batch-slices says otherwise."""
     import torch
     import gdsynth
     import paper_1310_0041_gb300 as gd
     gd.build()
     bseed = SEED + 200
-    sides = gdsynth.batch_sides(BATCH_N, BATCH_LO, BATCH_HI, seed=bseed)
-    bal = gdsynth.batch_alphas(BATCH_N, seed=bseed)
+    nsl = args.ncu_batch_slices
+    sides = gdsynth.batch_sides(nsl, BATCH_LO, BATCH_HI, seed=bseed)
+    bal = gdsynth.batch_alphas(nsl, seed=bseed)
     B0s, B1s = gdsynth.batch_slices(sides, sides, seed=bseed)
     BI0 = torch.from_numpy(gdsynth.pack(B0s)).cuda()
     BI1 = torch.from_numpy(gdsynth.pack(B1s)).cuda()
@@ -641,7 +643,7 @@ def run_ncu_batch(args):
                                        raise_on_error=False)
     torch.cuda.synchronize()
     gd.gd_batch_destroy(bh)
-    print(json.dumps({"ncu_batch": "sp_batch_%d_slices" % BATCH_N, "status": rep["status"],
+    print(json.dumps({"ncu_batch": "sp_batch_%d_slices" % nsl, "status": rep["status"],
                       "cycles": rep["cycles"], "voxels": int(BI0.numel())}))
     return 0 if rep["status"] == 0 else 1
 
@@ -659,6 +661,8 @@ def main(argv=None):
                     help="skip the Hybrid and Linear discretisation measurements")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="one solve of the 512-slice batch for ncu launch lists (no timing)")
+    ap.add_argument("--ncu-batch-slices", type=int, default=BATCH_N,
+                    help="slices of the --ncu-batch case (fewer for detailed captures)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case instead of the benchmark")
     args = ap.parse_args(argv)

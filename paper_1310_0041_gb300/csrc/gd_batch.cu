@@ -575,6 +575,7 @@ struct gd_batch {
   long long launches = 0;
   long long g_launches = 0;
   int occ_sweep = 1, occ_aux = 1, occ_tile = 1;
+  int occ_zero = 1, occ_prolong = 1, occ_restrict = 1;  // each variant's own occupancy
   std::vector<long long> lev_fine_cells, lev_coarse_cells;  // algorithmic traffic per level
   std::vector<std::vector<BEntry>> Eh;  // host copies of the entries, per level
   int chunk = CH;                       // rows per work item of the row marches
@@ -723,18 +724,18 @@ int bvcycle(gd_batch *B, int nu1, int nu2, cudaStream_t st) {
     gd_batch::Lev &v = B->L[l];
     if (v.nitems == 0) continue;  // every slice of this depth is at its coarsest level
     cur[l] = v.x;
-    const int g = grid_for(B, v.nitems, B->occ_sweep);
+    const int g = grid_for(B, v.nitems, B->occ_sweep), gz = grid_for(B, v.nitems, B->occ_zero);
     for (int k = 0; k < nu1; ++k) {
       const bool zero = k == 0;
       float *out = (cur[l] == v.x) ? v.t : v.x;
       if (zero)
-        k_bsweep<true, false><<<g, BNT, 0, st>>>(v.E, v.items, v.nitems, nullptr, v.b, out, nullptr);
+        k_bsweep<true, false><<<gz, BNT, 0, st>>>(v.E, v.items, v.nitems, nullptr, v.b, out, nullptr);
       else
         k_bsweep<false, false><<<g, BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b, out, nullptr);
       ++B->launches;
       cur[l] = out;
     }
-    k_brestrict<<<grid_for(B, v.nitems, B->occ_aux), BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b,
+    k_brestrict<<<grid_for(B, v.nitems, B->occ_restrict), BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b,
                                                                   B->L[l + 1].b);
     ++B->launches;
   }
@@ -752,11 +753,11 @@ int bvcycle(gd_batch *B, int nu1, int nu2, cudaStream_t st) {
   for (int l = D - 1; l >= 0; --l) {
     gd_batch::Lev &v = B->L[l];
     if (v.nitems == 0) continue;
-    const int g = grid_for(B, v.nitems, B->occ_sweep);
+    const int g = grid_for(B, v.nitems, B->occ_sweep), gp = grid_for(B, v.nitems, B->occ_prolong);
     for (int k = 0; k < nu2; ++k) {
       float *out = (cur[l] == v.x) ? v.t : v.x;
       if (k == 0)
-        k_bsweep<false, true><<<g, BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b, out, B->L[l + 1].x);
+        k_bsweep<false, true><<<gp, BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b, out, B->L[l + 1].x);
       else
         k_bsweep<false, false><<<g, BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b, out, nullptr);
       ++B->launches;
@@ -1015,7 +1016,10 @@ int batch_build(gd_batch *B) {
   int dev = 0;
   BCK(cudaGetDevice(&dev));
   BCK(cudaDeviceGetAttribute(&B->sm_count, cudaDevAttrMultiProcessorCount, dev));
-  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_sweep, k_bsweep<false, true>, BNT, 0));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_sweep, k_bsweep<false, false>, BNT, 0));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_zero, k_bsweep<true, false>, BNT, 0));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_prolong, k_bsweep<false, true>, BNT, 0));
+  BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_restrict, k_brestrict, BNT, 0));
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_aux, k_bouter<true>, BNT, 0));
   BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&B->occ_tile, k_brhs, BNT, 0));
   return GD_OK;
