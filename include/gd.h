@@ -357,6 +357,21 @@ long long gd_batch_launch_count(const gd_batch *b);      /* kernel launches sinc
 const char *gd_batch_last_error(const gd_batch *b);
 int gd_batch_destroy(gd_batch *b);
 
+/*
+ * gd_selftest_wait -- failure-detection self-test: one CTA waits on an
+ * mbarrier that nothing arrives at, with the same bounded try_wait (500 ns
+ * suspend hint per poll) the TMA kernels use, for `polls` polls (1 ..
+ * 2^24).  Returns GD_ERR_TIMEOUT when the wait gave up (the expected
+ * outcome; the kernel returns normally and the context stays usable),
+ * GD_OK if it completed, GD_ERR_CUDA on a launch error.  Runs on the legacy
+ * default stream of the current device.
+ */
+int gd_selftest_wait(unsigned polls);
+
+/* Fault injection for tests (host side): with the environment variable
+ * GD_FAIL_ALLOC_AFTER=N set when a stack is created, that stack's
+ * allocations after the first N fail with GD_ERR_OOM. */
+
 /* Number of kernel launches the stack has enqueued since creation. */
 long long gd_launch_count(gd_stack *s);
 

@@ -36,7 +36,7 @@ EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_
            "gd_version", "gd_smooth_noalloc", "gd_screened_poisson", "gd_npr_rhs",
            "gd_batch_create", "gd_batch_screened_poisson", "gd_batch_voxels", "gd_batch_offset",
            "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy",
-           "gd_batch_traffic", "gd_batch_tune", "gd_ad_then_sp")
+           "gd_batch_traffic", "gd_batch_tune", "gd_ad_then_sp", "gd_selftest_wait")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -125,6 +125,7 @@ def lib():
                 "gd_batch_levels": (I, [P]),
                 "gd_batch_traffic": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
                 "gd_batch_tune": (I, [P, ctypes.POINTER(I)]),
+                "gd_selftest_wait": (I, [ctypes.c_uint]),
                 "gd_batch_launch_count": (ctypes.c_longlong, [P]),
                 "gd_batch_last_error": (ctypes.c_char_p, [P]),
                 "gd_batch_destroy": (I, [P]),
@@ -461,6 +462,11 @@ def gd_batch_destroy(b: Batch) -> int:
     st = lib().gd_batch_destroy(b.handle)
     b.handle = None
     return st
+
+
+def gd_selftest_wait(polls: int) -> int:
+    """Bounded-wait self-test; returns the status (GD_ERR_TIMEOUT expected)."""
+    return lib().gd_selftest_wait(int(polls))
 
 
 def gd_last_error(s: Optional[Stack]) -> str:

@@ -126,6 +126,8 @@ struct gd_stack {
   long long launches = 0;
   bool no_tma = false;     // GD_DISABLE_TMA set at creation: plain (unfused) kernels only
   bool no_graph = false;   // GD_DISABLE_GRAPHS set at creation: direct launches only
+  long long fail_alloc_after = -1;  // GD_FAIL_ALLOC_AFTER at creation: fault injection on the host
+  long long allocs = 0;
   std::vector<VGraph *> replayed;  // graphs replayed since the last collection (profiling)
   cudaStream_t cap_stream = nullptr;
   bool capturing = false;  // events become graph nodes (external event records)
@@ -258,6 +260,15 @@ void graphs_free(gd_stack *s, Plan &P) {
 // ---- device memory helpers ----
 int dalloc(gd_stack *s, float **p, size_t n) {
   if (n == 0) n = 1;
+  if (s->fail_alloc_after >= 0 && s->allocs >= s->fail_alloc_after) {
+    // injected failure (host side): the allocation is refused as if the
+    // device were out of memory
+    *p = nullptr;
+    set_err(s, "allocation %lld refused by GD_FAIL_ALLOC_AFTER=%lld (injected)", s->allocs,
+            s->fail_alloc_after);
+    return GD_ERR_OOM;
+  }
+  ++s->allocs;
   cudaError_t e = cudaMalloc((void **)p, n * sizeof(float));
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -1403,6 +1414,8 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
   s->no_tma = nt && nt[0] && std::strcmp(nt, "0") != 0;
   const char *ng = std::getenv("GD_DISABLE_GRAPHS");
   s->no_graph = ng && ng[0] && std::strcmp(ng, "0") != 0;
+  const char *fa = std::getenv("GD_FAIL_ALLOC_AFTER");
+  if (fa && fa[0]) s->fail_alloc_after = std::atoll(fa);
   *out = s;
   return GD_OK;
 }
@@ -1508,6 +1521,13 @@ int gd_ad_then_sp(gd_stack *s, const float *I0h, float *I2h, gd_weights w_ad, do
     CK(cudaStreamSynchronize(s->stream));
   }
   return st != GD_OK ? st : st_ad;
+}
+
+int gd_selftest_wait(unsigned polls) {
+  if (polls == 0 || polls > (1u << 24)) return GD_ERR_INVALID_ARG;
+  const int r = zmarch_wait_selftest(polls, nullptr);
+  if (r < 0) return GD_ERR_CUDA;
+  return r == 1 ? GD_ERR_TIMEOUT : GD_OK;
 }
 
 int gd_screened_poisson(gd_stack *s, gd_weights w, const float *b, float *x, const gd_solve_ctl *ctl,

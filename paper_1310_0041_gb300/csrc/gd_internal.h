@@ -93,6 +93,10 @@ cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz
 cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, int esz_e, double *err, int *nblocks_out,
                           cudaStream_t st);
 int zouter_max_blocks(int nx, int ny, int nz);
+// self-test of the kernels' bounded mbarrier wait on a barrier nothing
+// arrives at: 1 if the wait gave up after `limit` polls, 0 if it completed,
+// -1 on a CUDA error
+int zmarch_wait_selftest(unsigned limit, cudaStream_t st);
 
 // Host-side launchers (gd_kernels.cu).  All enqueue on `st` and return the
 // cudaGetLastError() of the launch.

@@ -97,6 +97,33 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// Self-test of the bounded wait: one thread initialises an mbarrier that
+// expects one arrival, never arrives, and polls it `limit` times with the
+// same try_wait and suspend hint the kernels use; a wait that gives up sets
+// *flag to 1 and the kernel returns normally.
+__global__ void k_wait_selftest(uint32_t limit, int *flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  const uint32_t a = su32(&bar);
+  const uint32_t hint_ns = 500;
+  bool done = false;
+  for (uint32_t it = 0; it < limit && !done; ++it) {
+    uint32_t d;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(d)
+        : "r"(a), "r"(0u), "r"(hint_ns)
+        : "memory");
+    done = d != 0;
+  }
+  *flag = done ? 0 : 1;
+}
+
+
 __device__ __forceinline__ float mass_of(int i, int n, int s, int l) {
   return (float)((i == n - 1) ? l : s);
 }
@@ -1760,4 +1787,22 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, int esz_e, double *e
 int zouter_max_blocks(int nx, int ny, int nz) {
   const int gx = (nx + ZX - 1) / ZX, gy = (ny + OuterGeo::OY - 1) / OuterGeo::OY;
   return gx * gy * nz;
+}
+
+// Runs k_wait_selftest (one CTA) and returns 1 if its wait gave up, 0 if it
+// completed, or -1 on a CUDA error.
+int zmarch_wait_selftest(unsigned limit, cudaStream_t st) {
+  int *d = nullptr;
+  if (cudaMalloc((void **)&d, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int h = -1;
+  cudaMemsetAsync(d, 0xff, sizeof(int), st);
+  k_wait_selftest<<<1, 32, 0, st>>>(limit, d);
+  cudaError_t e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return -1;
+  return h;
 }
