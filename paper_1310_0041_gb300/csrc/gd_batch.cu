@@ -466,12 +466,16 @@ __global__ void __launch_bounds__(BNT) k_brhs(const BEntry *__restrict__ E, cons
 // I2 = h + l rounded to float32, from the internal layout to the caller's
 // packed array.
 __global__ void __launch_bounds__(BNT) k_bfinal(const BEntry *__restrict__ E, const int4 *__restrict__ items,
-                                                int nitems, const float *__restrict__ h,
-                                                const float *__restrict__ l, float *__restrict__ out) {
+                                                int nitems, const float *__restrict__ h0,
+                                                const float *__restrict__ l0, const float *__restrict__ h1,
+                                                const float *__restrict__ l1, const int *__restrict__ fin,
+                                                float *__restrict__ out) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int4 w = items[it];
     const BEntry e = E[w.x];
     const int i0 = w.y, j0 = w.z;
+    // the pair buffer holding this slice's final iterate
+    const float *h = fin[e.slice] ? h1 : h0, *l = fin[e.slice] ? l1 : l0;
     for (int q = threadIdx.x; q < TX * TY; q += BNT) {
       const int gi = i0 + (q % TX), gj = j0 + q / TX;
       if (gi >= e.nx || gj >= e.ny) continue;
@@ -579,6 +583,14 @@ struct gd_batch {
   std::vector<long long> lev_fine_cells, lev_coarse_cells;  // algorithmic traffic per level
   std::vector<std::vector<BEntry>> Eh;  // host copies of the entries, per level
   int chunk = CH;                       // rows per work item of the row marches
+  // slices still iterating (the work lists hold only theirs once some have
+  // converged), their last relative residuals and squared rhs norms, and the
+  // pair buffer that holds each slice's final iterate
+  std::vector<char> active;
+  std::vector<double> srel, sbb;
+  std::vector<int> fin;
+  int *d_fin = nullptr;
+  bool filtered = false;
   std::string err;
 };
 
@@ -634,6 +646,7 @@ void batch_free(gd_batch *B) {
   cudaFree(B->V);
   cudaFree(B->lam);
   cudaFree(B->acc);
+  cudaFree(B->d_fin);
   cudaFree(B->bf);
   for (int k = 0; k < 2; ++k) {
     cudaFree(B->ph[k]);
@@ -793,12 +806,18 @@ int read_rel(gd_batch *B, double *rel_max, double *bnorm, double *slice_rel) {
   BCK(cudaMemcpyAsync(B->h_acc, B->acc, 2 * B->ns * sizeof(double), cudaMemcpyDeviceToHost, B->stream));
   BCK(cudaStreamSynchronize(B->stream));
   double m = 0.0, bb = 0.0;
+  B->srel.resize(B->ns, 0.0);
+  B->sbb.resize(B->ns, 0.0);
   for (int s = 0; s < B->ns; ++s) {
-    const double r2 = B->h_acc[2 * s], b2 = B->h_acc[2 * s + 1];
-    const double rel = b2 > 0.0 ? std::sqrt(r2 / b2) : std::sqrt(r2);
+    if (B->active.empty() || B->active[s]) {  // converged slices keep their last values
+      const double r2 = B->h_acc[2 * s], b2 = B->h_acc[2 * s + 1];
+      B->srel[s] = b2 > 0.0 ? std::sqrt(r2 / b2) : std::sqrt(r2);
+      B->sbb[s] = b2;
+    }
+    const double rel = B->srel[s];
     if (slice_rel) slice_rel[s] = rel;
     m = std::isnan(rel) ? rel : (std::isnan(m) ? m : std::fmax(m, rel));
-    bb += b2;
+    bb += B->sbb[s];
   }
   *rel_max = m;
   *bnorm = std::sqrt(bb);
@@ -847,6 +866,7 @@ int build_lists(gd_batch *B, int ch) {
     std::vector<int4> it, sa;
     for (int k = 0; k < (int)B->Eh[l].size(); ++k) {
       const BEntry &e = B->Eh[l][k];
+      if (!B->active.empty() && !B->active[e.slice]) continue;
       if (e.coff >= 0) strips_of(k, e.nx, e.ny, ch, it);
       if (l == 0) strips_of(k, e.nx, e.ny, ch, sa);
     }
@@ -1162,6 +1182,16 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
   }
   gd_batch::Lev &f = B->L[0];
   B->cur = 0;
+  // every slice iterates again
+  B->active.assign(B->ns, 1);
+  B->fin.assign(B->ns, 0);
+  B->srel.assign(B->ns, 0.0);
+  B->sbb.assign(B->ns, 0.0);
+  if (B->filtered) {
+    const int st0 = build_lists(B, B->chunk);
+    if (st0 != GD_OK) return st0;
+    B->filtered = false;
+  }
   k_brhs<<<grid_for(B, f.ntiles_all, B->occ_tile, false), BNT, 0, B->stream>>>(
       f.E, f.tiles_all, f.ntiles_all, dv[0], dv[1], dv[2], B->bf, B->ph[0], B->pl[0]);
   ++B->launches;
@@ -1179,12 +1209,39 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
   int cycles = 0;
   int status = GD_OK;
   if ((st = ensure_graph(B, c.nu1, c.nu2)) != GD_OK) return st;
+  // slices at tolerance leave the work lists (their iterate stays in the
+  // pair buffer that holds it); the lists shrink at most once per cycle
+  auto retire = [&]() -> int {
+    int left = 0, newly = 0;
+    for (int q = 0; q < B->ns; ++q) {
+      if (!B->active[q]) continue;
+      if (B->srel[q] <= c.rel_tol) {
+        B->active[q] = 0;
+        B->fin[q] = B->cur;
+        ++newly;
+      } else {
+        ++left;
+      }
+    }
+    if (newly > 0 && left > 0 && cycles < c.max_cycles) {
+      const int r = build_lists(B, B->chunk);
+      if (r != GD_OK) return r;
+      B->filtered = true;
+    }
+    return GD_OK;
+  };
+  if ((st = retire()) != GD_OK) return st;
   while (!(rel <= c.rel_tol) && cycles < c.max_cycles) {
-    BCK(cudaGraphLaunch(B->gexec, B->stream));
-    B->launches += B->g_launches;
+    if (B->gexec) {
+      BCK(cudaGraphLaunch(B->gexec, B->stream));
+      B->launches += B->g_launches;
+    } else if ((st = bvcycle(B, c.nu1, c.nu2, B->stream)) != GD_OK) {
+      return st;
+    }
     if ((st = outer_pass(B, true)) != GD_OK) return st;
     ++cycles;
     if ((st = read_rel(B, &rel, &bn, slice_rel)) != GD_OK) return st;
+    if ((st = retire()) != GD_OK) return st;
     if (rep && cycles < GD_HISTORY) rep->history[cycles] = rel;
     if (!std::isfinite(rel)) {
       status = GD_ERR_DIVERGED;
@@ -1204,8 +1261,12 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
     }
     out = B->stage[3];
   }
+  for (int q = 0; q < B->ns; ++q)
+    if (B->active[q]) B->fin[q] = B->cur;
+  if (!B->d_fin && (st = balloc(B, &B->d_fin, (size_t)B->ns)) != GD_OK) return st;
+  BCK(cudaMemcpyAsync(B->d_fin, B->fin.data(), B->ns * sizeof(int), cudaMemcpyHostToDevice, B->stream));
   k_bfinal<<<grid_for(B, f.ntiles_all, B->occ_tile, false), BNT, 0, B->stream>>>(
-      f.E, f.tiles_all, f.ntiles_all, B->ph[B->cur], B->pl[B->cur], out);
+      f.E, f.tiles_all, f.ntiles_all, B->ph[0], B->pl[0], B->ph[1], B->pl[1], B->d_fin, out);
   ++B->launches;
   BCK(cudaGetLastError());
   if (out != I2) BCK(cudaMemcpyAsync(I2, out, n * sizeof(float), cudaMemcpyDeviceToHost, B->stream));
@@ -1225,6 +1286,8 @@ int gd_batch_tune(gd_batch *B, int *chunk_out) {
   // hold (the timing does not depend on the values); the next solve starts
   // from its own right-hand side
   static const int cand[] = {32, 64, 128, 256};
+  B->active.assign(B->ns, 1);
+  B->filtered = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   BCK(cudaEventCreate(&e0));
   BCK(cudaEventCreate(&e1));
