@@ -129,13 +129,14 @@ typedef struct {
  *         Hybrid and Linear need prec = GD_PREC_FP32 (else GD_ERR_UNSUPPORTED).
  *   prec: GD_PREC_FP32, or GD_PREC_MIXED: the correction solves of
  *         gd_diffuse_z / gd_screened_poisson_slices store every multigrid level
- *         but the coarsest (corrections, constraints, sweep arrays) as
- *         bfloat16 with float32 arithmetic -- the paper's 16-bit storage of
- *         intermediate solutions and constraints (Sec. 4.1, "Disk I/O").
- *         The iterate, the outer residual and the output stay float32
- *         (float pair), so the tolerance is reached the same way.  Levels
- *         whose x extent is not a multiple of 8 keep float32 for the whole
- *         hierarchy.  gd_vcycle, gd_residual and gd_smooth always use
+ *         between the fine and the coarsest (corrections, constraints, sweep
+ *         arrays) as bfloat16 with float32 arithmetic -- the paper's 16-bit
+ *         storage of intermediate solutions and constraints (Sec. 4.1, "Disk
+ *         I/O").  The fine level, the coarsest solve, the iterate, the outer
+ *         residual and the output stay float32 (float pair), so the tolerance
+ *         is reached the same way.  A hierarchy with a level whose x extent is
+ *         not a multiple of 8 (or with fewer than three levels) keeps float32
+ *         throughout.  gd_vcycle, gd_residual and gd_smooth always use
  *         float32.
  *   cuda_stream: a cudaStream_t, or NULL for the legacy default stream
  * If the environment variable GD_DISABLE_TMA is set (and not "0") when the

@@ -406,18 +406,20 @@ int plan_build_into(gd_stack *s, Plan &P, const double w[4], int batch_z, int cx
     P.L.push_back(C);
   }
   // Mixed precision (the paper's 16-bit storage of intermediate solutions
-  // and constraints, Sec. 4.1 "Disk I/O"): every level but the coarsest
-  // stores its correction, constraints and sweep array as bfloat16, when all
-  // of them meet TMA's row alignment (nx % 8); arithmetic stays float32 and
-  // the coarsest solve float32.
-  P.half = prec == GD_PREC_MIXED && !s->no_tma && P.L.size() > 1;
-  for (size_t li = 0; li + 1 < P.L.size() && P.half; ++li)
+  // and constraints, Sec. 4.1 "Disk I/O"): every level between the fine and
+  // the coarsest stores its correction, constraints and sweep array as
+  // bfloat16, when all of them meet TMA's row alignment (nx % 8); arithmetic
+  // stays float32, and the fine level and the coarsest solve stay float32
+  // (bfloat16 rounding of the fine correction is high-frequency noise that A
+  // amplifies by its largest eigenvalue, which costs an AD cycle).
+  P.half = prec == GD_PREC_MIXED && !s->no_tma && P.L.size() > 2 && zmarch_usable(P.L[0].d, 4);
+  for (size_t li = 1; li + 1 < P.L.size() && P.half; ++li)
     P.half = zmarch_usable(P.L[li].d, 2);
   // workspace
   for (size_t li = 0; li < P.L.size(); ++li) {
     Level &l = P.L[li];
     l.n = (size_t)l.d.nx * l.d.ny * l.d.nz;
-    l.esz = (P.half && li + 1 < P.L.size()) ? 2 : 4;
+    l.esz = (P.half && li > 0 && li + 1 < P.L.size()) ? 2 : 4;
     if (li == 0) {
       l.x = s->f_x;
       l.b = s->f_b;

@@ -1729,13 +1729,18 @@ cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zer
   // x is coarsened, else the fine box; y: the 36 fine box rows)
   CUtensorMap mc = mx;
   a.cpf = 0;
-  if (prolong) {
+  // (a float32 level above a bfloat16 one prefetches only when x is halved:
+  // its unhalved box starts i0 - 4 elements in, which is not 16-byte aligned
+  // in bfloat16)
+  if (prolong && !(esz == 4 && esz_c == 2 && !a.fx)) {
     const int ac = 16 / esz_c, ncz = a.fz ? (L.nz + 1) / 2 : L.nz;
     const int cw = a.fx ? 32 + 2 * ac : box_w(esz), ch = a.fy ? rows_x / 2 : rows_x;
     // (a coarse level whose rows break TMA's alignment is simply not prefetched)
     a.cpf = make_map(&mc, a.xc, a.ncx, a.ncy, ncz, cw, ch, esz_c) ? 1 : 0;
     if (!a.cpf) mc = mx;
   }
+  if (esz == 4 && esz_c == 2 && prolong)
+    return run_zsweep_variant<float, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
   if (esz == 4) return run_zsweep_variant<float, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
   if (esz_c == 2 || !prolong)
     return run_zsweep_variant<half_t, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
@@ -1754,6 +1759,7 @@ cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz
   if (a.fz && (a.zchunk & 1)) ++a.zchunk;  // both children of a coarse plane in one chunk
   const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
   dim3 grid(gx, gy, gz);
+  if (esz == 4 && esz_c == 2) return run_zrestrict_t<float, half_t>(mx, mb, a, grid, st);
   if (esz == 4) return run_zrestrict_t<float, float>(mx, mb, a, grid, st);
   if (esz_c == 2) return run_zrestrict_t<half_t, half_t>(mx, mb, a, grid, st);
   return run_zrestrict_t<half_t, float>(mx, mb, a, grid, st);
