@@ -333,7 +333,7 @@ def run_gpu(args):
     m1, m2 = mreps[-1]
     mixed = {"value": world * voxels * args.steps / (mms * 1e-3), "unit": UNIT,
              "ms_per_step": mms / args.steps,
-             "storage": "bfloat16 multigrid levels (coarsest float32), float32 arithmetic, "
+             "storage": "bfloat16 levels between the fine and the coarsest, float32 arithmetic, "
                         "float-pair outer refinement",
              "ad_cycles": m1["cycles"], "ad_rel_residual": m1["rel_residual"],
              "sp_cycles": m2["cycles"], "sp_rel_residual": m2["rel_residual"]}
