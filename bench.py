@@ -57,7 +57,7 @@ BATCH_TOL = 1e-7
 # full-size launch is that ratio times its algorithmic bytes.  Valid only while
 # the kernel source is the one it was taken from.
 NCU_TRAFFIC = {
-    "rb_sweep_fine": {"dram_over_alg": 1429.7 / 1543.6, "src_sha256": "33525bcd7a41689c53539a47a8fda5f828702b2dcf9b175d22e3d83f8ac490f0"},
+    "rb_sweep_fine": {"dram_over_alg": 1420.7 / 1543.6, "src_sha256": "dfb6fe1b86393b172145c3ca0f95156aa3c309850604d44cf2fcc60f380e1ecd"},
 }
 
 
@@ -481,10 +481,11 @@ def run_gpu(args):
         barrier(world)
         bms = reduce_max(e0.elapsed_time(e1), world, dev)
         blaunch = gd.gd_batch_launch_count(bh) - bl0
-        per_cycle, per_solve = gd.gd_batch_traffic(bh, 2, 2)
         bvox = int(BI0.numel())
         rb_ = breps[-1]
-        alg = per_solve + rb_["cycles"] * per_cycle
+        # the bytes each solve's passes actually move (slices at tolerance
+        # leave the later cycles)
+        alg = gd.gd_batch_last_traffic(bh)
         batch = {"workload": "sp_batch_%d_slices_%d_to_%d" % (BATCH_N, BATCH_LO, BATCH_HI),
                  "value": world * bvox * bsteps / (bms * 1e-3), "unit": UNIT,
                  "ms_per_step": bms / bsteps, "steps": bsteps, "voxels": bvox, "slices": BATCH_N,

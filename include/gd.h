@@ -354,6 +354,9 @@ int gd_batch_levels(const gd_batch *b);                  /* depth of the deepest
  * pass, and of the once-per-solve passes (input, first outer pass, output):
  * each pass's arrays read and written once. */
 int gd_batch_traffic(const gd_batch *b, int nu1, int nu2, double *per_cycle, double *per_solve);
+/* Algorithmic bytes of the last gd_batch_screened_poisson: the once-per-solve
+ * passes plus each cycle over the slices still iterating in it (-1 for NULL). */
+double gd_batch_last_traffic(const gd_batch *b);
 long long gd_batch_launch_count(const gd_batch *b);      /* kernel launches since creation */
 const char *gd_batch_last_error(const gd_batch *b);
 int gd_batch_destroy(gd_batch *b);

@@ -36,7 +36,8 @@ EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_
            "gd_version", "gd_smooth_noalloc", "gd_screened_poisson", "gd_npr_rhs",
            "gd_batch_create", "gd_batch_screened_poisson", "gd_batch_voxels", "gd_batch_offset",
            "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy",
-           "gd_batch_traffic", "gd_batch_tune", "gd_ad_then_sp", "gd_selftest_wait")
+           "gd_batch_traffic", "gd_batch_tune", "gd_ad_then_sp", "gd_selftest_wait",
+           "gd_batch_last_traffic")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -125,6 +126,7 @@ def lib():
                 "gd_batch_levels": (I, [P]),
                 "gd_batch_traffic": (I, [P, I, I, ctypes.POINTER(D), ctypes.POINTER(D)]),
                 "gd_batch_tune": (I, [P, ctypes.POINTER(I)]),
+                "gd_batch_last_traffic": (D, [P]),
                 "gd_selftest_wait": (I, [ctypes.c_uint]),
                 "gd_batch_launch_count": (ctypes.c_longlong, [P]),
                 "gd_batch_last_error": (ctypes.c_char_p, [P]),
@@ -436,6 +438,11 @@ def gd_batch_traffic(b: Batch, nu1: int = 2, nu2: int = 2) -> tuple:
     if st != GD_OK:
         raise GdError(st, gd_batch_last_error(b))
     return pc.value, ps.value
+
+
+def gd_batch_last_traffic(b: Batch) -> float:
+    """Algorithmic bytes of the last batched solve (the work actually done)."""
+    return lib().gd_batch_last_traffic(b.handle)
 
 
 def gd_batch_tune(b: Batch) -> int:

@@ -580,7 +580,6 @@ struct gd_batch {
   long long g_launches = 0;
   int occ_sweep = 1, occ_aux = 1, occ_tile = 1;
   int occ_zero = 1, occ_prolong = 1, occ_restrict = 1;  // each variant's own occupancy
-  std::vector<long long> lev_fine_cells, lev_coarse_cells;  // algorithmic traffic per level
   std::vector<std::vector<BEntry>> Eh;  // host copies of the entries, per level
   int chunk = CH;                       // rows per work item of the row marches
   // slices still iterating (the work lists hold only theirs once some have
@@ -591,6 +590,7 @@ struct gd_batch {
   std::vector<int> fin;
   int *d_fin = nullptr;
   bool filtered = false;
+  double last_bytes = 0.0;  // algorithmic bytes of the last solve (the work actually done)
   std::string err;
 };
 
@@ -858,6 +858,27 @@ int ensure_graph(gd_batch *B, int nu1, int nu2) {
   return GD_OK;
 }
 
+// Algorithmic bytes of one V(nu1, nu2) cycle with its outer pass over the
+// slices still iterating (all of them when `active` is empty).
+double cycle_bytes(const gd_batch *B, int nu1, int nu2) {
+  double cyc = 0.0;
+  for (size_t l = 0; l < B->Eh.size(); ++l) {
+    double nf = 0.0, nc = 0.0, n0 = 0.0;
+    for (const BEntry &e : B->Eh[l]) {
+      if (!B->active.empty() && !B->active[e.slice]) continue;
+      if (l == 0) n0 += (double)e.pitch * e.ny;
+      if (e.coff < 0) continue;
+      nf += (double)e.pitch * e.ny;
+      nc += (double)e.cpitch * e.cny;
+    }
+    // sweeps (the first from zero: 8 B, the others 12 B; the prolongation
+    // adds 4 B per coarse cell), restriction (8 B + 4 B per coarse cell),
+    // and at level 0 the outer pass (28 B)
+    cyc += nf * (8.0 + 12.0 * (nu1 - 1)) + nf * 12.0 * nu2 + 4.0 * nc + nf * 8.0 + 4.0 * nc + 28.0 * n0;
+  }
+  return cyc;
+}
+
 // (Re)builds the row-march work lists for chunks of `ch` rows.
 int build_lists(gd_batch *B, int ch) {
   int st;
@@ -958,14 +979,9 @@ int batch_build(gd_batch *B) {
     gd_batch::Lev &v = B->L[l];
     std::vector<int4> ta;
     for (int k = 0; k < (int)E[l].size() && l == 0; ++k) tiles_of(k, E[l][k].nx, E[l][k].ny, ta);
-    long long fc = 0, cc = 0;
+    long long fc = 0;  // cells of the entries that have a next level (they need a sweep buffer)
     for (const BEntry &e : E[l])
-      if (e.coff >= 0) {
-        fc += (long long)e.pitch * e.ny;
-        cc += (long long)e.cpitch * e.cny;
-      }
-    B->lev_fine_cells.push_back(fc);
-    B->lev_coarse_cells.push_back(cc);
+      if (e.coff >= 0) fc += (long long)e.pitch * e.ny;
     v.ne = (int)E[l].size();
     v.ntiles_all = (int)ta.size();
     if ((st = balloc(B, &v.x, (size_t)v.n)) != GD_OK) return st;
@@ -1113,27 +1129,17 @@ int gd_batch_levels(const gd_batch *b) { return b ? b->depth_max : -1; }
 
 int gd_batch_traffic(const gd_batch *b, int nu1, int nu2, double *per_cycle, double *per_solve) {
   if (!b || nu1 < 1 || nu2 < 1) return GD_ERR_INVALID_ARG;
-  // cells (padded rows) of the entries of each level that have a next level,
-  // and of their next levels
-  double cyc = 0.0;
-  for (size_t l = 0; l < b->L.size(); ++l) {
-    const double nf = (double)b->lev_fine_cells[l], nc = (double)b->lev_coarse_cells[l];
-    if (nf == 0.0) continue;
-    // pre-sweeps: the first from zero reads b and writes x (8 B), the others
-    // read x and b and write x (12 B); post-sweeps likewise, the first adding
-    // the parents (4 B per coarse cell); restriction reads x and b and writes
-    // the coarse b
-    cyc += nf * (8.0 + 12.0 * (nu1 - 1)) + nf * 12.0 * nu2 + 4.0 * nc;
-    cyc += nf * 8.0 + 4.0 * nc;
-  }
+  gd_batch tmp_view;  // every slice active
+  tmp_view.Eh = b->Eh;
   const double n0 = (double)b->L[0].n;
-  cyc += 28.0 * n0;  // outer pass: reads bf, h, l, e; writes h, l, r
-  if (per_cycle) *per_cycle = cyc;
+  if (per_cycle) *per_cycle = cycle_bytes(&tmp_view, nu1, nu2);
   // right-hand side (reads I0, I1; writes bf, h, l), first outer pass
   // (reads bf, h, l; writes h, l, r), output (reads h, l; writes I2)
   if (per_solve) *per_solve = 20.0 * (double)b->nvox + 24.0 * n0 + 12.0 * n0;
   return GD_OK;
 }
+
+double gd_batch_last_traffic(const gd_batch *b) { return b ? b->last_bytes : -1.0; }
 
 long long gd_batch_launch_count(const gd_batch *b) { return b ? b->launches : -1; }
 
@@ -1231,7 +1237,9 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
     return GD_OK;
   };
   if ((st = retire()) != GD_OK) return st;
+  double bytes = 20.0 * (double)B->nvox + 36.0 * (double)f.n;  // input, first outer pass, output
   while (!(rel <= c.rel_tol) && cycles < c.max_cycles) {
+    bytes += cycle_bytes(B, c.nu1, c.nu2);
     if (B->gexec) {
       BCK(cudaGraphLaunch(B->gexec, B->stream));
       B->launches += B->g_launches;
@@ -1261,6 +1269,7 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
     }
     out = B->stage[3];
   }
+  B->last_bytes = bytes;
   for (int q = 0; q < B->ns; ++q)
     if (B->active[q]) B->fin[q] = B->cur;
   if (!B->d_fin && (st = balloc(B, &B->d_fin, (size_t)B->ns)) != GD_OK) return st;
