@@ -320,7 +320,10 @@ __device__ __forceinline__ ff two_sum(float a, float b) {
 // every rounding error of the high parts captured, written as the
 // correction's right-hand side, and the per-slice sums of r^2 and bf^2 (FP64
 // slots acc[2 s], acc[2 s + 1]; lanes sum in FP32, the warp in FP64).
-template <bool ADD_E>
+// PAIR = false while the residual is large: the low words are neither read
+// nor written (both buffers' low words are still zero then), h += e is a
+// plain FP32 add and its rounding stays far below the residual.
+template <bool ADD_E, bool PAIR = true>
 __global__ void __launch_bounds__(BNT) k_bouter(const BEntry *__restrict__ E, const int4 *__restrict__ items,
                                                 int nitems, const float *__restrict__ bf,
                                                 const float *__restrict__ hin, const float *__restrict__ lin,
@@ -342,8 +345,11 @@ __global__ void __launch_bounds__(BNT) k_bouter(const BEntry *__restrict__ E, co
       if (t < 0 || t >= ny || !C.mem) return;
       const long long o = rb + (long long)t * e.pitch;
       h = ld4(hin + o);
-      l = ld4(lin + o);
-      if (ADD_E) {
+      if (PAIR) l = ld4(lin + o);
+      if (ADD_E && !PAIR) {
+        const float4 d = ld4(ein + o);
+        h = make_float4(h.x + d.x, h.y + d.y, h.z + d.z, h.w + d.w);
+      } else if (ADD_E) {
         const float4 d = ld4(ein + o);
         float hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
         const float dv[4] = {d.x, d.y, d.z, d.w};
@@ -411,7 +417,7 @@ __global__ void __launch_bounds__(BNT) k_bouter(const BEntry *__restrict__ E, co
         const long long o = rb + (long long)t * e.pitch;
         st4(r + o, make_float4(rv4[0], rv4[1], rv4[2], rv4[3]));
         st4(hout + o, C.mask(hc));
-        st4(lout + o, C.mask(lc));
+        if (PAIR) st4(lout + o, C.mask(lc));
       }
       hm = hc;
       lm = lc;
@@ -783,12 +789,15 @@ int bvcycle(gd_batch *B, int nu1, int nu2, cudaStream_t st) {
 
 // Outer pass: pair cur (+ e) -> pair 1 - cur, r = bf - A x into L[0].b and
 // the per-slice sums into acc.
-int outer_pass(gd_batch *B, bool add_e) {
+int outer_pass(gd_batch *B, bool add_e, bool pair = true) {
   gd_batch::Lev &f = B->L[0];
   const int a = B->cur, o = 1 - B->cur;
   BCK(cudaMemsetAsync(B->acc, 0, 2 * B->ns * sizeof(double), B->stream));
   const int g = grid_for(B, f.nstrips_all, B->occ_aux);
-  if (add_e)
+  if (add_e && !pair)
+    k_bouter<true, false><<<g, BNT, 0, B->stream>>>(f.E, f.strips_all, f.nstrips_all, B->bf, B->ph[a],
+                                                    B->pl[a], f.x, B->ph[o], B->pl[o], f.b, B->acc);
+  else if (add_e)
     k_bouter<true><<<g, BNT, 0, B->stream>>>(f.E, f.strips_all, f.nstrips_all, B->bf, B->ph[a], B->pl[a],
                                              f.x, B->ph[o], B->pl[o], f.b, B->acc);
   else
@@ -856,6 +865,14 @@ int ensure_graph(gd_batch *B, int nu1, int nu2) {
   B->g_nu1 = nu1;
   B->g_nu2 = nu2;
   return GD_OK;
+}
+
+// Cells (padded rows) of the fine level over the slices still iterating.
+double n_active_fine(const gd_batch *B) {
+  double n0 = 0.0;
+  for (const BEntry &e : B->Eh[0])
+    if (B->active.empty() || B->active[e.slice]) n0 += (double)e.pitch * e.ny;
+  return n0;
 }
 
 // Algorithmic bytes of one V(nu1, nu2) cycle with its outer pass over the
@@ -1238,6 +1255,7 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
   };
   if ((st = retire()) != GD_OK) return st;
   double bytes = 20.0 * (double)B->nvox + 36.0 * (double)f.n;  // input, first outer pass, output
+  bool exact = false;
   while (!(rel <= c.rel_tol) && cycles < c.max_cycles) {
     bytes += cycle_bytes(B, c.nu1, c.nu2);
     if (B->gexec) {
@@ -1246,7 +1264,11 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
     } else if ((st = bvcycle(B, c.nu1, c.nu2, B->stream)) != GD_OK) {
       return st;
     }
-    if ((st = outer_pass(B, true)) != GD_OK) return st;
+    // plain FP32 updates while the residual is large; from 1e-4 on (and from
+    // then on always) the pair carries the low words
+    if (rel < 1e-4) exact = true;
+    if ((st = outer_pass(B, true, exact)) != GD_OK) return st;
+    bytes -= exact ? 0.0 : 8.0 * (double)n_active_fine(B);
     ++cycles;
     if ((st = read_rel(B, &rel, &bn, slice_rel)) != GD_OK) return st;
     if ((st = retire()) != GD_OK) return st;
