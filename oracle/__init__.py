@@ -12,6 +12,12 @@ Two independent routes to the exact discrete solutions:
   loops: right-hand sides, operator, Gauss-Seidel, conjugate gradients, the
   paper's V-cycle (Sec. 4.1) and a dense Cholesky solve.
 
+Further modules: ``npr`` (the NPR gradient filter of Sec. 7), ``batch``
+(screened Poisson on independent slices of different sizes), ``linear``
+(the Linear discretisation of Sec. 4.2, trilinear elements) and ``learned``
+(the convolutional network of a learned initial guess: forward, backward,
+Adam).
+
 System (paper Sec. 3.1 and Sec. 4, 6-point discretisation of Sec. 4.2, read
 with homogeneous Neumann boundaries):
 
