@@ -133,3 +133,33 @@ def test_batch_validation_without_gpu(lib):
     assert lib.gd_batch_destroy(None) == gd.GD_ERR_INVALID_ARG
     assert lib.gd_batch_screened_poisson(None, None, None, None, None, None, None, None) == \
         gd.GD_ERR_INVALID_ARG
+
+
+def test_pipeline_and_selftest_validation_without_gpu(lib):
+    # argument checks of the newer entry points return before any CUDA call
+    h = ctypes.c_void_p()
+    assert lib.gd_stack_create(ctypes.byref(h), 8, 8, 2, 0, 0, 0, None) == gd.GD_OK
+    s = gd.Stack(h, 8, 8, 2)
+    try:
+        import numpy as np
+        a = np.zeros(8 * 8 * 2, np.float32)
+        b = np.zeros_like(a)
+        with pytest.raises(gd.GdError) as ei:
+            gd.gd_ad_then_sp(s, a, a, (0.0, 1.0, 1.0, 1.0), 0.01)
+        assert ei.value.status == gd.GD_ERR_INVALID_ARG
+        with pytest.raises(gd.GdError) as ei:
+            gd.gd_ad_then_sp(s, a, b, (0.0, 1.0, 1.0, 1.0), 0.0)
+        assert ei.value.status == gd.GD_ERR_INVALID_ARG
+        with pytest.raises(gd.GdError) as ei:
+            gd.gd_ad_then_sp(s, a, b, (0.0, 1.0, 1.0, 1.0), 0.01, I1=a)
+        assert ei.value.status == gd.GD_ERR_INVALID_ARG
+    finally:
+        gd.gd_destroy(s)
+    assert gd.gd_selftest_wait(0) == gd.GD_ERR_INVALID_ARG
+    assert gd.gd_selftest_wait(1 << 25) == gd.GD_ERR_INVALID_ARG
+    pc, ps = ctypes.c_double(), ctypes.c_double()
+    assert lib.gd_batch_traffic(None, 2, 2, ctypes.byref(pc), ctypes.byref(ps)) == gd.GD_ERR_INVALID_ARG
+    assert lib.gd_batch_last_traffic(None) == -1.0
+    assert lib.gd_batch_tune(None, None) == gd.GD_ERR_INVALID_ARG
+    with pytest.raises(ValueError):
+        gd.gd_batch_create([4, 4], [4], [0.01, 0.01])
