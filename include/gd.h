@@ -11,11 +11,14 @@
  *
  * both instances of the general screened anisotropic system of Sec. 4,
  *       (alpha - div W grad) I = alpha I0 - div W G,
- * discretised with the 6-point "Constant" stencil of Sec. 4.2: face-adjacent
- * neighbours have coefficient -1 and, with homogeneous Neumann boundaries, the
- * diagonal is the number of existing neighbours, i.e. along one axis
- * K_n = tridiag(-1, [1, 2, ..., 2, 1], -1).  Unit voxel spacing on all axes.
- * The singular AD system (alpha = 0) is solved with mean(I1) = mean(I0).
+ * discretised by default with the 6-point "Constant" stencil of Sec. 4.2:
+ * face-adjacent neighbours have coefficient -1 and, with homogeneous Neumann
+ * boundaries, the diagonal is the number of existing neighbours, i.e. along
+ * one axis K_n = tridiag(-1, [1, 2, ..., 2, 1], -1).  Unit voxel spacing on all
+ * axes.  The singular AD system (alpha = 0) is solved with mean(I1) =
+ * mean(I0).  The Hybrid and Linear discretisations of Sec. 4.2 are chosen at
+ * gd_stack_create; batches of independent slices of different sizes have
+ * their own handle (gd_batch_*, below).
  *
  * Solver: V-cycle multigrid (Sec. 4.1) with red-black Gauss-Seidel
  * relaxation, residual + down-sampling by summing children, up-sampling by
