@@ -276,13 +276,16 @@ int gd_profile_query(gd_stack *s, int k, char *name, int name_len, long long *la
  *   nx, ny >= 2, nz >= 1, nx*ny*nz <= GD_NOALLOC_MAX_VOXELS (else
  *     GD_ERR_INVALID_ARG, nothing launched);
  *   w: weights of A = alpha + bx Kx + by Ky + bz Kz (as gd_smooth);
- *   b (in), x (in/out): device arrays only (host arrays would need staging
- *     buffers, i.e. allocations: GD_ERR_INVALID_ARG);
+ *   b (in), x (in/out): device arrays of the current device only (host
+ *     arrays would need staging buffers, i.e. allocations; another GPU's
+ *     arrays are not addressable from this one's kernels): GD_ERR_INVALID_ARG;
+ *     b and x must not overlap (GD_ERR_INVALID_ARG);
  *   cuda_stream: a cudaStream_t or NULL; returns after the sweeps complete.
  * It allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  * The first call on a device looks up the scratch array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the one scratch
+ * before any stream capture.  The address is kept for the life of the
+ * process, so it assumes the device's context is not reset in between.  All calls on a device share the one scratch
  * array, which keeps the last call's contents (each call overwrites what it
  * reads): calls that overlap on the GPU (other streams, other threads) race.
  */

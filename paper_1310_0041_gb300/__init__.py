@@ -324,6 +324,13 @@ def gd_smooth(s: Stack, w, b, x, nsweeps: int) -> int:
 def gd_smooth_noalloc(nx: int, ny: int, nz: int, w, b, x, nsweeps: int, stream=None) -> int:
     """Red-black sweeps like gd_smooth with no device allocation (device
     arrays only, at most GD_NOALLOC_MAX_VOXELS voxels); returns the status."""
+    import torch
+    for name, t in (("b", b), ("x", x)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise ValueError("%s must be a CUDA tensor (no staging: nothing is allocated)" % name)
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("%s lives on %s, but cuda:%d is current" % (name, t.device,
+                                                                      torch.cuda.current_device()))
     if stream is None:
         stream = _default_stream()
     n = nx * ny * nz

@@ -555,6 +555,7 @@ struct gd_batch {
   int cxy = 16;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  int device = 0;  // current at creation; caller device arrays must live there
   int sm_count = 0;
   // levels (packed over the slices that reach them)
   struct Lev {
@@ -670,6 +671,17 @@ bool dev_ptr(const void *p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// A device array of a GPU other than `dev` (the batch's): refused, since the
+// batch's kernels would read it from the wrong device.
+bool other_dev_ptr(const void *p, int dev) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return dev >= 0 && at.type == cudaMemoryTypeDevice && at.device != dev;
 }
 
 struct SliceLevel {
@@ -1125,6 +1137,10 @@ int gd_batch_create(gd_batch **out, int nslices, const int *nx, const int *ny, c
   B->nvox = tot;
   B->cxy = coarsest_xy;
   B->stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&B->device) != cudaSuccess) {
+    cudaGetLastError();
+    B->device = -1;
+  }
   const int st = batch_build(B.get());
   if (st != GD_OK) {
     g_create_err = B->err;
@@ -1190,6 +1206,14 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
   // device views of the caller's arrays (host arrays are staged)
   const float *in[3] = {I0, I1, x0};
   const float *dv[3] = {nullptr, nullptr, nullptr};
+  for (int k = 0; k < 4; ++k) {
+    const void *p = k < 3 ? (const void *)in[k] : (const void *)I2;
+    if (other_dev_ptr(p, B->device)) {
+      bset_err(B, "array %p lives on another device than the batch's (device %d)", p, B->device);
+      if (rep) rep->status = GD_ERR_INVALID_ARG;
+      return GD_ERR_INVALID_ARG;
+    }
+  }
   for (int k = 0; k < 3; ++k) {
     if (!in[k]) continue;
     if (dev_ptr(in[k])) {

@@ -102,6 +102,7 @@ constexpr int kMaxPlans = 4;
 
 struct gd_stack {
   int nx = 0, ny = 0, nz = 0, bc = 0, disc = 0, prec = 0;
+  int device = -1;  // the device current at creation (-1: none): caller device arrays must live there
   cudaStream_t stream = nullptr;
   std::vector<std::unique_ptr<Plan>> plans;  // cache, least recently used evicted
   Plan *cur = nullptr;                       // the plan of the running call
@@ -974,12 +975,28 @@ bool is_device_ptr(const void *p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// A device array of another GPU: the stack's kernels would read it from the
+// wrong device (without peer access, an illegal address), so it is refused.
+bool on_other_device(const gd_stack *s, const void *p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return s->device >= 0 && at.type == cudaMemoryTypeDevice && at.device != s->device;
+}
+
 // Device view of a caller array: device pointers pass through; host arrays
 // are copied (if `in`) into staging buffer `slot`.
 int resolve(gd_stack *s, const float *p, bool in, int slot, float **dev) {
   if (!p) {
     *dev = nullptr;
     return GD_OK;
+  }
+  if (on_other_device(s, p)) {
+    set_err(s, "array %p lives on another device than the stack's (device %d)", (const void *)p,
+            s->device);
+    return GD_ERR_INVALID_ARG;
   }
   if (is_device_ptr(p)) {
     *dev = const_cast<float *>(p);
@@ -1412,6 +1429,10 @@ int gd_stack_create(gd_stack **out, int nx, int ny, int nz, int bc, int disc, in
   s->disc = disc;
   s->prec = prec;
   s->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&s->device) != cudaSuccess) {  // no device yet: creation needs none
+    cudaGetLastError();
+    s->device = -1;
+  }
   const char *nt = std::getenv("GD_DISABLE_TMA");
   s->no_tma = nt && nt[0] && std::strcmp(nt, "0") != 0;
   const char *ng = std::getenv("GD_DISABLE_GRAPHS");
@@ -1700,11 +1721,13 @@ int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps
   l.n = n;
   l.b = b;
   l.x = x;
-  if ((st = dalloc(s, &l.t, n)) != GD_OK) {
+  // the sweep's second array is the stack's fine workspace (allocated once,
+  // shared with the solves, which never run at the same time on one stack)
+  if (!s->f_t && (st = dalloc(s, &s->f_t, n)) != GD_OK) {
     s->cur = saved;
     return st;
   }
-  float *tmp = l.t;
+  l.t = s->f_t;
   tmp_plan.L.push_back(l);
   for (int k = 0; k < nsweeps && st == GD_OK; ++k) st = sweep(s, 0, false, false, false, false);
   Level &lr = tmp_plan.L[0];
@@ -1716,7 +1739,6 @@ int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps
     if (cudaMemcpyAsync(xh, x, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
       st = GD_ERR_CUDA;
   cudaStreamSynchronize(s->stream);
-  cudaFree(tmp);
   tmp_plan.L.clear();
   s->cur = saved;
   if (s->prof_on) prof_collect(s);

@@ -9,6 +9,7 @@
 // evaluated in difference form (x_p - x_n), which keeps the rounding error
 // relative to the local differences rather than to the voxel values.
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "gd.h"
@@ -631,13 +632,23 @@ constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 float *g_noalloc_ptr[kNoallocMaxDevices] = {};
 
-bool noalloc_device_ptr(const void *p) {
+// A device (or managed) array that the kernels on device `dev` can address:
+// device memory of another GPU is refused (without peer access it is an
+// illegal address there).
+bool noalloc_device_ptr(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// [a, a + n) and [b, b + n) share an element
+bool noalloc_overlap(const float *a, const float *b, size_t n) {
+  const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b, bytes = n * sizeof(float);
+  return pa < pb + bytes && pb < pa + bytes;
 }
 
 bool noalloc_weight_ok(double v) { return std::isfinite(v) && v >= 0.0; }
@@ -645,15 +656,17 @@ bool noalloc_weight_ok(double v) { return std::isfinite(v) && v >= 0.0; }
 
 extern "C" int gd_smooth_noalloc(int nx, int ny, int nz, gd_weights w, const float *b, float *x,
                                  int nsweeps, void *cuda_stream) {
-  if (nx < 2 || ny < 2 || nz < 1 || !b || !x || b == x || nsweeps < 0) return GD_ERR_INVALID_ARG;
+  if (nx < 2 || ny < 2 || nz < 1 || !b || !x || nsweeps < 0) return GD_ERR_INVALID_ARG;
   if ((double)nx * (double)ny * (double)nz > (double)GD_NOALLOC_MAX_VOXELS) return GD_ERR_INVALID_ARG;
+  // the sweep reads b and x through restrict pointers: they must not overlap
+  if (noalloc_overlap(b, x, (size_t)nx * ny * nz)) return GD_ERR_INVALID_ARG;
   if (!noalloc_weight_ok(w.alpha) || !noalloc_weight_ok(w.beta_x) || !noalloc_weight_ok(w.beta_y) ||
       !noalloc_weight_ok(w.beta_z))
     return GD_ERR_INVALID_ARG;
-  if (!noalloc_device_ptr(b) || !noalloc_device_ptr(x)) return GD_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return GD_ERR_CUDA;
   if (dev < 0 || dev >= kNoallocMaxDevices) return GD_ERR_UNSUPPORTED;
+  if (!noalloc_device_ptr(b, dev) || !noalloc_device_ptr(x, dev)) return GD_ERR_INVALID_ARG;
   float *scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);

@@ -177,7 +177,7 @@ struct Ring {
 extern __shared__ __align__(128) float zsm[];
 
 // ---- storage types ----
-// The hierarchy's arrays are float32, or float16 in the mixed-precision mode
+// The hierarchy's arrays are float32, or bfloat16 in the mixed-precision mode
 // (arithmetic is float32 either way).  A TMA box must start on a 16-byte
 // boundary: boxes start 4 floats / 8 halves left of the tile and are 72 / 80
 // elements wide.  Four consecutive cells are one float4 / one 8-byte pair of
