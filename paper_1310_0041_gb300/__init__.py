@@ -38,6 +38,13 @@ EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_
            "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy",
            "gd_batch_traffic", "gd_batch_tune", "gd_ad_then_sp", "gd_selftest_wait",
            "gd_batch_last_traffic")
+# the symbols include/gd_learn.h declares (the learned initial guess)
+EXPORTS_LEARN = ("gd_nn_conv3x3", "gd_nn_conv3x3_wgrad", "gd_nn_bias_grad", "gd_nn_flip_weights",
+                 "gd_nn_pool2", "gd_nn_pool2_backward", "gd_nn_up2_backward", "gd_nn_adam",
+                 "gd_learn_stack_tiles", "gd_learn_create", "gd_learn_destroy",
+                 "gd_learn_param_count", "gd_learn_set_params", "gd_learn_get_params",
+                 "gd_learn_get_grads", "gd_learn_forward", "gd_learn_train_step",
+                 "gd_learn_predict_stack", "gd_learn_launch_count", "gd_learn_last_error")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -131,6 +138,29 @@ def lib():
                 "gd_batch_launch_count": (ctypes.c_longlong, [P]),
                 "gd_batch_last_error": (ctypes.c_char_p, [P]),
                 "gd_batch_destroy": (I, [P]),
+                # learned initial guess (include/gd_learn.h)
+                "gd_nn_conv3x3": (I, [P, I, I, P, I, I, I, I, P, P, I, I, P, P, P, P]),
+                "gd_nn_conv3x3_wgrad": (I, [P, I, I, P, I, I, I, I, P, I, P, P]),
+                "gd_nn_bias_grad": (I, [P, ctypes.c_longlong, I, P, P]),
+                "gd_nn_flip_weights": (I, [P, I, I, P, P, P]),
+                "gd_nn_pool2": (I, [P, I, I, I, I, P, P]),
+                "gd_nn_pool2_backward": (I, [P, P, I, I, P, I, I, I, I, P, P]),
+                "gd_nn_up2_backward": (I, [P, I, I, P, I, I, I, P, P]),
+                "gd_nn_adam": (I, [P, P, P, P, ctypes.c_longlong, D, D, D, D, I, P]),
+                "gd_learn_stack_tiles": (I, [P, P, I, I, I, I, I, I, ctypes.c_longlong,
+                                             ctypes.c_longlong, D, D, P, P, P]),
+                "gd_learn_create": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I), I, I, I,
+                                        ctypes.c_ulonglong, P]),
+                "gd_learn_destroy": (I, [P]),
+                "gd_learn_param_count": (ctypes.c_longlong, [P]),
+                "gd_learn_set_params": (I, [P, P]),
+                "gd_learn_get_params": (I, [P, P]),
+                "gd_learn_get_grads": (I, [P, P]),
+                "gd_learn_forward": (I, [P, P, I, P]),
+                "gd_learn_train_step": (I, [P, P, P, ctypes.POINTER(I), I, D, ctypes.POINTER(D)]),
+                "gd_learn_predict_stack": (I, [P, P, I, I, I, D, D, D, P]),
+                "gd_learn_launch_count": (ctypes.c_longlong, [P]),
+                "gd_learn_last_error": (ctypes.c_char_p, [P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)

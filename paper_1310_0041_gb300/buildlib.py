@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgd.so")
-SOURCES = ["gd_kernels.cu", "gd_zmarch.cu", "gd_host.cu", "gd_batch.cu", "gd_hybrid.cu", "gd_eig.cpp"]
+SOURCES = ["gd_kernels.cu", "gd_zmarch.cu", "gd_host.cu", "gd_batch.cu", "gd_hybrid.cu", "gd_learn.cu",
+           "gd_eig.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,7 +42,7 @@ def _stale(out: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(INCLUDE, "gd.h"))
+    headers += [os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE) if h.endswith(".h")]
     cc = nvcc()
     common = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O3",
               "-I", INCLUDE, "-I", CSRC, *extra_flags]

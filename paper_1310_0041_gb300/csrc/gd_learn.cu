@@ -1,0 +1,1320 @@
+// The learned initial guess: a 3x3 convolutional encoder-decoder evaluated
+// and trained on the tensor cores (tcgen05 MMA, TMEM accumulators).
+//
+// The paper's V-cycle (Sec. 4.1) converges from any start; this network only
+// proposes the start (the anisotropic diffusion's change I1 - I0, Sec. 3.1),
+// and the multigrid solve remains the judge of the result.
+//
+// Convolutions are implicit GEMMs, one CTA output block = 128 pixels (M),
+// N = output channels, K = 9 taps x input channels:
+//  * forward (and input gradient, with flipped weights): the A tile of a
+//    64-wide K stage is gathered by cp.async straight from the channels-last
+//    activations (16 bytes = 8 channels of one pixel at one tap; zero fill
+//    for the padding), which also reads the decoder's concatenation
+//    [up(a), b] without materialising it; the weight stage is copied the
+//    same way.  Three stages are in flight; one thread issues the MMAs and
+//    commits each stage to an mbarrier that frees its slot.  The epilogue
+//    reads the FP32 accumulator from TMEM (tcgen05.ld), adds the bias,
+//    applies ReLU / a ReLU mask, and stores bfloat16, float32, or
+//    (inference) the solver's start x0 = I0 + s y directly into the stack.
+//  * weight gradient: K = pixels.  Each thread loads an 8-pixel x 8-channel
+//    block, transposes it in registers and stores it as one K-major core
+//    matrix; the FP32 result is added to the gradient with red.global.add.
+// Every mbarrier wait is bounded; a CTA that gives up records it in
+// g_nn_timeout, waits (bounded) for its own MMAs and releases its TMEM.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "gd.h"
+#include "gd_learn.h"
+#include "gd_tc.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace {
+
+__device__ int g_nn_timeout;  // set to 1 when a bounded wait gave up
+
+constexpr int CT = 128;                // threads of a conv CTA (4 warps: 128 TMEM lanes)
+constexpr int KS = 64;                 // K elements per pipeline stage (4 MMAs of K = 16)
+constexpr int NST = 3;                 // forward: stages in flight
+constexpr int NSTW = 2;                // weight gradient: stages in flight
+constexpr int A_BYTES = 128 * KS * 2;  // one A stage (128 rows x 64 bf16)
+
+// The (virtual) convolution input: channels [0, ca) from xa upsampled by
+// upa (nearest), channels [ca, ca + cb) from xb; both channels-last.
+struct Src {
+  const bf16 *xa, *xb;
+  int ca, cb, upa;
+  int H, W;
+  long long npix;  // tiles * H * W
+};
+
+// Address of the 8-channel chunk starting at channel c of pixel (t, hh, ww);
+// ok = false outside the tile (the zero padding).
+__device__ __forceinline__ const bf16 *src_chunk(const Src &s, int t, int hh, int ww, int c, bool &ok) {
+  ok = (unsigned)hh < (unsigned)s.H && (unsigned)ww < (unsigned)s.W;
+  if (!ok) return s.xa;
+  if (c < s.ca) {
+    const int Ha = s.H / s.upa, Wa = s.W / s.upa;
+    return s.xa + (((long long)t * Ha + hh / s.upa) * Wa + ww / s.upa) * s.ca + c;
+  }
+  return s.xb + (((long long)t * s.H + hh) * s.W + ww) * s.cb + (c - s.ca);
+}
+
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ void unpack8(const uint4 &u, float (&f)[8]) {
+  const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    f[2 * q] = __uint_as_float(w[q] << 16);
+    f[2 * q + 1] = __uint_as_float(w[q] & 0xFFFF0000u);
+  }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+  return make_uint4(pack_bf2(f[0], f[1]), pack_bf2(f[2], f[3]), pack_bf2(f[4], f[5]),
+                    pack_bf2(f[6], f[7]));
+}
+
+// ---------------------------------------------------------------------------
+// forward convolution
+// ---------------------------------------------------------------------------
+struct FwdArgs {
+  Src s;
+  const bf16 *w;      // [co][9][ci]
+  const float *bias;  // [co] or null
+  int co, ci, relu;
+  const bf16 *mask;  // [npix][co] or null
+  bf16 *y;           // [npix][co] or null
+  float *yf;         // [npix][co] or null
+  // stack output: out[z][y][x] = base[z][y][x] + out_scale * v
+  const float *base;
+  float *out;
+  int snx, sny, tiles_x, tiles_y;
+  long long tile0;
+  float out_scale;
+  int nblocks;
+};
+
+__global__ void __launch_bounds__(CT) k_conv_fwd(FwdArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_slot[NST];
+  __shared__ __align__(8) uint64_t bar_acc, bar_fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int co = a.co, ci = a.ci, K = 9 * ci;
+  const int ksteps = K / 16, nstages = (ksteps + 3) / 4;
+  const int stage_bytes = A_BYTES + co * KS * 2;
+  uint32_t ncols = 32;
+  while ((int)ncols < co) ncols <<= 1;
+  if (tid == 0) {
+    for (int i = 0; i < NST; ++i) gdtc::mbar_init(&bar_slot[i], 1);
+    gdtc::mbar_init(&bar_acc, 1);
+    gdtc::mbar_init(&bar_fin, 1);
+    gdtc::fence_mbar_init();
+    s_abort = 0;
+  }
+  if (warp == 0) gdtc::tmem_alloc(&s_tmem, ncols);
+  gdtc::fence_before();
+  __syncthreads();
+  gdtc::fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t sbase = gdtc::saddr(smem);
+  const uint32_t idesc = gdtc::idesc_bf16(128, co);
+  const int HW = a.s.H * a.s.W;
+  const int nmine = a.nblocks > (int)blockIdx.x ? (a.nblocks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const long long total = (long long)nmine * nstages;
+
+  auto load = [&](long long g) {
+    const int blk = (int)blockIdx.x + (int)(g / nstages) * (int)gridDim.x;
+    const int s = (int)(g % nstages);
+    const uint32_t sa = sbase + (uint32_t)((g % NST) * stage_bytes);
+    const uint32_t sb = sa + A_BYTES;
+    const long long p = (long long)blk * 128 + tid;
+    const bool prow = p < a.s.npix;
+    int t = 0, h = 0, w = 0;
+    if (prow) {
+      t = (int)(p / HW);
+      const int r = (int)(p - (long long)t * HW);
+      h = r / a.s.W;
+      w = r - h * a.s.W;
+    }
+    const uint32_t arow = sa + (uint32_t)((tid >> 3) * 1024 + (tid & 7) * 16);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int k0 = s * KS + 8 * j;
+      if (k0 < K) {
+        const int tap = k0 / ci, c = k0 - tap * ci;
+        bool ok;
+        const bf16 *src = src_chunk(a.s, t, h + tap / 3 - 1, w + tap % 3 - 1, c, ok);
+        gdtc::cp_async16(arow + j * 128, src, (ok && prow) ? 16u : 0u);
+      }
+    }
+    for (int e = tid; e < co * 8; e += CT) {
+      const int n = e % co, j = e / co;
+      const int k0 = s * KS + 8 * j;
+      if (k0 < K)
+        gdtc::cp_async16(sb + (uint32_t)((n >> 3) * 1024 + j * 128 + (n & 7) * 16),
+                         a.w + (long long)n * K + k0, 16u);
+    }
+  };
+
+  auto epilogue = [&](int blk) {
+    const int m = warp * 32 + lane;
+    const long long p = (long long)blk * 128 + m;
+    const bool valid = p < a.s.npix;
+    int t = 0, h = 0, w = 0;
+    if (valid) {
+      t = (int)(p / HW);
+      const int r = (int)(p - (long long)t * HW);
+      h = r / a.s.W;
+      w = r - h * a.s.W;
+    }
+    for (int c0 = 0; c0 < co; c0 += 16) {
+      float v[16];
+      gdtc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (!valid) continue;
+      if (a.bias) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + c0 + i);
+      }
+      if (a.relu) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+      }
+      if (a.mask) {
+        const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + p * co + c0);
+        float mk[8];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          unpack8(__ldg(mp + half), mk);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (!(mk[i] > 0.f)) v[8 * half + i] = 0.f;
+        }
+      }
+      if (a.y) {
+        uint4 *yp = reinterpret_cast<uint4 *>(a.y + p * co + c0);
+        yp[0] = make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                           pack_bf2(v[6], v[7]));
+        yp[1] = make_uint4(pack_bf2(v[8], v[9]), pack_bf2(v[10], v[11]), pack_bf2(v[12], v[13]),
+                           pack_bf2(v[14], v[15]));
+      }
+      if (a.yf) {
+        float4 *yp = reinterpret_cast<float4 *>(a.yf + p * co + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      }
+      if (a.out) {
+        const long long tg = a.tile0 + t;
+        const int tx = (int)(tg % a.tiles_x);
+        const long long r1 = tg / a.tiles_x;
+        const int ty = (int)(r1 % a.tiles_y);
+        const long long tz = r1 / a.tiles_y;
+        const long long plane = (long long)a.snx * a.sny;
+        const long long o0 = (tz * co + c0) * plane + (long long)(ty * a.s.H + h) * a.snx + tx * a.s.W + w;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const long long o = o0 + (long long)i * plane;
+          a.out[o] = __ldg(a.base + o) + a.out_scale * v[i];
+        }
+      }
+    }
+  };
+
+  for (int g = 0; g < NST - 1; ++g) {
+    if (g < total) load(g);
+    gdtc::cp_async_commit();
+  }
+  int nblk_done = 0;
+  for (long long g = 0; g < total; ++g) {
+    gdtc::cp_async_wait<NST - 2>();
+    gdtc::fence_proxy_async();
+    gdtc::fence_before();
+    __syncthreads();
+    if (s_abort) break;
+    const int s = (int)(g % nstages);
+    const int slot = (int)(g % NST);
+    if (tid == 0) {
+      gdtc::fence_after();
+      const uint32_t sa = sbase + (uint32_t)(slot * stage_bytes), sb = sa + A_BYTES;
+      const int nq = min(4, ksteps - 4 * s);
+      for (int q = 0; q < nq; ++q)
+        gdtc::mma_bf16(tmem, gdtc::desc(sa + q * 256), gdtc::desc(sb + q * 256), idesc,
+                       (s > 0 || q > 0) ? 1u : 0u);
+      gdtc::mma_commit(&bar_slot[slot]);
+      if (s == nstages - 1) gdtc::mma_commit(&bar_acc);
+    }
+    const long long gn = g + NST - 1;
+    if (gn < total) {
+      if (g >= 1) {
+        const long long gp = g - 1;  // the stage whose slot gn reuses
+        if (!gdtc::mbar_wait(&bar_slot[gp % NST], (uint32_t)((gp / NST) & 1))) s_abort = 1;
+      }
+      load(gn);
+    }
+    gdtc::cp_async_commit();
+    if (s == nstages - 1) {
+      bool ok = gdtc::mbar_wait(&bar_acc, (uint32_t)(nblk_done & 1));
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) s_abort = 1;
+      gdtc::fence_after();
+      if (ok) epilogue((int)blockIdx.x + (int)(g / nstages) * (int)gridDim.x);
+      ++nblk_done;
+    }
+  }
+  gdtc::cp_async_wait<0>();
+  __syncthreads();
+  if (s_abort) {
+    // leave nothing of ours in flight before the TMEM goes back
+    if (tid == 0) {
+      atomicExch(&g_nn_timeout, 1);
+      gdtc::mma_commit(&bar_fin);
+    }
+    gdtc::mbar_wait(&bar_fin, 0);
+  }
+  gdtc::fence_before();
+  __syncthreads();
+  gdtc::fence_after();
+  if (warp == 0) gdtc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// weight gradient
+// ---------------------------------------------------------------------------
+struct WgradArgs {
+  Src s;
+  const bf16 *dy;  // [npix][co]
+  int co, ci;
+  float *dw;  // [co][9][ci], accumulated
+  int chunk;  // pixels per CTA (multiple of 64)
+};
+
+// in[k] = 8 channels of pixel k -> out[r] = channel r of the 8 pixels
+__device__ __forceinline__ void transpose8(const uint4 (&in)[8], uint4 (&out)[8]) {
+  uint32_t a[8][4];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k][0] = in[k].x;
+    a[k][1] = in[k].y;
+    a[k][2] = in[k].z;
+    a[k][3] = in[k].w;
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const uint32_t sel = (r & 1) ? 0x7632u : 0x5410u;
+    out[r] = make_uint4(__byte_perm(a[0][r >> 1], a[1][r >> 1], sel), __byte_perm(a[2][r >> 1], a[3][r >> 1], sel),
+                        __byte_perm(a[4][r >> 1], a[5][r >> 1], sel), __byte_perm(a[6][r >> 1], a[7][r >> 1], sel));
+  }
+}
+
+__global__ void __launch_bounds__(CT) k_conv_wgrad(WgradArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_slot[NSTW];
+  __shared__ __align__(8) uint64_t bar_acc, bar_fin;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int co = a.co, ci = a.ci, K9 = 9 * ci;
+  const int mt = blockIdx.x;
+  const long long p0 = (long long)blockIdx.y * a.chunk;
+  const long long p1 = min(a.s.npix, p0 + a.chunk);
+  const int nst = p1 > p0 ? (int)((p1 - p0 + 63) / 64) : 0;
+  const int stage_bytes = A_BYTES + co * KS * 2;
+  uint32_t ncols = 32;
+  while ((int)ncols < co) ncols <<= 1;
+  if (tid == 0) {
+    for (int i = 0; i < NSTW; ++i) gdtc::mbar_init(&bar_slot[i], 1);
+    gdtc::mbar_init(&bar_acc, 1);
+    gdtc::mbar_init(&bar_fin, 1);
+    gdtc::fence_mbar_init();
+    s_abort = 0;
+  }
+  if (warp == 0) gdtc::tmem_alloc(&s_tmem, ncols);
+  gdtc::fence_before();
+  __syncthreads();
+  gdtc::fence_after();
+  const uint32_t tmem = s_tmem;
+  unsigned char *const sbase_g = smem;
+  const uint32_t sbase = gdtc::saddr(smem);
+  const uint32_t idesc = gdtc::idesc_bf16(128, co);
+  const int HW = a.s.H * a.s.W;
+  // A task: row group ag (8 rows (tap, i0..i0+7)) of this M tile, K chunk aj
+  const int ag = tid & 15, aj = tid >> 4;
+  const int r0 = mt * 128 + ag * 8;
+  const bool arow = r0 < K9;
+  const int atap = arow ? r0 / ci : 0, ai0 = arow ? r0 - atap * ci : 0;
+  const int ady = atap / 3 - 1, adx = atap % 3 - 1;
+  // B task: output-channel group bg, K chunk bj (co tasks)
+  const int ngrp = co / 8;
+  const bool btask = tid < co;
+  const int bg = btask ? tid % ngrp : 0, bj = btask ? tid / ngrp : 0;
+  uint4 ra[8], rb[8];
+  auto gather = [&](int st) {
+    const long long pb = p0 + (long long)st * 64;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      ra[k] = make_uint4(0, 0, 0, 0);
+      const long long p = pb + aj * 8 + k;
+      if (arow && p < p1) {
+        const int t = (int)(p / HW);
+        const int r = (int)(p - (long long)t * HW);
+        const int h = r / a.s.W, w = r - h * a.s.W;
+        bool ok;
+        const bf16 *src = src_chunk(a.s, t, h + ady, w + adx, ai0, ok);
+        if (ok) ra[k] = __ldg(reinterpret_cast<const uint4 *>(src));
+      }
+      rb[k] = make_uint4(0, 0, 0, 0);
+      const long long q = pb + bj * 8 + k;
+      if (btask && q < p1) rb[k] = __ldg(reinterpret_cast<const uint4 *>(a.dy + q * co + bg * 8));
+    }
+  };
+  auto store = [&](int slot) {
+    unsigned char *sa = sbase_g + slot * stage_bytes;
+    unsigned char *sb = sa + A_BYTES;
+    uint4 t[8];
+    transpose8(ra, t);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) *reinterpret_cast<uint4 *>(sa + ag * 1024 + aj * 128 + r * 16) = t[r];
+    if (btask) {
+      transpose8(rb, t);
+#pragma unroll
+      for (int r = 0; r < 8; ++r) *reinterpret_cast<uint4 *>(sb + bg * 1024 + bj * 128 + r * 16) = t[r];
+    }
+  };
+  if (nst > 0) gather(0);
+  for (int st = 0; st < nst; ++st) {
+    const int slot = st & 1;
+    if (st >= NSTW) {
+      const int sp = st - NSTW;  // the stage that used this slot
+      if (!gdtc::mbar_wait(&bar_slot[slot], (uint32_t)((sp / NSTW) & 1))) s_abort = 1;
+    }
+    store(slot);
+    gdtc::fence_proxy_async();
+    gdtc::fence_before();
+    __syncthreads();
+    if (s_abort) break;
+    if (tid == 0) {
+      gdtc::fence_after();
+      const uint32_t sa = sbase + (uint32_t)(slot * stage_bytes), sb = sa + A_BYTES;
+      for (int q = 0; q < 4; ++q)
+        gdtc::mma_bf16(tmem, gdtc::desc(sa + q * 256), gdtc::desc(sb + q * 256), idesc,
+                       (st > 0 || q > 0) ? 1u : 0u);
+      gdtc::mma_commit(&bar_slot[slot]);
+    }
+    if (st + 1 < nst) gather(st + 1);
+  }
+  __syncthreads();
+  if (nst > 0 && !s_abort) {
+    if (tid == 0) gdtc::mma_commit(&bar_acc);
+    bool ok = gdtc::mbar_wait(&bar_acc, 0);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) s_abort = 1;
+    gdtc::fence_after();
+    if (ok) {
+      const int r = mt * 128 + warp * 32 + lane;
+      for (int c0 = 0; c0 < co; c0 += 16) {
+        float v[16];
+        gdtc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (r < K9) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) atomicAdd(a.dw + (long long)(c0 + i) * K9 + r, v[i]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_abort) {
+    if (tid == 0) {
+      atomicExch(&g_nn_timeout, 1);
+      gdtc::mma_commit(&bar_fin);
+    }
+    gdtc::mbar_wait(&bar_fin, 0);
+  }
+  gdtc::fence_before();
+  __syncthreads();
+  gdtc::fence_after();
+  if (warp == 0) gdtc::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// element-wise and reduction kernels of the network
+// ---------------------------------------------------------------------------
+__global__ void k_bias_grad(const bf16 *dy, long long npix, int co, float *db) {
+  __shared__ float red[256];
+  const int R = blockDim.x / co;
+  const int c = threadIdx.x % co, r = threadIdx.x / co;
+  float s = 0.f;
+  if (r < R)
+    for (long long p = (long long)blockIdx.x * R + r; p < npix; p += (long long)gridDim.x * R)
+      s += __bfloat162float(dy[p * co + c]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (r == 0) {
+    for (int q = 1; q < R; ++q) s += red[q * co + c];
+    atomicAdd(db + c, s);
+  }
+}
+
+__global__ void k_pool2(const bf16 *x, bf16 *y, long long nout, int Ho, int Wo, int c) {
+  const int cg = c / 8;
+  const long long n = nout * cg;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / cg;
+    const int g = (int)(e - p * cg);
+    const long long t = p / ((long long)Ho * Wo);
+    const int r = (int)(p - t * Ho * Wo);
+    const int ho = r / Wo, wo = r - ho * Wo;
+    const long long rowc = (long long)2 * Wo * c;
+    const long long b0 = ((t * 2 * Ho + 2 * ho) * 2 * Wo + 2 * wo) * c + 8 * g;
+    float f0[8], f1[8], f2[8], f3[8], o[8];
+    unpack8(__ldg(reinterpret_cast<const uint4 *>(x + b0)), f0);
+    unpack8(__ldg(reinterpret_cast<const uint4 *>(x + b0 + c)), f1);
+    unpack8(__ldg(reinterpret_cast<const uint4 *>(x + b0 + rowc)), f2);
+    unpack8(__ldg(reinterpret_cast<const uint4 *>(x + b0 + rowc + c)), f3);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) o[i] = 0.25f * ((f0[i] + f1[i]) + (f2[i] + f3[i]));
+    *reinterpret_cast<uint4 *>(y + p * c + 8 * g) = pack8(o);
+  }
+}
+
+__global__ void k_pool2_bwd(const bf16 *dp, const bf16 *skip, int sstride, int soff, const bf16 *mask,
+                            bf16 *out, long long nfine, int H, int W, int c) {
+  const int cg = c / 8;
+  const long long n = nfine * cg;
+  const int Hc = H / 2, Wc = W / 2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / cg;
+    const int g = (int)(e - p * cg);
+    const long long t = p / ((long long)H * W);
+    const int r = (int)(p - t * H * W);
+    const int h = r / W, w = r - h * W;
+    const long long pc = (t * Hc + h / 2) * Wc + w / 2;
+    float d[8], m[8], v[8];
+    unpack8(__ldg(reinterpret_cast<const uint4 *>(dp + pc * c + 8 * g)), d);
+    unpack8(__ldg(reinterpret_cast<const uint4 *>(mask + p * c + 8 * g)), m);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = 0.25f * d[i];
+    if (skip) {
+      float sk[8];
+      unpack8(__ldg(reinterpret_cast<const uint4 *>(skip + p * sstride + soff + 8 * g)), sk);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] += sk[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (!(m[i] > 0.f)) v[i] = 0.f;
+    *reinterpret_cast<uint4 *>(out + p * c + 8 * g) = pack8(v);
+  }
+}
+
+__global__ void k_up2_bwd(const bf16 *dk, int ck, const bf16 *mask, bf16 *out, long long ncoarse, int Hc,
+                          int Wc, int c) {
+  const int cg = c / 8;
+  const long long n = ncoarse * cg;
+  const int W = 2 * Wc;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long p = e / cg;
+    const int g = (int)(e - p * cg);
+    const long long t = p / ((long long)Hc * Wc);
+    const int r = (int)(p - t * Hc * Wc);
+    const int h = r / Wc, w = r - h * Wc;
+    const long long f0 = ((t * 2 * Hc + 2 * h) * W + 2 * w);
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0}, f[8], m[8];
+    const long long kids[4] = {f0, f0 + 1, f0 + W, f0 + W + 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unpack8(__ldg(reinterpret_cast<const uint4 *>(dk + kids[q] * ck + 8 * g)), f);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s[i] += f[i];
+    }
+    unpack8(__ldg(reinterpret_cast<const uint4 *>(mask + p * c + 8 * g)), m);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (!(m[i] > 0.f)) s[i] = 0.f;
+    *reinterpret_cast<uint4 *>(out + p * c + 8 * g) = pack8(s);
+  }
+}
+
+// dy = scale (y - t) as bfloat16; acc += sum (y - t)^2
+__global__ void k_mse(const float *y, const float *t, long long n, float scale, bf16 *dy, double *acc) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    dy[i] = __float2bfloat16(scale * d);
+    s += (double)d * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+  }
+}
+
+__global__ void k_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+__global__ void k_wexport(const float *w, int co, int ci, bf16 *w16, bf16 *wf16) {
+  const int K = 9 * ci;
+  const long long n = (long long)co * K;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(e / K), r = (int)(e - (long long)o * K);
+    const int tap = r / ci, i = r - tap * ci;
+    const bf16 v = __float2bfloat16(w[e]);
+    if (w16) w16[e] = v;
+    if (wf16) wf16[((long long)i * 9 + (8 - tap)) * co + o] = v;
+  }
+}
+
+// tiles of a stack, slices as channels (8 channels per thread)
+__global__ void k_stack_tiles(const float *I, const float *Isub, int nx, int ny, int th, int tw, int tc,
+                              int tiles_x, int tiles_y, long long tile0, long long npix, float shift,
+                              float scale, bf16 *x, float *xf) {
+  const int cg = tc / 8;
+  const long long n = npix * cg;
+  const long long plane = (long long)nx * ny;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    // e: group-major so that consecutive threads read consecutive x
+    const int g = (int)(e / npix);
+    const long long p = e - (long long)g * npix;
+    const long long t = p / ((long long)th * tw);
+    const int r = (int)(p - t * th * tw);
+    const int h = r / tw, w = r - h * tw;
+    const long long tg = tile0 + t;
+    const int tx = (int)(tg % tiles_x);
+    const long long r1 = tg / tiles_x;
+    const int ty = (int)(r1 % tiles_y);
+    const long long tz = r1 / tiles_y;
+    const long long o0 = (tz * tc + 8 * g) * plane + (long long)(ty * th + h) * nx + tx * tw + w;
+    float v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const long long o = o0 + (long long)i * plane;
+      v[i] = Isub ? (__ldg(I + o) - __ldg(Isub + o)) * scale : (__ldg(I + o) - shift) * scale;
+    }
+    if (xf) {
+      float4 *d = reinterpret_cast<float4 *>(xf + p * tc + 8 * g);
+      d[0] = make_float4(v[0], v[1], v[2], v[3]);
+      d[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+      *reinterpret_cast<uint4 *>(x + p * tc + 8 * g) = pack8(v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
+}
+
+int grid_1d(long long n, int threads, int cap_per_sm = 8) {
+  long long b = (n + threads - 1) / threads;
+  const long long cap = (long long)num_sms() * cap_per_sm;
+  if (b > cap) b = cap;
+  return (int)std::max(1LL, b);
+}
+
+bool mult16(int c) { return c > 0 && c % 16 == 0; }
+
+// Dynamic shared memory for a tcgen05 kernel: at least `need` bytes, raised
+// until the CTAs that fit on one SM together hold at most the SM's 512 TMEM
+// columns (an allocation beyond that would wait for another CTA to exit).
+struct SmemKey {
+  const void *k;
+  int need, ncols, dev, smem, per_sm;
+};
+
+template <typename Kern>
+int tmem_safe_smem(Kern k, int need, int ncols, int *per_sm) {
+  static std::mutex mu;
+  static std::vector<SmemKey> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (const SmemKey &e : cache)
+    if (e.k == (const void *)k && e.need == need && e.ncols == ncols && e.dev == dev) {
+      *per_sm = e.per_sm;
+      return e.smem;
+    }
+  // the largest dynamic size this kernel may ask for: the per-block opt-in
+  // limit less its static shared memory (barriers)
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  const int cap = optin - (int)fa.sharedSizeBytes;
+  if (need > cap || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  int smem = need;
+  for (;;) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, CT, smem) != cudaSuccess) {
+      cudaGetLastError();
+      return -1;
+    }
+    if (occ >= 1 && occ * ncols <= 512) {
+      *per_sm = occ;
+      cache.push_back(SmemKey{(const void *)k, need, ncols, dev, smem, occ});
+      return smem;
+    }
+    if (occ < 1 || smem >= cap) return -1;
+    smem = std::min(cap, smem + 8192);
+  }
+}
+
+std::mutex g_nn_err_mu;
+std::string g_nn_err;  // last failure of a layer-level call or launch (for gd_learn_last_error(NULL))
+
+int nn_fail(int status, const char *what, cudaError_t e) {
+  std::lock_guard<std::mutex> lock(g_nn_err_mu);
+  g_nn_err = std::string(what) + ": " + (e == cudaSuccess ? "failed" : cudaGetErrorString(e));
+  return status;
+}
+
+// status of the launches just enqueued
+int launched(const char *what) {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GD_OK : nn_fail(GD_ERR_CUDA, what, e);
+}
+
+int check_timeout() {
+  int h = 0;
+  if (cudaMemcpyFromSymbol(&h, g_nn_timeout, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return GD_ERR_CUDA;
+  }
+  if (h) {
+    const int z = 0;
+    cudaMemcpyToSymbol(g_nn_timeout, &z, sizeof(int));
+    return GD_ERR_TIMEOUT;
+  }
+  return GD_OK;
+}
+
+int src_ok(const void *xa, int ca, int up_a, const void *xb, int cb, int ntiles, int h, int w) {
+  if (!xa || !mult16(ca) || (up_a != 1 && up_a != 2) || cb < 0 || (cb > 0 && (!xb || cb % 16)) ||
+      ntiles < 1 || h < 1 || w < 1 || h % up_a || w % up_a)
+    return GD_ERR_INVALID_ARG;
+  return GD_OK;
+}
+
+int launch_conv(const FwdArgs &a0, cudaStream_t st, long long *launches) {
+  FwdArgs a = a0;
+  const long long nb = (a.s.npix + 127) / 128;
+  if (nb > (1LL << 30)) return GD_ERR_INVALID_ARG;
+  a.nblocks = (int)nb;
+  uint32_t ncols = 32;
+  while ((int)ncols < a.co) ncols <<= 1;
+  int per_sm = 0;
+  const int smem = tmem_safe_smem(k_conv_fwd, NST * (A_BYTES + a.co * KS * 2), (int)ncols, &per_sm);
+  if (smem < 0) return nn_fail(GD_ERR_CUDA, "conv: shared memory / occupancy set-up", cudaSuccess);
+  const int grid = (int)std::min<long long>(nb, (long long)per_sm * num_sms());
+  k_conv_fwd<<<grid, CT, smem, st>>>(a);
+  if (launches) ++*launches;
+  return launched("k_conv_fwd launch");
+}
+
+int launch_wgrad(const Src &s, const bf16 *dy, int co, float *dw, cudaStream_t st, long long *launches) {
+  WgradArgs a;
+  a.s = s;
+  a.dy = dy;
+  a.co = co;
+  a.ci = s.ca + s.cb;
+  a.dw = dw;
+  const int mtiles = (9 * a.ci + 127) / 128;
+  uint32_t ncols = 32;
+  while ((int)ncols < co) ncols <<= 1;
+  int per_sm = 0;
+  const int smem = tmem_safe_smem(k_conv_wgrad, NSTW * (A_BYTES + co * KS * 2), (int)ncols, &per_sm);
+  if (smem < 0) return nn_fail(GD_ERR_CUDA, "wgrad: shared memory / occupancy set-up", cudaSuccess);
+  // about two waves of CTAs, each with at least 4096 pixels
+  const long long want = (long long)per_sm * num_sms() * 2 / mtiles;
+  long long chunk = (s.npix + std::max(1LL, want) - 1) / std::max(1LL, want);
+  chunk = std::max(4096LL, (chunk + 63) / 64 * 64);
+  const long long splits = (s.npix + chunk - 1) / chunk;
+  if (splits > 65535) chunk = ((s.npix + 65534) / 65535 + 63) / 64 * 64;
+  a.chunk = (int)chunk;
+  dim3 grid(mtiles, (unsigned)((s.npix + chunk - 1) / chunk));
+  k_conv_wgrad<<<grid, CT, smem, st>>>(a);
+  if (launches) ++*launches;
+  return launched("k_conv_wgrad launch");
+}
+
+int launch_bias_grad(const bf16 *dy, long long npix, int co, float *db, cudaStream_t st, long long *launches) {
+  const int R = 256 / co;
+  const int grid = (int)std::min<long long>((npix + R * 64 - 1) / (R * 64), (long long)num_sms() * 4);
+  k_bias_grad<<<std::max(1, grid), 256, 0, st>>>(dy, npix, co, db);
+  if (launches) ++*launches;
+  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA;
+}
+
+int finish(cudaStream_t st, int status) {
+  if (status != GD_OK) return status;
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return nn_fail(GD_ERR_CUDA, "stream synchronisation", e);
+  }
+  const int t = check_timeout();
+  if (t == GD_ERR_TIMEOUT) nn_fail(t, "a bounded wait on the tensor cores gave up", cudaSuccess);
+  return t;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the network
+// ---------------------------------------------------------------------------
+struct gd_learn {
+  int cin = 0, cout = 0, c[4] = {16, 32, 64, 128}, H = 0, W = 0, maxb = 0;
+  cudaStream_t st = nullptr;
+  struct Lay {
+    int ci, co;
+    long long w, b;  // offsets of the weights and the bias in the flat parameter array
+  };
+  Lay L[8];
+  long long np = 0;
+  float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+  bf16 *W16 = nullptr, *WF16 = nullptr;  // bf16 weights (same offsets as P) and flipped copies
+  int adam_t = 0;
+  // activations (bf16, channels last) and their gradients
+  bf16 *x = nullptr, *e1 = nullptr, *p1 = nullptr, *e2 = nullptr, *p2 = nullptr, *e3 = nullptr, *p3 = nullptr,
+       *e4 = nullptr, *d3 = nullptr, *d2 = nullptr, *d1 = nullptr;
+  float *y = nullptr, *tgt = nullptr;
+  bf16 *dy = nullptr, *gb1 = nullptr, *dk1 = nullptr, *gb2 = nullptr, *dk2 = nullptr, *gb3 = nullptr,
+       *dk3 = nullptr, *ga4 = nullptr, *dp3 = nullptr, *ga3 = nullptr, *dp2 = nullptr, *ga2 = nullptr,
+       *dp1 = nullptr, *ga1 = nullptr;
+  double *acc = nullptr;
+  std::vector<void *> allocs;
+  long long launches = 0;
+  std::string err;
+};
+
+namespace {
+
+enum { E1 = 0, E2, E3, E4, D3, D2, D1, YL };
+
+template <typename T>
+int lalloc(gd_learn *L, T **p, long long n) {
+  void *q = nullptr;
+  if (cudaMalloc(&q, std::max<long long>(n, 1) * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    L->err = "out of device memory";
+    return GD_ERR_OOM;
+  }
+  L->allocs.push_back(q);
+  *p = static_cast<T *>(q);
+  return GD_OK;
+}
+
+Src src1(const bf16 *x, int c, int B, int H, int W) {
+  Src s;
+  s.xa = x;
+  s.xb = nullptr;
+  s.ca = c;
+  s.cb = 0;
+  s.upa = 1;
+  s.H = H;
+  s.W = W;
+  s.npix = (long long)B * H * W;
+  return s;
+}
+Src src2(const bf16 *coarse, int cc, const bf16 *skip, int cs, int B, int H, int W) {
+  Src s = src1(coarse, cc, B, H, W);
+  s.xb = skip;
+  s.cb = cs;
+  s.upa = 2;
+  return s;
+}
+
+FwdArgs fwd_args(const Src &s, const bf16 *w, const float *bias, int co, int relu, const bf16 *mask, bf16 *y,
+                 float *yf) {
+  FwdArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.s = s;
+  a.w = w;
+  a.bias = bias;
+  a.co = co;
+  a.ci = s.ca + s.cb;
+  a.relu = relu;
+  a.mask = mask;
+  a.y = y;
+  a.yf = yf;
+  return a;
+}
+
+#define LTRY(expr)                   \
+  do {                               \
+    const int _st = (expr);          \
+    if (_st != GD_OK) return _st;    \
+  } while (0)
+
+int launch_pool(gd_learn *L, const bf16 *x, int B, int H, int W, int c, bf16 *y) {
+  const long long nout = (long long)B * (H / 2) * (W / 2);
+  k_pool2<<<grid_1d(nout * (c / 8), 256), 256, 0, L->st>>>(x, y, nout, H / 2, W / 2, c);
+  ++L->launches;
+  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA;
+}
+
+// forward of `B` tiles already in L->x; the output goes to yf, or (when out
+// is set) into the stack through the epilogue
+int net_forward(gd_learn *L, int B, float *yf, const FwdArgs *stack_out) {
+  const int H = L->H, W = L->W, *c = L->c;
+  const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4, H8 = H / 8, W8 = W / 8;
+  auto wl = [&](int l) { return L->W16 + L->L[l].w; };
+  auto bl = [&](int l) { return L->P + L->L[l].b; };
+  cudaStream_t st = L->st;
+  long long *nl = &L->launches;
+  LTRY(launch_conv(fwd_args(src1(L->x, L->cin, B, H, W), wl(E1), bl(E1), c[0], 1, nullptr, L->e1, nullptr), st, nl));
+  LTRY(launch_pool(L, L->e1, B, H, W, c[0], L->p1));
+  LTRY(launch_conv(fwd_args(src1(L->p1, c[0], B, H2, W2), wl(E2), bl(E2), c[1], 1, nullptr, L->e2, nullptr), st, nl));
+  LTRY(launch_pool(L, L->e2, B, H2, W2, c[1], L->p2));
+  LTRY(launch_conv(fwd_args(src1(L->p2, c[1], B, H4, W4), wl(E3), bl(E3), c[2], 1, nullptr, L->e3, nullptr), st, nl));
+  LTRY(launch_pool(L, L->e3, B, H4, W4, c[2], L->p3));
+  LTRY(launch_conv(fwd_args(src1(L->p3, c[2], B, H8, W8), wl(E4), bl(E4), c[3], 1, nullptr, L->e4, nullptr), st, nl));
+  LTRY(launch_conv(fwd_args(src2(L->e4, c[3], L->e3, c[2], B, H4, W4), wl(D3), bl(D3), c[2], 1, nullptr, L->d3, nullptr), st, nl));
+  LTRY(launch_conv(fwd_args(src2(L->d3, c[2], L->e2, c[1], B, H2, W2), wl(D2), bl(D2), c[1], 1, nullptr, L->d2, nullptr), st, nl));
+  LTRY(launch_conv(fwd_args(src2(L->d2, c[1], L->e1, c[0], B, H, W), wl(D1), bl(D1), c[0], 1, nullptr, L->d1, nullptr), st, nl));
+  FwdArgs a = fwd_args(src1(L->d1, c[0], B, H, W), wl(YL), bl(YL), L->cout, 0, nullptr, nullptr, yf);
+  if (stack_out) {
+    a.base = stack_out->base;
+    a.out = stack_out->out;
+    a.snx = stack_out->snx;
+    a.sny = stack_out->sny;
+    a.tiles_x = stack_out->tiles_x;
+    a.tiles_y = stack_out->tiles_y;
+    a.tile0 = stack_out->tile0;
+    a.out_scale = stack_out->out_scale;
+  }
+  return launch_conv(a, st, nl);
+}
+
+int net_backward(gd_learn *L, int B) {
+  const int H = L->H, W = L->W, *c = L->c;
+  const int H2 = H / 2, W2 = W / 2, H4 = H / 4, W4 = W / 4, H8 = H / 8, W8 = W / 8;
+  const long long n1 = (long long)B * H * W, n2 = n1 / 4, n4 = n1 / 16, n8 = n1 / 64;
+  cudaStream_t st = L->st;
+  long long *nl = &L->launches;
+  auto wf = [&](int l) { return L->WF16 + L->L[l].w; };
+  auto gw = [&](int l) { return L->G + L->L[l].w; };
+  auto gb = [&](int l) { return L->G + L->L[l].b; };
+  if (cudaMemsetAsync(L->G, 0, L->np * sizeof(float), st) != cudaSuccess) return GD_ERR_CUDA;
+  // y = conv(d1)
+  LTRY(launch_wgrad(src1(L->d1, c[0], B, H, W), L->dy, L->cout, gw(YL), st, nl));
+  LTRY(launch_bias_grad(L->dy, n1, L->cout, gb(YL), st, nl));
+  LTRY(launch_conv(fwd_args(src1(L->dy, L->cout, B, H, W), wf(YL), nullptr, c[0], 0, L->d1, L->gb1, nullptr), st, nl));
+  // d1 = relu(conv([up d2, e1]))
+  LTRY(launch_wgrad(src2(L->d2, c[1], L->e1, c[0], B, H, W), L->gb1, c[0], gw(D1), st, nl));
+  LTRY(launch_bias_grad(L->gb1, n1, c[0], gb(D1), st, nl));
+  LTRY(launch_conv(fwd_args(src1(L->gb1, c[0], B, H, W), wf(D1), nullptr, c[1] + c[0], 0, nullptr, L->dk1, nullptr), st, nl));
+  k_up2_bwd<<<grid_1d(n2 * (c[1] / 8), 256), 256, 0, st>>>(L->dk1, c[1] + c[0], L->d2, L->gb2, n2, H2, W2, c[1]);
+  ++*nl;
+  // d2 = relu(conv([up d3, e2]))
+  LTRY(launch_wgrad(src2(L->d3, c[2], L->e2, c[1], B, H2, W2), L->gb2, c[1], gw(D2), st, nl));
+  LTRY(launch_bias_grad(L->gb2, n2, c[1], gb(D2), st, nl));
+  LTRY(launch_conv(fwd_args(src1(L->gb2, c[1], B, H2, W2), wf(D2), nullptr, c[2] + c[1], 0, nullptr, L->dk2, nullptr), st, nl));
+  k_up2_bwd<<<grid_1d(n4 * (c[2] / 8), 256), 256, 0, st>>>(L->dk2, c[2] + c[1], L->d3, L->gb3, n4, H4, W4, c[2]);
+  ++*nl;
+  // d3 = relu(conv([up e4, e3]))
+  LTRY(launch_wgrad(src2(L->e4, c[3], L->e3, c[2], B, H4, W4), L->gb3, c[2], gw(D3), st, nl));
+  LTRY(launch_bias_grad(L->gb3, n4, c[2], gb(D3), st, nl));
+  LTRY(launch_conv(fwd_args(src1(L->gb3, c[2], B, H4, W4), wf(D3), nullptr, c[3] + c[2], 0, nullptr, L->dk3, nullptr), st, nl));
+  k_up2_bwd<<<grid_1d(n8 * (c[3] / 8), 256), 256, 0, st>>>(L->dk3, c[3] + c[2], L->e4, L->ga4, n8, H8, W8, c[3]);
+  ++*nl;
+  // e4 = relu(conv(pool e3))
+  LTRY(launch_wgrad(src1(L->p3, c[2], B, H8, W8), L->ga4, c[3], gw(E4), st, nl));
+  LTRY(launch_bias_grad(L->ga4, n8, c[3], gb(E4), st, nl));
+  LTRY(launch_conv(fwd_args(src1(L->ga4, c[3], B, H8, W8), wf(E4), nullptr, c[2], 0, nullptr, L->dp3, nullptr), st, nl));
+  k_pool2_bwd<<<grid_1d(n4 * (c[2] / 8), 256), 256, 0, st>>>(L->dp3, L->dk3, c[3] + c[2], c[3], L->e3, L->ga3, n4, H4, W4, c[2]);
+  ++*nl;
+  // e3 = relu(conv(pool e2))
+  LTRY(launch_wgrad(src1(L->p2, c[1], B, H4, W4), L->ga3, c[2], gw(E3), st, nl));
+  LTRY(launch_bias_grad(L->ga3, n4, c[2], gb(E3), st, nl));
+  LTRY(launch_conv(fwd_args(src1(L->ga3, c[2], B, H4, W4), wf(E3), nullptr, c[1], 0, nullptr, L->dp2, nullptr), st, nl));
+  k_pool2_bwd<<<grid_1d(n2 * (c[1] / 8), 256), 256, 0, st>>>(L->dp2, L->dk2, c[2] + c[1], c[2], L->e2, L->ga2, n2, H2, W2, c[1]);
+  ++*nl;
+  // e2 = relu(conv(pool e1))
+  LTRY(launch_wgrad(src1(L->p1, c[0], B, H2, W2), L->ga2, c[1], gw(E2), st, nl));
+  LTRY(launch_bias_grad(L->ga2, n2, c[1], gb(E2), st, nl));
+  LTRY(launch_conv(fwd_args(src1(L->ga2, c[1], B, H2, W2), wf(E2), nullptr, c[0], 0, nullptr, L->dp1, nullptr), st, nl));
+  k_pool2_bwd<<<grid_1d(n1 * (c[0] / 8), 256), 256, 0, st>>>(L->dp1, L->dk1, c[1] + c[0], c[1], L->e1, L->ga1, n1, H, W, c[0]);
+  ++*nl;
+  // e1 = relu(conv(x))
+  LTRY(launch_wgrad(src1(L->x, L->cin, B, H, W), L->ga1, c[0], gw(E1), st, nl));
+  LTRY(launch_bias_grad(L->ga1, n1, c[0], gb(E1), st, nl));
+  (void)n8;
+  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA;
+}
+
+int export_weights(gd_learn *L) {
+  for (int l = 0; l < 8; ++l) {
+    const auto &y = L->L[l];
+    const long long n = (long long)y.co * 9 * y.ci;
+    k_wexport<<<grid_1d(n, 256), 256, 0, L->st>>>(L->P + y.w, y.co, y.ci, L->W16 + y.w, L->WF16 + y.w);
+    ++L->launches;
+  }
+  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gd_nn_conv3x3(const void *xa, int ca, int up_a, const void *xb, int cb, int ntiles, int h, int w,
+                  const void *wt, const float *bias, int co, int relu, const void *mask, void *y, float *yf,
+                  void *stream) {
+  LTRY(src_ok(xa, ca, up_a, xb, cb, ntiles, h, w));
+  if (!wt || !mult16(co) || co > 256 || (relu != 0 && relu != 1) || (!y && !yf)) return GD_ERR_INVALID_ARG;
+  Src s = src1(static_cast<const bf16 *>(xa), ca, ntiles, h, w);
+  s.xb = static_cast<const bf16 *>(xb);
+  s.cb = cb;
+  s.upa = up_a;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const FwdArgs a = fwd_args(s, static_cast<const bf16 *>(wt), bias, co, relu, static_cast<const bf16 *>(mask),
+                             static_cast<bf16 *>(y), yf);
+  return finish(st, launch_conv(a, st, nullptr));
+}
+
+int gd_nn_conv3x3_wgrad(const void *xa, int ca, int up_a, const void *xb, int cb, int ntiles, int h, int w,
+                        const void *dy, int co, float *dw, void *stream) {
+  LTRY(src_ok(xa, ca, up_a, xb, cb, ntiles, h, w));
+  if (!dy || !dw || !mult16(co) || co > 128) return GD_ERR_INVALID_ARG;
+  Src s = src1(static_cast<const bf16 *>(xa), ca, ntiles, h, w);
+  s.xb = static_cast<const bf16 *>(xb);
+  s.cb = cb;
+  s.upa = up_a;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return finish(st, launch_wgrad(s, static_cast<const bf16 *>(dy), co, dw, st, nullptr));
+}
+
+int gd_nn_bias_grad(const void *dy, long long npix, int co, float *db, void *stream) {
+  if (!dy || !db || npix < 1 || !mult16(co) || co > 256) return GD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return finish(st, launch_bias_grad(static_cast<const bf16 *>(dy), npix, co, db, st, nullptr));
+}
+
+int gd_nn_flip_weights(const float *w, int co, int ci, void *w16, void *wf16, void *stream) {
+  if (!w || co < 1 || ci < 1 || (!w16 && !wf16)) return GD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long n = (long long)co * 9 * ci;
+  k_wexport<<<grid_1d(n, 256), 256, 0, st>>>(w, co, ci, static_cast<bf16 *>(w16), static_cast<bf16 *>(wf16));
+  return finish(st, cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA);
+}
+
+int gd_nn_pool2(const void *x, int ntiles, int h, int w, int c, void *y, void *stream) {
+  if (!x || !y || ntiles < 1 || h < 2 || w < 2 || h % 2 || w % 2 || c < 8 || c % 8) return GD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long nout = (long long)ntiles * (h / 2) * (w / 2);
+  k_pool2<<<grid_1d(nout * (c / 8), 256), 256, 0, st>>>(static_cast<const bf16 *>(x), static_cast<bf16 *>(y), nout,
+                                                        h / 2, w / 2, c);
+  return finish(st, cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA);
+}
+
+int gd_nn_pool2_backward(const void *dp, const void *skip, int skip_stride, int skip_off, const void *mask,
+                         int ntiles, int h, int w, int c, void *out, void *stream) {
+  if (!dp || !mask || !out || ntiles < 1 || h < 2 || w < 2 || h % 2 || w % 2 || c < 8 || c % 8)
+    return GD_ERR_INVALID_ARG;
+  if (skip && (skip_off < 0 || skip_off % 8 || skip_stride % 8 || skip_off + c > skip_stride))
+    return GD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long n = (long long)ntiles * h * w;
+  k_pool2_bwd<<<grid_1d(n * (c / 8), 256), 256, 0, st>>>(static_cast<const bf16 *>(dp), static_cast<const bf16 *>(skip),
+                                                        skip_stride, skip_off, static_cast<const bf16 *>(mask),
+                                                        static_cast<bf16 *>(out), n, h, w, c);
+  return finish(st, cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA);
+}
+
+int gd_nn_up2_backward(const void *dk, int ck, int c, const void *mask, int ntiles, int h, int w, void *out,
+                       void *stream) {
+  if (!dk || !mask || !out || ntiles < 1 || h < 1 || w < 1 || c < 8 || c % 8 || ck % 8 || c > ck)
+    return GD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long n = (long long)ntiles * h * w;
+  k_up2_bwd<<<grid_1d(n * (c / 8), 256), 256, 0, st>>>(static_cast<const bf16 *>(dk), ck, static_cast<const bf16 *>(mask),
+                                                      static_cast<bf16 *>(out), n, h, w, c);
+  return finish(st, cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA);
+}
+
+int gd_nn_adam(float *p, const float *g, float *m, float *v, long long n, double lr, double b1, double b2, double eps,
+               int t, void *stream) {
+  if (!p || !g || !m || !v || n < 1 || t < 1 || !(lr >= 0) || !(b1 >= 0 && b1 < 1) || !(b2 >= 0 && b2 < 1) || !(eps > 0))
+    return GD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double c1 = 1.0 / (1.0 - std::pow(b1, t)), c2 = 1.0 / (1.0 - std::pow(b2, t));
+  k_adam<<<grid_1d(n, 256), 256, 0, st>>>(p, g, m, v, n, (float)lr, (float)b1, (float)b2, (float)eps, (float)c1,
+                                          (float)c2);
+  return finish(st, cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA);
+}
+
+int gd_learn_stack_tiles(const float *I, const float *I_sub, int nx, int ny, int nz, int th, int tw, int tc,
+                         long long tile0, long long ntiles, double shift, double scale, void *x, float *xf,
+                         void *stream) {
+  if (!I || nx < 1 || ny < 1 || nz < 1 || th < 1 || tw < 1 || tc < 8 || tc % 8 || nx % tw || ny % th || nz % tc)
+    return GD_ERR_INVALID_ARG;
+  if (I_sub ? !xf : !x) return GD_ERR_INVALID_ARG;
+  const long long tiles = (long long)(nx / tw) * (ny / th) * (nz / tc);
+  if (tile0 < 0 || ntiles < 1 || tile0 + ntiles > tiles) return GD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const long long npix = ntiles * th * tw;
+  k_stack_tiles<<<grid_1d(npix * (tc / 8), 256), 256, 0, st>>>(I, I_sub, nx, ny, th, tw, tc, nx / tw, ny / th, tile0,
+                                                              npix, (float)shift, (float)scale,
+                                                              static_cast<bf16 *>(x), xf);
+  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA;
+}
+
+int gd_learn_create(gd_learn **out, int c_in, int c_out, const int *widths, int tile_h, int tile_w, int max_batch,
+                    unsigned long long seed, void *stream) {
+  if (!out) return GD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mult16(c_in) || !mult16(c_out) || c_out > 256 || tile_h < 8 || tile_w < 8 || tile_h % 8 || tile_w % 8 ||
+      max_batch < 1)
+    return GD_ERR_INVALID_ARG;
+  gd_learn *L = new (std::nothrow) gd_learn();
+  if (!L) return GD_ERR_OOM;
+  if (widths)
+    for (int i = 0; i < 4; ++i) L->c[i] = widths[i];
+  for (int i = 0; i < 4; ++i)
+    if (!mult16(L->c[i]) || L->c[i] > 128) {
+      delete L;
+      return GD_ERR_INVALID_ARG;
+    }
+  if (L->c[3] + L->c[2] > 256) {
+    delete L;
+    return GD_ERR_INVALID_ARG;
+  }
+  L->cin = c_in;
+  L->cout = c_out;
+  L->H = tile_h;
+  L->W = tile_w;
+  L->maxb = max_batch;
+  L->st = static_cast<cudaStream_t>(stream);
+  const int *c = L->c;
+  const int shapes[8][2] = {{c_in, c[0]}, {c[0], c[1]}, {c[1], c[2]}, {c[2], c[3]},
+                            {c[3] + c[2], c[2]}, {c[2] + c[1], c[1]}, {c[1] + c[0], c[0]}, {c[0], c_out}};
+  long long off = 0;
+  for (int l = 0; l < 8; ++l) {
+    L->L[l].ci = shapes[l][0];
+    L->L[l].co = shapes[l][1];
+    L->L[l].w = off;
+    off += (long long)shapes[l][1] * 9 * shapes[l][0];
+    L->L[l].b = off;
+    off += shapes[l][1];
+  }
+  L->np = off;
+  const long long B = max_batch, n1 = B * tile_h * tile_w, n2 = n1 / 4, n4 = n1 / 16, n8 = n1 / 64;
+  int st = GD_OK;
+  auto A = [&](auto **p, long long n) {
+    if (st == GD_OK) st = lalloc(L, p, n);
+  };
+  A(&L->P, L->np);
+  A(&L->G, L->np);
+  A(&L->M, L->np);
+  A(&L->V, L->np);
+  A(&L->W16, L->np);
+  A(&L->WF16, L->np);
+  A(&L->x, n1 * c_in);
+  A(&L->e1, n1 * c[0]);
+  A(&L->p1, n2 * c[0]);
+  A(&L->e2, n2 * c[1]);
+  A(&L->p2, n4 * c[1]);
+  A(&L->e3, n4 * c[2]);
+  A(&L->p3, n8 * c[2]);
+  A(&L->e4, n8 * c[3]);
+  A(&L->d3, n4 * c[2]);
+  A(&L->d2, n2 * c[1]);
+  A(&L->d1, n1 * c[0]);
+  A(&L->y, n1 * c_out);
+  A(&L->tgt, n1 * c_out);
+  A(&L->dy, n1 * c_out);
+  A(&L->gb1, n1 * c[0]);
+  A(&L->dk1, n1 * (c[1] + c[0]));
+  A(&L->gb2, n2 * c[1]);
+  A(&L->dk2, n2 * (c[2] + c[1]));
+  A(&L->gb3, n4 * c[2]);
+  A(&L->dk3, n4 * (c[3] + c[2]));
+  A(&L->ga4, n8 * c[3]);
+  A(&L->dp3, n8 * c[2]);
+  A(&L->ga3, n4 * c[2]);
+  A(&L->dp2, n4 * c[1]);
+  A(&L->ga2, n2 * c[1]);
+  A(&L->dp1, n2 * c[0]);
+  A(&L->ga1, n1 * c[0]);
+  A(&L->acc, 1);
+  if (st != GD_OK) {
+    gd_learn_destroy(L);
+    return st;
+  }
+  // He-normal initialisation on the host, zero biases
+  std::vector<float> h(L->np, 0.f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l < 8; ++l) {
+    std::normal_distribution<double> nd(0.0, std::sqrt(2.0 / (9.0 * L->L[l].ci)));
+    const long long n = (long long)L->L[l].co * 9 * L->L[l].ci;
+    for (long long i = 0; i < n; ++i) h[L->L[l].w + i] = (float)nd(rng);
+  }
+  st = gd_learn_set_params(L, h.data());
+  if (st != GD_OK) {
+    gd_learn_destroy(L);
+    return st;
+  }
+  *out = L;
+  return GD_OK;
+}
+
+int gd_learn_destroy(gd_learn *L) {
+  if (!L) return GD_OK;
+  cudaStreamSynchronize(L->st);
+  for (void *p : L->allocs) cudaFree(p);
+  delete L;
+  return GD_OK;
+}
+
+long long gd_learn_param_count(const gd_learn *L) { return L ? L->np : -1; }
+
+int gd_learn_set_params(gd_learn *L, const float *host) {
+  if (!L || !host) return GD_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(L->P, host, L->np * sizeof(float), cudaMemcpyHostToDevice, L->st) != cudaSuccess ||
+      cudaMemsetAsync(L->M, 0, L->np * sizeof(float), L->st) != cudaSuccess ||
+      cudaMemsetAsync(L->V, 0, L->np * sizeof(float), L->st) != cudaSuccess) {
+    cudaGetLastError();
+    return GD_ERR_CUDA;
+  }
+  L->adam_t = 0;
+  LTRY(export_weights(L));
+  return finish(L->st, GD_OK);
+}
+
+int gd_learn_get_params(gd_learn *L, float *host) {
+  if (!L || !host) return GD_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(host, L->P, L->np * sizeof(float), cudaMemcpyDeviceToHost, L->st) != cudaSuccess) return GD_ERR_CUDA;
+  return finish(L->st, GD_OK);
+}
+
+int gd_learn_get_grads(gd_learn *L, float *host) {
+  if (!L || !host) return GD_ERR_INVALID_ARG;
+  if (cudaMemcpyAsync(host, L->G, L->np * sizeof(float), cudaMemcpyDeviceToHost, L->st) != cudaSuccess) return GD_ERR_CUDA;
+  return finish(L->st, GD_OK);
+}
+
+int gd_learn_forward(gd_learn *L, const void *x, int batch, float *yf) {
+  if (!L || !x || !yf || batch < 1 || batch > L->maxb) return GD_ERR_INVALID_ARG;
+  const size_t xb = (size_t)batch * L->H * L->W * L->cin * sizeof(bf16);
+  if (cudaMemcpyAsync(L->x, x, xb, cudaMemcpyDeviceToDevice, L->st) != cudaSuccess) return GD_ERR_CUDA;
+  LTRY(net_forward(L, batch, yf, nullptr));
+  return finish(L->st, GD_OK);
+}
+
+int gd_learn_train_step(gd_learn *L, const void *x_pool, const float *t_pool, const int *idx_host, int batch,
+                        double lr, double *loss) {
+  if (!L || !x_pool || !t_pool || batch < 1 || batch > L->maxb || !(lr >= 0)) {
+    if (L) L->err = "invalid arguments";
+    return GD_ERR_INVALID_ARG;
+  }
+  const size_t xt = (size_t)L->H * L->W * L->cin * sizeof(bf16);
+  const size_t tt = (size_t)L->H * L->W * L->cout * sizeof(float);
+  const char *xp = static_cast<const char *>(x_pool);
+  const char *tp = reinterpret_cast<const char *>(t_pool);
+  for (int b = 0; b < batch; ++b) {
+    const long long i = idx_host ? idx_host[b] : b;
+    if (i < 0) return GD_ERR_INVALID_ARG;
+    if (cudaMemcpyAsync(reinterpret_cast<char *>(L->x) + b * xt, xp + i * xt, xt, cudaMemcpyDeviceToDevice, L->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(reinterpret_cast<char *>(L->tgt) + b * tt, tp + i * tt, tt, cudaMemcpyDeviceToDevice, L->st) !=
+            cudaSuccess)
+      return GD_ERR_CUDA;
+  }
+  LTRY(net_forward(L, batch, L->y, nullptr));
+  const long long n = (long long)batch * L->H * L->W * L->cout;
+  if (cudaMemsetAsync(L->acc, 0, sizeof(double), L->st) != cudaSuccess) return GD_ERR_CUDA;
+  k_mse<<<grid_1d(n, 256, 4), 256, 0, L->st>>>(L->y, L->tgt, n, (float)(2.0 / (double)n), L->dy, L->acc);
+  ++L->launches;
+  LTRY(net_backward(L, batch));
+  ++L->adam_t;
+  const double b1 = 0.9, b2 = 0.999;
+  const double c1 = 1.0 / (1.0 - std::pow(b1, L->adam_t)), c2 = 1.0 / (1.0 - std::pow(b2, L->adam_t));
+  k_adam<<<grid_1d(L->np, 256), 256, 0, L->st>>>(L->P, L->G, L->M, L->V, L->np, (float)lr, (float)b1, (float)b2, 1e-8f,
+                                                  (float)c1, (float)c2);
+  ++L->launches;
+  LTRY(export_weights(L));
+  double h = 0.0;
+  if (cudaMemcpyAsync(&h, L->acc, sizeof(double), cudaMemcpyDeviceToHost, L->st) != cudaSuccess) return GD_ERR_CUDA;
+  const int st = finish(L->st, GD_OK);
+  if (st != GD_OK) return st;
+  if (loss) *loss = h / (double)n;
+  return std::isfinite(h) ? GD_OK : GD_ERR_DIVERGED;
+}
+
+int gd_learn_predict_stack(gd_learn *L, const float *I0, int nx, int ny, int nz, double in_shift, double in_scale,
+                           double out_scale, float *x0) {
+  if (!L || !I0 || !x0 || I0 == x0 || L->cin != L->cout || nx % L->W || ny % L->H || nz % L->cin || nx < 1 ||
+      ny < 1 || nz < 1)
+    return GD_ERR_INVALID_ARG;
+  const long long tx = nx / L->W, ty = ny / L->H, tz = nz / L->cin, T = tx * ty * tz;
+  FwdArgs so;
+  std::memset(&so, 0, sizeof so);
+  so.base = I0;
+  so.out = x0;
+  so.snx = nx;
+  so.sny = ny;
+  so.tiles_x = (int)tx;
+  so.tiles_y = (int)ty;
+  so.out_scale = (float)out_scale;
+  for (long long t0 = 0; t0 < T; t0 += L->maxb) {
+    const int B = (int)std::min<long long>(L->maxb, T - t0);
+    LTRY(gd_learn_stack_tiles(I0, nullptr, nx, ny, nz, L->H, L->W, L->cin, t0, B, in_shift, in_scale, L->x, nullptr,
+                              L->st));
+    ++L->launches;
+    so.tile0 = t0;
+    LTRY(net_forward(L, B, nullptr, &so));
+  }
+  return finish(L->st, GD_OK);
+}
+
+long long gd_learn_launch_count(const gd_learn *L) { return L ? L->launches : -1; }
+const char *gd_learn_last_error(const gd_learn *L) {
+  if (L && !L->err.empty()) return L->err.c_str();
+  std::lock_guard<std::mutex> lock(g_nn_err_mu);
+  return g_nn_err.c_str();
+}
+
+}  // extern "C"

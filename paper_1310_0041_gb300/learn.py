@@ -1,0 +1,198 @@
+"""Python binding of the learned initial guess (``include/gd_learn.h``).
+
+ctypes marshalling only, with the C names: every convolution, gradient,
+optimiser step and tile transform runs in libgd's CUDA kernels.  Activations
+are bfloat16 CUDA tensors, channels last ``(tiles, h, w, c)``; parameters and
+gradients float32.  There is no CPU fallback: without libgd.so every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import GD_OK, GdError, _default_stream, lib
+
+LAYERS = ("e1", "e2", "e3", "e4", "d3", "d2", "d1", "y")
+
+
+def _p(t):
+    """Device pointer of a contiguous CUDA tensor (None passes through)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _s(stream):
+    if stream is None:
+        stream = _default_stream()
+    return ctypes.c_void_p(stream) if stream else None
+
+
+def last_error(net=None) -> str:
+    return (lib().gd_learn_last_error(net.handle if net is not None else None) or b"").decode()
+
+
+def _ok(st, what):
+    if st != GD_OK:
+        raise GdError(st, "%s: %s" % (what, last_error()))
+    return st
+
+
+# ---------------------------------------------------------------------------
+# layer-level calls
+# ---------------------------------------------------------------------------
+def gd_nn_conv3x3(xa, ca, up_a, xb, cb, ntiles, h, w, wt, bias, co, relu, mask=None, y=None,
+                  yf=None, stream=None) -> int:
+    return lib().gd_nn_conv3x3(_p(xa), ca, up_a, _p(xb), cb, ntiles, h, w, _p(wt), _p(bias), co,
+                               int(relu), _p(mask), _p(y), _p(yf), _s(stream))
+
+
+def gd_nn_conv3x3_wgrad(xa, ca, up_a, xb, cb, ntiles, h, w, dy, co, dw, stream=None) -> int:
+    return lib().gd_nn_conv3x3_wgrad(_p(xa), ca, up_a, _p(xb), cb, ntiles, h, w, _p(dy), co,
+                                     _p(dw), _s(stream))
+
+
+def gd_nn_bias_grad(dy, npix, co, db, stream=None) -> int:
+    return lib().gd_nn_bias_grad(_p(dy), npix, co, _p(db), _s(stream))
+
+
+def gd_nn_flip_weights(w, co, ci, w16=None, wf16=None, stream=None) -> int:
+    return lib().gd_nn_flip_weights(_p(w), co, ci, _p(w16), _p(wf16), _s(stream))
+
+
+def gd_nn_pool2(x, ntiles, h, w, c, y, stream=None) -> int:
+    return lib().gd_nn_pool2(_p(x), ntiles, h, w, c, _p(y), _s(stream))
+
+
+def gd_nn_pool2_backward(dp, skip, skip_stride, skip_off, mask, ntiles, h, w, c, out,
+                         stream=None) -> int:
+    return lib().gd_nn_pool2_backward(_p(dp), _p(skip), skip_stride, skip_off, _p(mask), ntiles,
+                                      h, w, c, _p(out), _s(stream))
+
+
+def gd_nn_up2_backward(dk, ck, c, mask, ntiles, h, w, out, stream=None) -> int:
+    return lib().gd_nn_up2_backward(_p(dk), ck, c, _p(mask), ntiles, h, w, _p(out), _s(stream))
+
+
+def gd_nn_adam(p, g, m, v, lr, b1, b2, eps, t, stream=None) -> int:
+    return lib().gd_nn_adam(_p(p), _p(g), _p(m), _p(v), p.numel(), lr, b1, b2, eps, t, _s(stream))
+
+
+def gd_learn_stack_tiles(I, I_sub, nx, ny, nz, th, tw, tc, tile0, ntiles, shift, scale, x=None,
+                         xf=None, stream=None) -> int:
+    return lib().gd_learn_stack_tiles(_p(I), _p(I_sub), nx, ny, nz, th, tw, tc, tile0, ntiles,
+                                      shift, scale, _p(x), _p(xf), _s(stream))
+
+
+# ---------------------------------------------------------------------------
+# the network
+# ---------------------------------------------------------------------------
+class Net:
+    """Handle of a gd_learn network."""
+
+    def __init__(self, handle, c_in, c_out, widths, tile_h, tile_w, max_batch):
+        self.handle = handle
+        self.c_in, self.c_out, self.widths = c_in, c_out, tuple(widths)
+        self.tile_h, self.tile_w, self.max_batch = tile_h, tile_w, max_batch
+
+    def shapes(self):
+        """(co, ci) of every layer, in the flat parameter order."""
+        c1, c2, c3, c4 = self.widths
+        return [(c1, self.c_in), (c2, c1), (c3, c2), (c4, c3), (c3, c4 + c3), (c2, c3 + c2),
+                (c1, c2 + c1), (self.c_out, c1)]
+
+
+def gd_learn_create(c_in=16, c_out=16, widths=(16, 32, 64, 128), tile_h=256, tile_w=256,
+                    max_batch=32, seed=0, stream=None) -> Net:
+    h = ctypes.c_void_p()
+    W = (ctypes.c_int * 4)(*widths)
+    _ok(lib().gd_learn_create(ctypes.byref(h), c_in, c_out, W, tile_h, tile_w, max_batch, seed,
+                              _s(stream)), "gd_learn_create")
+    return Net(h, c_in, c_out, widths, tile_h, tile_w, max_batch)
+
+
+def gd_learn_destroy(net: Net) -> int:
+    st = lib().gd_learn_destroy(net.handle)
+    net.handle = None
+    return st
+
+
+def gd_learn_param_count(net: Net) -> int:
+    return int(lib().gd_learn_param_count(net.handle))
+
+
+def gd_learn_set_params(net: Net, flat: np.ndarray) -> int:
+    flat = np.ascontiguousarray(flat, dtype=np.float32)
+    assert flat.size == gd_learn_param_count(net)
+    return _ok(lib().gd_learn_set_params(net.handle, ctypes.c_void_p(flat.ctypes.data)),
+               "gd_learn_set_params")
+
+
+def gd_learn_get_params(net: Net) -> np.ndarray:
+    out = np.empty(gd_learn_param_count(net), np.float32)
+    _ok(lib().gd_learn_get_params(net.handle, ctypes.c_void_p(out.ctypes.data)), "gd_learn_get_params")
+    return out
+
+
+def gd_learn_get_grads(net: Net) -> np.ndarray:
+    out = np.empty(gd_learn_param_count(net), np.float32)
+    _ok(lib().gd_learn_get_grads(net.handle, ctypes.c_void_p(out.ctypes.data)), "gd_learn_get_grads")
+    return out
+
+
+def gd_learn_forward(net: Net, x, batch, yf) -> int:
+    return _ok(lib().gd_learn_forward(net.handle, _p(x), batch, _p(yf)), "gd_learn_forward")
+
+
+def gd_learn_train_step(net: Net, x_pool, t_pool, idx=None, batch=None, lr=1e-3) -> float:
+    """One training step; returns the loss before it."""
+    if idx is not None:
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        batch = idx.size
+        ip = idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    else:
+        ip = None
+    loss = ctypes.c_double(0.0)
+    st = lib().gd_learn_train_step(net.handle, _p(x_pool), _p(t_pool), ip, int(batch), float(lr),
+                                   ctypes.byref(loss))
+    if st != GD_OK:
+        raise GdError(st, (lib().gd_learn_last_error(net.handle) or b"").decode())
+    return loss.value
+
+
+def gd_learn_predict_stack(net: Net, I0, nx, ny, nz, in_shift, in_scale, out_scale, x0) -> int:
+    return _ok(lib().gd_learn_predict_stack(net.handle, _p(I0), nx, ny, nz, in_shift, in_scale,
+                                            out_scale, _p(x0)), "gd_learn_predict_stack")
+
+
+def gd_learn_launch_count(net: Net) -> int:
+    return int(lib().gd_learn_launch_count(net.handle))
+
+
+# ---------------------------------------------------------------------------
+# parameter layout conversions (the oracle's dict <-> the flat array)
+# ---------------------------------------------------------------------------
+def params_to_flat(net: Net, p: dict) -> np.ndarray:
+    """{name.w: [co][ci][3][3], name.b: [co]} -> flat [co][9][ci] + bias per layer."""
+    parts = []
+    for name in LAYERS:
+        w = np.asarray(p[name + ".w"])
+        co, ci = w.shape[:2]
+        parts.append(w.reshape(co, ci, 9).transpose(0, 2, 1).reshape(-1))
+        parts.append(np.asarray(p[name + ".b"]).reshape(-1))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def flat_to_params(net: Net, flat: np.ndarray) -> dict:
+    out, o = {}, 0
+    for name, (co, ci) in zip(LAYERS, net.shapes()):
+        n = co * 9 * ci
+        out[name + ".w"] = flat[o:o + n].reshape(co, 9, ci).transpose(0, 2, 1).reshape(co, ci, 3, 3)
+        o += n
+        out[name + ".b"] = flat[o:o + co]
+        o += co
+    return out

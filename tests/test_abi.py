@@ -11,8 +11,8 @@ import paper_1310_0041_gb300 as gd
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "gd.h")).read()
+def declared_functions(header="gd.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_ ]+\*?\s*\b(gd_[a-z0-9_]+)\s*\(", src, flags=re.M)))
 
@@ -31,8 +31,12 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol(lib):
-    for name in declared_functions():
+    for name in declared_functions() + declared_functions("gd_learn.h"):
         assert hasattr(lib, name), name
+
+
+def test_learn_header_declares_the_network_calls():
+    assert set(declared_functions("gd_learn.h")) == set(gd.EXPORTS_LEARN)
 
 
 def test_status_strings_and_version(lib):
