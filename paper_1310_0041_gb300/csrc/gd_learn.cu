@@ -47,7 +47,6 @@ __device__ int g_nn_timeout;  // set to 1 when a bounded wait gave up
 
 constexpr int CT = 128;                // threads of a conv CTA (4 warps: 128 TMEM lanes)
 constexpr int KS = 64;                 // K elements per pipeline stage (4 MMAs of K = 16)
-constexpr int NST = 3;                 // forward: stages in flight
 constexpr int NSTW = 2;                // weight gradient: stages in flight
 constexpr int A_BYTES = 128 * KS * 2;  // one A stage (128 rows x 64 bf16)
 
@@ -106,23 +105,55 @@ struct FwdArgs {
   int snx, sny, tiles_x, tiles_y;
   long long tile0;
   float out_scale;
+  // launch geometry (filled in by launch_conv)
+  int ntiles;      // tiles in the batch
+  int nm;          // 128-row M sub-tiles per block
+  int nq;          // staged positions per block: nm * 128 + 2 P + 2
+  int nqp;         // their pitch in shared memory, in positions
+  int w_resident;  // every weight slab stays in shared memory
   int nblocks;
 };
 
+constexpr int NSB = 3;  // slab stages in flight
+
+// Shared-memory carve-up of k_conv_fwd (byte offsets; the same on host and device)
+struct FwdSmem {
+  int a_slot, b_slot, a0, b0, w0, tab0, total;
+};
+__host__ __device__ inline FwdSmem fwd_smem(int co, int ci, int nq, int nqp, int w_resident) {
+  FwdSmem m;
+  m.a_slot = 2 * nqp * 16;                    // one 16-channel slab of the staged positions
+  m.b_slot = w_resident ? 0 : 18 * co * 16;   // one slab of weights (9 taps x 16 channels)
+  m.a0 = 0;
+  m.b0 = m.a0 + NSB * m.a_slot;
+  m.w0 = m.b0 + NSB * m.b_slot;               // resident weights: ci / 16 slabs
+  m.tab0 = m.w0 + (w_resident ? (ci / 16) * 18 * co * 16 : 0);
+  m.total = m.tab0 + ((nq * 4 + 15) / 16) * 16;
+  return m;
+}
+
+// Forward 3x3 convolution as an implicit GEMM over the padded raster.  Every
+// tile is laid out with a one-pixel zero border, pitch P = W + 2, so that
+// tap (dy, dx) of the output anchored at raster position m reads position
+// m + dy P + dx: a fixed shift.  A block of nm x 128 anchors stages the
+// nm * 128 + 2P + 2 positions it needs, 16 channels (one slab) at a time, in
+// K-major core-matrix form (position-contiguous 16-byte rows, LBO = one
+// 8-channel chunk), and each tap's A operand is that slab seen through a
+// descriptor whose start address is shifted by (dy P + dx) rows.
 __global__ void __launch_bounds__(CT) k_conv_fwd(FwdArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_slot[NST];
+  __shared__ __align__(8) uint64_t bar_slot[NSB];
   __shared__ __align__(8) uint64_t bar_acc, bar_fin;
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int co = a.co, ci = a.ci, K = 9 * ci;
-  const int ksteps = K / 16, nstages = (ksteps + 3) / 4;
-  const int stage_bytes = A_BYTES + co * KS * 2;
+  const int co = a.co, ci = a.ci, nslab = ci / 16, nm = a.nm;
+  const int H = a.s.H, W = a.s.W, P = W + 2, TP = (H + 2) * P;
+  const FwdSmem L = fwd_smem(co, ci, a.nq, a.nqp, a.w_resident);
   uint32_t ncols = 32;
-  while ((int)ncols < co) ncols <<= 1;
+  while ((int)ncols < nm * co) ncols <<= 1;
   if (tid == 0) {
-    for (int i = 0; i < NST; ++i) gdtc::mbar_init(&bar_slot[i], 1);
+    for (int i = 0; i < NSB; ++i) gdtc::mbar_init(&bar_slot[i], 1);
     gdtc::mbar_init(&bar_acc, 1);
     gdtc::mbar_init(&bar_fin, 1);
     gdtc::fence_mbar_init();
@@ -134,146 +165,173 @@ __global__ void __launch_bounds__(CT) k_conv_fwd(FwdArgs a) {
   gdtc::fence_after();
   const uint32_t tmem = s_tmem;
   const uint32_t sbase = gdtc::saddr(smem);
+  int *const tab = reinterpret_cast<int *>(smem + L.tab0);
   const uint32_t idesc = gdtc::idesc_bf16(128, co);
-  const int HW = a.s.H * a.s.W;
   const int nmine = a.nblocks > (int)blockIdx.x ? (a.nblocks - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const long long total = (long long)nmine * nstages;
+  const long long total = (long long)nmine * nslab;
+  const int sh = a.s.upa == 2 ? 1 : 0;
+  const int Wa = W >> sh;
+
+  // resident weights: every slab, once per CTA
+  if (a.w_resident) {
+    for (int e = tid; e < nslab * 18 * co; e += CT) {
+      const int n = e % co, r = e / co;  // r = slab * 18 + tap * 2 + chunk
+      const int sl = r / 18, J = r - sl * 18;
+      gdtc::cp_async16(sbase + (uint32_t)(L.w0 + r * co * 16 + n * 16),
+                       a.w + (long long)n * 9 * ci + (J >> 1) * ci + sl * 16 + (J & 1) * 8, 16u);
+    }
+    gdtc::cp_async_commit();
+  }
 
   auto load = [&](long long g) {
-    const int blk = (int)blockIdx.x + (int)(g / nstages) * (int)gridDim.x;
-    const int s = (int)(g % nstages);
-    const uint32_t sa = sbase + (uint32_t)((g % NST) * stage_bytes);
-    const uint32_t sb = sa + A_BYTES;
-    const long long p = (long long)blk * 128 + tid;
-    const bool prow = p < a.s.npix;
-    int t = 0, h = 0, w = 0;
-    if (prow) {
-      t = (int)(p / HW);
-      const int r = (int)(p - (long long)t * HW);
-      h = r / a.s.W;
-      w = r - h * a.s.W;
-    }
-    const uint32_t arow = sa + (uint32_t)((tid >> 3) * 1024 + (tid & 7) * 16);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int k0 = s * KS + 8 * j;
-      if (k0 < K) {
-        const int tap = k0 / ci, c = k0 - tap * ci;
-        bool ok;
-        const bf16 *src = src_chunk(a.s, t, h + tap / 3 - 1, w + tap % 3 - 1, c, ok);
-        gdtc::cp_async16(arow + j * 128, src, (ok && prow) ? 16u : 0u);
+    const int blk = (int)blockIdx.x + (int)(g / nslab) * (int)gridDim.x;
+    const int sl = (int)(g % nslab);
+    const uint32_t as = sbase + (uint32_t)(L.a0 + (int)(g % NSB) * L.a_slot);
+    const long long m0 = (long long)blk * nm * 128;
+    if (sl == 0) {
+      // this thread's staged positions: packed (tile row << 10 | column), -1 on the border
+      for (int i = tid; i < a.nq; i += CT) {
+        const long long q = m0 + i;
+        const long long t = q / TP;
+        const int rem = (int)(q - t * TP);
+        const int R = rem / P, C = rem - R * P;
+        tab[i] = (t < a.ntiles && R >= 1 && R <= H && C >= 1 && C <= W)
+                     ? (int)(((t * H + R - 1) << 10) | (C - 1))
+                     : -1;
       }
     }
-    for (int e = tid; e < co * 8; e += CT) {
-      const int n = e % co, j = e / co;
-      const int k0 = s * KS + 8 * j;
-      if (k0 < K)
-        gdtc::cp_async16(sb + (uint32_t)((n >> 3) * 1024 + j * 128 + (n & 7) * 16),
-                         a.w + (long long)n * K + k0, 16u);
+    const int c0 = sl * 16;
+    const bool from_a = c0 < a.s.ca;
+    for (int i = tid; i < a.nq; i += CT) {
+      const int pk = tab[i];
+      const bf16 *src = a.s.xa;
+      uint32_t bytes = 0;
+      if (pk >= 0) {
+        const int rowg = pk >> 10, c = pk & 1023;
+        src = from_a ? a.s.xa + ((long long)(rowg >> sh) * Wa + (c >> sh)) * a.s.ca + c0
+                     : a.s.xb + ((long long)rowg * W + c) * a.s.cb + (c0 - a.s.ca);
+        bytes = 16u;
+      }
+      gdtc::cp_async16(as + (uint32_t)(i * 16), src, bytes);
+      gdtc::cp_async16(as + (uint32_t)((a.nqp + i) * 16), src + 8, bytes);
+    }
+    if (!a.w_resident) {
+      const uint32_t bs = sbase + (uint32_t)(L.b0 + (int)(g % NSB) * L.b_slot);
+      for (int e = tid; e < 18 * co; e += CT) {
+        const int n = e % co, J = e / co;
+        gdtc::cp_async16(bs + (uint32_t)(J * co * 16 + n * 16),
+                         a.w + (long long)n * 9 * ci + (J >> 1) * ci + c0 + (J & 1) * 8, 16u);
+      }
     }
   };
 
   auto epilogue = [&](int blk) {
-    const int m = warp * 32 + lane;
-    const long long p = (long long)blk * 128 + m;
-    const bool valid = p < a.s.npix;
-    int t = 0, h = 0, w = 0;
-    if (valid) {
-      t = (int)(p / HW);
-      const int r = (int)(p - (long long)t * HW);
-      h = r / a.s.W;
-      w = r - h * a.s.W;
-    }
-    for (int c0 = 0; c0 < co; c0 += 16) {
-      float v[16];
-      gdtc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (!valid) continue;
-      if (a.bias) {
+    const long long m0 = (long long)blk * nm * 128;
+    for (int u = 0; u < nm; ++u) {
+      const long long o = m0 + u * 128 + warp * 32 + lane + P + 1;  // the anchor's centre
+      const long long t = o / TP;
+      const int rem = (int)(o - t * TP);
+      const int R = rem / P, C = rem - R * P;
+      const bool valid = t < a.ntiles && R >= 1 && R <= H && C >= 1 && C <= W;
+      const int h = R - 1, w = C - 1;
+      const long long p = (t * H + h) * W + w;
+      for (int c0 = 0; c0 < co; c0 += 16) {
+        float v[16];
+        gdtc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(u * co + c0), v);
+        if (!valid) continue;
+        if (a.bias) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + c0 + i);
-      }
-      if (a.relu) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
-      }
-      if (a.mask) {
-        const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + p * co + c0);
-        float mk[8];
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          unpack8(__ldg(mp + half), mk);
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (!(mk[i] > 0.f)) v[8 * half + i] = 0.f;
+          for (int i = 0; i < 16; ++i) v[i] += __ldg(a.bias + c0 + i);
         }
-      }
-      if (a.y) {
-        uint4 *yp = reinterpret_cast<uint4 *>(a.y + p * co + c0);
-        yp[0] = make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
-                           pack_bf2(v[6], v[7]));
-        yp[1] = make_uint4(pack_bf2(v[8], v[9]), pack_bf2(v[10], v[11]), pack_bf2(v[12], v[13]),
-                           pack_bf2(v[14], v[15]));
-      }
-      if (a.yf) {
-        float4 *yp = reinterpret_cast<float4 *>(a.yf + p * co + c0);
+        if (a.relu) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-      }
-      if (a.out) {
-        const long long tg = a.tile0 + t;
-        const int tx = (int)(tg % a.tiles_x);
-        const long long r1 = tg / a.tiles_x;
-        const int ty = (int)(r1 % a.tiles_y);
-        const long long tz = r1 / a.tiles_y;
-        const long long plane = (long long)a.snx * a.sny;
-        const long long o0 = (tz * co + c0) * plane + (long long)(ty * a.s.H + h) * a.snx + tx * a.s.W + w;
+          for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], 0.f);
+        }
+        if (a.mask) {
+          const uint4 *mp = reinterpret_cast<const uint4 *>(a.mask + p * co + c0);
+          float mk[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const long long o = o0 + (long long)i * plane;
-          a.out[o] = __ldg(a.base + o) + a.out_scale * v[i];
+          for (int half = 0; half < 2; ++half) {
+            unpack8(__ldg(mp + half), mk);
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (!(mk[i] > 0.f)) v[8 * half + i] = 0.f;
+          }
+        }
+        if (a.y) {
+          uint4 *yp = reinterpret_cast<uint4 *>(a.y + p * co + c0);
+          yp[0] = make_uint4(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]), pack_bf2(v[4], v[5]),
+                             pack_bf2(v[6], v[7]));
+          yp[1] = make_uint4(pack_bf2(v[8], v[9]), pack_bf2(v[10], v[11]), pack_bf2(v[12], v[13]),
+                             pack_bf2(v[14], v[15]));
+        }
+        if (a.yf) {
+          float4 *yp = reinterpret_cast<float4 *>(a.yf + p * co + c0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) yp[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+        if (a.out) {
+          const long long tg = a.tile0 + t;
+          const int tx = (int)(tg % a.tiles_x);
+          const long long r1 = tg / a.tiles_x;
+          const int ty = (int)(r1 % a.tiles_y);
+          const long long tz = r1 / a.tiles_y;
+          const long long plane = (long long)a.snx * a.sny;
+          const long long o0 = (tz * co + c0) * plane + (long long)(ty * H + h) * a.snx + tx * W + w;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const long long oi = o0 + (long long)i * plane;
+            a.out[oi] = __ldg(a.base + oi) + a.out_scale * v[i];
+          }
         }
       }
     }
   };
 
-  for (int g = 0; g < NST - 1; ++g) {
+  for (int g = 0; g < NSB - 1; ++g) {
     if (g < total) load(g);
     gdtc::cp_async_commit();
   }
   int nblk_done = 0;
   for (long long g = 0; g < total; ++g) {
-    gdtc::cp_async_wait<NST - 2>();
+    gdtc::cp_async_wait<NSB - 2>();
+    if (g == 0 && a.w_resident) gdtc::cp_async_wait<0>();
     gdtc::fence_proxy_async();
     gdtc::fence_before();
     __syncthreads();
     if (s_abort) break;
-    const int s = (int)(g % nstages);
-    const int slot = (int)(g % NST);
+    const int sl = (int)(g % nslab);
+    const int slot = (int)(g % NSB);
     if (tid == 0) {
       gdtc::fence_after();
-      const uint32_t sa = sbase + (uint32_t)(slot * stage_bytes), sb = sa + A_BYTES;
-      const int nq = min(4, ksteps - 4 * s);
-      for (int q = 0; q < nq; ++q)
-        gdtc::mma_bf16(tmem, gdtc::desc(sa + q * 256), gdtc::desc(sb + q * 256), idesc,
-                       (s > 0 || q > 0) ? 1u : 0u);
+      const uint32_t as = sbase + (uint32_t)(L.a0 + slot * L.a_slot);
+      const uint32_t bs = sbase + (uint32_t)(a.w_resident ? L.w0 + sl * 18 * co * 16 : L.b0 + slot * L.b_slot);
+      const uint32_t lbo_a = (uint32_t)a.nqp * 16, lbo_b = (uint32_t)co * 16;
+      for (int u = 0; u < nm; ++u)
+        for (int tap = 0; tap < 9; ++tap) {
+          const uint32_t ashift = (uint32_t)((u * 128 + (tap / 3) * P + tap % 3) * 16);
+          gdtc::mma_bf16(tmem + (uint32_t)(u * co), gdtc::desc(as + ashift, lbo_a, 128),
+                         gdtc::desc(bs + (uint32_t)(tap * 2 * co * 16), lbo_b, 128), idesc,
+                         (sl > 0 || tap > 0) ? 1u : 0u);
+        }
       gdtc::mma_commit(&bar_slot[slot]);
-      if (s == nstages - 1) gdtc::mma_commit(&bar_acc);
+      if (sl == nslab - 1) gdtc::mma_commit(&bar_acc);
     }
-    const long long gn = g + NST - 1;
+    const long long gn = g + NSB - 1;
     if (gn < total) {
       if (g >= 1) {
         const long long gp = g - 1;  // the stage whose slot gn reuses
-        if (!gdtc::mbar_wait(&bar_slot[gp % NST], (uint32_t)((gp / NST) & 1))) s_abort = 1;
+        if (!gdtc::mbar_wait(&bar_slot[gp % NSB], (uint32_t)((gp / NSB) & 1))) s_abort = 1;
       }
       load(gn);
     }
     gdtc::cp_async_commit();
-    if (s == nstages - 1) {
+    if (sl == nslab - 1) {
       bool ok = gdtc::mbar_wait(&bar_acc, (uint32_t)(nblk_done & 1));
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) s_abort = 1;
       gdtc::fence_after();
-      if (ok) epilogue((int)blockIdx.x + (int)(g / nstages) * (int)gridDim.x);
+      if (ok) epilogue((int)blockIdx.x + (int)(g / nslab) * (int)gridDim.x);
       ++nblk_done;
     }
   }
@@ -651,55 +709,32 @@ int grid_1d(long long n, int threads, int cap_per_sm = 8) {
 
 bool mult16(int c) { return c > 0 && c % 16 == 0; }
 
-// Dynamic shared memory for a tcgen05 kernel: at least `need` bytes, raised
-// until the CTAs that fit on one SM together hold at most the SM's 512 TMEM
-// columns (an allocation beyond that would wait for another CTA to exit).
-struct SmemKey {
-  const void *k;
-  int need, ncols, dev, smem, per_sm;
-};
-
-template <typename Kern>
-int tmem_safe_smem(Kern k, int need, int ncols, int *per_sm) {
+// CTAs of a tcgen05 kernel that fit on one SM with `smem` bytes of dynamic
+// shared memory, never more than the SM's 512 TMEM columns allow (a further
+// allocation would wait for another CTA to exit).  Also raises the kernel's
+// dynamic shared-memory limit; -1 when `smem` is beyond the per-block limit.
+int conv_occupancy(const void *k, int smem, int ncols) {
   static std::mutex mu;
-  static std::vector<SmemKey> cache;
   std::lock_guard<std::mutex> lock(mu);
-  int dev = 0;
-  cudaGetDevice(&dev);
-  for (const SmemKey &e : cache)
-    if (e.k == (const void *)k && e.need == need && e.ncols == ncols && e.dev == dev) {
-      *per_sm = e.per_sm;
-      return e.smem;
-    }
-  // the largest dynamic size this kernel may ask for: the per-block opt-in
-  // limit less its static shared memory (barriers)
-  int optin = 0;
+  int dev = 0, optin = 0, per_sm_smem = 0;
   cudaFuncAttributes fa;
-  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
       cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
   const int cap = optin - (int)fa.sharedSizeBytes;
-  if (need > cap || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
+  if (smem > cap || cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
     cudaGetLastError();
     return -1;
   }
-  int smem = need;
-  for (;;) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, CT, smem) != cudaSuccess) {
-      cudaGetLastError();
-      return -1;
-    }
-    if (occ >= 1 && occ * ncols <= 512) {
-      *per_sm = occ;
-      cache.push_back(SmemKey{(const void *)k, need, ncols, dev, smem, occ});
-      return smem;
-    }
-    if (occ < 1 || smem >= cap) return -1;
-    smem = std::min(cap, smem + 8192);
-  }
+  const int by_smem = per_sm_smem / (smem + (int)fa.sharedSizeBytes + 1024);  // 1 KB reserved per CTA
+  const int by_regs = 65536 / (std::max(fa.numRegs, 1) * CT);
+  const int by_threads = 2048 / CT;
+  const int by_tmem = 512 / ncols;
+  return std::max(1, std::min(std::min(by_smem, by_regs), std::min(by_threads, by_tmem)));
 }
 
 std::mutex g_nn_err_mu;
@@ -740,14 +775,33 @@ int src_ok(const void *xa, int ca, int up_a, const void *xb, int cb, int ntiles,
 
 int launch_conv(const FwdArgs &a0, cudaStream_t st, long long *launches) {
   FwdArgs a = a0;
-  const long long nb = (a.s.npix + 127) / 128;
-  if (nb > (1LL << 30)) return GD_ERR_INVALID_ARG;
+  const int H = a.s.H, W = a.s.W, P = W + 2;
+  const long long ntiles = a.s.npix / ((long long)H * W);
+  if (W > 1024 || ntiles * H >= (1LL << 21) || a.ci % 16 || a.co % 16)
+    return nn_fail(GD_ERR_INVALID_ARG, "conv: tile or batch too large", cudaSuccess);
+  a.ntiles = (int)ntiles;
+  const int nslab = a.ci / 16;
+  a.w_resident = nslab * 18 * a.co * 16 <= 48 * 1024 ? 1 : 0;
+  // the widest block (more rows per staged halo) that leaves room for two CTAs per SM
+  int smem = 0;
+  for (int nm : {4, 2, 1}) {
+    if (nm > 1 && nm * a.co > 256) continue;
+    const int nq = nm * 128 + 2 * P + 2;
+    const int nqp = nq + ((4 - nq % 8) + 8) % 8;
+    a.nm = nm;
+    a.nq = nq;
+    a.nqp = nqp;
+    smem = fwd_smem(a.co, a.ci, nq, nqp, a.w_resident).total;
+    if (smem <= 110 * 1024) break;
+  }
+  const long long TP = (long long)(H + 2) * P;
+  const long long nb = (ntiles * TP + a.nm * 128 - 1) / (a.nm * 128);
+  if (nb > (1LL << 30)) return nn_fail(GD_ERR_INVALID_ARG, "conv: batch too large", cudaSuccess);
   a.nblocks = (int)nb;
   uint32_t ncols = 32;
-  while ((int)ncols < a.co) ncols <<= 1;
-  int per_sm = 0;
-  const int smem = tmem_safe_smem(k_conv_fwd, NST * (A_BYTES + a.co * KS * 2), (int)ncols, &per_sm);
-  if (smem < 0) return nn_fail(GD_ERR_CUDA, "conv: shared memory / occupancy set-up", cudaSuccess);
+  while ((int)ncols < a.nm * a.co) ncols <<= 1;
+  const int per_sm = conv_occupancy((const void *)k_conv_fwd, smem, (int)ncols);
+  if (per_sm < 1) return nn_fail(GD_ERR_CUDA, "conv: shared memory set-up", cudaSuccess);
   const int grid = (int)std::min<long long>(nb, (long long)per_sm * num_sms());
   k_conv_fwd<<<grid, CT, smem, st>>>(a);
   if (launches) ++*launches;
@@ -764,9 +818,9 @@ int launch_wgrad(const Src &s, const bf16 *dy, int co, float *dw, cudaStream_t s
   const int mtiles = (9 * a.ci + 127) / 128;
   uint32_t ncols = 32;
   while ((int)ncols < co) ncols <<= 1;
-  int per_sm = 0;
-  const int smem = tmem_safe_smem(k_conv_wgrad, NSTW * (A_BYTES + co * KS * 2), (int)ncols, &per_sm);
-  if (smem < 0) return nn_fail(GD_ERR_CUDA, "wgrad: shared memory / occupancy set-up", cudaSuccess);
+  const int smem = NSTW * (A_BYTES + co * KS * 2);
+  const int per_sm = conv_occupancy((const void *)k_conv_wgrad, smem, (int)ncols);
+  if (per_sm < 1) return nn_fail(GD_ERR_CUDA, "wgrad: shared memory set-up", cudaSuccess);
   // about two waves of CTAs, each with at least 4096 pixels
   const long long want = (long long)per_sm * num_sms() * 2 / mtiles;
   long long chunk = (s.npix + std::max(1LL, want) - 1) / std::max(1LL, want);
