@@ -528,6 +528,18 @@ def run_gpu(args):
         del BI0, BI1, BO, PO, views
         torch.cuda.empty_cache()
 
+    # The learned initial guess (the 2048 x 2048 x 512 workload): the
+    # encoder-decoder is trained here on the GPU (untimed) on 20k
+    # (256 x 256 x 16 tile, AD solution) pairs that the solver produces from
+    # fresh stacks, then the plain FP32 method (zero start) is timed against
+    # mixed precision with the learned start (network inference over the whole
+    # stack + exact projection of its lowest xy modes), AD to 1e-6 and SP to
+    # 1e-7 each, inference included in the timed region.
+    learned = None
+    if not args.no_learned:
+        learned = bench_learned(args, gd, gdsynth, torch, stream, world, rank, dev, e0, e1)
+        torch.cuda.empty_cache()
+
     # end to end through the C ABI with pinned host buffers, the one call a
     # user makes for the two steps (gd_ad_then_sp): H2D of I0 and D2H of I2
     # inside the timed region
@@ -594,6 +606,7 @@ def run_gpu(args):
             "batch": batch,
             "hybrid": hybrid,
             "linear": linear,
+            "learned": learned,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -601,6 +614,96 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+LEARN_NX, LEARN_NY, LEARN_NZ = 2048, 2048, 512
+LEARN_LOWMODES = 4
+
+
+def bench_learned(args, gd, gdsynth, torch, stream, world, rank, dev, e0, e1):
+    from paper_1310_0041_gb300 import guess, learn
+    gdsynth.build_cuda()
+    t0 = time.perf_counter()
+    net = learn.gd_learn_create(16, 16, (16, 32, 64, 128), 256, 256, 32, seed=1,
+                                stream=stream.cuda_stream)
+    tr = guess.train_on_solver_pairs(
+        net, lambda sd: gdsynth.em_stack_cuda(1024, 1024, 128, seed=sd), args.learned_pairs,
+        passes=4, lr=2e-3, seed0=100000 + 1000 * rank)
+    train_s = time.perf_counter() - t0
+    nx, ny, nz = LEARN_NX, LEARN_NY, LEARN_NZ
+    I0 = gdsynth.em_stack_cuda(nx, ny, nz, seed=SEED + 300 + rank).float()
+    I1 = torch.empty_like(I0)
+    I2 = torch.empty_like(I0)
+    x0 = torch.empty_like(I0)
+    w_ad = (0.0, BETA[0], BETA[1], BETA[2])
+    ctl = gd.solve_ctl(40, TOL, 2, 2, 16)
+    ctl_sp = gd.solve_ctl(40, TOL_SP, 2, 2, 16)
+    nsteps = max(1, min(args.steps, 2))
+    out = {}
+    for mode, prec, use_net in (("plain_fp32", gd.GD_PREC_FP32, False),
+                                ("mixed", gd.GD_PREC_MIXED, False),
+                                ("mixed_learned", gd.GD_PREC_MIXED, True)):
+        s = gd.gd_stack_create(nx, ny, nz, prec=prec, stream=stream.cuda_stream)
+        reps = []
+        parts = {"network_ms": 0.0, "lowmodes_ms": 0.0}
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+        def one(timed_parts):
+            xs = None
+            if use_net:
+                ev[0].record(stream)
+                guess.learned_start(net, I0, x0)
+                ev[1].record(stream)
+                learn.gd_learn_lowmodes(net, I0, x0, nx, ny, nz, w_ad, LEARN_LOWMODES)
+                ev[2].record(stream)
+                xs = x0
+            r1 = gd.gd_diffuse_z(s, I0, I1, w_ad, ctl, x0=xs)
+            r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, ALPHA, ctl_sp)
+            reps.append((r1, r2))
+            if use_net and timed_parts:
+                torch.cuda.synchronize()
+                parts["network_ms"] += ev[0].elapsed_time(ev[1])
+                parts["lowmodes_ms"] += ev[1].elapsed_time(ev[2])
+
+        one(False)
+        reps.clear()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(nsteps):
+            one(False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = reduce_max(e0.elapsed_time(e1), world, dev) / nsteps
+        if use_net:  # a separate pass for the split (the events synchronise)
+            one(True)
+        gd.gd_destroy(s)
+        r1, r2 = reps[-1]
+        out[mode] = {"value": world * nx * ny * nz / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "ad_cycles": r1["cycles"], "ad_rel_residual": r1["rel_residual"],
+                     "ad_history": r1["history"], "sp_cycles": r2["cycles"],
+                     "sp_rel_residual": r2["rel_residual"]}
+        if use_net:
+            out[mode]["network_ms"] = parts["network_ms"]
+            out[mode]["lowmodes_ms"] = parts["lowmodes_ms"]
+    launches = learn.gd_learn_launch_count(net)
+    learn.gd_learn_destroy(net)
+    del I0, I1, I2, x0
+    p, m = out["plain_fp32"], out["mixed_learned"]
+    return {"workload": "learned_guess_%dx%dx%d" % (nx, ny, nz), "steps": nsteps,
+            "network": "3x3 encoder-decoder 16-32-64-128, bf16 tcgen05 convolutions, fp32 accumulation, "
+                       "256x256x16 tiles (slices as channels), predicts I1 - I0",
+            "start": "x0 = I0 + net(I0), then its %dx%d lowest xy cosine modes per slice replaced by the "
+                     "exact AD solution's (gd_learn_lowmodes)" % (LEARN_LOWMODES, LEARN_LOWMODES),
+            "training": {"pairs": tr["pairs"], "stacks": tr["stacks"], "steps": tr["steps"],
+                         "stack": "1024x1024x128", "seconds": train_s,
+                         "loss_first": float(np.mean(tr["losses"][:20])),
+                         "loss_last": float(np.mean(tr["losses"][-20:]))},
+            "plain_fp32": p, "mixed": out["mixed"], "mixed_learned": m,
+            "ad_cycles_saved": p["ad_cycles"] - m["ad_cycles"],
+            "speedup_vs_plain": p["ms_per_step"] / m["ms_per_step"],
+            "network_launches": launches}
 
 
 def run_ncu_case(args):
@@ -660,6 +763,10 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-slices measurement")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the Hybrid and Linear discretisation measurements")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-initial-guess measurement (training + 2048x2048x512)")
+    ap.add_argument("--learned-pairs", type=int, default=20000,
+                    help="training pairs of the learned initial guess")
     ap.add_argument("--ncu-batch", action="store_true",
                     help="one solve of the 512-slice batch for ncu launch lists (no timing)")
     ap.add_argument("--ncu-batch-slices", type=int, default=BATCH_N,

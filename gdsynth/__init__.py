@@ -46,6 +46,44 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_CU_SRC = os.path.join(_HERE, "synth_cuda.cu")
+_CU_LIB_PATH = os.path.join(_HERE, "libgdsynth_cuda.so")
+_cu_lib = None
+
+
+def build_cuda(force: bool = False) -> str:
+    """Compile ``synth_cuda.cu`` (the same generator on the GPU) into
+    ``libgdsynth_cuda.so`` (nvcc, sm_103a)."""
+    deps = [_CU_SRC, _SRC]
+    if force or not os.path.exists(_CU_LIB_PATH) or any(
+            os.path.getmtime(_CU_LIB_PATH) < os.path.getmtime(d) for d in deps):
+        nvcc = os.environ.get("NVCC") or "nvcc"
+        if not os.path.exists(nvcc) and os.path.exists("/usr/local/cuda/bin/nvcc"):
+            nvcc = "/usr/local/cuda/bin/nvcc"
+        tmp = _CU_LIB_PATH + ".tmp%d" % os.getpid()
+        cmd = [nvcc, "-O2", "-std=c++17", "-fmad=false", "-gencode", "arch=compute_103a,code=sm_103a",
+               "-Xcompiler", "-fPIC", "-shared", "-I", _HERE, _CU_SRC, "-o", tmp]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _CU_LIB_PATH)
+    return _CU_LIB_PATH
+
+
+def _load_cuda():
+    global _cu_lib
+    with _lock:
+        if _cu_lib is None:
+            build_cuda()
+            lib = ctypes.CDLL(_CU_LIB_PATH)
+            lib.gds_em_window_cuda.restype = ctypes.c_int
+            lib.gds_em_window_cuda.argtypes = [
+                ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_double,
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                ctypes.c_void_p]
+            _cu_lib = lib
+    return _cu_lib
+
+
 def _load():
     global _lib
     with _lock:
@@ -93,6 +131,35 @@ def em_stack(nx: int, ny: int, nz: int, seed: int = 0, ncells: int | None = None
                            x0, y0, z0, wx, wy, wz)
     if rc != 0:
         raise ValueError("gds_em_window failed with status %d" % rc)
+    return out
+
+
+def em_stack_cuda(nx: int, ny: int, nz: int, seed: int = 0, ncells: int | None = None,
+                  photo_seed: int | None = None, noise_seed: int | None = None,
+                  noise_sigma: float = 3.0, window=None, out=None):
+    """The stack of :func:`em_stack` drawn on the GPU: a torch uint8 CUDA
+    tensor ``[nz][ny][nx]`` (or the window), written into ``out`` if given."""
+    import torch
+    lib = _load_cuda()
+    if ncells is None:
+        ncells = default_cells(nx, ny)
+    if photo_seed is None:
+        photo_seed = seed * 2 + 1
+    if noise_seed is None:
+        noise_seed = seed * 2 + 2
+    if window is None:
+        window = (0, 0, 0, nx, ny, nz)
+    x0, y0, z0, wx, wy, wz = (int(v) for v in window)
+    if out is None:
+        out = torch.empty((wz, wy, wx), dtype=torch.uint8, device="cuda")
+    assert out.is_cuda and out.dtype == torch.uint8 and out.numel() == wx * wy * wz
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.gds_em_window_cuda(ctypes.c_void_p(out.data_ptr()), nx, ny, nz, int(ncells),
+                                int(seed) & (2**64 - 1), int(photo_seed) & (2**64 - 1),
+                                int(noise_seed) & (2**64 - 1), float(noise_sigma),
+                                x0, y0, z0, wx, wy, wz, ctypes.c_void_p(stream) if stream else None)
+    if rc != 0:
+        raise ValueError("gds_em_window_cuda failed with status %d" % rc)
     return out
 
 

@@ -164,6 +164,23 @@ int gd_learn_train_step(gd_learn *L, const void *x_pool, const float *t_pool, co
 int gd_learn_predict_stack(gd_learn *L, const float *I0, int nx, int ny, int nz, double in_shift,
                            double in_scale, double out_scale, float *x0);
 
+/*
+ * gd_learn_lowmodes -- replaces, in every slice z of the start x, the
+ * components along the first K x K two-dimensional cosine modes
+ * phi_k(x) phi_l(y) (orthonormal DCT-II vectors, the eigenvectors of the
+ * Neumann K_nx and K_ny) by those of the exact anisotropic-diffusion
+ * solution of I0 with weights w (Sec. 3.1; Sec. 3.2 gives the filter: in
+ * the cosine basis the solution of mode (k, l, m) is I0's times
+ * (bx lk + by ll) / (bx lk + by ll + bz lm), l_j = 4 sin^2(pi j / 2n), and
+ * the mean is kept).  A tile-wise prediction cannot see the whole stack, so
+ * its slice means and slow illumination gradients are wrong; those modes are
+ * the ones the V-cycle reduces slowly, and here they are made exact.
+ * I0, x: float32 [nz][ny][nx] device arrays; K in {1, 2, 4, 8};
+ * w.beta_z > 0.  Uses L's stream and a workspace of 3 nz K^2 doubles held
+ * by L; returns after the correction is applied.
+ */
+int gd_learn_lowmodes(gd_learn *L, const float *I0, float *x, int nx, int ny, int nz, gd_weights w, int K);
+
 /* Kernel launches issued by this network since creation. */
 long long gd_learn_launch_count(const gd_learn *L);
 /* Message of the network's last failure; with L = NULL (or a network with

@@ -44,7 +44,8 @@ EXPORTS_LEARN = ("gd_nn_conv3x3", "gd_nn_conv3x3_wgrad", "gd_nn_bias_grad", "gd_
                  "gd_learn_stack_tiles", "gd_learn_create", "gd_learn_destroy",
                  "gd_learn_param_count", "gd_learn_set_params", "gd_learn_get_params",
                  "gd_learn_get_grads", "gd_learn_forward", "gd_learn_train_step",
-                 "gd_learn_predict_stack", "gd_learn_launch_count", "gd_learn_last_error")
+                 "gd_learn_predict_stack", "gd_learn_lowmodes", "gd_learn_launch_count",
+                 "gd_learn_last_error")
 GD_NOALLOC_MAX_VOXELS = 4 * 1024 * 1024
 
 
@@ -159,6 +160,7 @@ def lib():
                 "gd_learn_forward": (I, [P, P, I, P]),
                 "gd_learn_train_step": (I, [P, P, P, ctypes.POINTER(I), I, D, ctypes.POINTER(D)]),
                 "gd_learn_predict_stack": (I, [P, P, I, I, I, D, D, D, P]),
+                "gd_learn_lowmodes": (I, [P, P, P, I, I, I, GdWeights, I]),
                 "gd_learn_launch_count": (ctypes.c_longlong, [P]),
                 "gd_learn_last_error": (ctypes.c_char_p, [P]),
             }

@@ -688,6 +688,118 @@ __global__ void k_stack_tiles(const float *I, const float *Isub, int nx, int ny,
 }
 
 // ---------------------------------------------------------------------------
+// exact low-mode projection of a start (the frequency filter of Sec. 3.2)
+// ---------------------------------------------------------------------------
+// The basis tables hold phi_k(i) = orthonormal DCT-II vector k on n points,
+// the eigenvector of the Neumann K_n with eigenvalue 4 sin^2(pi k / 2n):
+// phx[k][x] (k < K, x < nx) and phy[l][y].
+
+// c[z][k][l] += sum over the block's rows y and all x of v[z][y][x] phx[k][x] phy[l][y]
+template <int K>
+__global__ void k_lowmode_coef(const float *v, int nx, int ny, int rows, const float *phx, const float *phy,
+                               double *c) {
+  __shared__ double red[K * K][8];
+  const int z = blockIdx.y;
+  const int y0 = blockIdx.x * rows, y1 = min(ny, y0 + rows);
+  float acc[K][K];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int l = 0; l < K; ++l) acc[k][l] = 0.f;
+  const float *vz = v + (size_t)z * nx * ny;
+  for (int y = y0; y < y1; ++y) {
+    float r[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) r[k] = 0.f;
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      const float val = __ldg(vz + (size_t)y * nx + x);
+#pragma unroll
+      for (int k = 0; k < K; ++k) r[k] += val * __ldg(phx + k * nx + x);
+    }
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      const float pl = __ldg(phy + l * ny + y);
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k][l] += r[k] * pl;
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+      double d = acc[k][l];
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+      if (lane == 0) red[k * K + l][warp] = d;
+    }
+  __syncthreads();
+  if (threadIdx.x < K * K) {
+    double d = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) d += red[threadIdx.x][w];
+    atomicAdd(c + (size_t)z * K * K + threadIdx.x, d);
+  }
+}
+
+// x[z][y][x] += sum_{k,l} delta[z][k][l] phx[k][x] phy[l][y]
+template <int K>
+__global__ void k_lowmode_add(float *v, int nx, int ny, int rows, const float *phx, const float *phy,
+                              const double *delta) {
+  const int z = blockIdx.y;
+  const int y0 = blockIdx.x * rows, y1 = min(ny, y0 + rows);
+  float dz[K][K];
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int l = 0; l < K; ++l) dz[k][l] = (float)delta[(size_t)z * K * K + k * K + l];
+  float *vz = v + (size_t)z * nx * ny;
+  for (int y = y0; y < y1; ++y) {
+    float d[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      d[k] = 0.f;
+#pragma unroll
+      for (int l = 0; l < K; ++l) d[k] += dz[k][l] * __ldg(phy + l * ny + y);
+    }
+    for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+      float add = 0.f;
+#pragma unroll
+      for (int k = 0; k < K; ++k) add += d[k] * __ldg(phx + k * nx + x);
+      vz[(size_t)y * nx + x] += add;
+    }
+  }
+}
+
+// One block per mode (k, l): the exact solution's z-profile of that mode is
+// I0's filtered along z in the cosine basis psi_m(z) (DCT-II) by
+// (bx lk + by ll) / (bx lk + by ll + bz lm), the DC mode keeping the mean;
+// delta = that profile - x's.  cI, cx, delta: [nz][K][K]; spec: [K*K][nz].
+__global__ void k_lowmode_filter(const double *cI, const double *cx, double *delta, double *spec, int nx, int ny,
+                                 int nz, int K, double bx, double by, double bz) {
+  const int kl = blockIdx.x, k = kl / K, l = kl % K;
+  auto lam = [&](int j, int n) {
+    const double sn = sinpi(j / (2.0 * n));
+    return 4.0 * sn * sn;
+  };
+  const double lxy = bx * lam(k, nx) + by * lam(l, ny);
+  const float nrm0 = rsqrtf((float)nz), nrm = sqrtf(2.0f / (float)nz);
+  double *sp = spec + (size_t)kl * nz;
+  for (int m = threadIdx.x; m < nz; m += blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < nz; ++z)
+      acc += (double)((m ? nrm : nrm0) * cospif((float)m * (2.f * z + 1.f) / (2.f * nz))) * cI[(size_t)z * K * K + kl];
+    const double ratio = (k == 0 && l == 0) ? (m == 0 ? 1.0 : 0.0) : lxy / (lxy + bz * lam(m, nz));
+    sp[m] = ratio * acc;
+  }
+  __syncthreads();
+  for (int z = threadIdx.x; z < nz; z += blockDim.x) {
+    double acc = 0.0;
+    for (int m = 0; m < nz; ++m)
+      acc += (double)((m ? nrm : nrm0) * cospif((float)m * (2.f * z + 1.f) / (2.f * nz))) * sp[m];
+    delta[(size_t)z * K * K + kl] = acc - cx[(size_t)z * K * K + kl];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 int num_sms() {
@@ -879,6 +991,9 @@ struct gd_learn {
        *dk3 = nullptr, *ga4 = nullptr, *dp3 = nullptr, *ga3 = nullptr, *dp2 = nullptr, *ga2 = nullptr,
        *dp1 = nullptr, *ga1 = nullptr;
   double *acc = nullptr;
+  double *lm = nullptr;   // low-mode projection: coefficients of I0, of x, the correction, basis tables
+  long long lm_cap = 0;   // doubles held by lm
+  int lm_tab[3] = {0, 0, 0};  // (K, nx, ny) of the basis tables in lm
   std::vector<void *> allocs;
   long long launches = 0;
   std::string err;
@@ -1259,6 +1374,7 @@ int gd_learn_destroy(gd_learn *L) {
   if (!L) return GD_OK;
   cudaStreamSynchronize(L->st);
   for (void *p : L->allocs) cudaFree(p);
+  if (L->lm) cudaFree(L->lm);
   delete L;
   return GD_OK;
 }
@@ -1362,6 +1478,80 @@ int gd_learn_predict_stack(gd_learn *L, const float *I0, int nx, int ny, int nz,
     LTRY(net_forward(L, B, nullptr, &so));
   }
   return finish(L->st, GD_OK);
+}
+
+}  // extern "C"
+
+namespace {
+template <int K>
+int lowmodes_k(gd_learn *L, const float *I0, float *x, int nx, int ny, int nz, gd_weights w) {
+  cudaStream_t st = L->st;
+  const long long n3 = (long long)nz * K * K;
+  const long long ntab = ((long long)K * (nx + ny) + 1) / 2 + 1;  // float tables, in doubles
+  if (L->lm_cap < 4 * n3 + ntab) {
+    if (L->lm) {
+      cudaStreamSynchronize(st);
+      cudaFree(L->lm);
+      L->lm = nullptr;
+      L->lm_cap = 0;
+    }
+    if (cudaMalloc(&L->lm, (4 * n3 + ntab) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      L->lm = nullptr;
+      return nn_fail(GD_ERR_OOM, "low-mode workspace", cudaSuccess);
+    }
+    L->lm_cap = 4 * n3 + ntab;
+    L->lm_tab[0] = 0;
+  }
+  double *cI = L->lm, *cx = L->lm + n3, *dl = L->lm + 2 * n3, *spec = L->lm + 3 * n3;
+  float *phx = reinterpret_cast<float *>(L->lm + 4 * n3), *phy = phx + (long long)K * nx;
+  if (L->lm_tab[0] != K || L->lm_tab[1] != nx || L->lm_tab[2] != ny) {
+    const double pi = 3.14159265358979323846;
+    std::vector<float> tab((size_t)K * (nx + ny));
+    for (int k = 0; k < K; ++k) {
+      for (int i = 0; i < nx; ++i)
+        tab[(size_t)k * nx + i] = (float)((k == 0 ? std::sqrt(1.0 / nx) : std::sqrt(2.0 / nx)) *
+                                          std::cos(pi * k * (2.0 * i + 1.0) / (2.0 * nx)));
+      for (int i = 0; i < ny; ++i)
+        tab[(size_t)K * nx + (size_t)k * ny + i] = (float)((k == 0 ? std::sqrt(1.0 / ny) : std::sqrt(2.0 / ny)) *
+                                                           std::cos(pi * k * (2.0 * i + 1.0) / (2.0 * ny)));
+    }
+    if (cudaMemcpyAsync(phx, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return GD_ERR_CUDA;
+    L->lm_tab[0] = K;
+    L->lm_tab[1] = nx;
+    L->lm_tab[2] = ny;
+  }
+  if (cudaMemsetAsync(L->lm, 0, 2 * n3 * sizeof(double), st) != cudaSuccess) return GD_ERR_CUDA;
+  const int rows = 16;
+  const dim3 grid((ny + rows - 1) / rows, nz);
+  k_lowmode_coef<K><<<grid, 256, 0, st>>>(I0, nx, ny, rows, phx, phy, cI);
+  k_lowmode_coef<K><<<grid, 256, 0, st>>>(x, nx, ny, rows, phx, phy, cx);
+  L->launches += 2;
+  LTRY(launched("k_lowmode_coef"));
+  k_lowmode_filter<<<K * K, 256, 0, st>>>(cI, cx, dl, spec, nx, ny, nz, K, w.beta_x, w.beta_y, w.beta_z);
+  ++L->launches;
+  LTRY(launched("k_lowmode_filter"));
+  k_lowmode_add<K><<<grid, 256, 0, st>>>(x, nx, ny, rows, phx, phy, dl);
+  ++L->launches;
+  LTRY(launched("k_lowmode_add"));
+  return finish(st, GD_OK);
+}
+}  // namespace
+
+extern "C" {
+
+int gd_learn_lowmodes(gd_learn *L, const float *I0, float *x, int nx, int ny, int nz, gd_weights w, int K) {
+  if (!L || !I0 || !x || nx < 1 || ny < 1 || nz < 1 || !(w.beta_x >= 0) || !(w.beta_y >= 0) || !(w.beta_z > 0))
+    return GD_ERR_INVALID_ARG;
+  switch (K) {
+    case 1: return lowmodes_k<1>(L, I0, x, nx, ny, nz, w);
+    case 2: return lowmodes_k<2>(L, I0, x, nx, ny, nz, w);
+    case 4: return lowmodes_k<4>(L, I0, x, nx, ny, nz, w);
+    case 8: return lowmodes_k<8>(L, I0, x, nx, ny, nz, w);
+    default: return GD_ERR_INVALID_ARG;
+  }
 }
 
 long long gd_learn_launch_count(const gd_learn *L) { return L ? L->launches : -1; }

@@ -169,6 +169,12 @@ def gd_learn_predict_stack(net: Net, I0, nx, ny, nz, in_shift, in_scale, out_sca
                                             out_scale, _p(x0)), "gd_learn_predict_stack")
 
 
+def gd_learn_lowmodes(net: Net, I0, x, nx, ny, nz, w, K) -> int:
+    from . import _weights
+    return _ok(lib().gd_learn_lowmodes(net.handle, _p(I0), _p(x), nx, ny, nz, _weights(w), K),
+               "gd_learn_lowmodes")
+
+
 def gd_learn_launch_count(net: Net) -> int:
     return int(lib().gd_learn_launch_count(net.handle))
 

@@ -381,3 +381,31 @@ def test_predict_stack_matches_tiles_and_forward(env):
         assert (x0 - want).abs().max().item() <= 1e-4 * max(1.0, want.abs().max().item())
     finally:
         learn.gd_learn_destroy(net)
+
+
+@pytest.mark.parametrize("shape,K,bz", [((16, 48, 64), 4, 10.0), ((12, 40, 24), 2, 0.1), ((8, 32, 32), 8, 1.0)])
+def test_lowmode_projection_matches_closed_form(env, shape, K, bz):
+    """After gd_learn_lowmodes, the start's K x K lowest xy cosine modes are
+    those of the exact anisotropic-diffusion solution (the oracle's FP64 DCT
+    closed form) and every other mode is left as it was."""
+    from scipy.fft import dctn
+    from oracle import closed_form as cf
+    torch, learn = env
+    nz, ny, nx = shape
+    rng = np.random.default_rng(nz * 100 + K)
+    I0 = rng.integers(0, 256, size=shape).astype(np.float32)
+    x = (I0 + rng.normal(0, 20, size=shape)).astype(np.float32)
+    net = learn.gd_learn_create(16, 16, WIDTHS, 16, 16, 1, seed=0)
+    try:
+        xd = torch.from_numpy(x).cuda()
+        learn.gd_learn_lowmodes(net, torch.from_numpy(I0).cuda(), xd, nx, ny, nz, (0.0, 1.0, 1.0, bz), K)
+        got = dctn(xd.cpu().numpy().astype(np.float64), axes=(1, 2), norm="ortho")
+    finally:
+        learn.gd_learn_destroy(net)
+    want_low = dctn(cf.ad(I0.astype(np.float64), 1.0, 1.0, bz), axes=(1, 2), norm="ortho")[:, :K, :K]
+    before = dctn(x.astype(np.float64), axes=(1, 2), norm="ortho")
+    scale = np.abs(before).max()
+    assert np.abs(got[:, :K, :K] - want_low).max() <= 2e-5 * scale
+    rest = np.ones(got.shape, bool)
+    rest[:, :K, :K] = False
+    assert np.abs(got[rest] - before[rest]).max() <= 2e-5 * scale

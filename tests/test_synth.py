@@ -1,5 +1,6 @@
 """The seeded input generator: determinism, windows, and the recipe's statistics."""
 import numpy as np
+import pytest
 
 import gdsynth
 
@@ -58,3 +59,21 @@ def test_batch_inputs():
     # seeded
     J0s, _ = gdsynth.batch_slices(nx, ny, seed=4)
     assert all(np.array_equal(a, b) for a, b in zip(I0s, J0s))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape,window", [
+    ((300, 200, 20), (37, 11, 3, 200, 150, 12)),
+    ((256, 256, 80), (0, 0, 0, 256, 256, 80)),   # more than one 64-slice chunk
+])
+def test_gpu_generator_draws_the_same_bytes(shape, window):
+    """The GPU version of the generator reproduces the CPU generator's bytes
+    (a differing byte would need a value within ~1e-13 of a rounding
+    boundary: at most a handful are allowed, none expected)."""
+    import torch
+    assert torch.cuda.is_available()
+    nx, ny, nz = shape
+    want = gdsynth.em_stack(nx, ny, nz, seed=9, window=window)
+    got = gdsynth.em_stack_cuda(nx, ny, nz, seed=9, window=window).cpu().numpy()
+    assert got.shape == want.shape
+    assert int((got != want).sum()) <= 2
