@@ -15,7 +15,14 @@ import paper_1310_0041_gb300 as gd
 pytestmark = pytest.mark.gpu
 
 
-def test_fullsize_1024x1024x128():
+@pytest.mark.parametrize("disc,prec", [(gd.GD_DISC_CONSTANT, gd.GD_PREC_FP32),
+                                       (gd.GD_DISC_CONSTANT, gd.GD_PREC_MIXED),
+                                       (gd.GD_DISC_HYBRID, gd.GD_PREC_FP32)],
+                         ids=["fp32", "mixed", "hybrid"])
+def test_fullsize_1024x1024x128(disc, prec):
+    """The float32 mode, the mixed-precision mode (bfloat16 levels) and the
+    Hybrid discretisation (same fine system, B-spline transfers) at the size
+    the benchmark quotes them on, against the same exact solutions."""
     import torch
     gd.build()
     nx, ny, nz = 1024, 1024, 128
@@ -23,7 +30,7 @@ def test_fullsize_1024x1024x128():
     I0 = torch.from_numpy(I0n).cuda().float()
     I1 = torch.empty_like(I0)
     I2 = torch.empty_like(I0)
-    s = gd.gd_stack_create(nx, ny, nz)
+    s = gd.gd_stack_create(nx, ny, nz, disc=disc, prec=prec)
     try:
         r1 = gd.gd_diffuse_z(s, I0, I1, (0.0, 1.0, 1.0, 10.0),
                              gd.solve_ctl(30, 1e-6, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL))

@@ -73,3 +73,24 @@ def test_linear_kernel_level_calls_are_unsupported(torch):
         assert ei.value.status == gd.GD_ERR_UNSUPPORTED
     finally:
         gd.gd_destroy(s)
+
+
+def test_linear_at_256x256x32(torch):
+    """Both steps on a 256 x 256 x 32 stack (2.1 M unknowns of the 27-point
+    system) against the oracle's fast-diagonalisation solves."""
+    nz, ny, nx = 32, 256, 256
+    I0h = gdsynth.em_stack(nx, ny, nz, seed=41).astype(np.float32)
+    I0 = torch.from_numpy(I0h).cuda()
+    I1, I2 = torch.empty_like(I0), torch.empty_like(I0)
+    s = gd.gd_stack_create(nx, ny, nz, disc=gd.GD_DISC_LINEAR)
+    try:
+        r1 = gd.gd_diffuse_z(s, I0, I1, (0.0, 1.0, 1.0, 10.0), gd.solve_ctl(60, 1e-9))
+        r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, 0.01, gd.solve_ctl(60, 1e-9))
+    finally:
+        gd.gd_destroy(s)
+    assert r1["status"] == gd.GD_OK and r2["status"] == gd.GD_OK, (r1, r2)
+    I0d = I0h.astype(np.float64)
+    got1 = I1.cpu().numpy().astype(np.float64)
+    assert np.abs(got1 - ol.ad_fdm(I0d, 1.0, 1.0, 10.0)).max() <= 1e-3
+    got2 = I2.cpu().numpy().astype(np.float64)
+    assert np.abs(got2 - ol.sp_fdm(I0d, got1, 0.01)).max() <= 1e-3

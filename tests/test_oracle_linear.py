@@ -10,6 +10,7 @@ and the special cases the equations fix.
 import itertools
 
 import numpy as np
+import pytest
 
 import gdsynth
 import oracle.linear as ol
@@ -99,3 +100,20 @@ def test_special_cases():
     A = ol.operator(I0.shape, 0.0, 1.0, 1.0, 10.0)
     assert ol.rel_residual(A, ol.rhs_ad(I0), wrong) > 1e-3
     assert ol.rel_residual(A, ol.rhs_ad(I0), I1) < 1e-11
+
+
+@pytest.mark.parametrize("shape,bz", [((5, 7, 9), 10.0), ((1, 6, 11), 1.0), ((4, 1, 8), 0.1), ((3, 10, 4), 2.0)])
+def test_fast_diagonalisation_equals_the_sparse_solves(shape, bz):
+    """ad_fdm / sp_fdm (per-axis generalised eigenpairs) against the sparse
+    CG and direct solves of the assembled Kronecker systems, ragged shapes
+    and one-node axes included."""
+    rng = np.random.default_rng(sum(shape))
+    I0 = rng.uniform(0, 255, size=shape)
+    I1 = rng.uniform(0, 255, size=shape)
+    a = ol.ad_fdm(I0, 1.0, 1.3, bz)
+    b = ol.ad(I0, 1.0, 1.3, bz)
+    assert np.abs(a - b).max() <= 1e-8 * np.abs(b).max()
+    assert abs(a.sum() - I0.sum()) <= 1e-8 * abs(I0.sum())
+    c = ol.sp_fdm(I0, I1, 0.05)
+    d = ol.sp_solve(I0, I1, 0.05)
+    assert np.abs(c - d).max() <= 1e-8 * np.abs(d).max()
