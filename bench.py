@@ -207,12 +207,31 @@ def run_reference(args):
 
 
 def cpu_baseline_bounded() -> dict:
-    """The oracle timed once on the bounded sample (about 10-30 s of CPU work)."""
+    """The oracle timed once on the bounded sample (about 10-30 s of CPU work)
+    on all host cores, then one run of the sample on a single thread."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     with ctx.Pool(1) as pool:
         res = pool.apply(_cpu_baseline_child)
+    old = os.environ.get("OMP_NUM_THREADS")
+    os.environ["OMP_NUM_THREADS"] = "1"  # read by the spawned child's OpenMP runtime
+    try:
+        with ctx.Pool(1) as pool:
+            t1, v1, thr = pool.apply(_cpu_single_thread_child)
+    finally:
+        if old is None:
+            os.environ.pop("OMP_NUM_THREADS", None)
+        else:
+            os.environ["OMP_NUM_THREADS"] = old
+    res["single_thread"] = {"value": v1 / t1, "unit": UNIT, "seconds": t1, "threads": thr,
+                            "sample": "one run of the same sample"}
     return res
+
+
+def _cpu_single_thread_child():
+    import oracle
+    t, v = oracle_sample_step(oracle_crop())
+    return t, v, oracle.threads()
 
 
 def _cpu_baseline_child():
@@ -390,8 +409,12 @@ def run_gpu(args):
         sh = gd.gd_stack_create(NX, NY, NZ, disc=gd.GD_DISC_HYBRID, stream=stream.cuda_stream)
         hreps = []
 
+        # AD to 1e-7: the Hybrid hierarchy leaves a smoother residual, and at
+        # 1e-6 max |d| against the exact solution is ~5e-3 (1e-3 needs 1e-7)
+        ctl_h = gd.solve_ctl(40, TOL_SP, 2, 2, 16)
+
         def hstep():
-            h1 = gd.gd_diffuse_z(sh, I0, I1, w_ad, ctl)
+            h1 = gd.gd_diffuse_z(sh, I0, I1, w_ad, ctl_h)
             h2 = gd.gd_screened_poisson_slices(sh, I0, I1, I2, ALPHA, ctl_sp)
             hreps.append((h1, h2))
 
@@ -413,6 +436,7 @@ def run_gpu(args):
         hybrid = {"value": world * voxels * hsteps / (hms * 1e-3), "unit": UNIT,
                   "ms_per_step": hms / hsteps, "steps": hsteps,
                   "discretisation": "hybrid: 6-point fine, B-spline transfers, Galerkin 27-point coarse",
+                  "rel_tol_ad": TOL_SP, "rel_tol_sp": TOL_SP,
                   "ad_cycles": h1["cycles"], "ad_rho_per_cycle": h1["rho_per_cycle"],
                   "ad_rel_residual": h1["rel_residual"], "sp_cycles": h2["cycles"],
                   "sp_rho_per_cycle": h2["rho_per_cycle"], "sp_rel_residual": h2["rel_residual"],
@@ -535,6 +559,15 @@ def run_gpu(args):
     # mixed precision with the learned start (network inference over the whole
     # stack + exact projection of its lowest xy modes), AD to 1e-6 and SP to
     # 1e-7 each, inference included in the timed region.
+    # The mixed-precision workload (4096 x 4096 x 256, 4.3 G voxels): AD then
+    # SP in the float32 and the mixed mode, timed like the main workload, with
+    # the per-level effect of 16-bit storage measured on a 1024 x 1024 x 64
+    # crop solved as its own problem.
+    config3 = None
+    if not args.no_config3:
+        config3 = bench_config3(args, gd, gdsynth, torch, stream, world, dev, e0, e1)
+        torch.cuda.empty_cache()
+
     learned = None
     if not args.no_learned:
         learned = bench_learned(args, gd, gdsynth, torch, stream, world, rank, dev, e0, e1)
@@ -607,6 +640,7 @@ def run_gpu(args):
             "hybrid": hybrid,
             "linear": linear,
             "learned": learned,
+            "mixed_config3": config3,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -614,6 +648,142 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def level_operator(info: dict) -> np.ndarray:
+    """Dense FP64 matrix of a level's operator from gd_level_info:
+    wx Kx(x)My(x)Mz + wy Mx(x)Ky(x)Mz + wz Mx(x)My(x)Kz + wm Mx(x)My(x)Mz, K the
+    1D Neumann Laplacian, M = diag(children counts); x fastest (z outermost)."""
+    def K(n):
+        A = np.zeros((n, n))
+        for i in range(n - 1):
+            A[i, i] += 1
+            A[i + 1, i + 1] += 1
+            A[i, i + 1] -= 1
+            A[i + 1, i] -= 1
+        return A
+
+    def M(n, s_, l_):
+        d = np.full(n, float(s_))
+        d[-1] = l_
+        return np.diag(d)
+    nx, ny, nz = info["dims"]
+    Kx, Ky, Kz = K(nx), K(ny), K(nz)
+    Mx, My, Mz = (M(n, s_, l_) for n, s_, l_ in zip((nx, ny, nz), info["s"], info["l"]))
+    wx, wy, wz, wm = info["weights"]
+    kr = lambda a, b, c: np.kron(a, np.kron(b, c))
+    return wx * kr(Mz, My, Kx) + wy * kr(Mz, Ky, Mx) + wz * kr(Kz, My, Mx) + wm * kr(Mz, My, Mx)
+
+
+def mixed_level_errors(gd, torch, I0, w, stream=None) -> dict:
+    """What 16-bit storage does to each level: one AD V-cycle from the zero
+    start (the same input) on a float32-storage stack and on a mixed stack;
+    per level, max and RMS of the difference of the stored corrections
+    relative to the float32 hierarchy's, both taken modulo the AD operator's
+    null space (the constants: mass-weighted mean removed); and the coarsest
+    solve (float32 fast diagonalisation on the device) against an FP64 dense
+    solve of the same coarsest system on the host."""
+    nz, ny, nx = I0.shape
+    out = torch.empty_like(I0)
+    levels = {}
+    coarse = None
+    for prec in (gd.GD_PREC_FP32, gd.GD_PREC_MIXED):
+        s = gd.gd_stack_create(nx, ny, nz, prec=prec, stream=stream)
+        try:
+            gd.gd_diffuse_z(s, I0, out, w, gd.solve_ctl(1, 1e-30), raise_on_error=False)
+            L = gd.gd_level_count(s)
+            for lv in range(1, L):
+                info = gd.gd_level_info(s, lv)
+                buf = np.empty(int(np.prod(info["dims"])), np.float32)
+                gd.gd_level_fetch(s, lv, 0, buf)
+                levels.setdefault(lv, {})[prec] = (info, buf.astype(np.float64))
+            if prec == gd.GD_PREC_FP32:
+                info = gd.gd_level_info(s, L - 1)
+                bL = np.empty(int(np.prod(info["dims"])), np.float32)
+                gd.gd_level_fetch(s, L - 1, 1, bL)
+                coarse = (info, bL.astype(np.float64), levels[L - 1][prec][1])
+        finally:
+            gd.gd_destroy(s)
+    def masses(info):
+        (nxl, nyl, nzl), s_, l_ = info["dims"], info["s"], info["l"]
+        ax = [np.r_[[s_[d]] * (n - 1), l_[d]].astype(np.float64) for d, n in enumerate((nxl, nyl, nzl))]
+        return np.kron(ax[2], np.kron(ax[1], ax[0]))
+
+    def null_free(info, v):
+        # the AD operator (no screening term) is singular: a level's correction
+        # is defined up to a constant, which the fine level's mean fix removes
+        if info["weights"][3] != 0.0:
+            return v
+        m = masses(info)
+        return v - np.dot(m, v) / m.sum()
+
+    rows = []
+    for lv in sorted(levels):
+        (i32, x32), (imx, xmx) = levels[lv][gd.GD_PREC_FP32], levels[lv][gd.GD_PREC_MIXED]
+        x32, xmx = null_free(i32, x32), null_free(imx, xmx)
+        d = xmx - x32
+        scale = max(np.abs(x32).max(), 1e-30)
+        rows.append({"level": lv, "dims": list(i32["dims"]), "storage": "bf16" if imx["bytes"] == 2 else "fp32",
+                     "rel_max_diff": float(np.abs(d).max() / scale),
+                     "rel_rms_diff": float(np.sqrt(np.mean(d * d)) / max(np.sqrt(np.mean(x32 * x32)), 1e-30))})
+    info, bL, xL = coarse
+    A = level_operator(info)
+    xref = np.linalg.lstsq(A, bL, rcond=None)[0]
+    m = masses(info)
+    mf = lambda v: v - np.dot(m, v) / m.sum()
+    e = mf(xL) - mf(xref)
+    coarsest = {"dims": list(info["dims"]), "device": "fp32 fast diagonalisation",
+                "rel_max_err_vs_fp64": float(np.abs(e).max() / max(np.abs(mf(xref)).max(), 1e-30)),
+                "rel_residual_fp32_solve": float(np.linalg.norm(bL - A @ xL) / max(np.linalg.norm(bL), 1e-30))}
+    return {"levels": rows, "coarsest": coarsest}
+
+
+C3_NX, C3_NY, C3_NZ = 4096, 4096, 256
+
+
+def bench_config3(args, gd, gdsynth, torch, stream, world, dev, e0, e1):
+    gdsynth.build_cuda()
+    nx, ny, nz = C3_NX, C3_NY, C3_NZ
+    I0 = gdsynth.em_stack_cuda(nx, ny, nz, seed=SEED + 400).float()
+    I1 = torch.empty_like(I0)
+    I2 = torch.empty_like(I0)
+    w_ad = (0.0, BETA[0], BETA[1], BETA[2])
+    ctl = gd.solve_ctl(40, TOL, 2, 2, 16)
+    ctl_sp = gd.solve_ctl(40, TOL_SP, 2, 2, 16)
+    nsteps = max(1, min(args.steps, 2))
+    out = {"workload": "mixed_precision_%dx%dx%d" % (nx, ny, nz), "steps": nsteps}
+    for name, prec in (("fp32", gd.GD_PREC_FP32), ("mixed", gd.GD_PREC_MIXED)):
+        s = gd.gd_stack_create(nx, ny, nz, prec=prec, stream=stream.cuda_stream)
+        reps = []
+
+        def one():
+            r1 = gd.gd_diffuse_z(s, I0, I1, w_ad, ctl)
+            r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, ALPHA, ctl_sp)
+            reps.append((r1, r2))
+
+        one()
+        reps.clear()
+        torch.cuda.synchronize()
+        barrier(world)
+        e0.record(stream)
+        for _ in range(nsteps):
+            one()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = reduce_max(e0.elapsed_time(e1), world, dev) / nsteps
+        gd.gd_destroy(s)
+        r1, r2 = reps[-1]
+        out[name] = {"value": world * nx * ny * nz / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "ad_cycles": r1["cycles"], "ad_rel_residual": r1["rel_residual"],
+                     "sp_cycles": r2["cycles"], "sp_rel_residual": r2["rel_residual"]}
+    out["mixed_speedup"] = out["fp32"]["ms_per_step"] / out["mixed"]["ms_per_step"]
+    del I0, I1, I2
+    torch.cuda.empty_cache()
+    crop = gdsynth.em_stack_cuda(nx, ny, nz, seed=SEED + 400, window=(1536, 1024, 96, 1024, 1024, 64)).float()
+    out["per_level"] = mixed_level_errors(gd, torch, crop, w_ad, stream=stream.cuda_stream)
+    out["per_level"]["measured_on"] = "one AD V-cycle on a 1024x1024x64 crop solved as its own problem"
+    return out
 
 
 LEARN_NX, LEARN_NY, LEARN_NZ = 2048, 2048, 512
@@ -763,6 +933,8 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-slices measurement")
     ap.add_argument("--no-hybrid", action="store_true",
                     help="skip the Hybrid and Linear discretisation measurements")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 4096x4096x256 float32 / mixed-precision measurement")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-initial-guess measurement (training + 2048x2048x512)")
     ap.add_argument("--learned-pairs", type=int, default=20000,

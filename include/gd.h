@@ -385,6 +385,28 @@ int gd_selftest_wait(unsigned polls);
 /* Number of kernel launches the stack has enqueued since creation. */
 long long gd_launch_count(gd_stack *s);
 
+/*
+ * Level inspection (the Constant discretisation), for measuring what the
+ * mixed-precision mode's 16-bit storage does to each level (Sec. 4.1 "Disk
+ * I/O" stores intermediate levels in 16 bits).  They describe the hierarchy
+ * of the stack's last solve or gd_vcycle call.
+ *   gd_level_count: levels (0 before any solve).
+ *   gd_level_info: info[10] = {nx, ny, nz, sx, sy, sz, lx, ly, lz, bytes per
+ *     value (4 float32, 2 bfloat16)} -- the level's size and, per axis, the
+ *     children counts of its cells (s, and l for the last one) -- and
+ *     weights[4] = {wx, wy, wz, wm}: the level's operator is
+ *     wx Kx(x)My(x)Mz + wy Mx(x)Ky(x)Mz + wz Mx(x)My(x)Kz + wm Mx(x)My(x)Mz with
+ *     K the 1D Neumann Laplacian and M_d = diag(children counts).
+ *   gd_level_fetch: copies level `level` (>= 1; level 0 is the caller's
+ *     array) -- which = 0: its correction x after the last cycle's
+ *     post-smoothing, 1: its right-hand side b -- into dst (nx*ny*nz floats,
+ *     device or host), widening bfloat16 to float32; synchronises the stream.
+ * GD_ERR_UNSUPPORTED for the Hybrid and Linear discretisations.
+ */
+int gd_level_count(gd_stack *s);
+int gd_level_info(gd_stack *s, int level, int *info, double *weights);
+int gd_level_fetch(gd_stack *s, int level, int which, float *dst);
+
 const char *gd_status_string(int status);
 const char *gd_last_error(gd_stack *s);
 int gd_version(void);

@@ -37,7 +37,7 @@ EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_
            "gd_batch_create", "gd_batch_screened_poisson", "gd_batch_voxels", "gd_batch_offset",
            "gd_batch_levels", "gd_batch_launch_count", "gd_batch_last_error", "gd_batch_destroy",
            "gd_batch_traffic", "gd_batch_tune", "gd_ad_then_sp", "gd_selftest_wait",
-           "gd_batch_last_traffic")
+           "gd_batch_last_traffic", "gd_level_count", "gd_level_info", "gd_level_fetch")
 # the symbols include/gd_learn.h declares (the learned initial guess)
 EXPORTS_LEARN = ("gd_nn_conv3x3", "gd_nn_conv3x3_wgrad", "gd_nn_bias_grad", "gd_nn_flip_weights",
                  "gd_nn_pool2", "gd_nn_pool2_backward", "gd_nn_up2_backward", "gd_nn_adam",
@@ -139,6 +139,9 @@ def lib():
                 "gd_batch_launch_count": (ctypes.c_longlong, [P]),
                 "gd_batch_last_error": (ctypes.c_char_p, [P]),
                 "gd_batch_destroy": (I, [P]),
+                "gd_level_count": (I, [P]),
+                "gd_level_info": (I, [P, I, ctypes.POINTER(I), ctypes.POINTER(D)]),
+                "gd_level_fetch": (I, [P, I, I, P]),
                 # learned initial guess (include/gd_learn.h)
                 "gd_nn_conv3x3": (I, [P, I, I, P, I, I, I, I, P, P, I, I, P, P, P, P]),
                 "gd_nn_conv3x3_wgrad": (I, [P, I, I, P, I, I, I, I, P, I, P, P]),
@@ -368,6 +371,22 @@ def gd_smooth_noalloc(nx: int, ny: int, nz: int, w, b, x, nsweeps: int, stream=N
     n = nx * ny * nz
     return lib().gd_smooth_noalloc(nx, ny, nz, _weights(w), _ptr(b, n, "b"), _ptr(x, n, "x"),
                                    nsweeps, ctypes.c_void_p(stream) if stream else None)
+
+
+def gd_level_count(s: Stack) -> int:
+    return lib().gd_level_count(s.handle)
+
+
+def gd_level_info(s: Stack, level: int) -> dict:
+    info = (ctypes.c_int * 10)()
+    w = (ctypes.c_double * 4)()
+    _check(lib().gd_level_info(s.handle, level, info, w), s)
+    return {"dims": tuple(info[0:3]), "s": tuple(info[3:6]), "l": tuple(info[6:9]),
+            "bytes": info[9], "weights": tuple(w)}
+
+
+def gd_level_fetch(s: Stack, level: int, which: int, dst) -> int:
+    return _check(lib().gd_level_fetch(s.handle, level, which, _ptr(dst)), s)
 
 
 def gd_profile_enable(s: Stack, on: bool) -> int:

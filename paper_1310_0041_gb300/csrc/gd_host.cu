@@ -1781,4 +1781,56 @@ int gd_profile_query(gd_stack *s, int k, char *name, int name_len, long long *la
 
 long long gd_launch_count(gd_stack *s) { return s ? s->launches : -1; }
 
+int gd_level_count(gd_stack *s) { return s && s->cur ? (int)s->cur->L.size() : 0; }
+
+int gd_level_info(gd_stack *s, int level, int *info, double *weights) {
+  if (!s || !s->cur || level < 0 || level >= (int)s->cur->L.size() || !info || !weights)
+    return GD_ERR_INVALID_ARG;
+  if (s->disc != GD_DISC_CONSTANT) {
+    set_err(s, "level inspection describes the Constant discretisation's 6-point levels");
+    return GD_ERR_UNSUPPORTED;
+  }
+  const Level &l = s->cur->L[level];
+  const int v[10] = {l.d.nx, l.d.ny, l.d.nz, l.d.sx, l.d.sy, l.d.sz, l.d.lx, l.d.ly, l.d.lz, l.esz};
+  for (int k = 0; k < 10; ++k) info[k] = v[k];
+  weights[0] = l.d.wx;
+  weights[1] = l.d.wy;
+  weights[2] = l.d.wz;
+  weights[3] = l.d.wm;
+  return GD_OK;
+}
+
+int gd_level_fetch(gd_stack *s, int level, int which, float *dst) {
+  if (!s || !s->cur || level < 1 || level >= (int)s->cur->L.size() || (which != 0 && which != 1) || !dst)
+    return GD_ERR_INVALID_ARG;
+  if (s->disc != GD_DISC_CONSTANT) {
+    set_err(s, "level inspection describes the Constant discretisation's 6-point levels");
+    return GD_ERR_UNSUPPORTED;
+  }
+  if (on_other_device(s, dst)) return GD_ERR_INVALID_ARG;
+  const Level &l = s->cur->L[level];
+  const float *src = which == 0 ? l.x : l.b;
+  if (!src) return GD_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return GD_ERR_CUDA;
+  const bool dev = is_device_ptr(dst);
+  if (l.esz == 4) {
+    return cudaMemcpy(dst, src, l.n * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost) ==
+                   cudaSuccess
+               ? GD_OK
+               : GD_ERR_CUDA;
+  }
+  // bfloat16 storage: widen on the host (a bfloat16 is the high half of a float32)
+  std::vector<uint16_t> h(l.n);
+  std::vector<float> f(l.n);
+  if (cudaMemcpy(h.data(), src, l.n * sizeof(uint16_t), cudaMemcpyDeviceToHost) != cudaSuccess) return GD_ERR_CUDA;
+  for (size_t i = 0; i < l.n; ++i) {
+    const uint32_t u = (uint32_t)h[i] << 16;
+    std::memcpy(&f[i], &u, sizeof u);
+  }
+  return cudaMemcpy(dst, f.data(), l.n * sizeof(float), dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost) ==
+                 cudaSuccess
+             ? GD_OK
+             : GD_ERR_CUDA;
+}
+
 }  // extern "C"

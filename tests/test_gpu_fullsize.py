@@ -30,15 +30,17 @@ def test_fullsize_1024x1024x128(disc, prec):
     I0 = torch.from_numpy(I0n).cuda().float()
     I1 = torch.empty_like(I0)
     I2 = torch.empty_like(I0)
+    # the Hybrid hierarchy leaves a smoother residual: AD to 1e-7 for max |d| <= 1e-3
+    tol_ad = 1e-7 if disc == gd.GD_DISC_HYBRID else 1e-6
     s = gd.gd_stack_create(nx, ny, nz, disc=disc, prec=prec)
     try:
         r1 = gd.gd_diffuse_z(s, I0, I1, (0.0, 1.0, 1.0, 10.0),
-                             gd.solve_ctl(30, 1e-6, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL))
+                             gd.solve_ctl(30, tol_ad, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL))
         r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, 0.01,
                                            gd.solve_ctl(30, 1e-7, flags=gd.GD_FLAG_REPORT_OUTPUT_RESIDUAL))
     finally:
         gd.gd_destroy(s)
-    assert r1["status"] == gd.GD_OK and r1["rel_residual"] <= 1e-6, r1
+    assert r1["status"] == gd.GD_OK and r1["rel_residual"] <= tol_ad, r1
     assert r2["status"] == gd.GD_OK and r2["rel_residual"] <= 1e-7, r2
     i0 = I0n.astype(np.float64)
     a1 = I1.cpu().numpy().astype(np.float64)
