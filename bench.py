@@ -53,11 +53,11 @@ BATCH_TOL = 1e-7
 # DRAM traffic of the dominant kernel class from one ncu capture: the ratio of
 # dram__bytes_read.sum + dram__bytes_write.sum to the algorithmic bytes over the
 # four fine-level sweeps of one AD V-cycle (zero start, plain, prolongation,
-# plain) of the 1024 x 512 x 64 case (bench.py --ncu-case); the traffic of a
-# full-size launch is that ratio times its algorithmic bytes.  Valid only while
-# the kernel source is the one it was taken from.
+# plain) of the 1024 x 1024 x 64 case (bench.py --ncu-case; 268 MB arrays, twice
+# the L2); the traffic of a full-size launch is that ratio times its algorithmic
+# bytes.  Valid only while the kernel source is the one it was taken from.
 NCU_TRAFFIC = {
-    "rb_sweep_fine": {"dram_over_alg": 1420.7 / 1543.6, "src_sha256": "dfb6fe1b86393b172145c3ca0f95156aa3c309850604d44cf2fcc60f380e1ecd"},
+    "rb_sweep_fine": {"dram_over_alg": 3075.3 / 3087.0, "src_sha256": "5734ebb5d4f5d3f10e195ea2279e0353eecbd6cd4d491a5b563f8f039fe103b8"},
 }
 
 
@@ -878,21 +878,43 @@ def bench_learned(args, gd, gdsynth, torch, stream, world, rank, dev, e0, e1):
 
 def run_ncu_case(args):
     """A small case for detailed ncu captures (not a benchmark): one AD
-    V-cycle on a 1024 x 512 x 64 stack (arrays of 134 MB, above L2; about
-    2 GB on the device)."""
+    V-cycle on a 1024 x 1024 x 64 stack (arrays of 268 MB, twice the L2;
+    about 4 GB on the device), or 1024 x 512 x 64 with --ncu-case-ny 512."""
     import torch
     import gdsynth
     import paper_1310_0041_gb300 as gd
     gd.build()
-    nx, ny, nz = 1024, 512, 64
-    I0 = torch.from_numpy(gdsynth.em_stack(nx, ny, nz, seed=SEED, ncells=1000)).cuda().float()
+    nx, ny, nz = 1024, args.ncu_case_ny, 64
+    I0 = torch.from_numpy(gdsynth.em_stack(nx, ny, nz, seed=SEED, ncells=nx * ny // 524)).cuda().float()
     I1 = torch.empty_like(I0)
     s = gd.gd_stack_create(nx, ny, nz)
     rep = gd.gd_diffuse_z(s, I0, I1, (0.0,) + BETA, gd.solve_ctl(1, TOL), raise_on_error=False)
     gd.gd_destroy(s)
-    print(json.dumps({"ncu_case": "ad_1024x512x64_one_vcycle", "status": rep["status"],
+    print(json.dumps({"ncu_case": "ad_%dx%dx%d_one_vcycle" % (nx, ny, nz), "status": rep["status"],
                       "cycles": rep["cycles"]}))
     return 0 if rep["status"] in (0, 5) else 1
+
+
+def run_ncu_conv(args):
+    """The learned guess's forward pass on 32 tiles of 256 x 256 x 16, four
+    times (for ncu captures of the convolution kernels; not a benchmark):
+    each forward launches e1, pool, e2, pool, e3, pool, e4, d3, d2, d1, y."""
+    import torch
+    import paper_1310_0041_gb300 as gd
+    from paper_1310_0041_gb300 import learn
+    gd.build()
+    B = 32
+    net = learn.gd_learn_create(16, 16, (16, 32, 64, 128), 256, 256, B, seed=0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.randn((B, 256, 256, 16), device="cuda", generator=g).to(torch.bfloat16)
+    yf = torch.empty((B, 256, 256, 16), device="cuda")
+    for _ in range(4):
+        learn.gd_learn_forward(net, x, B, yf)
+    torch.cuda.synchronize()
+    learn.gd_learn_destroy(net)
+    print(json.dumps({"ncu_conv": "forward_32x256x256x16", "forwards": 4}))
+    return 0
 
 
 def run_ncu_batch(args):
@@ -945,9 +967,15 @@ def main(argv=None):
                     help="slices of the --ncu-batch case (fewer for detailed captures)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case instead of the benchmark")
+    ap.add_argument("--ncu-case-ny", type=int, default=1024,
+                    help="y extent of the --ncu-case stack (1024 x ny x 64)")
+    ap.add_argument("--ncu-conv", action="store_true",
+                    help="four forward passes of the learned guess's network, for ncu")
     args = ap.parse_args(argv)
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.ncu_conv:
+        return run_ncu_conv(args)
     if args.ncu_batch:
         return run_ncu_batch(args)
     if args.impl == "reference":
