@@ -160,11 +160,12 @@ __device__ __forceinline__ float resid(const BEntry &e, const Cols &C, const Row
 // value of each cell's parent (piecewise-constant prolongation).
 template <bool ZERO_IN, bool PROLONG>
 __global__ void __launch_bounds__(BNT) k_bsweep(const BEntry *__restrict__ E, const int4 *__restrict__ items,
-                                                int nitems, const float *__restrict__ xin,
+                                                const int *__restrict__ nitems_p, const float *__restrict__ xin,
                                                 const float *__restrict__ b, float *__restrict__ xout,
                                                 const float *__restrict__ xc) {
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * WPB;
+  const int nitems = *nitems_p;  // read at run time: the list shrinks as slices converge
   for (int it = blockIdx.x * WPB + (threadIdx.x >> 5); it < nitems; it += nw) {
     const int4 w = items[it];
     const BEntry e = E[w.x];
@@ -248,10 +249,11 @@ __global__ void __launch_bounds__(BNT) k_bsweep(const BEntry *__restrict__ E, co
 // Chunks start at even rows and strips at even columns, so a coarse cell's
 // children lie in one lane's float4 and one chunk.
 __global__ void __launch_bounds__(BNT) k_brestrict(const BEntry *__restrict__ E, const int4 *__restrict__ items,
-                                                   int nitems, const float *__restrict__ x,
+                                                   const int *__restrict__ nitems_p, const float *__restrict__ x,
                                                    const float *__restrict__ b, float *__restrict__ bc) {
   const int lane = threadIdx.x & 31;
   const int nw = gridDim.x * WPB;
+  const int nitems = *nitems_p;
   for (int it = blockIdx.x * WPB + (threadIdx.x >> 5); it < nitems; it += nw) {
     const int4 w = items[it];
     const BEntry e = E[w.x];
@@ -563,10 +565,12 @@ struct gd_batch {
     float *x = nullptr, *t = nullptr, *b = nullptr;
     BEntry *E = nullptr;            // device
     int ne = 0;
-    int4 *items = nullptr;          // strips of the entries that have a next level
-    int nitems = 0;
-    int4 *strips_all = nullptr;     // level 0: strips of every entry (outer pass)
-    int nstrips_all = 0;
+    int4 *items = nullptr;          // strips of the entries that have a next level (active ones first)
+    int nitems = 0;                 // all entries' strips (the buffer's size; the graph's grids)
+    int *cnt = nullptr;             // device: strips of the active entries (read by the kernels)
+    int4 *strips_all = nullptr;     // level 0: strips of every entry (outer pass), active ones first
+    int nstrips_all = 0;            // of the active entries
+    int nstrips_all_cap = 0;        // of every entry (the buffer's size)
     int4 *tiles_all = nullptr;      // level 0: 64 x 32 tiles of every entry (input / output)
     int ntiles_all = 0;
   };
@@ -596,6 +600,7 @@ struct gd_batch {
   std::vector<double> srel, sbb;
   std::vector<int> fin;
   int *d_fin = nullptr;
+  int *d_cnt = nullptr;  // device: one active-strip count per level
   bool filtered = false;
   double last_bytes = 0.0;  // algorithmic bytes of the last solve (the work actually done)
   std::string err;
@@ -654,6 +659,7 @@ void batch_free(gd_batch *B) {
   cudaFree(B->lam);
   cudaFree(B->acc);
   cudaFree(B->d_fin);
+  cudaFree(B->d_cnt);
   cudaFree(B->bf);
   for (int k = 0; k < 2; ++k) {
     cudaFree(B->ph[k]);
@@ -760,13 +766,13 @@ int bvcycle(gd_batch *B, int nu1, int nu2, cudaStream_t st) {
       const bool zero = k == 0;
       float *out = (cur[l] == v.x) ? v.t : v.x;
       if (zero)
-        k_bsweep<true, false><<<gz, BNT, 0, st>>>(v.E, v.items, v.nitems, nullptr, v.b, out, nullptr);
+        k_bsweep<true, false><<<gz, BNT, 0, st>>>(v.E, v.items, v.cnt, nullptr, v.b, out, nullptr);
       else
-        k_bsweep<false, false><<<g, BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b, out, nullptr);
+        k_bsweep<false, false><<<g, BNT, 0, st>>>(v.E, v.items, v.cnt, cur[l], v.b, out, nullptr);
       ++B->launches;
       cur[l] = out;
     }
-    k_brestrict<<<grid_for(B, v.nitems, B->occ_restrict), BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b,
+    k_brestrict<<<grid_for(B, v.nitems, B->occ_restrict), BNT, 0, st>>>(v.E, v.items, v.cnt, cur[l], v.b,
                                                                   B->L[l + 1].b);
     ++B->launches;
   }
@@ -788,9 +794,9 @@ int bvcycle(gd_batch *B, int nu1, int nu2, cudaStream_t st) {
     for (int k = 0; k < nu2; ++k) {
       float *out = (cur[l] == v.x) ? v.t : v.x;
       if (k == 0)
-        k_bsweep<false, true><<<gp, BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b, out, B->L[l + 1].x);
+        k_bsweep<false, true><<<gp, BNT, 0, st>>>(v.E, v.items, v.cnt, cur[l], v.b, out, B->L[l + 1].x);
       else
-        k_bsweep<false, false><<<g, BNT, 0, st>>>(v.E, v.items, v.nitems, cur[l], v.b, out, nullptr);
+        k_bsweep<false, false><<<g, BNT, 0, st>>>(v.E, v.items, v.cnt, cur[l], v.b, out, nullptr);
       ++B->launches;
       cur[l] = out;
     }
@@ -908,35 +914,84 @@ double cycle_bytes(const gd_batch *B, int nu1, int nu2) {
   return cyc;
 }
 
-// (Re)builds the row-march work lists for chunks of `ch` rows.
-int build_lists(gd_batch *B, int ch) {
-  int st;
-  for (size_t l = 0; l < B->L.size(); ++l) {
-    gd_batch::Lev &v = B->L[l];
-    std::vector<int4> it, sa;
+// Host work lists of the active slices (all slices when `all`) for chunks of
+// `ch` rows: per level the strips of the entries that have a next level, and
+// at level 0 the strips of every entry (the outer pass).
+void host_lists(const gd_batch *B, int ch, bool all, std::vector<std::vector<int4>> &it,
+                std::vector<int4> &sa) {
+  it.assign(B->L.size(), std::vector<int4>());
+  sa.clear();
+  for (size_t l = 0; l < B->L.size(); ++l)
     for (int k = 0; k < (int)B->Eh[l].size(); ++k) {
       const BEntry &e = B->Eh[l][k];
-      if (!B->active.empty() && !B->active[e.slice]) continue;
-      if (e.coff >= 0) strips_of(k, e.nx, e.ny, ch, it);
+      if (!all && !B->active.empty() && !B->active[e.slice]) continue;
+      if (e.coff >= 0) strips_of(k, e.nx, e.ny, ch, it[l]);
       if (l == 0) strips_of(k, e.nx, e.ny, ch, sa);
     }
+}
+
+// (Re)builds the row-march work lists for chunks of `ch` rows, every slice
+// included; the buffers keep this size, so a captured V-cycle stays valid
+// when filter_lists later shrinks their contents.
+int build_lists(gd_batch *B, int ch) {
+  int st;
+  std::vector<std::vector<int4>> it;
+  std::vector<int4> sa;
+  host_lists(B, ch, true, it, sa);
+  if (!B->d_cnt && (st = balloc(B, &B->d_cnt, (size_t)B->L.size())) != GD_OK) return st;
+  std::vector<int> cnt(B->L.size());
+  for (size_t l = 0; l < B->L.size(); ++l) {
+    gd_batch::Lev &v = B->L[l];
     cudaFree(v.items);
     cudaFree(v.strips_all);
     v.items = v.strips_all = nullptr;
-    v.nitems = (int)it.size();
-    v.nstrips_all = (int)sa.size();
-    if ((st = balloc(B, &v.items, it.size())) != GD_OK) return st;
-    if ((st = balloc(B, &v.strips_all, sa.size())) != GD_OK) return st;
-    if (!it.empty()) BCK(cudaMemcpy(v.items, it.data(), it.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    if (!sa.empty())
-      BCK(cudaMemcpy(v.strips_all, sa.data(), sa.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    v.nitems = (int)it[l].size();
+    v.cnt = B->d_cnt + l;
+    cnt[l] = v.nitems;
+    if ((st = balloc(B, &v.items, it[l].size())) != GD_OK) return st;
+    if (!it[l].empty())
+      BCK(cudaMemcpy(v.items, it[l].data(), it[l].size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (l == 0) {
+      v.nstrips_all = v.nstrips_all_cap = (int)sa.size();
+      if ((st = balloc(B, &v.strips_all, sa.size())) != GD_OK) return st;
+      if (!sa.empty())
+        BCK(cudaMemcpy(v.strips_all, sa.data(), sa.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
   }
+  BCK(cudaMemcpy(B->d_cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice));
   B->chunk = ch;
-  if (B->gexec) {  // the graph holds the old lists
+  if (B->gexec) {  // the graph holds the old buffers
     cudaGraphExecDestroy(B->gexec);
     B->gexec = nullptr;
     B->g_nu1 = B->g_nu2 = -1;
   }
+  return GD_OK;
+}
+
+// Writes the active slices' strips into the front of the existing list
+// buffers and their counts into d_cnt (stream-ordered, then synchronised):
+// the kernels read the counts at run time, so the captured V-cycle stays
+// valid as slices leave.
+int filter_lists(gd_batch *B) {
+  std::vector<std::vector<int4>> it;
+  std::vector<int4> sa;
+  host_lists(B, B->chunk, false, it, sa);
+  std::vector<int> cnt(B->L.size());
+  for (size_t l = 0; l < B->L.size(); ++l) {
+    gd_batch::Lev &v = B->L[l];
+    cnt[l] = (int)it[l].size();
+    if (cnt[l] > v.nitems) return GD_ERR_CUDA;  // cannot happen: a subset of the full list
+    if (cnt[l])
+      BCK(cudaMemcpyAsync(v.items, it[l].data(), it[l].size() * sizeof(int4), cudaMemcpyHostToDevice,
+                          B->stream));
+  }
+  gd_batch::Lev &f = B->L[0];
+  if ((int)sa.size() > f.nstrips_all_cap) return GD_ERR_CUDA;
+  if (!sa.empty())
+    BCK(cudaMemcpyAsync(f.strips_all, sa.data(), sa.size() * sizeof(int4), cudaMemcpyHostToDevice, B->stream));
+  f.nstrips_all = (int)sa.size();
+  BCK(cudaMemcpyAsync(B->d_cnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, B->stream));
+  BCK(cudaStreamSynchronize(B->stream));  // the host vectors go out of scope
   return GD_OK;
 }
 
@@ -1234,8 +1289,8 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
   B->fin.assign(B->ns, 0);
   B->srel.assign(B->ns, 0.0);
   B->sbb.assign(B->ns, 0.0);
-  if (B->filtered) {
-    const int st0 = build_lists(B, B->chunk);
+  if (B->filtered) {  // every slice iterates again: the full lists, same buffers
+    const int st0 = filter_lists(B);
     if (st0 != GD_OK) return st0;
     B->filtered = false;
   }
@@ -1271,7 +1326,7 @@ int gd_batch_screened_poisson(gd_batch *B, const float *I0, const float *I1, flo
       }
     }
     if (newly > 0 && left > 0 && cycles < c.max_cycles) {
-      const int r = build_lists(B, B->chunk);
+      const int r = filter_lists(B);
       if (r != GD_OK) return r;
       B->filtered = true;
     }
