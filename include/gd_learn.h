@@ -101,6 +101,13 @@ int gd_nn_up2_backward(const void *dk, int ck, int c, const void *mask, int ntil
 int gd_nn_adam(float *p, const float *g, float *m, float *v, long long n, double lr, double b1,
                double b2, double eps, int t, void *stream);
 
+/* Self-test of the failure path of the tensor-core kernels: a kernel polls
+ * an mbarrier that nothing arrives at, `limit` times (1 .. 2^21) with the
+ * kernels' try_wait and suspend hint, gives up and raises the same device
+ * flag a conv kernel raises when its bounded wait gives up; returns
+ * GD_ERR_TIMEOUT (and clears the flag), leaving the context usable. */
+int gd_nn_selftest_wait(unsigned limit);
+
 /* ---- tiles of a stack ---- */
 
 /*
@@ -110,7 +117,8 @@ int gd_nn_adam(float *p, const float *g, float *m, float *v, long long n, double
  * bfloat16, tile t = (tz * (ny/th) + ty) * (nx/tw) + tx, for the ntiles
  * tiles starting at tile0.  When I_sub is given the value is
  * (I - I_sub) * scale and the output is float32 (xf) instead: the training
- * target.  nx, ny, nz multiples of tw, th, tc; tc a multiple of 8.
+ * target.  nx, ny, nz multiples of tw, th, tc; tc a multiple of 8.  Returns
+ * after the transform completes.
  */
 int gd_learn_stack_tiles(const float *I, const float *I_sub, int nx, int ny, int nz, int th, int tw,
                          int tc, long long tile0, long long ntiles, double shift, double scale,
@@ -147,12 +155,13 @@ int gd_learn_forward(gd_learn *L, const void *x, int batch, float *yf);
  * gd_learn_train_step -- forward, mean squared error against target
  * (float [.][h][w][c_out]), backward and one Adam step with learning rate
  * lr (lr = 0 leaves the parameters as they are).  x_pool / t_pool hold
- * tiles; idx_host (host, `batch` indices into the pools) picks the batch,
- * or NULL for the first `batch` tiles.  *loss (host, nullable) receives the
- * loss before the step.
+ * pool_tiles tiles each; idx_host (host, `batch` indices in
+ * [0, pool_tiles)) picks the batch, or NULL for the first `batch` tiles
+ * (GD_ERR_INVALID_ARG for an index outside the pool).  *loss (host,
+ * nullable) receives the loss before the step.
  */
-int gd_learn_train_step(gd_learn *L, const void *x_pool, const float *t_pool, const int *idx_host,
-                        int batch, double lr, double *loss);
+int gd_learn_train_step(gd_learn *L, const void *x_pool, const float *t_pool, long long pool_tiles,
+                        const int *idx_host, int batch, double lr, double *loss);
 
 /*
  * gd_learn_predict_stack -- the learned start of a solve:

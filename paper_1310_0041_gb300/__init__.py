@@ -41,6 +41,7 @@ EXPORTS = ("gd_stack_create", "gd_diffuse_z", "gd_screened_poisson_slices", "gd_
 # the symbols include/gd_learn.h declares (the learned initial guess)
 EXPORTS_LEARN = ("gd_nn_conv3x3", "gd_nn_conv3x3_wgrad", "gd_nn_bias_grad", "gd_nn_flip_weights",
                  "gd_nn_pool2", "gd_nn_pool2_backward", "gd_nn_up2_backward", "gd_nn_adam",
+                 "gd_nn_selftest_wait",
                  "gd_learn_stack_tiles", "gd_learn_create", "gd_learn_destroy",
                  "gd_learn_param_count", "gd_learn_set_params", "gd_learn_get_params",
                  "gd_learn_get_grads", "gd_learn_forward", "gd_learn_train_step",
@@ -151,6 +152,7 @@ def lib():
                 "gd_nn_pool2_backward": (I, [P, P, I, I, P, I, I, I, I, P, P]),
                 "gd_nn_up2_backward": (I, [P, I, I, P, I, I, I, P, P]),
                 "gd_nn_adam": (I, [P, P, P, P, ctypes.c_longlong, D, D, D, D, I, P]),
+                "gd_nn_selftest_wait": (I, [ctypes.c_uint]),
                 "gd_learn_stack_tiles": (I, [P, P, I, I, I, I, I, I, ctypes.c_longlong,
                                              ctypes.c_longlong, D, D, P, P, P]),
                 "gd_learn_create": (I, [ctypes.POINTER(P), I, I, ctypes.POINTER(I), I, I, I,
@@ -161,7 +163,8 @@ def lib():
                 "gd_learn_get_params": (I, [P, P]),
                 "gd_learn_get_grads": (I, [P, P]),
                 "gd_learn_forward": (I, [P, P, I, P]),
-                "gd_learn_train_step": (I, [P, P, P, ctypes.POINTER(I), I, D, ctypes.POINTER(D)]),
+                "gd_learn_train_step": (I, [P, P, P, ctypes.c_longlong, ctypes.POINTER(I), I, D,
+                                            ctypes.POINTER(D)]),
                 "gd_learn_predict_stack": (I, [P, P, I, I, I, D, D, D, P]),
                 "gd_learn_lowmodes": (I, [P, P, P, I, I, I, GdWeights, I]),
                 "gd_learn_launch_count": (ctypes.c_longlong, [P]),

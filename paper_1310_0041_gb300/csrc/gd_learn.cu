@@ -687,6 +687,31 @@ __global__ void k_stack_tiles(const float *I, const float *Isub, int nx, int ny,
   }
 }
 
+// Self-test of the tensor-core kernels' failure path: one thread initialises
+// an mbarrier that expects one arrival, never arrives, and polls it `limit`
+// times with the same try_wait and suspend hint as gdtc::mbar_wait; giving up
+// raises g_nn_timeout exactly as a conv kernel would, and the kernel returns.
+__global__ void k_nn_wait_selftest(uint32_t limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  gdtc::mbar_init(&bar, 1);
+  gdtc::fence_mbar_init();
+  const uint32_t a = gdtc::saddr(&bar);
+  bool done = false;
+  for (uint32_t it = 0; it < limit && !done; ++it) {
+    uint32_t d;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(d)
+        : "r"(a), "r"(0u), "r"(500u)
+        : "memory");
+    done = d != 0;
+  }
+  if (!done) atomicExch(&g_nn_timeout, 1);
+}
+
 // ---------------------------------------------------------------------------
 // exact low-mode projection of a start (the frequency filter of Sec. 3.2)
 // ---------------------------------------------------------------------------
@@ -1255,20 +1280,33 @@ int gd_nn_adam(float *p, const float *g, float *m, float *v, long long n, double
   return finish(st, cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA);
 }
 
-int gd_learn_stack_tiles(const float *I, const float *I_sub, int nx, int ny, int nz, int th, int tw, int tc,
-                         long long tile0, long long ntiles, double shift, double scale, void *x, float *xf,
-                         void *stream) {
+}  // extern "C"
+
+namespace {
+// enqueues the tile transform (no synchronisation): the inference loop's step
+int stack_tiles_async(const float *I, const float *I_sub, int nx, int ny, int nz, int th, int tw, int tc,
+                      long long tile0, long long ntiles, double shift, double scale, void *x, float *xf,
+                      cudaStream_t st) {
   if (!I || nx < 1 || ny < 1 || nz < 1 || th < 1 || tw < 1 || tc < 8 || tc % 8 || nx % tw || ny % th || nz % tc)
     return GD_ERR_INVALID_ARG;
   if (I_sub ? !xf : !x) return GD_ERR_INVALID_ARG;
   const long long tiles = (long long)(nx / tw) * (ny / th) * (nz / tc);
   if (tile0 < 0 || ntiles < 1 || tile0 + ntiles > tiles) return GD_ERR_INVALID_ARG;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   const long long npix = ntiles * th * tw;
   k_stack_tiles<<<grid_1d(npix * (tc / 8), 256), 256, 0, st>>>(I, I_sub, nx, ny, th, tw, tc, nx / tw, ny / th, tile0,
                                                               npix, (float)shift, (float)scale,
                                                               static_cast<bf16 *>(x), xf);
-  return cudaGetLastError() == cudaSuccess ? GD_OK : GD_ERR_CUDA;
+  return launched("k_stack_tiles");
+}
+}  // namespace
+
+extern "C" {
+
+int gd_learn_stack_tiles(const float *I, const float *I_sub, int nx, int ny, int nz, int th, int tw, int tc,
+                         long long tile0, long long ntiles, double shift, double scale, void *x, float *xf,
+                         void *stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return finish(st, stack_tiles_async(I, I_sub, nx, ny, nz, th, tw, tc, tile0, ntiles, shift, scale, x, xf, st));
 }
 
 int gd_learn_create(gd_learn **out, int c_in, int c_out, const int *widths, int tile_h, int tile_w, int max_batch,
@@ -1414,9 +1452,10 @@ int gd_learn_forward(gd_learn *L, const void *x, int batch, float *yf) {
   return finish(L->st, GD_OK);
 }
 
-int gd_learn_train_step(gd_learn *L, const void *x_pool, const float *t_pool, const int *idx_host, int batch,
-                        double lr, double *loss) {
-  if (!L || !x_pool || !t_pool || batch < 1 || batch > L->maxb || !(lr >= 0)) {
+int gd_learn_train_step(gd_learn *L, const void *x_pool, const float *t_pool, long long pool_tiles,
+                        const int *idx_host, int batch, double lr, double *loss) {
+  if (!L || !x_pool || !t_pool || batch < 1 || batch > L->maxb || !(lr >= 0) || pool_tiles < 1 ||
+      (!idx_host && batch > pool_tiles)) {
     if (L) L->err = "invalid arguments";
     return GD_ERR_INVALID_ARG;
   }
@@ -1426,7 +1465,10 @@ int gd_learn_train_step(gd_learn *L, const void *x_pool, const float *t_pool, co
   const char *tp = reinterpret_cast<const char *>(t_pool);
   for (int b = 0; b < batch; ++b) {
     const long long i = idx_host ? idx_host[b] : b;
-    if (i < 0) return GD_ERR_INVALID_ARG;
+    if (i < 0 || i >= pool_tiles) {
+      L->err = "tile index " + std::to_string(i) + " outside the pool of " + std::to_string(pool_tiles);
+      return GD_ERR_INVALID_ARG;
+    }
     if (cudaMemcpyAsync(reinterpret_cast<char *>(L->x) + b * xt, xp + i * xt, xt, cudaMemcpyDeviceToDevice, L->st) !=
             cudaSuccess ||
         cudaMemcpyAsync(reinterpret_cast<char *>(L->tgt) + b * tt, tp + i * tt, tt, cudaMemcpyDeviceToDevice, L->st) !=
@@ -1471,8 +1513,8 @@ int gd_learn_predict_stack(gd_learn *L, const float *I0, int nx, int ny, int nz,
   so.out_scale = (float)out_scale;
   for (long long t0 = 0; t0 < T; t0 += L->maxb) {
     const int B = (int)std::min<long long>(L->maxb, T - t0);
-    LTRY(gd_learn_stack_tiles(I0, nullptr, nx, ny, nz, L->H, L->W, L->cin, t0, B, in_shift, in_scale, L->x, nullptr,
-                              L->st));
+    LTRY(stack_tiles_async(I0, nullptr, nx, ny, nz, L->H, L->W, L->cin, t0, B, in_shift, in_scale, L->x, nullptr,
+                           L->st));
     ++L->launches;
     so.tile0 = t0;
     LTRY(net_forward(L, B, nullptr, &so));
@@ -1552,6 +1594,12 @@ int gd_learn_lowmodes(gd_learn *L, const float *I0, float *x, int nx, int ny, in
     case 8: return lowmodes_k<8>(L, I0, x, nx, ny, nz, w);
     default: return GD_ERR_INVALID_ARG;
   }
+}
+
+int gd_nn_selftest_wait(unsigned limit) {
+  if (limit < 1 || limit > (1u << 21)) return GD_ERR_INVALID_ARG;
+  k_nn_wait_selftest<<<1, 32>>>(limit);
+  return finish(nullptr, launched("k_nn_wait_selftest"));
 }
 
 long long gd_learn_launch_count(const gd_learn *L) { return L ? L->launches : -1; }

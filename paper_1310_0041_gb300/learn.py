@@ -17,12 +17,18 @@ from . import GD_OK, GdError, _default_stream, lib
 LAYERS = ("e1", "e2", "e3", "e4", "d3", "d2", "d1", "y")
 
 
-def _p(t):
-    """Device pointer of a contiguous CUDA tensor (None passes through)."""
+def _p(t, dtype=None):
+    """Device pointer of a contiguous CUDA tensor (None passes through);
+    `dtype` ("bf16" or "f32") is checked when given."""
     if t is None:
         return None
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None:
+        import torch
+        want = torch.bfloat16 if dtype == "bf16" else torch.float32
+        if t.dtype != want:
+            raise ValueError("expected a %s tensor, got %s" % (want, t.dtype))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -47,45 +53,50 @@ def _ok(st, what):
 # ---------------------------------------------------------------------------
 def gd_nn_conv3x3(xa, ca, up_a, xb, cb, ntiles, h, w, wt, bias, co, relu, mask=None, y=None,
                   yf=None, stream=None) -> int:
-    return lib().gd_nn_conv3x3(_p(xa), ca, up_a, _p(xb), cb, ntiles, h, w, _p(wt), _p(bias), co,
-                               int(relu), _p(mask), _p(y), _p(yf), _s(stream))
+    return lib().gd_nn_conv3x3(_p(xa, "bf16"), ca, up_a, _p(xb, "bf16"), cb, ntiles, h, w,
+                               _p(wt, "bf16"), _p(bias, "f32"), co, int(relu), _p(mask, "bf16"),
+                               _p(y, "bf16"), _p(yf, "f32"), _s(stream))
 
 
 def gd_nn_conv3x3_wgrad(xa, ca, up_a, xb, cb, ntiles, h, w, dy, co, dw, stream=None) -> int:
-    return lib().gd_nn_conv3x3_wgrad(_p(xa), ca, up_a, _p(xb), cb, ntiles, h, w, _p(dy), co,
-                                     _p(dw), _s(stream))
+    return lib().gd_nn_conv3x3_wgrad(_p(xa, "bf16"), ca, up_a, _p(xb, "bf16"), cb, ntiles, h, w,
+                                     _p(dy, "bf16"), co, _p(dw, "f32"), _s(stream))
 
 
 def gd_nn_bias_grad(dy, npix, co, db, stream=None) -> int:
-    return lib().gd_nn_bias_grad(_p(dy), npix, co, _p(db), _s(stream))
+    return lib().gd_nn_bias_grad(_p(dy, "bf16"), npix, co, _p(db, "f32"), _s(stream))
 
 
 def gd_nn_flip_weights(w, co, ci, w16=None, wf16=None, stream=None) -> int:
-    return lib().gd_nn_flip_weights(_p(w), co, ci, _p(w16), _p(wf16), _s(stream))
+    return lib().gd_nn_flip_weights(_p(w, "f32"), co, ci, _p(w16, "bf16"), _p(wf16, "bf16"),
+                                    _s(stream))
 
 
 def gd_nn_pool2(x, ntiles, h, w, c, y, stream=None) -> int:
-    return lib().gd_nn_pool2(_p(x), ntiles, h, w, c, _p(y), _s(stream))
+    return lib().gd_nn_pool2(_p(x, "bf16"), ntiles, h, w, c, _p(y, "bf16"), _s(stream))
 
 
 def gd_nn_pool2_backward(dp, skip, skip_stride, skip_off, mask, ntiles, h, w, c, out,
                          stream=None) -> int:
-    return lib().gd_nn_pool2_backward(_p(dp), _p(skip), skip_stride, skip_off, _p(mask), ntiles,
-                                      h, w, c, _p(out), _s(stream))
+    return lib().gd_nn_pool2_backward(_p(dp, "bf16"), _p(skip, "bf16"), skip_stride, skip_off,
+                                      _p(mask, "bf16"), ntiles, h, w, c, _p(out, "bf16"), _s(stream))
 
 
 def gd_nn_up2_backward(dk, ck, c, mask, ntiles, h, w, out, stream=None) -> int:
-    return lib().gd_nn_up2_backward(_p(dk), ck, c, _p(mask), ntiles, h, w, _p(out), _s(stream))
+    return lib().gd_nn_up2_backward(_p(dk, "bf16"), ck, c, _p(mask, "bf16"), ntiles, h, w,
+                                    _p(out, "bf16"), _s(stream))
 
 
 def gd_nn_adam(p, g, m, v, lr, b1, b2, eps, t, stream=None) -> int:
-    return lib().gd_nn_adam(_p(p), _p(g), _p(m), _p(v), p.numel(), lr, b1, b2, eps, t, _s(stream))
+    return lib().gd_nn_adam(_p(p, "f32"), _p(g, "f32"), _p(m, "f32"), _p(v, "f32"), p.numel(), lr,
+                            b1, b2, eps, t, _s(stream))
 
 
 def gd_learn_stack_tiles(I, I_sub, nx, ny, nz, th, tw, tc, tile0, ntiles, shift, scale, x=None,
                          xf=None, stream=None) -> int:
-    return lib().gd_learn_stack_tiles(_p(I), _p(I_sub), nx, ny, nz, th, tw, tc, tile0, ntiles,
-                                      shift, scale, _p(x), _p(xf), _s(stream))
+    return lib().gd_learn_stack_tiles(_p(I, "f32"), _p(I_sub, "f32"), nx, ny, nz, th, tw, tc, tile0,
+                                      ntiles, shift, scale, _p(x, "bf16"), _p(xf, "f32"),
+                                      _s(stream))
 
 
 # ---------------------------------------------------------------------------
@@ -145,7 +156,8 @@ def gd_learn_get_grads(net: Net) -> np.ndarray:
 
 
 def gd_learn_forward(net: Net, x, batch, yf) -> int:
-    return _ok(lib().gd_learn_forward(net.handle, _p(x), batch, _p(yf)), "gd_learn_forward")
+    return _ok(lib().gd_learn_forward(net.handle, _p(x, "bf16"), batch, _p(yf, "f32")),
+               "gd_learn_forward")
 
 
 def gd_learn_train_step(net: Net, x_pool, t_pool, idx=None, batch=None, lr=1e-3) -> float:
@@ -157,21 +169,24 @@ def gd_learn_train_step(net: Net, x_pool, t_pool, idx=None, batch=None, lr=1e-3)
     else:
         ip = None
     loss = ctypes.c_double(0.0)
-    st = lib().gd_learn_train_step(net.handle, _p(x_pool), _p(t_pool), ip, int(batch), float(lr),
-                                   ctypes.byref(loss))
+    pool = x_pool.shape[0]
+    if t_pool.shape[0] != pool:
+        raise ValueError("x_pool and t_pool hold different numbers of tiles")
+    st = lib().gd_learn_train_step(net.handle, _p(x_pool, "bf16"), _p(t_pool, "f32"), int(pool), ip,
+                                   int(batch), float(lr), ctypes.byref(loss))
     if st != GD_OK:
         raise GdError(st, (lib().gd_learn_last_error(net.handle) or b"").decode())
     return loss.value
 
 
 def gd_learn_predict_stack(net: Net, I0, nx, ny, nz, in_shift, in_scale, out_scale, x0) -> int:
-    return _ok(lib().gd_learn_predict_stack(net.handle, _p(I0), nx, ny, nz, in_shift, in_scale,
-                                            out_scale, _p(x0)), "gd_learn_predict_stack")
+    return _ok(lib().gd_learn_predict_stack(net.handle, _p(I0, "f32"), nx, ny, nz, in_shift, in_scale,
+                                            out_scale, _p(x0, "f32")), "gd_learn_predict_stack")
 
 
 def gd_learn_lowmodes(net: Net, I0, x, nx, ny, nz, w, K) -> int:
     from . import _weights
-    return _ok(lib().gd_learn_lowmodes(net.handle, _p(I0), _p(x), nx, ny, nz, _weights(w), K),
+    return _ok(lib().gd_learn_lowmodes(net.handle, _p(I0, "f32"), _p(x, "f32"), nx, ny, nz, _weights(w), K),
                "gd_learn_lowmodes")
 
 

@@ -80,3 +80,21 @@ def test_poisoned_batch_is_reported_as_diverged(torch):
     finally:
         gd.gd_batch_destroy(b)
     assert r["status"] == gd.GD_ERR_DIVERGED, r
+
+
+def test_tensor_core_kernels_bounded_wait_reports_timeout_and_recovers():
+    """The learned guess's tcgen05 kernels share the solver's failure path: a
+    bounded wait that runs out raises a device flag, the call returns
+    GD_ERR_TIMEOUT, and the next call runs normally (no GPU fault involved:
+    the wait is on a barrier that nothing arrives at)."""
+    import numpy as np
+    import torch
+    from paper_1310_0041_gb300 import learn
+    gd.build()
+    assert gd.lib().gd_nn_selftest_wait(1000) == gd.GD_ERR_TIMEOUT
+    x = torch.ones((1, 8, 8, 16), dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros((16, 9, 16), dtype=torch.bfloat16, device="cuda")
+    w[:, 4, :] = torch.eye(16, dtype=torch.bfloat16, device="cuda")  # the centre tap: identity
+    y = torch.empty((1, 8, 8, 16), dtype=torch.float32, device="cuda")
+    assert learn.gd_nn_conv3x3(x, 16, 1, None, 0, 1, 8, 8, w, None, 16, 0, yf=y) == gd.GD_OK
+    assert np.array_equal(y.cpu().numpy(), np.ones((1, 8, 8, 16), np.float32))
