@@ -35,6 +35,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 
@@ -1596,30 +1597,74 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// z chunking: a few waves of resident CTAs; coupled chunks are even and >= 16
-// planes deep (each chunk re-reads a few halo planes)
-int pick_zchunk(int tiles, int nz, bool coupled, int ctas_per_sm) {
-  const long target = (long)sm_count() * ctas_per_sm * 4;
-  long chunks = (target + tiles - 1) / tiles;
-  const int min_chunk = coupled ? 16 : 1;
-  const long max_chunks = (nz + min_chunk - 1) / min_chunk;
-  if (chunks > max_chunks) chunks = max_chunks;
-  if (chunks < 1) chunks = 1;
-  int zc = (int)((nz + chunks - 1) / chunks);
-  if (coupled && (zc & 1)) ++zc;
+// z chunking.  A CTA marches one chunk of planes of one column tile; all
+// CTAs of a launch do (nearly) the same work, so a launch takes about
+// ceil(CTAs / resident slots) CTA durations, and a CTA's duration grows with
+// its chunk plus the planes it touches beyond it (coupled levels: the red
+// pass below the chunk and the x planes around it, about three planes; one
+// for the pipeline fill otherwise).  The chunk count minimises that product:
+// a nearly empty last wave costs as much as a full one.  Chunks are even on
+// coupled levels and where z is coarsened (both children of a coarse plane
+// in one chunk).
+struct ZPlan {
+  int tiles, nz;
+  bool coupled, even;
+  int *nblocks_out;
+};
+int pick_zchunk(const ZPlan &p, int slots) {
+  const int h = p.coupled ? 3 : 1;
+  const int min_chunk = p.coupled ? 4 : 1;
+  const int max_chunks = std::max(1, p.nz / min_chunk);
+  long best_cost = -1;
+  int best = p.nz + (p.even && (p.nz & 1) ? 1 : 0);
+  for (int c = 1; c <= max_chunks; ++c) {
+    int zc = (p.nz + c - 1) / c;
+    if (p.even && (zc & 1)) ++zc;
+    const long gz = (p.nz + zc - 1) / zc;
+    const long waves = ((long)p.tiles * gz + slots - 1) / slots;
+    const long cost = waves * (zc + h);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  return best;
+}
+// resident CTAs of one instantiation on the whole GPU (queried once)
+template <typename K>
+int resident_slots(K kernel, int threads, size_t smem, int &cache) {
+  if (!cache) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 1;
+    }
+    cache = n * sm_count();
+  }
+  return cache;
+}
+// fills in the z extent of the grid and the chunk for one instantiation
+template <typename K>
+int plan_z(K kernel, int threads, size_t smem, int &cache, const ZPlan &p, dim3 &grid) {
+  const int zc = pick_zchunk(p, resident_slots(kernel, threads, smem, cache));
+  grid.z = (p.nz + zc - 1) / zc;
+  if (p.nblocks_out) *p.nblocks_out = (int)(grid.x * grid.y * grid.z);
   return zc;
 }
 
 template <typename T, typename TC, bool Z, bool P, bool S, bool U, bool C>
 cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc,
-                          const ZSweepArgs &a, dim3 grid, cudaStream_t st) {
+                          const ZSweepArgs &a0, dim3 grid, const ZPlan &zp, cudaStream_t st) {
   const size_t bytes = SweepGeo<T>::smem_bytes();
   static bool attr = false;
+  static int slots = 0;
   if (!attr) {
     cudaError_t e = set_smem(k_zsweep<T, TC, Z, P, S, U, C>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  ZSweepArgs a = a0;
+  a.zchunk = plan_z(k_zsweep<T, TC, Z, P, S, U, C>, SweepGeo<T>::NT, bytes, slots, zp, grid);
   k_zsweep<T, TC, Z, P, S, U, C><<<grid, SweepGeo<T>::NT, bytes, st>>>(mx, mb, mc, a);
   return cudaGetLastError();
 }
@@ -1627,72 +1672,77 @@ bool level_uniform(const LevelDev &L) { return L.sx == L.lx && L.sy == L.ly && L
 bool level_coupled(const LevelDev &L) { return L.wz != 0.f && L.nz > 1; }
 template <typename T, typename TC, bool Z, bool P, bool S>
 cudaError_t run_zsweep(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc,
-                       const ZSweepArgs &a, dim3 grid, cudaStream_t st) {
+                       const ZSweepArgs &a, dim3 grid, const ZPlan &zp, cudaStream_t st) {
   const bool u = level_uniform(a.L), c = level_coupled(a.L);
-  if (u && c) return run_zsweep_uc<T, TC, Z, P, S, true, true>(mx, mb, mc, a, grid, st);
-  if (u) return run_zsweep_uc<T, TC, Z, P, S, true, false>(mx, mb, mc, a, grid, st);
-  if (c) return run_zsweep_uc<T, TC, Z, P, S, false, true>(mx, mb, mc, a, grid, st);
-  return run_zsweep_uc<T, TC, Z, P, S, false, false>(mx, mb, mc, a, grid, st);
+  if (u && c) return run_zsweep_uc<T, TC, Z, P, S, true, true>(mx, mb, mc, a, grid, zp, st);
+  if (u) return run_zsweep_uc<T, TC, Z, P, S, true, false>(mx, mb, mc, a, grid, zp, st);
+  if (c) return run_zsweep_uc<T, TC, Z, P, S, false, true>(mx, mb, mc, a, grid, zp, st);
+  return run_zsweep_uc<T, TC, Z, P, S, false, false>(mx, mb, mc, a, grid, zp, st);
 }
 // the five sweep variants of a V-cycle; the coarse type matters only with
 // the prolongation
 template <typename T, typename TC>
 cudaError_t run_zsweep_variant(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc,
                                const ZSweepArgs &a, bool zero_in, bool prolong, bool sum, dim3 grid,
-                               cudaStream_t st) {
-  if (zero_in && !prolong && !sum) return run_zsweep<T, T, true, false, false>(mx, mb, mc, a, grid, st);
-  if (!zero_in && prolong && !sum) return run_zsweep<T, TC, false, true, false>(mx, mb, mc, a, grid, st);
-  if (!zero_in && prolong && sum) return run_zsweep<T, TC, false, true, true>(mx, mb, mc, a, grid, st);
-  if (!zero_in && !prolong && !sum) return run_zsweep<T, T, false, false, false>(mx, mb, mc, a, grid, st);
-  if (!zero_in && !prolong && sum) return run_zsweep<T, T, false, false, true>(mx, mb, mc, a, grid, st);
+                               const ZPlan &zp, cudaStream_t st) {
+  if (zero_in && !prolong && !sum) return run_zsweep<T, T, true, false, false>(mx, mb, mc, a, grid, zp, st);
+  if (!zero_in && prolong && !sum) return run_zsweep<T, TC, false, true, false>(mx, mb, mc, a, grid, zp, st);
+  if (!zero_in && prolong && sum) return run_zsweep<T, TC, false, true, true>(mx, mb, mc, a, grid, zp, st);
+  if (!zero_in && !prolong && !sum) return run_zsweep<T, T, false, false, false>(mx, mb, mc, a, grid, zp, st);
+  if (!zero_in && !prolong && sum) return run_zsweep<T, T, false, false, true>(mx, mb, mc, a, grid, zp, st);
   return cudaErrorNotSupported;
 }
 template <typename T, typename TC, bool U, bool C>
-cudaError_t run_zrestrict(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
-                          dim3 grid, cudaStream_t st) {
+cudaError_t run_zrestrict(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a0,
+                          dim3 grid, const ZPlan &zp, cudaStream_t st) {
   const size_t bytes = RestrictGeo<T>::smem_bytes();
   static bool attr = false;
+  static int slots = 0;
   if (!attr) {
     cudaError_t e = set_smem(k_zrestrict<T, TC, U, C>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  ZSweepArgs a = a0;
+  a.zchunk = plan_z(k_zrestrict<T, TC, U, C>, RestrictGeo<T>::NT, bytes, slots, zp, grid);
   k_zrestrict<T, TC, U, C><<<grid, RestrictGeo<T>::NT, bytes, st>>>(mx, mb, a);
   return cudaGetLastError();
 }
 template <typename T, typename TC>
 cudaError_t run_zrestrict_t(const CUtensorMap &mx, const CUtensorMap &mb, const ZSweepArgs &a,
-                            dim3 grid, cudaStream_t st) {
+                            dim3 grid, const ZPlan &zp, cudaStream_t st) {
   const bool u = level_uniform(a.L), c = level_coupled(a.L);
-  if (u && c) return run_zrestrict<T, TC, true, true>(mx, mb, a, grid, st);
-  if (u) return run_zrestrict<T, TC, true, false>(mx, mb, a, grid, st);
-  if (c) return run_zrestrict<T, TC, false, true>(mx, mb, a, grid, st);
-  return run_zrestrict<T, TC, false, false>(mx, mb, a, grid, st);
+  if (u && c) return run_zrestrict<T, TC, true, true>(mx, mb, a, grid, zp, st);
+  if (u) return run_zrestrict<T, TC, true, false>(mx, mb, a, grid, zp, st);
+  if (c) return run_zrestrict<T, TC, false, true>(mx, mb, a, grid, zp, st);
+  return run_zrestrict<T, TC, false, false>(mx, mb, a, grid, zp, st);
 }
 
 template <typename TE, int RHS, bool XL, bool E, bool ACC>
-cudaError_t run_zouter(const CUtensorMap *m, const OuterArgs &a, int zchunk, double *err, dim3 grid,
+cudaError_t run_zouter(const CUtensorMap *m, const OuterArgs &a, const ZPlan &zp, double *err, dim3 grid,
                        cudaStream_t st) {
   const size_t bytes = OuterGeo::smem_bytes(XL, E, RHS == RHS_SP, (int)sizeof(TE));
   static bool attr = false;
+  static int slots = 0;
   if (!attr) {
     cudaError_t e = set_smem(k_zouter<TE, RHS, XL, E, ACC>, bytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  const int zchunk = plan_z(k_zouter<TE, RHS, XL, E, ACC>, OuterGeo::NT, bytes, slots, zp, grid);
   k_zouter<TE, RHS, XL, E, ACC><<<grid, OuterGeo::NT, bytes, st>>>(m[0], m[1], m[2], m[3], m[4], a, zchunk,
                                                                     err);
   return cudaGetLastError();
 }
 template <typename TE>
-cudaError_t run_zouter_t(const CUtensorMap *m, const OuterArgs &a, int rhs_mode, int zchunk, double *err,
+cudaError_t run_zouter_t(const CUtensorMap *m, const OuterArgs &a, int rhs_mode, const ZPlan &zp, double *err,
                          dim3 grid, cudaStream_t st) {
   const bool xl = a.xl_in != nullptr, e = a.e != nullptr;
-#define GD_ZO2(R, ACC)                                                                 \
-  if (xl && e) return run_zouter<TE, R, true, true, ACC>(m, a, zchunk, err, grid, st);  \
-  if (xl) return run_zouter<TE, R, true, false, ACC>(m, a, zchunk, err, grid, st);      \
-  if (e) return run_zouter<TE, R, false, true, ACC>(m, a, zchunk, err, grid, st);       \
-  return run_zouter<TE, R, false, false, ACC>(m, a, zchunk, err, grid, st);
+#define GD_ZO2(R, ACC)                                                              \
+  if (xl && e) return run_zouter<TE, R, true, true, ACC>(m, a, zp, err, grid, st);  \
+  if (xl) return run_zouter<TE, R, true, false, ACC>(m, a, zp, err, grid, st);      \
+  if (e) return run_zouter<TE, R, false, true, ACC>(m, a, zp, err, grid, st);       \
+  return run_zouter<TE, R, false, false, ACC>(m, a, zp, err, grid, st);
 #define GD_ZO(R)    \
   if (a.accurate) { \
     GD_ZO2(R, true) \
@@ -1720,10 +1770,8 @@ cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zer
   if (!make_map(&mb, b, L.nx, L.ny, L.nz, box_w(esz), rows_b, esz)) return cudaErrorNotSupported;
   if (((uintptr_t)a.xout & 15) != 0) return cudaErrorNotSupported;
   const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
-  a.zchunk = pick_zchunk(gx * gy, L.nz, level_coupled(L), 2);
-  const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
-  if (nblocks_out) *nblocks_out = gx * gy * gz;
-  dim3 grid(gx, gy, gz);
+  const ZPlan zp{gx * gy, L.nz, level_coupled(L), level_coupled(L), nblocks_out};
+  dim3 grid(gx, gy, 1);
   // prolongation: a map over the coarse level for the L2 prefetch of the
   // boxes the correction reads (x: 32 coarse cells + alignment margins when
   // x is coarsened, else the fine box; y: the 36 fine box rows)
@@ -1740,11 +1788,11 @@ cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zer
     if (!a.cpf) mc = mx;
   }
   if (esz == 4 && esz_c == 2 && prolong)
-    return run_zsweep_variant<float, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
-  if (esz == 4) return run_zsweep_variant<float, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
+    return run_zsweep_variant<float, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
+  if (esz == 4) return run_zsweep_variant<float, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
   if (esz_c == 2 || !prolong)
-    return run_zsweep_variant<half_t, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
-  return run_zsweep_variant<half_t, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, st);
+    return run_zsweep_variant<half_t, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
+  return run_zsweep_variant<half_t, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
 }
 
 cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz, int esz_c, cudaStream_t st) {
@@ -1755,14 +1803,12 @@ cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz
   if (((uintptr_t)a.bc & 15) != 0) return cudaErrorNotSupported;
   const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
   const bool coupled = level_coupled(L);
-  a.zchunk = pick_zchunk(gx * gy, L.nz, coupled || a.fz, 2);
-  if (a.fz && (a.zchunk & 1)) ++a.zchunk;  // both children of a coarse plane in one chunk
-  const int gz = (L.nz + a.zchunk - 1) / a.zchunk;
-  dim3 grid(gx, gy, gz);
-  if (esz == 4 && esz_c == 2) return run_zrestrict_t<float, half_t>(mx, mb, a, grid, st);
-  if (esz == 4) return run_zrestrict_t<float, float>(mx, mb, a, grid, st);
-  if (esz_c == 2) return run_zrestrict_t<half_t, half_t>(mx, mb, a, grid, st);
-  return run_zrestrict_t<half_t, float>(mx, mb, a, grid, st);
+  const ZPlan zp{gx * gy, L.nz, coupled, coupled || a.fz != 0, nullptr};
+  dim3 grid(gx, gy, 1);
+  if (esz == 4 && esz_c == 2) return run_zrestrict_t<float, half_t>(mx, mb, a, grid, zp, st);
+  if (esz == 4) return run_zrestrict_t<float, float>(mx, mb, a, grid, zp, st);
+  if (esz_c == 2) return run_zrestrict_t<half_t, half_t>(mx, mb, a, grid, zp, st);
+  return run_zrestrict_t<half_t, float>(mx, mb, a, grid, zp, st);
 }
 
 cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, int esz_e, double *err, int *nblocks_out,
@@ -1782,12 +1828,10 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, int esz_e, double *e
     return cudaErrorNotSupported;
   const int gx = (a.nx + ZX - 1) / ZX, gy = (a.ny + OuterGeo::OY - 1) / OuterGeo::OY;
   const bool coupled = (a.bz != 0.f) && (a.nz > 1);
-  const int zchunk = pick_zchunk(gx * gy, a.nz, coupled, 2);
-  const int gz = (a.nz + zchunk - 1) / zchunk;
-  if (nblocks_out) *nblocks_out = gx * gy * gz;
-  dim3 grid(gx, gy, gz);
-  if (esz_e == 2) return run_zouter_t<half_t>(m, a, rhs_mode, zchunk, err, grid, st);
-  return run_zouter_t<float>(m, a, rhs_mode, zchunk, err, grid, st);
+  const ZPlan zp{gx * gy, a.nz, coupled, coupled, nblocks_out};
+  dim3 grid(gx, gy, 1);
+  if (esz_e == 2) return run_zouter_t<half_t>(m, a, rhs_mode, zp, err, grid, st);
+  return run_zouter_t<float>(m, a, rhs_mode, zp, err, grid, st);
 }
 
 int zouter_max_blocks(int nx, int ny, int nz) {
