@@ -194,6 +194,7 @@ struct St<float> {
   __device__ static __forceinline__ void st1(float *p, float v) { *p = v; }
   __device__ static __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
   __device__ static __forceinline__ float2 ldg2(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+  __device__ static __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
   __device__ static __forceinline__ void stg2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 };
 template <>
@@ -219,6 +220,9 @@ struct St<__nv_bfloat16> {
     const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
   }
+  __device__ static __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+  }
   __device__ static __forceinline__ void stg2(__nv_bfloat16 *p, float2 v) {
     *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
   }
@@ -237,23 +241,34 @@ __host__ __device__ constexpr int pad128(int n) {
 // a service warp (TMA issue, mbarrier polling) and a ring warp (the red ring).
 constexpr int SY = 32;  // sweep tile rows
 
-template <typename T>
+template <typename T, typename TC = T, bool PRO = false>
 struct SweepGeo {
   static constexpr int W = St<T>::W, OFF = St<T>::OFF;
   static constexpr int H = 2;                    // x box halo rows
   static constexpr int XH = SY + 2 * H;          // x box rows j0-2 .. j0+SY+1
   static constexpr int BH = SY + 2 * (H - 1);    // b box rows j0-1 .. j0+SY
-  static constexpr int PFS = 2;                  // planes in flight ahead of use
+  static constexpr int PFS = 2;                  // x planes in flight ahead of use
+  // b planes in flight: the prolongation sweep gives up one (its b copies
+  // land within one step) so that its two coarse staging slots fit beside
+  // the rings at two CTAs per SM
+  static constexpr int PFSB = PRO ? 1 : 2;
   // ring depths: an x plane is last read two steps after its red pass (its
   // red cells are the z-neighbours of the next black pass but one), a b
   // plane one step after it (by the black pass)
   static constexpr int XR = 6;                   // needs PFS + 4
-  static constexpr int BR = 4;                   // needs PFS + 2 (power of two)
-  static_assert(XR >= PFS + 4 && BR >= PFS + 2, "ring depth");
+  static constexpr int BR = PFSB + 2;
+  static_assert(XR >= PFS + 4, "ring depth");
   static constexpr int XS = pad128<T>(XH * W);   // elements per x slot
   static constexpr int BS = pad128<T>(BH * W);
   static constexpr int BOFF = XR * XS;           // b slots
-  static constexpr int MOFF = BOFF + BR * BS;    // mbarriers (element offset)
+  // coarse staging (prolongation): two slots, each the largest coarse box:
+  // the x box's extent in coarse elements, or 80 wide for a bfloat16 level
+  // under a float32 one (its box starts 8 elements left of the tile, which is
+  // where 16-byte alignment puts it)
+  static constexpr int CW_MAX = (sizeof(T) == 4 && sizeof(TC) == 2) ? 80 : W;
+  static constexpr size_t CSB = PRO ? (XH * CW_MAX * sizeof(TC) + 127) / 128 * 128 : 0;
+  static constexpr size_t COFF_B = sizeof(T) * (size_t)(BOFF + BR * BS);  // bytes
+  static constexpr size_t MOFF_B = COFF_B + 2 * CSB;                      // mbarriers (bytes)
   static constexpr int TILE_WARPS = 8;
   static constexpr int NT = 32 * (TILE_WARPS + 2);  // + the service and ring warps
   static constexpr int SVC = 32 * TILE_WARPS;       // first thread of the service warp
@@ -264,7 +279,7 @@ struct SweepGeo {
   static constexpr int RING_IT = NRING / 32;
   static_assert(NRING % 32 == 0, "ring cells per lane");
   __host__ __device__ static constexpr size_t smem_bytes() {
-    return sizeof(T) * (size_t)MOFF + sizeof(uint64_t) * (XR + BR) + sizeof(double) * 32 + 16;
+    return MOFF_B + sizeof(uint64_t) * (XR + BR + 2) + sizeof(double) * 32 + 16;
   }
 };
 
@@ -276,11 +291,11 @@ struct SweepGeo {
 // from the shared-memory rings), so one CTA barrier per plane orders all the
 // in-plane exchanges.
 template <typename T, typename TC, bool ZERO_IN, bool PROLONG, bool SUM, bool UNIFORM, bool COUPLED>
-__global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
+__global__ void __launch_bounds__(SweepGeo<T, TC, PROLONG>::NT, 2) k_zsweep(const __grid_constant__ CUtensorMap tmx,
                                                                const __grid_constant__ CUtensorMap tmb,
                                                                const __grid_constant__ CUtensorMap tmc,
                                                                const ZSweepArgs a) {
-  using G = SweepGeo<T>;
+  using G = SweepGeo<T, TC, PROLONG>;
   using S = St<T>;
   constexpr int H = G::H;
   constexpr int PFS = G::PFS;
@@ -290,9 +305,11 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
   T *sm = reinterpret_cast<T *>(zsm);
   auto lds4 = [&](int off) { return S::ld4(sm + off); };
   auto sts4 = [&](int off, float4 v) { S::st4(sm + off, v); };
-  uint64_t *xbar = reinterpret_cast<uint64_t *>(sm + G::MOFF);
+  uint64_t *xbar = reinterpret_cast<uint64_t *>(reinterpret_cast<char *>(zsm) + G::MOFF_B);
   uint64_t *bbar = xbar + G::XR;
-  double *dsh = reinterpret_cast<double *>(bbar + G::BR);
+  uint64_t *cbar = bbar + G::BR;  // coarse staging slots (prolongation)
+  double *dsh = reinterpret_cast<double *>(cbar + 2);
+  TC *cstage = reinterpret_cast<TC *>(reinterpret_cast<char *>(zsm) + G::COFF_B);
   __shared__ int abort_flag;
 
   const LevelDev &L = a.L;
@@ -327,6 +344,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
     } else {
       for (int q = 0; q < G::XR; ++q) mbar_init(&xbar[q], 1);
       for (int q = 0; q < G::BR; ++q) mbar_init(&bbar[q], 1);
+      for (int q = 0; q < 2; ++q) mbar_init(&cbar[q], 1);
       fence_mbar_init();
     }
   }
@@ -357,9 +375,45 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
   // x plane issued at step t, and the last x plane a step reads or corrects
   auto x_issue_at = [&](int t) { return t + (zc ? 1 : 0) + PFS; };
   auto x_need_at = [&](int t) { return t + (zc ? 1 : 0) + (PROLONG ? 1 : 0); };
+  // ---- coarse staging of the prolongation: step t corrects x plane
+  // corr_plane(t) from coarse plane corr_plane(t) >> fz, which the service
+  // lane brings by TMA into one of two slots a step ahead (a slot is reused
+  // once the steps that read its previous plane are past a CTA barrier)
+  const bool stage = PROLONG && a.cpf;
+  constexpr int AC = 16 / (int)sizeof(TC);  // TMA x alignment in coarse elements
+  // the coarse box: its x start (16-byte aligned) and extent
+  const int cxs = a.fx ? (i0 >> 1) - AC : (G::CW_MAX != W ? i0 - 8 : i0 - OFF);
+  const int cw = a.fx ? 32 + 2 * AC : G::CW_MAX, ch = a.fy ? G::XH / 2 : G::XH;
+  auto corr_plane = [&](int t) { return zc ? t + 2 : t + 1; };
+  const int c_lo = corr_plane(t0) >> a.fz;
+  int cissued = c_lo - 1, cwait = c_lo - 1;
+  auto cslot = [&](int c) { return (c - c_lo) & 1; };
+  auto cpar = [&](int c) { return (uint32_t)((c - c_lo) >> 1) & 1u; };
+  auto issue_c_for = [&](int t) {
+    if (!stage || corr_plane(t) > rx.hi) return;
+    const int c = corr_plane(t) >> a.fz;
+    for (int q = cissued + 1; q <= c; ++q) {
+      const int sl = cslot(q);
+      mbar_expect_tx(&cbar[sl], (uint32_t)(cw * ch * (int)sizeof(TC)));
+      tma_plane(cstage + sl * (int)(G::CSB / sizeof(TC)), &tmc, cxs, (j0 - H) >> a.fy, q, &cbar[sl]);
+      cissued = q;
+    }
+  };
+  auto wait_c_for = [&](int t) -> bool {
+    if (!stage || corr_plane(t) > rx.hi) return true;
+    const int c = min(corr_plane(t) >> a.fz, cissued);
+    bool ok = true;
+    for (int q = cwait + 1; q <= c && ok; ++q) {
+      ok = mbar_wait(&cbar[cslot(q)], cpar(q));
+      if (ok) cwait = q;
+    }
+    return ok;
+  };
   if (tid == G::SVC) {
     for (int p = rx.lo; p < x_issue_at(t0) && p <= rx.hi; ++p) issue_x(p);
-    for (int p = rb.lo; p < t0 + PFS && p <= rb.hi; ++p) issue_b(p);
+    for (int p = rb.lo; p < t0 + G::PFSB && p <= rb.hi; ++p) issue_b(p);
+    issue_c_for(t0);
+    issue_c_for(t0 + 1);
   }
   int xwait = rx.lo - 1, bwait = rb.lo - 1;  // planes whose wait succeeded (service warp)
   auto wait_planes = [&](int ux, int ub) -> bool {
@@ -465,35 +519,79 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
 
   // ---- prolongation by replication: every float4 of the x box inside the
   // domain gets the coarse value of each of its cells (with x coarsened the
-  // four cells take two coarse values; nx % 4 == 0 keeps both loads aligned)
-  constexpr int PQ = G::XH * (W / 4);
-  constexpr int PMAX = PROLONG ? (PQ + G::NT - 1) / G::NT : 1;
+  // four cells take two coarse values; nx % 4 == 0 keeps both loads aligned).
+  // Thread tid takes float4 column tid % QW of box rows tid / QW + k RP, so
+  // its columns (fine, staged and coarse) and its validity in x are fixed.
+  constexpr int QW = W / 4;                       // float4 columns of the box
+  constexpr int RP = G::NT / QW;                  // box rows per pass
+  constexpr int KP = PROLONG ? (G::XH + RP - 1) / RP : 1;
+  const int ccq = tid % QW, crr = tid / QW;
+  const int cgi = i0 - OFF + 4 * ccq;
+  const bool cxok = PROLONG && crr < RP && cgi >= 0 && cgi < nx;
+  const bool cunmasked = !a.fx && !a.fy;
+  const int cxoff = crr * W + 4 * ccq;  // this thread's first float4 in an x slot
+  // its first coarse value in a staging slot (unmasked form: row crr
+  // included)
+  const int ccoff = ((cgi >> a.fx) - cxs) + (cunmasked ? crr * cw : 0);
+  auto add4 = [&](int so, float4 c) {
+    float4 v = lds4(so);
+    v.x += c.x;
+    v.y += c.y;
+    v.z += c.z;
+    v.w += c.w;
+    sts4(so, v);
+  };
+  // the staged form: x plane p += its coarse values from the staging slot
+  auto correct_staged = [&](int p) {
+    const TC *cs = cstage + cslot(p >> a.fz) * (int)(G::CSB / sizeof(TC)) + ccoff;
+    const int xop = xo(p) + cxoff;
+    if (cunmasked) {
+      // the staged box has the x box's cells, and the copy's zero fill gives
+      // every cell outside the domain a correction of 0: no masks
+      if (crr < RP) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k)
+          if (k + 1 < KP || crr + k * RP < G::XH) add4(xop + k * RP * W, St<TC>::ld4(cs + k * RP * cw));
+      }
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const int rr = crr + k * RP, gcj = j0 - H + rr;
+      if (cxok && rr < G::XH && gcj >= 0 && gcj < ny) {
+        const TC *q = cs + (a.fy ? rr >> 1 : rr) * cw;
+        float4 c;
+        if (a.fx) {
+          const float2 c2 = St<TC>::ld2(q);
+          c = make_float4(c2.x, c2.x, c2.y, c2.y);
+        } else {
+          c = St<TC>::ld4(q);
+        }
+        add4(xop + k * RP * W, c);
+      }
+    }
+  };
+  // the direct form (no coarse tensor map, and the planes before the first
+  // step): the coarse values come from global memory
+  const int ccol = max(cgi, 0) >> a.fx;
   int corrected = rx.lo - 1;  // planes that hold the coarse correction
   auto correct_upto = [&](int u) {
     for (int p = corrected + 1; p <= min(u, rx.hi); ++p) {
-      const int xop = xo(p);
-      const TC *xcp = reinterpret_cast<const TC *>(a.xc) + (size_t)(p >> a.fz) * a.ncy * a.ncx;
+      const TC *xcp = reinterpret_cast<const TC *>(a.xc) + (size_t)(p >> a.fz) * a.ncy * a.ncx + ccol;
+      const int xop = xo(p) + cxoff;
 #pragma unroll
-      for (int m = 0; m < PMAX; ++m) {
-        const int q = tid + m * G::NT;
-        const int rr = q / (W / 4), cq = q - rr * (W / 4);
-        const int gci = i0 - OFF + 4 * cq, gcj = j0 - H + rr;
-        if (q < PQ && gci >= 0 && gci < nx && gcj >= 0 && gcj < ny) {
-          const int pc = (gcj >> a.fy) * a.ncx + (gci >> a.fx);
+      for (int k = 0; k < KP; ++k) {
+        const int rr = crr + k * RP, gcj = j0 - H + rr;
+        if (cxok && rr < G::XH && gcj >= 0 && gcj < ny) {
+          const TC *q = xcp + (size_t)(gcj >> a.fy) * a.ncx;
           float4 c;
           if (a.fx) {
-            const float2 c2 = St<TC>::ldg2(xcp + pc);
+            const float2 c2 = St<TC>::ldg2(q);
             c = make_float4(c2.x, c2.x, c2.y, c2.y);
           } else {
-            c = St<TC>::ldg4(xcp + pc);
+            c = St<TC>::ldg4(q);
           }
-          const int so = xop + rr * W + 4 * cq;
-          float4 v = lds4(so);
-          v.x += c.x;
-          v.y += c.y;
-          v.z += c.z;
-          v.w += c.w;
-          sts4(so, v);
+          add4(xop + k * RP * W, c);
         }
       }
       corrected = p;
@@ -503,7 +601,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
   // The service warp polls the mbarriers for the planes of the next step
   // just before the CTA barrier that releases that step.
   bool failed = false;
-  if (svc) failed = !wait_planes(x_need_at(t0), t0);
+  if (svc) failed = !wait_planes(x_need_at(t0), t0) || !wait_c_for(t0);
   if (__syncthreads_or(failed)) abort_flag = 1;
   if (PROLONG && !abort_flag) {
     // the planes the first step reads get their correction before it
@@ -561,20 +659,25 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
       if (tid == G::SVC) {
         fence_proxy_async();
         issue_x(x_issue_at(t));
-        issue_b(t + PFS);
-        // prolongation: warm L2 with the coarse box the correction of a
-        // plane two steps on reads (its loads then hit L2)
+        issue_b(t + G::PFSB);
+        issue_c_for(t + 1);
+        // prolongation: warm L2 with the coarse box of the plane corrected
+        // two steps on (its staging copy, issued a step later, then hits L2)
         if (PROLONG) {
-          const int pn = (zc ? t + 2 : t + 1) + 2;
-          constexpr int AC = 16 / (int)sizeof(TC);  // TMA x alignment in coarse elements
-          if (a.cpf && pn <= rx.hi)
-            prefetch_plane(&tmc, a.fx ? (i0 >> 1) - AC : i0 - OFF, (j0 - H) >> a.fy, pn >> a.fz);
+          const int pn = corr_plane(t) + 2;
+          if (a.cpf && pn <= rx.hi) prefetch_plane(&tmc, cxs, (j0 - H) >> a.fy, pn >> a.fz);
         }
       }
       const int xs_p = (xs_t == (G::XR - 1) * XS) ? 0 : xs_t + XS;   // plane t + 1
       const int xs_m = (xs_t == 0) ? (G::XR - 1) * XS : xs_t - XS;   // plane t - 1
       const int xs_mm = (xs_m == 0) ? (G::XR - 1) * XS : xs_m - XS;  // plane t - 2
-      if (PROLONG) correct_upto(zc ? t + 2 : t + 1);
+      if (PROLONG) {
+        if (stage) {
+          if (corr_plane(t) <= rx.hi) correct_staged(corr_plane(t));
+        } else {
+          correct_upto(corr_plane(t));
+        }
+      }
 
       // ---- red pass of plane t ----
       const bool do_red = t >= red_lo && t <= red_hi;
@@ -664,7 +767,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
       }
       if (!zc) {
         // uncoupled planes: the black pass of plane t reads this red pass
-        if (svc && !failed && t < t1) failed = !wait_planes(x_need_at(t + 1), t + 1);
+        if (svc && !failed && t < t1) failed = !wait_planes(x_need_at(t + 1), t + 1) || !wait_c_for(t + 1);
         if (__syncthreads_or(failed)) {
           abort_flag = 1;
           break;
@@ -726,7 +829,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
       have_prev = do_red;
       if (zc) {
         // the next black pass reads this red pass; slots of old planes are free
-        if (svc && !failed && t < t1) failed = !wait_planes(x_need_at(t + 1), t + 1);
+        if (svc && !failed && t < t1) failed = !wait_planes(x_need_at(t + 1), t + 1) || !wait_c_for(t + 1);
         if (__syncthreads_or(failed)) {
           abort_flag = 1;
           break;
@@ -752,6 +855,7 @@ __global__ void __launch_bounds__(SweepGeo<T>::NT, 2) k_zsweep(const __grid_cons
       a.err[0] = 1.0;
       for (int p = xwait + 1; p <= xissued; ++p) mbar_wait(&xbar[rx.slot(p)], rx.parity(p));
       for (int p = bwait + 1; p <= bissued; ++p) mbar_wait(&bbar[rb.slot(p)], rb.parity(p));
+      for (int q = cwait + 1; q <= cissued; ++q) mbar_wait(&cbar[cslot(q)], cpar(q));
     }
     return;
   }
@@ -1655,7 +1759,7 @@ int plan_z(K kernel, int threads, size_t smem, int &cache, const ZPlan &p, dim3 
 template <typename T, typename TC, bool Z, bool P, bool S, bool U, bool C>
 cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc,
                           const ZSweepArgs &a0, dim3 grid, const ZPlan &zp, cudaStream_t st) {
-  const size_t bytes = SweepGeo<T>::smem_bytes();
+  const size_t bytes = SweepGeo<T, TC, P>::smem_bytes();
   static bool attr = false;
   static int slots = 0;
   if (!attr) {
@@ -1664,8 +1768,8 @@ cudaError_t run_zsweep_uc(const CUtensorMap &mx, const CUtensorMap &mb, const CU
     attr = true;
   }
   ZSweepArgs a = a0;
-  a.zchunk = plan_z(k_zsweep<T, TC, Z, P, S, U, C>, SweepGeo<T>::NT, bytes, slots, zp, grid);
-  k_zsweep<T, TC, Z, P, S, U, C><<<grid, SweepGeo<T>::NT, bytes, st>>>(mx, mb, mc, a);
+  a.zchunk = plan_z(k_zsweep<T, TC, Z, P, S, U, C>, SweepGeo<T, TC, P>::NT, bytes, slots, zp, grid);
+  k_zsweep<T, TC, Z, P, S, U, C><<<grid, SweepGeo<T, TC, P>::NT, bytes, st>>>(mx, mb, mc, a);
   return cudaGetLastError();
 }
 bool level_uniform(const LevelDev &L) { return L.sx == L.lx && L.sy == L.ly && L.sz == L.lz; }
@@ -1772,17 +1876,17 @@ cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zer
   const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
   const ZPlan zp{gx * gy, L.nz, level_coupled(L), level_coupled(L), nblocks_out};
   dim3 grid(gx, gy, 1);
-  // prolongation: a map over the coarse level for the L2 prefetch of the
-  // boxes the correction reads (x: 32 coarse cells + alignment margins when
-  // x is coarsened, else the fine box; y: the 36 fine box rows)
+  // prolongation: a map over the coarse level for the staging copies (and
+  // L2 prefetches) of the boxes the correction reads (x: 32 coarse cells +
+  // alignment margins when x is coarsened, else the fine box -- 80 wide from
+  // 8 cells left of the tile for a bfloat16 level under a float32 one, where
+  // 16-byte alignment puts its start; y: the 36 fine box rows, or 18 when y
+  // is coarsened).  Without the map the correction loads from global memory.
   CUtensorMap mc = mx;
   a.cpf = 0;
-  // (a float32 level above a bfloat16 one prefetches only when x is halved:
-  // its unhalved box starts i0 - 4 elements in, which is not 16-byte aligned
-  // in bfloat16)
-  if (prolong && !(esz == 4 && esz_c == 2 && !a.fx)) {
+  if (prolong) {
     const int ac = 16 / esz_c, ncz = a.fz ? (L.nz + 1) / 2 : L.nz;
-    const int cw = a.fx ? 32 + 2 * ac : box_w(esz), ch = a.fy ? rows_x / 2 : rows_x;
+    const int cw = a.fx ? 32 + 2 * ac : (esz == 4 && esz_c == 2 ? 80 : box_w(esz)), ch = a.fy ? rows_x / 2 : rows_x;
     // (a coarse level whose rows break TMA's alignment is simply not prefetched)
     a.cpf = make_map(&mc, a.xc, a.ncx, a.ncy, ncz, cw, ch, esz_c) ? 1 : 0;
     if (!a.cpf) mc = mx;
