@@ -15,7 +15,9 @@
   distributed two-level iteration converges to the exact solution.
 """
 import os
+import queue
 import socket
+import time
 
 import numpy as np
 import pytest
@@ -31,6 +33,9 @@ def _free_port():
 
 
 def _run(target, world=2, *args):
+    """Runs target(rank, world, port, queue, *args) on `world` spawned ranks
+    and returns {rank: the value it put}.  A rank that exits without putting
+    its value fails the test at once (the other ranks are terminated)."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -38,9 +43,26 @@ def _run(target, world=2, *args):
     for p in procs:
         p.start()
     out = {}
-    for _ in range(world):
-        r, v = q.get(timeout=300)
-        out[r] = v
+    deadline = time.monotonic() + 300
+    try:
+        while len(out) < world:
+            try:
+                r, v = q.get(timeout=1.0)
+                out[r] = v
+                continue
+            except queue.Empty:
+                pass
+            dead = [(i, p.exitcode) for i, p in enumerate(procs) if p.exitcode not in (None, 0)]
+            if dead:
+                pytest.fail("rank(s) %s exited without a result (exit codes %s)" %
+                            ([i for i, _ in dead], [c for _, c in dead]))
+            if time.monotonic() > deadline:
+                pytest.fail("ranks did not report within 300 s")
+    finally:
+        if len(out) < world:
+            for p in procs:
+                if p.is_alive():
+                    p.terminate()
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -261,7 +283,9 @@ def _zslab_worker(rank, world, port, q, shape, w, ncycles):
                 rc_full[c0:c0 + piece.shape[0]] = piece
             # singular (pure Neumann): make the right-hand side exactly consistent
             rc_full -= rc_full.mean()
-            ec, info = oracle.cg(rc_full, np.zeros_like(rc_full), *wc, tol=1e-13)
+            # (1e-11: the consistent singular system's rounding floor is
+            # near 1e-13, and the bars below need far less)
+            ec, info = oracle.cg(rc_full, np.zeros_like(rc_full), *wc, tol=1e-11)
             assert info["status"] == 0, info
             ec_box = [ec]
         dist.broadcast_object_list(ec_box, src=0)
