@@ -9,6 +9,7 @@
 // The V-cycle itself is the paper's (Sec. 4.1): relax, compute the residual
 // and down-sample it to the next level's constraints, ..., direct solve at
 // the coarsest level, up-sample and add the correction, relax again.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1128,7 +1129,8 @@ int solve_linear(gd_stack *s, int system, const float *I0h, const float *I1h, fl
       CK(launch_fill(xh, n, 0.f, s->stream));
     CK(launch_fill(xl, n, 0.f, s->stream));
   }
-  if ((st = ensure_partials(s, linear_grid((long long)n) + 8)) != GD_OK) return report(rep, st);
+  if ((st = ensure_partials(s, std::max(linear_grid((long long)n), linear_zmax_blocks(L0)) + 8)) != GD_OK)
+    return report(rep, st);
   double sum_i0 = 0.0;
   auto reduce_read = [&](int lo, int hi, double *outv) -> int {
     CK(launch_reduce(s->partials, nb, s->scalars, lo, hi, 0, s->stream));

@@ -17,6 +17,8 @@
 // per colour, in place.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gd_internal.h"
 
 namespace {
@@ -319,119 +321,256 @@ __device__ __forceinline__ void block_sums(double a, double b, double *partials,
   }
 }
 
-// Integer-weighted neighbourhood sums, compensated.  With the fine factors
-// scaled to integers (K_n as is, the P1 mass times 6), every product of
-// three factor entries is a small integer, exact in FP32; each term p (h + l)
-// enters a float pair by TwoProd and TwoSum, so the four sums
-//   S_kx = sum (Kx My Mz) x, S_ky = sum (Mx Ky Mz) x,
-//   S_kz = sum (Mx My Kz) x, S_m = sum (Mx My Mz) x
-// come out exact to ~1e-12 of their terms, and the operator is their
-// weighted sum, formed in FP64 (a few operations per cell).
-struct Sums {
-  float h[4], l[4];
+// Integer-weighted Kronecker sums, compensated, as a z-march.  With the fine
+// factors scaled to integers (K_n as is, the P1 mass times 6), the four sums
+//   S_kx = (Kx My Mz) x, S_ky = (Mx Ky Mz) x, S_kz = (Mx My Kz) x,
+//   S_m = (Mx My Mz) x
+// are separable: three-tap filters along z (Mz x, Kz x), then y (My, Ky),
+// then x (Kx, Mx), with shared intermediates -- 27 taps per cell for all
+// four instead of 4 x 27.  Every tap is a float pair times a small integer
+// (TwoProd) added by TwoSum, so the sums come out exact to ~1e-12 of their
+// terms (the 27 coefficients nearly cancel on smooth data; plain FP32 would
+// lose ~1e-5 of the right-hand side), and the weighted combination is done
+// in float-pair arithmetic too (GB300's FP64 rate is 1/64 of its FP32 rate).
+//
+// A CTA owns an LZ_TX x LZ_TY column tile and marches z over a chunk of
+// planes.  cp.async brings each plane's box (the tile and a one-cell ring,
+// zero outside the domain) into a ring of four planes (k - 1, k, k + 1 in
+// use, k + 2 in flight); per plane the z, y and x stages each write shared
+// memory, with a CTA barrier between them.
+constexpr int LZ_TX = 32, LZ_TY = 16, LZ_NT = 256;
+constexpr int LZ_BW = LZ_TX + 2, LZ_BH = LZ_TY + 2;  // box
+constexpr int LZ_BC = LZ_BW * LZ_BH;                 // box cells
+constexpr int LZ_YC = LZ_BW * LZ_TY;                 // y-stage cells
+constexpr int LZ_NS = 4;                             // planes in the ring
+constexpr int LZ_MAX_CHUNKS = 64;
+enum { LZ_RESID = 0, LZ_RHS = 1 };
+
+struct DF {
+  float h, l;
 };
-__device__ __forceinline__ void acc_term(float P, float xh, float xl, float &sh, float &sl) {
-  if (P == 0.f) return;
+// s += P (xh + xl), P a small integer (TwoProd keeps any float P exact)
+__device__ __forceinline__ void df_tap(DF &s, float P, float xh, float xl) {
   const float p = P * xh;
   const float e = fmaf(P, xh, -p);
-  const float s = sh + p;
-  const float bb = s - sh;
-  const float err = (sh - (s - bb)) + (p - bb);
-  sh = s;
-  sl += err + e + P * xl;
+  const float t = s.h + p;
+  const float bb = t - s.h;
+  const float err = (s.h - (t - bb)) + (p - bb);
+  s.h = t;
+  s.l += err + e + P * xl;
 }
-template <bool ZC, typename V>
-__device__ __forceinline__ Sums kron_sums(const HLevelDev &L, bool want_kz, bool want_m, int i, int j, int k,
-                                          V val) {
-  Sums S;
+// v += w S, the double w split as (wh, wl)
+__device__ __forceinline__ void df_wadd(DF &v, float wh, float wl, DF S) {
+  const float p = wh * S.h;
+  const float e = fmaf(wh, S.h, -p) + fmaf(wh, S.l, wl * S.h);
+  const float t = v.h + p;
+  const float bb = t - v.h;
+  const float err = (v.h - (t - bb)) + (p - bb);
+  v.h = t;
+  v.l += err + e;
+}
+// 4-byte asynchronous copy; ok = false writes 0 (no global access)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+struct LzArgs {
+  // RESID: a0 = h, a1 = l of the iterate; RHS: a0 = I0, a1 = I1 (no low words)
+  const float *a0, *a1;
+  const float *bh, *bl;  // RESID: the right-hand side pair
+  float *r;              // RESID: r = b - A x (nullable)
+  float *oh, *ol;        // RHS: the right-hand side pair
+  double *partials;      // RESID: sums of r^2 and b^2 per block
+  // weights split as float pairs (RESID: ax, ay, az, am; RHS: gx, gy, gm)
+  float wh[4], wl[4];
+  int zchunk;
+  int want_kz, want_m;
+};
+
+template <bool ZC, int MODE>
+__global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
+  __shared__ __align__(16) float ring[LZ_NS][2][LZ_BC];  // per plane: a0, a1
+  __shared__ __align__(16) float zst[4][LZ_BC];          // z stage: two float pairs
+  __shared__ __align__(16) float yst[6][LZ_YC];          // y stage: three float pairs
+  __shared__ float wx[2][3][LZ_BW], wy[2][3][LZ_BH];     // [K|M][tap][box column / row]
+  __shared__ double red[2][LZ_NT / 32];
+  const int tid = threadIdx.x;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const int i0 = blockIdx.x * LZ_TX, j0 = blockIdx.y * LZ_TY;
+  const int zs0 = blockIdx.z * a.zchunk, ze = min(zs0 + a.zchunk, nz);
+  const size_t plane = (size_t)nx * ny;
+  const bool y3 = MODE == LZ_RESID ? a.want_kz != 0 : a.want_m != 0;  // third y / z sum in use
+
+  // factor rows of the box's columns and rows, taps that leave the domain set to 0
+  for (int q = tid; q < 3 * LZ_BW; q += LZ_NT) {
+    const int c = q % LZ_BW, t = q / LZ_BW, gi = i0 - 1 + c, nb = gi + t - 1;
+    const bool ok = gi >= 0 && gi < nx && nb >= 0 && nb < nx;
+    wx[0][t][c] = ok ? L.kx[3 * gi + t] : 0.f;
+    wx[1][t][c] = ok ? L.mx[3 * gi + t] : 0.f;
+  }
+  for (int q = tid; q < 3 * LZ_BH; q += LZ_NT) {
+    const int c = q % LZ_BH, t = q / LZ_BH, gj = j0 - 1 + c, nb = gj + t - 1;
+    const bool ok = gj >= 0 && gj < ny && nb >= 0 && nb < ny;
+    wy[0][t][c] = ok ? L.ky[3 * gj + t] : 0.f;
+    wy[1][t][c] = ok ? L.my[3 * gj + t] : 0.f;
+  }
+  // plane p of the box into its ring slot (zeros outside the domain)
+  auto load_plane = [&](int p) {
+    const int sl = p & (LZ_NS - 1);
+    const bool pin = p >= 0 && p < nz;
+    const bool second = MODE == LZ_RESID || a.want_m != 0;
+    for (int q = tid; q < LZ_BC; q += LZ_NT) {
+      const int gi = i0 - 1 + q % LZ_BW, gj = j0 - 1 + q / LZ_BW;
+      const bool ok = pin && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+      const size_t o = ok ? (size_t)p * plane + (size_t)gj * nx + gi : 0;
+      cp_async4(&ring[sl][0][q], a.a0 + o, ok);
+      cp_async4(&ring[sl][1][q], ok && second ? a.a1 + o : a.a0, ok && second);
+    }
+    cp_async_commit();
+  };
+  for (int p = ZC ? zs0 - 1 : zs0; p <= (ZC ? zs0 + 1 : zs0); ++p) load_plane(p);
+
+  float srr = 0.f, sbb = 0.f;
+  for (int k = zs0; k < ze; ++k) {
+    load_plane(ZC ? k + 2 : k + 1);
+    cp_async_wait1();
+    __syncthreads();
+    // ---- z stage: Zm = Mz x and Zk = Kz x (RHS: Zm of a0 and of a1) ----
+    const float mz1 = L.mz[3 * k + 1];
+    float mz0 = 0.f, mz2 = 0.f, kz0 = 0.f, kz1 = 0.f, kz2 = 0.f;
+    if (ZC) {
+      kz1 = L.kz[3 * k + 1];
+      if (k > 0) {
+        mz0 = L.mz[3 * k];
+        kz0 = L.kz[3 * k];
+      }
+      if (k < nz - 1) {
+        mz2 = L.mz[3 * k + 2];
+        kz2 = L.kz[3 * k + 2];
+      }
+    }
+    const int sm = (k - 1) & (LZ_NS - 1), s0 = k & (LZ_NS - 1), sp = (k + 1) & (LZ_NS - 1);
+    for (int q = tid; q < LZ_BC; q += LZ_NT) {
+      DF zm = {0.f, 0.f}, z2 = {0.f, 0.f};
+      if (MODE == LZ_RESID) {
+        const float h0 = ring[s0][0][q], l0 = ring[s0][1][q];
+        df_tap(zm, mz1, h0, l0);
+        if (ZC) {
+          const float hm = ring[sm][0][q], lm = ring[sm][1][q], hp = ring[sp][0][q], lp = ring[sp][1][q];
+          df_tap(zm, mz0, hm, lm);
+          df_tap(zm, mz2, hp, lp);
+          if (y3) {
+            df_tap(z2, kz1, h0, l0);
+            df_tap(z2, kz0, hm, lm);
+            df_tap(z2, kz2, hp, lp);
+          }
+        }
+      } else {
+        df_tap(zm, mz1, ring[s0][0][q], 0.f);
+        if (y3) df_tap(z2, mz1, ring[s0][1][q], 0.f);
+        if (ZC) {
+          df_tap(zm, mz0, ring[sm][0][q], 0.f);
+          df_tap(zm, mz2, ring[sp][0][q], 0.f);
+          if (y3) {
+            df_tap(z2, mz0, ring[sm][1][q], 0.f);
+            df_tap(z2, mz2, ring[sp][1][q], 0.f);
+          }
+        }
+      }
+      zst[0][q] = zm.h;
+      zst[1][q] = zm.l;
+      zst[2][q] = z2.h;
+      zst[3][q] = z2.l;
+    }
+    __syncthreads();
+    // ---- y stage: My Zm, Ky Zm and My Z2 ----
+    for (int q = tid; q < LZ_YC; q += LZ_NT) {
+      const int c = q % LZ_BW, by = q / LZ_BW + 1;
+      DF ymm = {0.f, 0.f}, ykm = {0.f, 0.f}, yz = {0.f, 0.f};
 #pragma unroll
-  for (int q = 0; q < 4; ++q) S.h[q] = S.l[q] = 0.f;
-  const float *kx = L.kx + 3 * i, *mx = L.mx + 3 * i;
-  const float *ky = L.ky + 3 * j, *my = L.my + 3 * j;
-  const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
-  const int c0 = ZC ? -1 : 0, c1 = ZC ? 1 : 0;
-  for (int c = c0; c <= c1; ++c) {
-    const int kk = k + c;
-    if (kk < 0 || kk >= L.nz) continue;
-    const float mzc = mz[c + 1], kzc = ZC ? kz[c + 1] : 0.f;
-    for (int b = -1; b <= 1; ++b) {
-      const int jj = j + b;
-      if (jj < 0 || jj >= L.ny) continue;
-      const float myb = my[b + 1], kyb = ky[b + 1];
-      for (int a = -1; a <= 1; ++a) {
-        const int ii = i + a;
-        if (ii < 0 || ii >= L.nx) continue;
-        float xh, xl;
-        val(((long long)kk * L.ny + jj) * L.nx + ii, xh, xl);
-        const float mxa = mx[a + 1], kxa = kx[a + 1];
-        acc_term(kxa * myb * mzc, xh, xl, S.h[0], S.l[0]);
-        acc_term(mxa * kyb * mzc, xh, xl, S.h[1], S.l[1]);
-        if (want_kz) acc_term(mxa * myb * kzc, xh, xl, S.h[2], S.l[2]);
-        if (want_m) acc_term(mxa * myb * mzc, xh, xl, S.h[3], S.l[3]);
+      for (int t = 0; t < 3; ++t) {
+        const int o = (by + t - 1) * LZ_BW + c;
+        const float zh = zst[0][o], zl = zst[1][o];
+        df_tap(ymm, wy[1][t][by], zh, zl);
+        df_tap(ykm, wy[0][t][by], zh, zl);
+        if (y3) df_tap(yz, wy[1][t][by], zst[2][o], zst[3][o]);
+      }
+      yst[0][q] = ymm.h;
+      yst[1][q] = ymm.l;
+      yst[2][q] = ykm.h;
+      yst[3][q] = ykm.l;
+      yst[4][q] = yz.h;
+      yst[5][q] = yz.l;
+    }
+    __syncthreads();
+    // ---- x stage: Kx Ymm, Mx Ykm, Mx Y3 (and Mx Ymm), then the output ----
+    for (int q = tid; q < LZ_TX * LZ_TY; q += LZ_NT) {
+      const int tx = q % LZ_TX, ty = q / LZ_TX, gi = i0 + tx, gj = j0 + ty;
+      if (gi >= nx || gj >= ny) continue;
+      const int bx = tx + 1;
+      DF skx = {0.f, 0.f}, sky = {0.f, 0.f}, s3 = {0.f, 0.f}, smm = {0.f, 0.f};
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        const int o = ty * LZ_BW + bx + t - 1;
+        const float kx = wx[0][t][bx], mx = wx[1][t][bx];
+        df_tap(skx, kx, yst[0][o], yst[1][o]);
+        df_tap(sky, mx, yst[2][o], yst[3][o]);
+        if (y3) df_tap(s3, mx, yst[4][o], yst[5][o]);
+        if (MODE == LZ_RESID && a.want_m) df_tap(smm, mx, yst[0][o], yst[1][o]);
+      }
+      DF v = {0.f, 0.f};
+      df_wadd(v, a.wh[0], a.wl[0], skx);
+      df_wadd(v, a.wh[1], a.wl[1], sky);
+      const size_t o = (size_t)k * plane + (size_t)gj * nx + gi;
+      if (MODE == LZ_RESID) {
+        if (y3) df_wadd(v, a.wh[2], a.wl[2], s3);
+        if (a.want_m) df_wadd(v, a.wh[3], a.wl[3], smm);
+        // r = b - v in float-pair arithmetic, rounded once
+        const float bhv = a.bh[o], blv = a.bl[o];
+        const float t = bhv - v.h;
+        const float bb = t - bhv;
+        const float err = (bhv - (t - bb)) + (-v.h - bb);
+        const float rv = t + (err + (blv - v.l));
+        if (a.r) a.r[o] = rv;
+        srr = fmaf(rv, rv, srr);
+        const float bv = bhv + blv;
+        sbb = fmaf(bv, bv, sbb);
+      } else {
+        if (y3) df_wadd(v, a.wh[2], a.wl[2], s3);
+        const float sh = v.h + v.l;
+        a.oh[o] = sh;
+        a.ol[o] = v.l - (sh - v.h);
       }
     }
   }
-  return S;
-}
-__device__ __forceinline__ double sum_of(const Sums &S, int q) { return (double)S.h[q] + (double)S.l[q]; }
-
-// b = gx' S_kx(I0) + gy' S_ky(I0) + gm' S_m(I1) (weights already divided by
-// the factor scales), stored as a float pair
-template <bool ZC>
-__global__ void __launch_bounds__(HNT) k_l_rhs(HLevelDev L, LinW w, const float *__restrict__ I0,
-                                               const float *__restrict__ I1, float *__restrict__ bh,
-                                               float *__restrict__ bl) {
-  const long long n = (long long)L.nx * L.ny * L.nz;
-  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
-    const int i = (int)(q % L.nx);
-    const long long t = q / L.nx;
-    const int j = (int)(t % L.ny), k = (int)(t / L.ny);
-    const Sums S0 = kron_sums<ZC>(L, false, false, i, j, k, [&](long long o, float &h, float &l) {
-      h = I0[o];
-      l = 0.f;
-    });
-    double v = w.gx * sum_of(S0, 0) + w.gy * sum_of(S0, 1);
-    if (w.gm != 0.0) {
-      const Sums S1 = kron_sums<ZC>(L, false, true, i, j, k, [&](long long o, float &h, float &l) {
-        h = I1[o];
-        l = 0.f;
-      });
-      v += w.gm * sum_of(S1, 3);
+  cp_async_wait0();  // the last plane's copies (past the chunk) land before exit
+  if (MODE == LZ_RESID) {
+    double dr = srr, db = sbb;
+    for (int o = 16; o > 0; o >>= 1) {
+      dr += __shfl_down_sync(0xffffffffu, dr, o);
+      db += __shfl_down_sync(0xffffffffu, db, o);
     }
-    const float hv = (float)v;
-    bh[q] = hv;
-    bl[q] = (float)(v - (double)hv);
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = dr;
+      red[1][tid >> 5] = db;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int w = 0; w < LZ_NT / 32; ++w) {
+        s0 += red[0][w];
+        s1 += red[1][w];
+      }
+      const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      a.partials[blk * S_NUM + S_RR] = s0;
+      a.partials[blk * S_NUM + S_BB] = s1;
+    }
   }
-}
-
-// r = b - A (h + l) from the compensated sums (stored as float), and the
-// block sums of r^2 (slot S_RR) and b^2 (slot S_BB)
-template <bool ZC>
-__global__ void __launch_bounds__(HNT) k_l_resid(HLevelDev L, LinW w, const float *__restrict__ bh,
-                                                 const float *__restrict__ bl, const float *__restrict__ h,
-                                                 const float *__restrict__ l, float *__restrict__ r,
-                                                 double *__restrict__ partials) {
-  const long long n = (long long)L.nx * L.ny * L.nz;
-  const bool want_kz = w.az != 0.0, want_m = w.am != 0.0;
-  double srr = 0.0, sbb = 0.0;
-  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
-    const int i = (int)(q % L.nx);
-    const long long t = q / L.nx;
-    const int j = (int)(t % L.ny), k = (int)(t / L.ny);
-    const Sums S = kron_sums<ZC>(L, want_kz, want_m, i, j, k, [&](long long o, float &xh, float &xl) {
-      xh = h[o];
-      xl = l[o];
-    });
-    double ax = w.ax * sum_of(S, 0) + w.ay * sum_of(S, 1);
-    if (want_kz) ax += w.az * sum_of(S, 2);
-    if (want_m) ax += w.am * sum_of(S, 3);
-    const double b = (double)bh[q] + (double)bl[q];
-    const double rv = b - ax;
-    if (r) r[q] = (float)rv;
-    srr += rv * rv;
-    sbb += b * b;
-  }
-  block_sums(srr, sbb, partials, S_RR, S_BB);
 }
 
 // (h, l) += e exactly in FP64 and rounded back to a float pair; block sums
@@ -468,26 +607,91 @@ __global__ void __launch_bounds__(HNT) k_l_final(long long n, const float *__res
 
 int linear_grid(long long n) { return grid_of(n); }
 
+namespace {
+// z chunks of a k_lz launch: a launch lasts about ceil(CTAs / resident
+// slots) CTA durations and a CTA's duration is its chunk plus the planes
+// it loads beyond it, so the chunk count minimises that product
+template <typename K>
+dim3 lz_grid(K kernel, const HLevelDev &L, bool zc, int &zchunk) {
+  static int slots_cache[2] = {0, 0};
+  int &slots = slots_cache[zc ? 1 : 0];
+  if (!slots) {
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, LZ_NT, 0) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    slots = occ * (sms > 0 ? sms : 1);
+  }
+  const int gx = (L.nx + LZ_TX - 1) / LZ_TX, gy = (L.ny + LZ_TY - 1) / LZ_TY;
+  const long tiles = (long)gx * gy;
+  const int h = zc ? 3 : 1;
+  long best = -1;
+  zchunk = L.nz;
+  for (int c = 1; c <= std::min(L.nz, LZ_MAX_CHUNKS); ++c) {
+    const int zcq = (L.nz + c - 1) / c;
+    const long gz = (L.nz + zcq - 1) / zcq;
+    const long cost = ((tiles * gz + slots - 1) / slots) * (zcq + h);
+    if (best < 0 || cost < best) {
+      best = cost;
+      zchunk = zcq;
+    }
+  }
+  return dim3(gx, gy, (L.nz + zchunk - 1) / zchunk);
+}
+void split_w(double w, float &h, float &l) {
+  h = (float)w;
+  l = (float)(w - (double)h);
+}
+template <int MODE>
+cudaError_t run_lz(const HLevelDev &L, LzArgs a, int *nblocks, cudaStream_t st) {
+  const bool zc = L.wz != 0.f && L.nz > 1;
+  dim3 g = zc ? lz_grid(k_lz<true, MODE>, L, true, a.zchunk) : lz_grid(k_lz<false, MODE>, L, false, a.zchunk);
+  if (nblocks) *nblocks = (int)(g.x * g.y * g.z);
+  if (zc)
+    k_lz<true, MODE><<<g, LZ_NT, 0, st>>>(L, a);
+  else
+    k_lz<false, MODE><<<g, LZ_NT, 0, st>>>(L, a);
+  return cudaGetLastError();
+}
+}  // namespace
+
+int linear_zmax_blocks(const HLevelDev &L) {
+  return ((L.nx + LZ_TX - 1) / LZ_TX) * ((L.ny + LZ_TY - 1) / LZ_TY) * std::min(L.nz, LZ_MAX_CHUNKS);
+}
+
 cudaError_t launch_l_rhs(const HLevelDev &L, const LinW &w, const float *I0, const float *I1, float *bh, float *bl,
                          cudaStream_t st) {
-  const long long n = (long long)L.nx * L.ny * L.nz;
-  if (L.wz != 0.f && L.nz > 1)
-    k_l_rhs<true><<<grid_of(n), HNT, 0, st>>>(L, w, I0, I1, bh, bl);
-  else
-    k_l_rhs<false><<<grid_of(n), HNT, 0, st>>>(L, w, I0, I1, bh, bl);
-  return cudaGetLastError();
+  LzArgs a{};
+  a.a0 = I0;
+  a.a1 = I1;
+  a.oh = bh;
+  a.ol = bl;
+  split_w(w.gx, a.wh[0], a.wl[0]);
+  split_w(w.gy, a.wh[1], a.wl[1]);
+  split_w(w.gm, a.wh[2], a.wl[2]);
+  a.want_m = (w.gm != 0.0 && I1) ? 1 : 0;
+  return run_lz<LZ_RHS>(L, a, nullptr, st);
 }
 
 cudaError_t launch_l_resid(const HLevelDev &L, const LinW &w, const float *bh, const float *bl, const float *h,
                            const float *l, float *r, double *partials, int *nblocks, cudaStream_t st) {
-  const long long n = (long long)L.nx * L.ny * L.nz;
-  const int g = grid_of(n);
-  if (nblocks) *nblocks = g;
-  if (L.wz != 0.f && L.nz > 1)
-    k_l_resid<true><<<g, HNT, 0, st>>>(L, w, bh, bl, h, l, r, partials);
-  else
-    k_l_resid<false><<<g, HNT, 0, st>>>(L, w, bh, bl, h, l, r, partials);
-  return cudaGetLastError();
+  LzArgs a{};
+  a.a0 = h;
+  a.a1 = l;
+  a.bh = bh;
+  a.bl = bl;
+  a.r = r;
+  a.partials = partials;
+  split_w(w.ax, a.wh[0], a.wl[0]);
+  split_w(w.ay, a.wh[1], a.wl[1]);
+  split_w(w.az, a.wh[2], a.wl[2]);
+  split_w(w.am, a.wh[3], a.wl[3]);
+  a.want_kz = w.az != 0.0 ? 1 : 0;
+  a.want_m = w.am != 0.0 ? 1 : 0;
+  return run_lz<LZ_RESID>(L, a, nblocks, st);
 }
 
 cudaError_t launch_l_update(long long n, const float *e, float *h, float *l, double *partials, int *nblocks,

@@ -153,6 +153,8 @@ struct LinW {
   double ax, ay, az, am;
   double gx, gy, gm;
 };
+// upper bound of the blocks (partial-sum rows) of a launch_l_resid launch
+int linear_zmax_blocks(const HLevelDev &L);
 cudaError_t launch_l_rhs(const HLevelDev &L, const LinW &w, const float *I0, const float *I1, float *bh, float *bl,
                          cudaStream_t st);
 // r = b - A (h + l) (r nullable) with FP64 sums of r^2, b^2 per block (S_RR, S_BB)
