@@ -404,6 +404,16 @@ def run_gpu(args):
     # The Hybrid discretisation (Sec. 4.2: 6-point fine operator, first-order
     # B-spline transfers, Galerkin 27-point coarse operators) on the same
     # stack and tolerances.
+    def profiled_step(stk, fn):
+        """Kernel-class times (ms) of one more step with a CUDA event pair
+        around every launch (not part of any timed value)."""
+        gd.gd_profile_reset(stk)
+        gd.gd_profile_enable(stk, True)
+        fn()
+        torch.cuda.synchronize()
+        gd.gd_profile_enable(stk, False)
+        return {name: round(ms, 3) for name, n, ms, _ in gd.gd_profile_all(stk) if n > 0}
+
     hybrid = None
     if not args.no_hybrid:
         sh = gd.gd_stack_create(NX, NY, NZ, disc=gd.GD_DISC_HYBRID, stream=stream.cuda_stream)
@@ -431,8 +441,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
         barrier(world)
         hms = reduce_max(e0.elapsed_time(e1), world, dev)
-        gd.gd_destroy(sh)
         h1, h2 = hreps[-1]
+        hkern = profiled_step(sh, hstep)
+        gd.gd_destroy(sh)
         hybrid = {"value": world * voxels * hsteps / (hms * 1e-3), "unit": UNIT,
                   "ms_per_step": hms / hsteps, "steps": hsteps,
                   "discretisation": "hybrid: 6-point fine, B-spline transfers, Galerkin 27-point coarse",
@@ -441,7 +452,8 @@ def run_gpu(args):
                   "ad_rel_residual": h1["rel_residual"], "sp_cycles": h2["cycles"],
                   "sp_rho_per_cycle": h2["rho_per_cycle"], "sp_rel_residual": h2["rel_residual"],
                   "constant_ad_rho_per_cycle": reps[-1][0]["rho_per_cycle"],
-                  "constant_sp_rho_per_cycle": reps[-1][1]["rho_per_cycle"]}
+                  "constant_sp_rho_per_cycle": reps[-1][1]["rho_per_cycle"],
+                  "kernel_ms_profiled_step": hkern}
 
     # The Linear discretisation (Sec. 4.2, trilinear finite elements: a
     # 27-point fine operator, FP64 residuals) on the same stack.
@@ -465,13 +477,15 @@ def run_gpu(args):
         torch.cuda.synchronize()
         barrier(world)
         lms = reduce_max(e0.elapsed_time(e1), world, dev)
-        gd.gd_destroy(sl)
         l1, l2 = lreps[-1]
+        lkern = profiled_step(sl, lstep)
+        gd.gd_destroy(sl)
         linear = {"value": world * voxels / (lms * 1e-3), "unit": UNIT, "ms_per_step": lms, "steps": 1,
                   "discretisation": "linear: trilinear elements, 27-point fine operator",
                   "ad_cycles": l1["cycles"], "ad_rho_per_cycle": l1["rho_per_cycle"],
                   "ad_rel_residual": l1["rel_residual"], "sp_cycles": l2["cycles"],
-                  "sp_rho_per_cycle": l2["rho_per_cycle"], "sp_rel_residual": l2["rel_residual"]}
+                  "sp_rho_per_cycle": l2["rho_per_cycle"], "sp_rel_residual": l2["rel_residual"],
+                  "kernel_ms_profiled_step": lkern}
 
     # Batched screened Poisson on 512 independent slices, square, sides
     # log-uniform in [256, 4096], alpha ~ U(0.001, 0.1) per slice; every

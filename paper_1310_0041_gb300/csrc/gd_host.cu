@@ -730,7 +730,7 @@ int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
   auto gs = [&](Level &v) -> int {
     ProfScope ps(s, P_SWEEP_COARSE, (double)v.n * 12.0);
     CK(launch_h_gs(v.hd, v.x, v.b, s->stream));
-    s->launches += 7;  // eight colour launches
+    s->launches += h_gs_launches(v.hd) - 1;  // one colour launch per colour
     return GD_OK;
   };
   for (int l = 0; l < nl - 1; ++l) {

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "gd_internal.h"
 
@@ -97,23 +98,167 @@ __device__ __forceinline__ void apply_off(const HLevelDev &L, const float *__res
   }
 }
 
-// One colour of the eight-colour Gauss-Seidel sweep on a 27-point level.
+// 4-byte asynchronous copy; ok = false writes 0 (no global access)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// One colour of the Gauss-Seidel sweep on a 27-point level, as a z-march.
+// Colour (px, py, pz) holds the cells with i = px, j = py (mod 2) and, on
+// coupled levels, k = pz (mod 2); same-colour cells are never neighbours,
+// so a launch updates them all from the values before it.  Uncoupled
+// levels (no z terms) use the four in-plane colours over every plane: the
+// same iterates in half the launches.
+//
+// A CTA owns a GZ_TX x GZ_TY column tile (one colour cell per thread per
+// plane) and marches z over a chunk of planes; cp.async brings each plane's
+// box (the tile, one row above and below, four columns left and right: a
+// 16-byte aligned start) into a ring.  The 27 coefficients factor per axis,
+//   cf(a, b, c) = U(a, b) Z1(c) + V(a, b) MZ(c),
+//   U = mx(a) my(b), V = wy mx(a) ky(b) + wx kx(a) my(b),
+//   Z1 = wz kz(c) + wm mz(c), MZ = mz(c),
+// with U, V fixed per thread and Z1, MZ per plane, so a cell's update is
+// two 9-point in-plane dot products per plane: x += (b - A x) / cf(0,0,0).
+constexpr int GZ_TX = 64, GZ_TY = 16, GZ_NT = 256;
+constexpr int GZ_BW = GZ_TX + 8, GZ_BH = GZ_TY + 2;  // box: columns i0-4 .., rows j0-1 ..
+constexpr int GZ_BC = GZ_BW * GZ_BH;
+constexpr int GZ_MAX_CHUNKS = 64;
+
+__device__ __forceinline__ void cp_async16z(float *dst, const float *src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(ok ? 16 : 0)
+               : "memory");
+}
+
 template <bool ZC>
-__global__ void __launch_bounds__(HNT) k_h_gs(HLevelDev L, int colour, float *__restrict__ x,
-                                              const float *__restrict__ b) {
+__global__ void __launch_bounds__(GZ_NT, 3) k_h_gsz(HLevelDev L, int colour, int zchunk, int vec,
+                                                   float *__restrict__ x, const float *__restrict__ b) {
+  constexpr int NS = ZC ? 8 : 4;  // ring: planes k-1 .. k+3 (coupled), k .. k+2
+  __shared__ __align__(16) float ring[NS][GZ_BC];
+  const int tid = threadIdx.x;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int px = colour & 1, py = (colour >> 1) & 1, pz = (colour >> 2) & 1;
-  const int hx = (L.nx - px + 1) / 2, hy = (L.ny - py + 1) / 2, hz = (L.nz - pz + 1) / 2;
-  const long long n = (long long)hx * hy * hz;
-  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
-    const int ti = (int)(q % hx);
-    const long long r = q / hx;
-    const int tj = (int)(r % hy), tk = (int)(r / hy);
-    const int i = 2 * ti + px, j = 2 * tj + py, k = 2 * tk + pz;
-    float off, dg;
-    apply_off<ZC, false>(L, x, i, j, k, off, dg);
-    const long long o = cell(L, i, j, k);
-    x[o] = (b[o] - off) / dg;
+  const int i0 = blockIdx.x * GZ_TX, j0 = blockIdx.y * GZ_TY;
+  const int zs = blockIdx.z * zchunk, ze = min(zs + zchunk, nz);
+  const size_t plane = (size_t)nx * ny;
+
+  // plane p's box into its slot (zeros outside the domain)
+  auto load_plane = [&](int p) {
+    float *dst = ring[(p + NS) % NS];
+    const bool pin = p >= 0 && p < nz;
+    if (vec) {
+      for (int q = tid; q < GZ_BC / 4; q += GZ_NT) {
+        const int c4 = q % (GZ_BW / 4), r = q / (GZ_BW / 4);
+        const int gi = i0 - 4 + 4 * c4, gj = j0 - 1 + r;
+        const bool ok = pin && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+        cp_async16z(dst + 4 * q, ok ? x + (size_t)p * plane + (size_t)gj * nx + gi : x, ok);
+      }
+    } else {
+      for (int q = tid; q < GZ_BC; q += GZ_NT) {
+        const int c = q % GZ_BW, r = q / GZ_BW;
+        const int gi = i0 - 4 + c, gj = j0 - 1 + r;
+        const bool ok = pin && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+        cp_async4(dst + q, ok ? x + (size_t)p * plane + (size_t)gj * nx + gi : x, ok);
+      }
+    }
+  };
+
+  // this thread's cell and its per-thread coefficient factors
+  const int l = tid & 31, tyh = tid >> 5;
+  const int gi = i0 + 2 * l + px, gj = j0 + 2 * tyh + py;
+  const bool act = gi < nx && gj < ny;
+  float U[3][3], V[3][3];  // [b][a]
+  {
+    float kxr[3] = {0.f, 0.f, 0.f}, mxr[3] = {0.f, 0.f, 0.f}, kyr[3] = {0.f, 0.f, 0.f}, myr[3] = {0.f, 0.f, 0.f};
+    if (act) {
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        if (gi + t - 1 >= 0 && gi + t - 1 < nx) {
+          kxr[t] = L.kx[3 * gi + t];
+          mxr[t] = L.mx[3 * gi + t];
+        }
+        if (gj + t - 1 >= 0 && gj + t - 1 < ny) {
+          kyr[t] = L.ky[3 * gj + t];
+          myr[t] = L.my[3 * gj + t];
+        }
+      }
+    }
+#pragma unroll
+    for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+      for (int aa = 0; aa < 3; ++aa) {
+        U[bb][aa] = mxr[aa] * myr[bb];
+        V[bb][aa] = L.wy * mxr[aa] * kyr[bb] + L.wx * kxr[aa] * myr[bb];
+      }
   }
+  // shared-memory offset of the float2 that starts this thread's three
+  // columns' pairs (columns gi - 1 .. gi + 1 sit in two aligned float2)
+  const int ci = gi - i0 + 4;                // box column of the cell
+  const int c2 = (ci - 1) & ~1;              // first float2 (even)
+  const int row0 = (gj - j0 + 1 - 1) * GZ_BW;  // box row of gj - 1
+
+  // first updated plane of the chunk and the stride
+  const int kstep = ZC ? 2 : 1;
+  const int k0 = ZC ? zs + ((zs & 1) != pz ? 1 : 0) : zs;
+  if (ZC) {
+    for (int p = k0 - 1; p <= k0 + 1; ++p) load_plane(p);
+  } else {
+    load_plane(k0);
+  }
+  cp_async_commit();
+  for (int k = k0; k < ze; k += kstep) {
+    if (ZC) {
+      load_plane(k + 2);
+      load_plane(k + 3);
+    } else {
+      load_plane(k + 1);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    if (act) {
+      float Z1[3] = {0.f, 0.f, 0.f}, MZ[3] = {0.f, 0.f, 0.f};
+      const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
+      if (ZC) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (k + c - 1 >= 0 && k + c - 1 < nz) {
+            MZ[c] = mz[c];
+            Z1[c] = L.wz * kz[c] + L.wm * mz[c];
+          }
+      } else {
+        MZ[1] = mz[1];
+        Z1[1] = L.wm * mz[1];
+      }
+      float ax = 0.f, xc = 0.f;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (!ZC && c != 1) continue;
+        const float *pl = ring[(k + c - 1 + NS) % NS] + row0 + c2;
+        float su = 0.f, sv = 0.f;
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+          const float2 lo = *reinterpret_cast<const float2 *>(pl + bb * GZ_BW);
+          const float2 hi = *reinterpret_cast<const float2 *>(pl + bb * GZ_BW + 2);
+          // columns gi-1, gi, gi+1: (lo.y, hi.x, hi.y) if ci is even, else (lo.x, lo.y, hi.x)
+          const float v0 = (ci & 1) ? lo.x : lo.y, v1 = (ci & 1) ? lo.y : hi.x, v2 = (ci & 1) ? hi.x : hi.y;
+          su = fmaf(U[bb][0], v0, fmaf(U[bb][1], v1, fmaf(U[bb][2], v2, su)));
+          sv = fmaf(V[bb][0], v0, fmaf(V[bb][1], v1, fmaf(V[bb][2], v2, sv)));
+          if (c == 1 && bb == 1) xc = v1;
+        }
+        ax = fmaf(Z1[c], su, fmaf(MZ[c], sv, ax));
+      }
+      const float dg = U[1][1] * Z1[1] + V[1][1] * MZ[1];
+      const size_t o = (size_t)k * plane + (size_t)gj * nx + gi;
+      x[o] = xc + (b[o] - ax) / dg;
+    }
+  }
+  cp_async_wait0();  // copies of planes past the chunk land before exit
 }
 
 // r = b - A x (SIX: the fine 6-point operator).
@@ -245,17 +390,56 @@ int grid_of(long long n) {
 
 }  // namespace
 
+namespace {
+// z chunks of a colour launch: as for the other z-march kernels, the chunk
+// count minimises ceil(CTAs / resident slots) x (chunk + the planes loaded
+// beyond it)
+template <typename K>
+int gsz_chunk(K kernel, int slot_idx, long tiles, int nz, int h) {
+  static int slots_cache[2] = {0, 0};
+  int &slots = slots_cache[slot_idx];
+  if (!slots) {
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, GZ_NT, 0) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    slots = occ * (sms > 0 ? sms : 1);
+  }
+  long best = -1;
+  int zc = nz;
+  for (int c = 1; c <= std::min(nz, GZ_MAX_CHUNKS); ++c) {
+    const int q = (nz + c - 1) / c;
+    const long gz = (nz + q - 1) / q;
+    const long cost = ((tiles * gz + slots - 1) / slots) * (q + h);
+    if (best < 0 || cost < best) {
+      best = cost;
+      zc = q;
+    }
+  }
+  return zc;
+}
+}  // namespace
+
 cudaError_t launch_h_gs(const HLevelDev &L, float *x, const float *b, cudaStream_t st) {
-  const long long n8 = ((long long)L.nx * L.ny * L.nz + 7) / 8;
   const bool zc = L.wz != 0.f && L.nz > 1;
-  for (int c = 0; c < 8; ++c) {
+  const int gx = (L.nx + GZ_TX - 1) / GZ_TX, gy = (L.ny + GZ_TY - 1) / GZ_TY;
+  const int vec = ((L.nx & 3) == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
+  const int chunk = zc ? gsz_chunk(k_h_gsz<true>, 1, (long)gx * gy, L.nz, 3)
+                       : gsz_chunk(k_h_gsz<false>, 0, (long)gx * gy, L.nz, 1);
+  const dim3 grid(gx, gy, (L.nz + chunk - 1) / chunk);
+  for (int c = 0; c < (zc ? 8 : 4); ++c) {
     if (zc)
-      k_h_gs<true><<<grid_of(n8), HNT, 0, st>>>(L, c, x, b);
+      k_h_gsz<true><<<grid, GZ_NT, 0, st>>>(L, c, chunk, vec, x, b);
     else
-      k_h_gs<false><<<grid_of(n8), HNT, 0, st>>>(L, c, x, b);
+      k_h_gsz<false><<<grid, GZ_NT, 0, st>>>(L, c, chunk, vec, x, b);
   }
   return cudaGetLastError();
 }
+
+int h_gs_launches(const HLevelDev &L) { return (L.wz != 0.f && L.nz > 1) ? 8 : 4; }
 
 cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const float *b, float *r,
                            cudaStream_t st) {
@@ -369,16 +553,6 @@ __device__ __forceinline__ void df_wadd(DF &v, float wh, float wl, DF S) {
   v.h = t;
   v.l += err + e;
 }
-// 4-byte asynchronous copy; ok = false writes 0 (no global access)
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
-               "l"(src), "r"(ok ? 4 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 struct LzArgs {
   // RESID: a0 = h, a1 = l of the iterate; RHS: a0 = I0, a1 = I1 (no low words)
   const float *a0, *a1;

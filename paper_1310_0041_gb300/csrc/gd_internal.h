@@ -135,6 +135,7 @@ struct HLevelDev {
 };
 // eight-colour Gauss-Seidel sweep of a 27-point level, in place
 cudaError_t launch_h_gs(const HLevelDev &L, float *x, const float *b, cudaStream_t st);
+int h_gs_launches(const HLevelDev &L);  // colour launches of one launch_h_gs
 // r = b - A x (six: the fine 6-point operator, factors unused)
 cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const float *b, float *r,
                            cudaStream_t st);
