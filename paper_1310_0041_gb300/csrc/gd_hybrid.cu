@@ -26,78 +26,6 @@ namespace {
 
 constexpr int HNT = 256;
 
-__device__ __forceinline__ long long cell(const HLevelDev &L, int i, int j, int k) {
-  return ((long long)k * L.ny + j) * L.nx + i;
-}
-
-// A x at (i, j, k) without the diagonal term (off) and the diagonal (dg).
-template <bool ZC, bool SIX>
-__device__ __forceinline__ void apply_off(const HLevelDev &L, const float *__restrict__ x, int i, int j, int k,
-                                          float &off, float &dg) {
-  off = 0.f;
-  dg = 0.f;
-  if (SIX) {
-    // fine level: K = 1D Neumann Laplacian, M = I
-    float cnt = 0.f, s = 0.f;
-    if (i > 0) { s += L.wx * x[cell(L, i - 1, j, k)]; cnt += L.wx; }
-    if (i < L.nx - 1) { s += L.wx * x[cell(L, i + 1, j, k)]; cnt += L.wx; }
-    if (j > 0) { s += L.wy * x[cell(L, i, j - 1, k)]; cnt += L.wy; }
-    if (j < L.ny - 1) { s += L.wy * x[cell(L, i, j + 1, k)]; cnt += L.wy; }
-    if (ZC) {
-      if (k > 0) { s += L.wz * x[cell(L, i, j, k - 1)]; cnt += L.wz; }
-      if (k < L.nz - 1) { s += L.wz * x[cell(L, i, j, k + 1)]; cnt += L.wz; }
-    }
-    off = -s;
-    dg = cnt + L.wm;
-    return;
-  }
-  if (i >= L.ilo[0] && i <= L.ihi[0] && j >= L.ilo[1] && j <= L.ihi[1] &&
-      (!ZC || (k >= L.ilo[2] && k <= L.ihi[2]))) {
-    // interior: constant coefficients, every neighbour exists
-    const int c0 = ZC ? -1 : 0, c1 = ZC ? 1 : 0;
-#pragma unroll
-    for (int c = c0; c <= c1; ++c)
-#pragma unroll
-      for (int b = -1; b <= 1; ++b) {
-        const float *xr = x + cell(L, i, j + b, k + c);
-#pragma unroll
-        for (int a = -1; a <= 1; ++a) {
-          if (a == 0 && b == 0 && c == 0) continue;
-          off = fmaf(L.cst[(c + 1) * 9 + (b + 1) * 3 + (a + 1)], xr[a], off);
-        }
-      }
-    dg = L.cst[13];
-    return;
-  }
-  const float *kx = L.kx + 3 * i, *mx = L.mx + 3 * i;
-  const float *ky = L.ky + 3 * j, *my = L.my + 3 * j;
-  const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
-  const int c0 = ZC ? -1 : 0, c1 = ZC ? 1 : 0;
-  for (int c = c0; c <= c1; ++c) {
-    const int kk = k + c;
-    if (kk < 0 || kk >= L.nz) continue;
-    const float mzc = mz[c + 1], kzc = ZC ? kz[c + 1] : 0.f;
-    const float zterm = L.wz * kzc + L.wm * mzc;
-    for (int b = -1; b <= 1; ++b) {
-      const int jj = j + b;
-      if (jj < 0 || jj >= L.ny) continue;
-      const float myb = my[b + 1], kyb = ky[b + 1];
-      const float yz = myb * zterm + L.wy * kyb * mzc;  // coefficient of mx
-      const float xz = L.wx * myb * mzc;                // coefficient of kx
-      const float *xr = x + cell(L, 0, jj, kk);
-      for (int a = -1; a <= 1; ++a) {
-        const int ii = i + a;
-        if (ii < 0 || ii >= L.nx) continue;
-        const float cf = mx[a + 1] * yz + kx[a + 1] * xz;
-        if (a == 0 && b == 0 && c == 0)
-          dg = cf;
-        else
-          off = fmaf(cf, xr[ii], off);
-      }
-    }
-  }
-}
-
 // 4-byte asynchronous copy; ok = false writes 0 (no global access)
 __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool ok) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -261,19 +189,164 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_gsz(HLevelDev L, int colour, int
   cp_async_wait0();  // copies of planes past the chunk land before exit
 }
 
-// r = b - A x (SIX: the fine 6-point operator).
+// r = b - A x as a z-march (SIX: the fine 6-point operator of the Hybrid
+// discretisation with Neumann neighbour counts; else the level's 27-point
+// Kronecker operator).  Same tiles and boxes as the colour sweep, an
+// eight-plane ring with copies two planes ahead; a thread owns four
+// consecutive cells of one row.  Tiles whose cells all have the uniform
+// interior factor rows use the level's 27 interior coefficients; the others
+// form each cell's coefficients from its factor rows (the same per-axis
+// factoring as the sweep, taps leaving the domain set to 0).
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+
 template <bool ZC, bool SIX>
-__global__ void __launch_bounds__(HNT) k_h_resid(HLevelDev L, const float *__restrict__ x,
-                                                 const float *__restrict__ b, float *__restrict__ r) {
-  const long long n = (long long)L.nx * L.ny * L.nz;
-  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
-    const int i = (int)(q % L.nx);
-    const long long t = q / L.nx;
-    const int j = (int)(t % L.ny), k = (int)(t / L.ny);
-    float off, dg;
-    apply_off<ZC, SIX>(L, x, i, j, k, off, dg);
-    r[q] = b[q] - (dg * x[q] + off);
+__global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, int vec, int vec_br,
+                                                      const float *__restrict__ x, const float *__restrict__ b,
+                                                      float *__restrict__ r) {
+  constexpr int NS = 8;
+  __shared__ __align__(16) float ring[NS][GZ_BC];
+  const int tid = threadIdx.x;
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
+  const int i0 = blockIdx.x * GZ_TX, j0 = blockIdx.y * GZ_TY;
+  const int zs = blockIdx.z * zchunk, ze = min(zs + zchunk, nz);
+  const size_t plane = (size_t)nx * ny;
+  auto load_plane = [&](int p) {
+    float *dst = ring[(p + NS) & (NS - 1)];
+    const bool pin = p >= 0 && p < nz;
+    if (vec) {
+      for (int q = tid; q < GZ_BC / 4; q += GZ_NT) {
+        const int c4 = q % (GZ_BW / 4), rr = q / (GZ_BW / 4);
+        const int gi = i0 - 4 + 4 * c4, gj = j0 - 1 + rr;
+        const bool ok = pin && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+        cp_async16z(dst + 4 * q, ok ? x + (size_t)p * plane + (size_t)gj * nx + gi : x, ok);
+      }
+    } else {
+      for (int q = tid; q < GZ_BC; q += GZ_NT) {
+        const int c = q % GZ_BW, rr = q / GZ_BW;
+        const int gi = i0 - 4 + c, gj = j0 - 1 + rr;
+        const bool ok = pin && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
+        cp_async4(dst + q, ok ? x + (size_t)p * plane + (size_t)gj * nx + gi : x, ok);
+      }
+    }
+    cp_async_commit();
+  };
+  const int l = tid & 15, ty = tid >> 4;
+  const int gi0 = i0 + 4 * l, gj = j0 + ty;
+  const bool row_in = gj < ny && gi0 < nx;
+  // all four cells interior in x and y (z is checked per plane)
+  const bool xy_int = gi0 >= L.ilo[0] && gi0 + 3 <= L.ihi[0] && gj >= L.ilo[1] && gj <= L.ihi[1];
+  const int cb = 4 * l;  // box column of the float4 left of the cells
+
+  // one copy group per plane, two planes ahead of the step that reads them
+  if (ZC) {
+    load_plane(zs - 1);
+    load_plane(zs);
+    load_plane(zs + 1);
+    load_plane(zs + 2);
+  } else {
+    load_plane(zs);
+    load_plane(zs + 1);
   }
+  for (int k = zs; k < ze; ++k) {
+    load_plane(ZC ? k + 3 : k + 2);
+    cp_async_wait2();  // all but the last two issued planes have landed: k + 1 (ZC) / k
+    __syncthreads();
+    if (row_in) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const bool fast = !SIX && xy_int && (!ZC || (k >= L.ilo[2] && k <= L.ihi[2]));
+      float Z1[3] = {0.f, 0.f, 0.f}, MZ[3] = {0.f, 0.f, 0.f};
+      if (!SIX && !fast) {
+        const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
+        if (ZC) {
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            if (k + c - 1 >= 0 && k + c - 1 < nz) {
+              MZ[c] = mz[c];
+              Z1[c] = L.wz * kz[c] + L.wm * mz[c];
+            }
+        } else {
+          MZ[1] = mz[1];
+          Z1[1] = L.wm * mz[1];
+        }
+      }
+      float xo[4] = {0.f, 0.f, 0.f, 0.f};  // the cells' own values
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (!ZC && c != 1) continue;
+        const float *pl = ring[(k + c - 1 + NS) & (NS - 1)];
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+          if (SIX && c != 1 && bb != 1) continue;
+          const int ro = (ty + bb) * GZ_BW + cb;  // box row of gj + bb - 1
+          const float4 lf = *reinterpret_cast<const float4 *>(pl + ro);
+          const float4 md = *reinterpret_cast<const float4 *>(pl + ro + 4);
+          const float4 rt = *reinterpret_cast<const float4 *>(pl + ro + 8);
+          const float v[6] = {lf.w, md.x, md.y, md.z, md.w, rt.x};
+          if (c == 1 && bb == 1) {
+            xo[0] = md.x;
+            xo[1] = md.y;
+            xo[2] = md.z;
+            xo[3] = md.w;
+          }
+          if (SIX) {
+            // neighbour sums only; the diagonal is applied below
+            if (c == 1 && bb == 1) {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) acc[m] += L.wx * (v[m] + v[m + 2]);
+            } else if (c == 1) {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) acc[m] += L.wy * v[m + 1];
+            } else {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) acc[m] += L.wz * v[m + 1];
+            }
+          } else if (fast) {
+            const float *cs = L.cst + c * 9 + bb * 3;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) acc[m] = fmaf(cs[0], v[m], fmaf(cs[1], v[m + 1], fmaf(cs[2], v[m + 2], acc[m])));
+          } else {
+            const int gjb = gj + bb - 1;
+            const bool yin = gjb >= 0 && gjb < ny;
+            const float myb = yin ? L.my[3 * gj + bb] : 0.f, kyb = yin ? L.ky[3 * gj + bb] : 0.f;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              const int gi = gi0 + m;
+              if (gi >= nx) continue;
+#pragma unroll
+              for (int aa = 0; aa < 3; ++aa) {
+                const int gia = gi + aa - 1;
+                if (gia < 0 || gia >= nx) continue;
+                const float mxa = L.mx[3 * gi + aa], kxa = L.kx[3 * gi + aa];
+                const float cf = mxa * myb * Z1[c] + (L.wy * mxa * kyb + L.wx * kxa * myb) * MZ[c];
+                acc[m] = fmaf(cf, v[m + aa], acc[m]);
+              }
+            }
+          }
+        }
+      }
+      const size_t o = (size_t)k * plane + (size_t)gj * nx + gi0;
+      if (SIX) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const int gi = gi0 + m;
+          float cnt = L.wm;
+          cnt += L.wx * (float)((gi > 0) + (gi < nx - 1));
+          cnt += L.wy * (float)((gj > 0) + (gj < ny - 1));
+          if (ZC) cnt += L.wz * (float)((k > 0) + (k < nz - 1));
+          acc[m] = cnt * xo[m] - acc[m];
+        }
+      }
+      if (vec_br) {  // nx % 4 == 0 and 16-byte aligned b, r: the four cells are one float4
+        const float4 bv = *reinterpret_cast<const float4 *>(b + o);
+        *reinterpret_cast<float4 *>(r + o) = make_float4(bv.x - acc[0], bv.y - acc[1], bv.z - acc[2], bv.w - acc[3]);
+      } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (gi0 + m < nx) r[o + m] = b[o + m] - acc[m];
+      }
+    }
+  }
+  cp_async_wait0();
 }
 
 // Fine cells of coarse cell I along one axis, with the weights of
@@ -396,7 +469,7 @@ namespace {
 // beyond it)
 template <typename K>
 int gsz_chunk(K kernel, int slot_idx, long tiles, int nz, int h) {
-  static int slots_cache[2] = {0, 0};
+  static int slots_cache[6] = {0, 0, 0, 0, 0, 0};
   int &slots = slots_cache[slot_idx];
   if (!slots) {
     int occ = 0, dev = 0, sms = 0;
@@ -443,19 +516,30 @@ int h_gs_launches(const HLevelDev &L) { return (L.wz != 0.f && L.nz > 1) ? 8 : 4
 
 cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const float *b, float *r,
                            cudaStream_t st) {
-  const long long n = (long long)L.nx * L.ny * L.nz;
   const bool zc = L.wz != 0.f && L.nz > 1;
+  const int gx = (L.nx + GZ_TX - 1) / GZ_TX, gy = (L.ny + GZ_TY - 1) / GZ_TY;
+  const long tiles = (long)gx * gy;
+  const bool nx4 = (L.nx & 3) == 0;
+  const int vec = (nx4 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
+  const int vec_br = (nx4 && ((uintptr_t)b & 15) == 0 && ((uintptr_t)r & 15) == 0) ? 1 : 0;
+  int chunk;
+#define GD_RZ(Z, S, I)                                                                    \
+  chunk = gsz_chunk(k_h_residz<Z, S>, I, tiles, L.nz, Z ? 3 : 1);                          \
+  k_h_residz<Z, S><<<dim3(gx, gy, (L.nz + chunk - 1) / chunk), GZ_NT, 0, st>>>(L, chunk, vec, vec_br, x, b, r);
   if (six) {
-    if (zc)
-      k_h_resid<true, true><<<grid_of(n), HNT, 0, st>>>(L, x, b, r);
-    else
-      k_h_resid<false, true><<<grid_of(n), HNT, 0, st>>>(L, x, b, r);
+    if (zc) {
+      GD_RZ(true, true, 2)
+    } else {
+      GD_RZ(false, true, 3)
+    }
   } else {
-    if (zc)
-      k_h_resid<true, false><<<grid_of(n), HNT, 0, st>>>(L, x, b, r);
-    else
-      k_h_resid<false, false><<<grid_of(n), HNT, 0, st>>>(L, x, b, r);
+    if (zc) {
+      GD_RZ(true, false, 4)
+    } else {
+      GD_RZ(false, false, 5)
+    }
   }
+#undef GD_RZ
   return cudaGetLastError();
 }
 
