@@ -909,6 +909,30 @@ def run_ncu_case(args):
     return 0 if rep["status"] in (0, 5) else 1
 
 
+def run_ncu_linear(args):
+    """One AD + SP step of the Linear discretisation on the 1024 x 1024 x 128
+    benchmark stack after one warm-up step (for ncu launch lists; not a
+    benchmark)."""
+    import torch
+    import gdsynth
+    import paper_1310_0041_gb300 as gd
+    gd.build()
+    I0 = torch.from_numpy(gdsynth.em_stack(NX, NY, NZ, seed=SEED, ncells=2000)).cuda().float()
+    I1 = torch.empty_like(I0)
+    I2 = torch.empty_like(I0)
+    s = gd.gd_stack_create(NX, NY, NZ, disc=gd.GD_DISC_LINEAR)
+    ctl = gd.solve_ctl(30, TOL, 2, 2, 16)
+    ctl_sp = gd.solve_ctl(30, TOL_SP, 2, 2, 16)
+    for _ in range(2):
+        r1 = gd.gd_diffuse_z(s, I0, I1, (0.0,) + BETA, ctl)
+        r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, ALPHA, ctl_sp)
+    torch.cuda.synchronize()
+    gd.gd_destroy(s)
+    print(json.dumps({"ncu_linear": "linear_ad_sp_%dx%dx%d" % (NX, NY, NZ), "ad_cycles": r1["cycles"],
+                      "sp_cycles": r2["cycles"]}))
+    return 0 if r1["status"] == 0 and r2["status"] == 0 else 1
+
+
 def run_ncu_conv(args):
     """The learned guess's forward pass on 32 tiles of 256 x 256 x 16, four
     times (for ncu captures of the convolution kernels; not a benchmark):
@@ -981,6 +1005,8 @@ def main(argv=None):
                     help="slices of the --ncu-batch case (fewer for detailed captures)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run the small profiling case instead of the benchmark")
+    ap.add_argument("--ncu-linear", action="store_true",
+                    help="one Linear AD + SP step on the benchmark stack after a warm-up (for ncu; not a benchmark)")
     ap.add_argument("--ncu-case-ny", type=int, default=1024,
                     help="y extent of the --ncu-case stack (1024 x ny x 64)")
     ap.add_argument("--ncu-conv", action="store_true",
@@ -988,6 +1014,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.ncu_linear:
+        return run_ncu_linear(args)
     if args.ncu_conv:
         return run_ncu_conv(args)
     if args.ncu_batch:

@@ -831,19 +831,32 @@ __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
   }
 }
 
-// (h, l) += e exactly in FP64 and rounded back to a float pair; block sums
-// of the new iterate (slot S_X)
+// (h, l) += e in float-pair arithmetic (TwoSum, then renormalised: the pair
+// keeps ~48 bits, as the FP64 update it replaces kept 53 -- GB300's FP64
+// pipe made that streaming pass five times slower than its bytes); block
+// sums of the new iterate (slot S_X), accumulated per thread as a float pair
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
 __global__ void __launch_bounds__(HNT) k_l_update(long long n, const float *__restrict__ e, float *__restrict__ h,
                                                   float *__restrict__ l, double *__restrict__ partials) {
-  double sx = 0.0;
+  float sxh = 0.f, sxl = 0.f;
   for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
-    const double v = (double)h[q] + (double)l[q] + (double)e[q];
-    const float hv = (float)v;
+    float s, t;
+    two_sum(h[q], e[q], s, t);
+    t += l[q];
+    const float hv = s + t;
+    const float lv = t - (hv - s);
     h[q] = hv;
-    l[q] = (float)(v - (double)hv);
-    sx += v;
+    l[q] = lv;
+    float u, err;
+    two_sum(sxh, hv, u, err);
+    sxh = u;
+    sxl += err + lv;
   }
-  block_sums(sx, 0.0, partials, S_X, -1);
+  block_sums((double)sxh + (double)sxl, 0.0, partials, S_X, -1);
 }
 
 // block sums of an array (slot)
@@ -854,11 +867,14 @@ __global__ void __launch_bounds__(HNT) k_l_sum(long long n, const float *__restr
   block_sums(s, 0.0, partials, slot, -1);
 }
 
-// out = h + l + shift, rounded to float
+// out = h + l + shift, rounded to float (the shift split as sh + sl)
 __global__ void __launch_bounds__(HNT) k_l_final(long long n, const float *__restrict__ h, const float *__restrict__ l,
-                                                 double shift, float *__restrict__ out) {
-  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT)
-    out[q] = (float)((double)h[q] + (double)l[q] + shift);
+                                                 float sh, float sl, float *__restrict__ out) {
+  for (long long q = blockIdx.x * (long long)HNT + threadIdx.x; q < n; q += (long long)gridDim.x * HNT) {
+    float s, e;
+    two_sum(h[q], sh, s, e);
+    out[q] = s + (e + (l[q] + sl));
+  }
 }
 
 }  // namespace
@@ -968,6 +984,7 @@ cudaError_t launch_l_sum(long long n, const float *a, double *partials, int slot
 }
 
 cudaError_t launch_l_final(long long n, const float *h, const float *l, double shift, float *out, cudaStream_t st) {
-  k_l_final<<<grid_of(n), HNT, 0, st>>>(n, h, l, shift, out);
+  const float sh = (float)shift, sl = (float)(shift - (double)sh);
+  k_l_final<<<grid_of(n), HNT, 0, st>>>(n, h, l, sh, sl, out);
   return cudaGetLastError();
 }
