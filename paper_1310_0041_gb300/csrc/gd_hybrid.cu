@@ -139,7 +139,12 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_gsz(HLevelDev L, int colour, int
     load_plane(k0);
   }
   cp_async_commit();
+  // b of this thread's cell, loaded a step ahead of its use
+  const size_t ocell = (size_t)gj * nx + gi;
+  float bnext = (act && k0 < ze) ? b[(size_t)k0 * plane + ocell] : 0.f;
   for (int k = k0; k < ze; k += kstep) {
+    const float bk = bnext;
+    if (act && k + kstep < ze) bnext = b[(size_t)(k + kstep) * plane + ocell];
     if (ZC) {
       load_plane(k + 2);
       load_plane(k + 3);
@@ -182,8 +187,7 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_gsz(HLevelDev L, int colour, int
         ax = fmaf(Z1[c], su, fmaf(MZ[c], sv, ax));
       }
       const float dg = U[1][1] * Z1[1] + V[1][1] * MZ[1];
-      const size_t o = (size_t)k * plane + (size_t)gj * nx + gi;
-      x[o] = xc + (b[o] - ax) / dg;
+      x[(size_t)k * plane + ocell] = xc + (bk - ax) / dg;
     }
   }
   cp_async_wait0();  // copies of planes past the chunk land before exit
@@ -247,7 +251,29 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, 
     load_plane(zs);
     load_plane(zs + 1);
   }
+  // b of this thread's cells, loaded a step ahead of its use
+  const size_t orow = (size_t)gj * nx + gi0;
+  auto load_b = [&](int k, float *bv) {
+    if (!row_in || k >= ze) return;
+    const float *bp = b + (size_t)k * plane + orow;
+    if (vec_br) {
+      const float4 t = *reinterpret_cast<const float4 *>(bp);
+      bv[0] = t.x;
+      bv[1] = t.y;
+      bv[2] = t.z;
+      bv[3] = t.w;
+    } else {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) bv[m] = gi0 + m < nx ? bp[m] : 0.f;
+    }
+  };
+  float bn[4] = {0.f, 0.f, 0.f, 0.f};
+  load_b(zs, bn);
   for (int k = zs; k < ze; ++k) {
+    float bk[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) bk[m] = bn[m];
+    load_b(k + 1, bn);
     load_plane(ZC ? k + 3 : k + 2);
     cp_async_wait2();  // all but the last two issued planes have landed: k + 1 (ZC) / k
     __syncthreads();
@@ -337,12 +363,11 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, 
         }
       }
       if (vec_br) {  // nx % 4 == 0 and 16-byte aligned b, r: the four cells are one float4
-        const float4 bv = *reinterpret_cast<const float4 *>(b + o);
-        *reinterpret_cast<float4 *>(r + o) = make_float4(bv.x - acc[0], bv.y - acc[1], bv.z - acc[2], bv.w - acc[3]);
+        *reinterpret_cast<float4 *>(r + o) = make_float4(bk[0] - acc[0], bk[1] - acc[1], bk[2] - acc[2], bk[3] - acc[3]);
       } else {
 #pragma unroll
         for (int m = 0; m < 4; ++m)
-          if (gi0 + m < nx) r[o + m] = b[o + m] - acc[m];
+          if (gi0 + m < nx) r[o + m] = bk[m] - acc[m];
       }
     }
   }
@@ -694,7 +719,32 @@ __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
   for (int p = ZC ? zs0 - 1 : zs0; p <= (ZC ? zs0 + 1 : zs0); ++p) load_plane(p);
 
   float srr = 0.f, sbb = 0.f;
+  // the right-hand side pair of this thread's two x-stage cells, loaded a
+  // step ahead of its use (RESID)
+  constexpr int XQ = LZ_TX * LZ_TY / LZ_NT;
+  static_assert(XQ * LZ_NT == LZ_TX * LZ_TY, "x-stage cells per thread");
+  float bnh[XQ], bnl[XQ];
+  auto load_b = [&](int k) {
+#pragma unroll
+    for (int u = 0; u < XQ; ++u) {
+      const int q = tid + u * LZ_NT, gi = i0 + q % LZ_TX, gj = j0 + q / LZ_TX;
+      bnh[u] = bnl[u] = 0.f;
+      if (MODE == LZ_RESID && k < ze && gi < nx && gj < ny) {
+        const size_t o = (size_t)k * plane + (size_t)gj * nx + gi;
+        bnh[u] = a.bh[o];
+        bnl[u] = a.bl[o];
+      }
+    }
+  };
+  load_b(zs0);
   for (int k = zs0; k < ze; ++k) {
+    float bkh[XQ], bkl[XQ];
+#pragma unroll
+    for (int u = 0; u < XQ; ++u) {
+      bkh[u] = bnh[u];
+      bkl[u] = bnl[u];
+    }
+    load_b(k + 1);
     load_plane(ZC ? k + 2 : k + 1);
     cp_async_wait1();
     __syncthreads();
@@ -767,7 +817,9 @@ __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
     }
     __syncthreads();
     // ---- x stage: Kx Ymm, Mx Ykm, Mx Y3 (and Mx Ymm), then the output ----
-    for (int q = tid; q < LZ_TX * LZ_TY; q += LZ_NT) {
+#pragma unroll
+    for (int u = 0; u < XQ; ++u) {
+      const int q = tid + u * LZ_NT;
       const int tx = q % LZ_TX, ty = q / LZ_TX, gi = i0 + tx, gj = j0 + ty;
       if (gi >= nx || gj >= ny) continue;
       const int bx = tx + 1;
@@ -789,7 +841,7 @@ __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
         if (y3) df_wadd(v, a.wh[2], a.wl[2], s3);
         if (a.want_m) df_wadd(v, a.wh[3], a.wl[3], smm);
         // r = b - v in float-pair arithmetic, rounded once
-        const float bhv = a.bh[o], blv = a.bl[o];
+        const float bhv = bkh[u], blv = bkl[u];
         const float t = bhv - v.h;
         const float bb = t - bhv;
         const float err = (bhv - (t - bb)) + (-v.h - bb);
