@@ -728,9 +728,12 @@ int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
     return GD_OK;
   }
   auto gs = [&](Level &v) -> int {
+    // out of place into the level's second buffer (free during sweeps),
+    // then the two swap, as the 6-point sweeps do
     ProfScope ps(s, P_SWEEP_COARSE, (double)v.n * 12.0);
-    CK(launch_h_gs(v.hd, v.x, v.b, s->stream));
-    s->launches += h_gs_launches(v.hd) - 1;  // one colour launch per colour
+    CK(launch_h_gsf(v.hd, v.x, v.t, v.b, s->stream));
+    s->launches += h_gsf_launches(v.hd) - 1;
+    std::swap(v.x, v.t);
     return GD_OK;
   };
   for (int l = 0; l < nl - 1; ++l) {

@@ -13,8 +13,8 @@
 // factors, so no stencil is stored.
 //
 // Relaxation on the 27-point levels is Gauss-Seidel with eight colours (the
-// parities of i, j and k; same-colour cells are never neighbours), one launch
-// per colour, in place.
+// parities of i, j and k; same-colour cells are never neighbours), the four
+// in-plane colours of a plane fused in one z-march launch (k_h_gsf).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,22 +36,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// One colour of the Gauss-Seidel sweep on a 27-point level, as a z-march.
-// Colour (px, py, pz) holds the cells with i = px, j = py (mod 2) and, on
-// coupled levels, k = pz (mod 2); same-colour cells are never neighbours,
-// so a launch updates them all from the values before it.  Uncoupled
-// levels (no z terms) use the four in-plane colours over every plane: the
-// same iterates in half the launches.
-//
-// A CTA owns a GZ_TX x GZ_TY column tile (one colour cell per thread per
-// plane) and marches z over a chunk of planes; cp.async brings each plane's
-// box (the tile, one row above and below, four columns left and right: a
-// 16-byte aligned start) into a ring.  The 27 coefficients factor per axis,
-//   cf(a, b, c) = U(a, b) Z1(c) + V(a, b) MZ(c),
-//   U = mx(a) my(b), V = wy mx(a) ky(b) + wx kx(a) my(b),
-//   Z1 = wz kz(c) + wm mz(c), MZ = mz(c),
-// with U, V fixed per thread and Z1, MZ per plane, so a cell's update is
-// two 9-point in-plane dot products per plane: x += (b - A x) / cf(0,0,0).
+// Tiles and boxes of the 27-point residual's z-march: a CTA owns a
+// GZ_TX x GZ_TY column tile; a plane's box is the tile, one row above and
+// below and four columns left and right (a 16-byte aligned start).
 constexpr int GZ_TX = 64, GZ_TY = 16, GZ_NT = 256;
 constexpr int GZ_BW = GZ_TX + 8, GZ_BH = GZ_TY + 2;  // box: columns i0-4 .., rows j0-1 ..
 constexpr int GZ_BC = GZ_BW * GZ_BH;
@@ -63,99 +50,121 @@ __device__ __forceinline__ void cp_async16z(float *dst, const float *src, bool o
                : "memory");
 }
 
+// One Gauss-Seidel sweep of a 27-point level with the in-plane colours
+// fused, out of place.  The eight colours (parities of i, j, k) run in the
+// order of the colour launches: on a coupled level the even planes' four
+// in-plane colours (launch pz = 0: every plane read from xin, the even
+// planes written to xout), then the odd planes' (pz = 1: the odd planes
+// read from xin, their even neighbours from xout, the odd planes written to
+// xout); an uncoupled level takes the four colours on every plane in one
+// launch.  A CTA owns an FS_TX x FS_TY tile of a plane and relaxes colour c
+// (c = px + 2 py) on the tile and a ring of 3 - c cells around it in shared
+// memory, in place: colour c + 1 on a ring one narrower reads exactly the
+// colour-c values it needs.  Ring cells are computed from the same values,
+// with the same arithmetic, as by the CTA that owns them, so the result does
+// not depend on the tiling; only tile cells are written.  The CTA marches z
+// with the planes in a shared-memory ring (cp.async, a step ahead).
+constexpr int FS_TX = 64, FS_TY = 32, FS_NT = 256;
+constexpr int FS_R = 4;                                    // box margin (ring 3 + its neighbours)
+constexpr int FS_BW = FS_TX + 2 * FS_R, FS_BH = FS_TY + 2 * FS_R;
+constexpr int FS_BC = FS_BW * FS_BH;
+constexpr int FS_CPT = 3;  // colour cells per thread and colour (<= (64 + 6)(32 + 6) / 4 / 256)
+static_assert(((FS_TX + 6) / 2) * ((FS_TY + 6) / 2) <= FS_CPT * FS_NT, "colour cells per thread");
+__host__ __device__ constexpr size_t gsf_smem(bool zc) { return (zc ? 5 : 2) * (size_t)FS_BC * sizeof(float); }
+
 template <bool ZC>
-__global__ void __launch_bounds__(GZ_NT, 3) k_h_gsz(HLevelDev L, int colour, int zchunk, int vec,
-                                                   float *__restrict__ x, const float *__restrict__ b) {
-  constexpr int NS = ZC ? 8 : 4;  // ring: planes k-1 .. k+3 (coupled), k .. k+2
-  __shared__ __align__(16) float ring[NS][GZ_BC];
+__global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zchunk, int vec,
+                                                   const float *__restrict__ xc, const float *xn,
+                                                   const float *__restrict__ b, float *xout) {
+  extern __shared__ __align__(16) float fsm[];
+  float *cur = fsm;                // two slots: the updated planes k, k + 2 (or k, k + 1)
+  float *nbs = fsm + 2 * FS_BC;    // three slots: neighbour planes (coupled levels)
   const int tid = threadIdx.x;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
-  const int px = colour & 1, py = (colour >> 1) & 1, pz = (colour >> 2) & 1;
-  const int i0 = blockIdx.x * GZ_TX, j0 = blockIdx.y * GZ_TY;
+  const int i0 = blockIdx.x * FS_TX, j0 = blockIdx.y * FS_TY;
   const int zs = blockIdx.z * zchunk, ze = min(zs + zchunk, nz);
   const size_t plane = (size_t)nx * ny;
+  const int kstep = ZC ? 2 : 1;
+  const int k0 = ZC ? zs + ((zs & 1) != pz ? 1 : 0) : zs;
 
-  // plane p's box into its slot (zeros outside the domain)
-  auto load_plane = [&](int p) {
-    float *dst = ring[(p + NS) % NS];
+  auto load_box = [&](float *dst, const float *src, int p) {
     const bool pin = p >= 0 && p < nz;
     if (vec) {
-      for (int q = tid; q < GZ_BC / 4; q += GZ_NT) {
-        const int c4 = q % (GZ_BW / 4), r = q / (GZ_BW / 4);
-        const int gi = i0 - 4 + 4 * c4, gj = j0 - 1 + r;
+      for (int q = tid; q < FS_BC / 4; q += FS_NT) {
+        const int c4 = q % (FS_BW / 4), rr = q / (FS_BW / 4);
+        const int gi = i0 - FS_R + 4 * c4, gj = j0 - FS_R + rr;
         const bool ok = pin && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-        cp_async16z(dst + 4 * q, ok ? x + (size_t)p * plane + (size_t)gj * nx + gi : x, ok);
+        cp_async16z(dst + 4 * q, ok ? src + (size_t)p * plane + (size_t)gj * nx + gi : src, ok);
       }
     } else {
-      for (int q = tid; q < GZ_BC; q += GZ_NT) {
-        const int c = q % GZ_BW, r = q / GZ_BW;
-        const int gi = i0 - 4 + c, gj = j0 - 1 + r;
+      for (int q = tid; q < FS_BC; q += FS_NT) {
+        const int c = q % FS_BW, rr = q / FS_BW;
+        const int gi = i0 - FS_R + c, gj = j0 - FS_R + rr;
         const bool ok = pin && gi >= 0 && gi < nx && gj >= 0 && gj < ny;
-        cp_async4(dst + q, ok ? x + (size_t)p * plane + (size_t)gj * nx + gi : x, ok);
+        cp_async4(dst + q, ok ? src + (size_t)p * plane + (size_t)gj * nx + gi : src, ok);
       }
     }
   };
+  auto cur_slot = [&](int k) { return cur + (((k - k0) / kstep) & 1) * FS_BC; };
+  auto nb_slot = [&](int p) { return nbs + (((p - k0 + 1) >> 1) % 3) * FS_BC; };  // p = k0 - 1, k0 + 1, ...
 
-  // this thread's cell and its per-thread coefficient factors
-  const int l = tid & 31, tyh = tid >> 5;
-  const int gi = i0 + 2 * l + px, gj = j0 + 2 * tyh + py;
-  const bool act = gi < nx && gj < ny;
-  float U[3][3], V[3][3];  // [b][a]
-  {
-    float kxr[3] = {0.f, 0.f, 0.f}, mxr[3] = {0.f, 0.f, 0.f}, kyr[3] = {0.f, 0.f, 0.f}, myr[3] = {0.f, 0.f, 0.f};
-    if (act) {
+  // colour c's cells on the tile and a ring of 3 - c: the m-th of this thread
+  auto colour_cell = [&](int c, int m, int &ci, int &cj) -> bool {
+    const int px = c & 1, py = c >> 1, d = 3 - c;
+    int ia = max(i0 - d, 0), ja = max(j0 - d, 0);
+    const int ib = min(i0 + FS_TX - 1 + d, nx - 1), jb = min(j0 + FS_TY - 1 + d, ny - 1);
+    ia += (ia & 1) != px;
+    ja += (ja & 1) != py;
+    if (ia > ib || ja > jb) return false;
+    const int ncx = (ib - ia) / 2 + 1, ncy = (jb - ja) / 2 + 1;
+    const int q = tid + m * FS_NT;
+    if (q >= ncx * ncy) return false;
+    ci = ia + 2 * (q % ncx);
+    cj = ja + 2 * (q / ncx);
+    return true;
+  };
+
+  // this thread's colour cells are the same on every plane: their box
+  // coordinates packed as bx | by << 8 (-1: none), computed once
+  int cell[4][FS_CPT];
 #pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        if (gi + t - 1 >= 0 && gi + t - 1 < nx) {
-          kxr[t] = L.kx[3 * gi + t];
-          mxr[t] = L.mx[3 * gi + t];
-        }
-        if (gj + t - 1 >= 0 && gj + t - 1 < ny) {
-          kyr[t] = L.ky[3 * gj + t];
-          myr[t] = L.my[3 * gj + t];
-        }
-      }
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int m = 0; m < FS_CPT; ++m) {
+      int ci, cj;
+      cell[c][m] = colour_cell(c, m, ci, cj) ? (ci - i0 + FS_R) | ((cj - j0 + FS_R) << 8) : -1;
     }
-#pragma unroll
-    for (int bb = 0; bb < 3; ++bb)
-#pragma unroll
-      for (int aa = 0; aa < 3; ++aa) {
-        U[bb][aa] = mxr[aa] * myr[bb];
-        V[bb][aa] = L.wy * mxr[aa] * kyr[bb] + L.wx * kxr[aa] * myr[bb];
-      }
-  }
-  // shared-memory offset of the float2 that starts this thread's three
-  // columns' pairs (columns gi - 1 .. gi + 1 sit in two aligned float2)
-  const int ci = gi - i0 + 4;                // box column of the cell
-  const int c2 = (ci - 1) & ~1;              // first float2 (even)
-  const int row0 = (gj - j0 + 1 - 1) * GZ_BW;  // box row of gj - 1
-
-  // first updated plane of the chunk and the stride
-  const int kstep = ZC ? 2 : 1;
-  const int k0 = ZC ? zs + ((zs & 1) != pz ? 1 : 0) : zs;
   if (ZC) {
-    for (int p = k0 - 1; p <= k0 + 1; ++p) load_plane(p);
+    load_box(cur_slot(k0), xc, k0);
+    load_box(nb_slot(k0 - 1), xn, k0 - 1);
+    load_box(nb_slot(k0 + 1), xn, k0 + 1);
   } else {
-    load_plane(k0);
+    load_box(cur_slot(k0), xc, k0);
   }
   cp_async_commit();
-  // b of this thread's cell, loaded a step ahead of its use
-  const size_t ocell = (size_t)gj * nx + gi;
-  float bnext = (act && k0 < ze) ? b[(size_t)k0 * plane + ocell] : 0.f;
   for (int k = k0; k < ze; k += kstep) {
-    const float bk = bnext;
-    if (act && k + kstep < ze) bnext = b[(size_t)(k + kstep) * plane + ocell];
-    if (ZC) {
-      load_plane(k + 2);
-      load_plane(k + 3);
-    } else {
-      load_plane(k + 1);
+    // the right-hand side of this step's cells (all four colours)
+    float bq[4][FS_CPT];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int m = 0; m < FS_CPT; ++m) {
+        const int pk = cell[c][m];
+        bq[c][m] = pk >= 0 ? b[(size_t)k * plane + (size_t)(j0 - FS_R + (pk >> 8)) * nx + (i0 - FS_R + (pk & 255))]
+                           : 0.f;
+      }
+    cp_async_wait0();
+    __syncthreads();  // this step's planes have landed; every thread is past the previous step
+    if (k + kstep < ze) {
+      load_box(cur_slot(k + kstep), xc, k + kstep);
+      if (ZC) load_box(nb_slot(k + 3), xn, k + 3);
     }
     cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
-    if (act) {
-      float Z1[3] = {0.f, 0.f, 0.f}, MZ[3] = {0.f, 0.f, 0.f};
+    float *pc = cur_slot(k);
+    const float *pm = ZC ? nb_slot(k - 1) : pc, *pp = ZC ? nb_slot(k + 1) : pc;
+    // per-plane z factors (general path)
+    float Z1[3] = {0.f, 0.f, 0.f}, MZ[3] = {0.f, 0.f, 0.f};
+    {
       const float *kz = L.kz + 3 * k, *mz = L.mz + 3 * k;
       if (ZC) {
 #pragma unroll
@@ -168,29 +177,77 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_gsz(HLevelDev L, int colour, int
         MZ[1] = mz[1];
         Z1[1] = L.wm * mz[1];
       }
-      float ax = 0.f, xc = 0.f;
+    }
+    const bool zint = !ZC || (k >= L.ilo[2] && k <= L.ihi[2]);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (!ZC && c != 1) continue;
-        const float *pl = ring[(k + c - 1 + NS) % NS] + row0 + c2;
-        float su = 0.f, sv = 0.f;
+    for (int c = 0; c < 4; ++c) {
 #pragma unroll
-        for (int bb = 0; bb < 3; ++bb) {
-          const float2 lo = *reinterpret_cast<const float2 *>(pl + bb * GZ_BW);
-          const float2 hi = *reinterpret_cast<const float2 *>(pl + bb * GZ_BW + 2);
-          // columns gi-1, gi, gi+1: (lo.y, hi.x, hi.y) if ci is even, else (lo.x, lo.y, hi.x)
-          const float v0 = (ci & 1) ? lo.x : lo.y, v1 = (ci & 1) ? lo.y : hi.x, v2 = (ci & 1) ? hi.x : hi.y;
-          su = fmaf(U[bb][0], v0, fmaf(U[bb][1], v1, fmaf(U[bb][2], v2, su)));
-          sv = fmaf(V[bb][0], v0, fmaf(V[bb][1], v1, fmaf(V[bb][2], v2, sv)));
-          if (c == 1 && bb == 1) xc = v1;
+      for (int m = 0; m < FS_CPT; ++m) {
+        const int pk = cell[c][m];
+        if (pk < 0) continue;
+        const int bx = pk & 255, by = pk >> 8;
+        const int ci = i0 - FS_R + bx, cj = j0 - FS_R + by;
+        const int o = by * FS_BW + bx;
+        // columns bx - 1 .. bx + 1 of a row as two aligned float2 loads
+        const int o2 = (by - 1) * FS_BW + ((bx - 1) & ~1);
+        const bool odd = bx & 1;
+        auto row3 = [&](const float *pl, int bb, float &v0, float &v1, float &v2) {
+          const float2 lo = *reinterpret_cast<const float2 *>(pl + o2 + bb * FS_BW);
+          const float2 hi = *reinterpret_cast<const float2 *>(pl + o2 + bb * FS_BW + 2);
+          v0 = odd ? lo.x : lo.y;
+          v1 = odd ? lo.y : hi.x;
+          v2 = odd ? hi.x : hi.y;
+        };
+        float ax = 0.f, dg;
+        if (zint && ci >= L.ilo[0] && ci <= L.ihi[0] && cj >= L.ilo[1] && cj <= L.ihi[1]) {
+          float az[3] = {0.f, 0.f, 0.f};  // one chain per plane
+#pragma unroll
+          for (int zc = 0; zc < 3; ++zc) {
+            if (!ZC && zc != 1) continue;
+            const float *pl = zc == 0 ? pm : (zc == 1 ? pc : pp);
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb) {
+              float v0, v1, v2;
+              row3(pl, bb, v0, v1, v2);
+              const float *cs = L.cst + zc * 9 + bb * 3;
+              az[zc] = fmaf(cs[0], v0, fmaf(cs[1], v1, fmaf(cs[2], v2, az[zc])));
+            }
+          }
+          ax = (az[0] + az[2]) + az[1];
+          dg = L.cst[13];
+        } else {
+          float kxr[3], mxr[3], kyr[3], myr[3];
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const bool xin = ci + t - 1 >= 0 && ci + t - 1 < nx, yin = cj + t - 1 >= 0 && cj + t - 1 < ny;
+            kxr[t] = xin ? L.kx[3 * ci + t] : 0.f;
+            mxr[t] = xin ? L.mx[3 * ci + t] : 0.f;
+            kyr[t] = yin ? L.ky[3 * cj + t] : 0.f;
+            myr[t] = yin ? L.my[3 * cj + t] : 0.f;
+          }
+#pragma unroll
+          for (int zc = 0; zc < 3; ++zc) {
+            if (!ZC && zc != 1) continue;
+            const float *pl = zc == 0 ? pm : (zc == 1 ? pc : pp);
+#pragma unroll
+            for (int bb = 0; bb < 3; ++bb)
+#pragma unroll
+              for (int aa = 0; aa < 3; ++aa) {
+                const float cf = mxr[aa] * myr[bb] * Z1[zc] + (L.wy * mxr[aa] * kyr[bb] + L.wx * kxr[aa] * myr[bb]) * MZ[zc];
+                ax = fmaf(cf, pl[o + (bb - 1) * FS_BW + aa - 1], ax);
+              }
+          }
+          dg = mxr[1] * myr[1] * Z1[1] + (L.wy * mxr[1] * kyr[1] + L.wx * kxr[1] * myr[1]) * MZ[1];
         }
-        ax = fmaf(Z1[c], su, fmaf(MZ[c], sv, ax));
+        const float v = pc[o] + (bq[c][m] - ax) / dg;
+        pc[o] = v;
+        if (ci >= i0 && ci < i0 + FS_TX && cj >= j0 && cj < j0 + FS_TY)
+          xout[(size_t)k * plane + (size_t)cj * nx + ci] = v;
       }
-      const float dg = U[1][1] * Z1[1] + V[1][1] * MZ[1];
-      x[(size_t)k * plane + ocell] = xc + (bk - ax) / dg;
+      if (c < 3) __syncthreads();
     }
   }
-  cp_async_wait0();  // copies of planes past the chunk land before exit
+  cp_async_wait0();
 }
 
 // r = b - A x as a z-march (SIX: the fine 6-point operator of the Hybrid
@@ -489,11 +546,11 @@ int grid_of(long long n) {
 }  // namespace
 
 namespace {
-// z chunks of a colour launch: as for the other z-march kernels, the chunk
-// count minimises ceil(CTAs / resident slots) x (chunk + the planes loaded
-// beyond it)
+// z chunks of a residual launch: as for the other z-march kernels, the
+// chunk count minimises ceil(CTAs / resident slots) x (chunk + the planes
+// loaded beyond it)
 template <typename K>
-int gsz_chunk(K kernel, int slot_idx, long tiles, int nz, int h) {
+int resid_chunk(K kernel, int slot_idx, long tiles, int nz, int h) {
   static int slots_cache[6] = {0, 0, 0, 0, 0, 0};
   int &slots = slots_cache[slot_idx];
   if (!slots) {
@@ -521,23 +578,67 @@ int gsz_chunk(K kernel, int slot_idx, long tiles, int nz, int h) {
 }
 }  // namespace
 
-cudaError_t launch_h_gs(const HLevelDev &L, float *x, const float *b, cudaStream_t st) {
-  const bool zc = L.wz != 0.f && L.nz > 1;
-  const int gx = (L.nx + GZ_TX - 1) / GZ_TX, gy = (L.ny + GZ_TY - 1) / GZ_TY;
-  const int vec = ((L.nx & 3) == 0 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
-  const int chunk = zc ? gsz_chunk(k_h_gsz<true>, 1, (long)gx * gy, L.nz, 3)
-                       : gsz_chunk(k_h_gsz<false>, 0, (long)gx * gy, L.nz, 1);
+
+namespace {
+// resident CTAs of a kernel with dynamic shared memory, then the z chunks
+// as for the other z-march kernels
+template <typename K>
+int plan_chunk_dyn(K kernel, int threads, size_t smem, int &slots, long tiles, int nz, int h) {
+  if (!slots) {
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem) != cudaSuccess || occ < 1) {
+      cudaGetLastError();
+      occ = 1;
+    }
+    slots = occ * (sms > 0 ? sms : 1);
+  }
+  long best = -1;
+  int zc = nz;
+  for (int c = 1; c <= std::min(nz, GZ_MAX_CHUNKS); ++c) {
+    const int q = (nz + c - 1) / c;
+    const long gz = (nz + q - 1) / q;
+    const long cost = ((tiles * gz + slots - 1) / slots) * (q + h);
+    if (best < 0 || cost < best) {
+      best = cost;
+      zc = q;
+    }
+  }
+  return zc;
+}
+template <bool ZC>
+cudaError_t run_gsf(const HLevelDev &L, const float *x, float *xout, const float *b, cudaStream_t st) {
+  static bool attr = false;
+  static int slots = 0;
+  const size_t smem = gsf_smem(ZC);
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_h_gsf<ZC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int gx = (L.nx + FS_TX - 1) / FS_TX, gy = (L.ny + FS_TY - 1) / FS_TY;
+  const int vec = ((L.nx & 3) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)xout & 15) == 0) ? 1 : 0;
+  const int chunk = plan_chunk_dyn(k_h_gsf<ZC>, FS_NT, smem, slots, (long)gx * gy, L.nz, ZC ? 3 : 1);
   const dim3 grid(gx, gy, (L.nz + chunk - 1) / chunk);
-  for (int c = 0; c < (zc ? 8 : 4); ++c) {
-    if (zc)
-      k_h_gsz<true><<<grid, GZ_NT, 0, st>>>(L, c, chunk, vec, x, b);
-    else
-      k_h_gsz<false><<<grid, GZ_NT, 0, st>>>(L, c, chunk, vec, x, b);
+  if (ZC) {
+    // even planes' colours from x into xout, then the odd planes' with their
+    // (updated) even neighbours from xout
+    k_h_gsf<true><<<grid, FS_NT, smem, st>>>(L, 0, chunk, vec, x, x, b, xout);
+    k_h_gsf<true><<<grid, FS_NT, smem, st>>>(L, 1, chunk, vec, x, xout, b, xout);
+  } else {
+    k_h_gsf<false><<<grid, FS_NT, smem, st>>>(L, 0, chunk, vec, x, x, b, xout);
   }
   return cudaGetLastError();
 }
+}  // namespace
 
-int h_gs_launches(const HLevelDev &L) { return (L.wz != 0.f && L.nz > 1) ? 8 : 4; }
+cudaError_t launch_h_gsf(const HLevelDev &L, const float *x, float *xout, const float *b, cudaStream_t st) {
+  if (L.wz != 0.f && L.nz > 1) return run_gsf<true>(L, x, xout, b, st);
+  return run_gsf<false>(L, x, xout, b, st);
+}
+
+int h_gsf_launches(const HLevelDev &L) { return (L.wz != 0.f && L.nz > 1) ? 2 : 1; }
 
 cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const float *b, float *r,
                            cudaStream_t st) {
@@ -549,7 +650,7 @@ cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const f
   const int vec_br = (nx4 && ((uintptr_t)b & 15) == 0 && ((uintptr_t)r & 15) == 0) ? 1 : 0;
   int chunk;
 #define GD_RZ(Z, S, I)                                                                    \
-  chunk = gsz_chunk(k_h_residz<Z, S>, I, tiles, L.nz, Z ? 3 : 1);                          \
+  chunk = resid_chunk(k_h_residz<Z, S>, I, tiles, L.nz, Z ? 3 : 1);                          \
   k_h_residz<Z, S><<<dim3(gx, gy, (L.nz + chunk - 1) / chunk), GZ_NT, 0, st>>>(L, chunk, vec, vec_br, x, b, r);
   if (six) {
     if (zc) {

@@ -133,9 +133,11 @@ struct HLevelDev {
   int ilo[3], ihi[3];
   float cst[27];
 };
-// eight-colour Gauss-Seidel sweep of a 27-point level, in place
-cudaError_t launch_h_gs(const HLevelDev &L, float *x, const float *b, cudaStream_t st);
-int h_gs_launches(const HLevelDev &L);  // colour launches of one launch_h_gs
+// eight-colour Gauss-Seidel sweep of a 27-point level with the in-plane
+// colours fused, out of place: the result is in xout (two launches on a
+// coupled level, one otherwise)
+cudaError_t launch_h_gsf(const HLevelDev &L, const float *x, float *xout, const float *b, cudaStream_t st);
+int h_gsf_launches(const HLevelDev &L);
 // r = b - A x (six: the fine 6-point operator, factors unused)
 cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const float *b, float *r,
                            cudaStream_t st);
