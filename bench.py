@@ -912,15 +912,17 @@ def run_ncu_case(args):
 def run_ncu_linear(args):
     """One AD + SP step of the Linear discretisation on the 1024 x 1024 x 128
     benchmark stack after one warm-up step (for ncu launch lists; not a
-    benchmark)."""
+    benchmark); 1024 x 512 x 64 with --ncu-linear-small (about 3 GB on the
+    device, for multi-pass captures)."""
     import torch
     import gdsynth
     import paper_1310_0041_gb300 as gd
     gd.build()
-    I0 = torch.from_numpy(gdsynth.em_stack(NX, NY, NZ, seed=SEED, ncells=2000)).cuda().float()
+    nx, ny, nz = (NX, NY // 2, NZ // 2) if args.ncu_linear_small else (NX, NY, NZ)
+    I0 = torch.from_numpy(gdsynth.em_stack(nx, ny, nz, seed=SEED, ncells=2000)).cuda().float()
     I1 = torch.empty_like(I0)
     I2 = torch.empty_like(I0)
-    s = gd.gd_stack_create(NX, NY, NZ, disc=gd.GD_DISC_LINEAR)
+    s = gd.gd_stack_create(nx, ny, nz, disc=gd.GD_DISC_LINEAR)
     ctl = gd.solve_ctl(30, TOL, 2, 2, 16)
     ctl_sp = gd.solve_ctl(30, TOL_SP, 2, 2, 16)
     for _ in range(2):
@@ -928,7 +930,7 @@ def run_ncu_linear(args):
         r2 = gd.gd_screened_poisson_slices(s, I0, I1, I2, ALPHA, ctl_sp)
     torch.cuda.synchronize()
     gd.gd_destroy(s)
-    print(json.dumps({"ncu_linear": "linear_ad_sp_%dx%dx%d" % (NX, NY, NZ), "ad_cycles": r1["cycles"],
+    print(json.dumps({"ncu_linear": "linear_ad_sp_%dx%dx%d" % (nx, ny, nz), "ad_cycles": r1["cycles"],
                       "sp_cycles": r2["cycles"]}))
     return 0 if r1["status"] == 0 and r2["status"] == 0 else 1
 
@@ -1007,6 +1009,8 @@ def main(argv=None):
                     help="run the small profiling case instead of the benchmark")
     ap.add_argument("--ncu-linear", action="store_true",
                     help="one Linear AD + SP step on the benchmark stack after a warm-up (for ncu; not a benchmark)")
+    ap.add_argument("--ncu-linear-small", action="store_true",
+                    help="--ncu-linear on a 1024 x 512 x 64 stack")
     ap.add_argument("--ncu-case-ny", type=int, default=1024,
                     help="y extent of the --ncu-case stack (1024 x ny x 64)")
     ap.add_argument("--ncu-conv", action="store_true",
@@ -1014,7 +1018,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.ncu_case:
         return run_ncu_case(args)
-    if args.ncu_linear:
+    if args.ncu_linear or args.ncu_linear_small:
         return run_ncu_linear(args)
     if args.ncu_conv:
         return run_ncu_conv(args)

@@ -743,16 +743,6 @@ enum { LZ_RESID = 0, LZ_RHS = 1 };
 struct DF {
   float h, l;
 };
-// s += P (xh + xl), P a small integer (TwoProd keeps any float P exact)
-__device__ __forceinline__ void df_tap(DF &s, float P, float xh, float xl) {
-  const float p = P * xh;
-  const float e = fmaf(P, xh, -p);
-  const float t = s.h + p;
-  const float bb = t - s.h;
-  const float err = (s.h - (t - bb)) + (p - bb);
-  s.h = t;
-  s.l += err + e + P * xl;
-}
 // v += w S, the double w split as (wh, wl)
 __device__ __forceinline__ void df_wadd(DF &v, float wh, float wl, DF S) {
   const float p = wh * S.h;
@@ -763,6 +753,20 @@ __device__ __forceinline__ void df_wadd(DF &v, float wh, float wl, DF S) {
   v.h = t;
   v.l += err + e;
 }
+// P0 x0 + P1 x1 + P2 x2 for float pairs x_t and weights whose products with
+// any float are exact (the integer-scaled fine factors: 0, +-1, 2, 4): the
+// high products added by two TwoSums, the low parts by one rounded sum
+__device__ __forceinline__ DF df_tap3(float P0, float2 x0, float P1, float2 x1, float P2, float2 x2) {
+  const float p0 = P0 * x0.x, p1 = P1 * x1.x, p2 = P2 * x2.x;
+  float s1 = p0 + p1;
+  float bb = s1 - p0;
+  const float e1 = (p0 - (s1 - bb)) + (p1 - bb);
+  const float s2 = s1 + p2;
+  bb = s2 - s1;
+  const float e2 = (s1 - (s2 - bb)) + (p2 - bb);
+  return DF{s2, (e1 + e2) + fmaf(P0, x0.y, fmaf(P1, x1.y, P2 * x2.y))};
+}
+
 struct LzArgs {
   // RESID: a0 = h, a1 = l of the iterate; RHS: a0 = I0, a1 = I1 (no low words)
   const float *a0, *a1;
@@ -779,8 +783,8 @@ struct LzArgs {
 template <bool ZC, int MODE>
 __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
   __shared__ __align__(16) float ring[LZ_NS][2][LZ_BC];  // per plane: a0, a1
-  __shared__ __align__(16) float zst[4][LZ_BC];          // z stage: two float pairs
-  __shared__ __align__(16) float yst[6][LZ_YC];          // y stage: three float pairs
+  __shared__ __align__(16) float2 zst[2][LZ_BC];         // z stage: two float pairs
+  __shared__ __align__(16) float2 yst[3][LZ_YC];         // y stage: three float pairs
   __shared__ float wx[2][3][LZ_BW], wy[2][3][LZ_BH];     // [K|M][tap][box column / row]
   __shared__ double red[2][LZ_NT / 32];
   const int tid = threadIdx.x;
@@ -867,54 +871,41 @@ __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
     for (int q = tid; q < LZ_BC; q += LZ_NT) {
       DF zm = {0.f, 0.f}, z2 = {0.f, 0.f};
       if (MODE == LZ_RESID) {
-        const float h0 = ring[s0][0][q], l0 = ring[s0][1][q];
-        df_tap(zm, mz1, h0, l0);
+        const float2 x0 = make_float2(ring[s0][0][q], ring[s0][1][q]);
         if (ZC) {
-          const float hm = ring[sm][0][q], lm = ring[sm][1][q], hp = ring[sp][0][q], lp = ring[sp][1][q];
-          df_tap(zm, mz0, hm, lm);
-          df_tap(zm, mz2, hp, lp);
-          if (y3) {
-            df_tap(z2, kz1, h0, l0);
-            df_tap(z2, kz0, hm, lm);
-            df_tap(z2, kz2, hp, lp);
-          }
+          const float2 xm = make_float2(ring[sm][0][q], ring[sm][1][q]);
+          const float2 xp = make_float2(ring[sp][0][q], ring[sp][1][q]);
+          zm = df_tap3(mz0, xm, mz1, x0, mz2, xp);
+          if (y3) z2 = df_tap3(kz0, xm, kz1, x0, kz2, xp);
+        } else {
+          zm = DF{mz1 * x0.x, mz1 * x0.y};
         }
       } else {
-        df_tap(zm, mz1, ring[s0][0][q], 0.f);
-        if (y3) df_tap(z2, mz1, ring[s0][1][q], 0.f);
+        const float2 a0 = make_float2(ring[s0][0][q], 0.f), b0 = make_float2(ring[s0][1][q], 0.f);
         if (ZC) {
-          df_tap(zm, mz0, ring[sm][0][q], 0.f);
-          df_tap(zm, mz2, ring[sp][0][q], 0.f);
-          if (y3) {
-            df_tap(z2, mz0, ring[sm][1][q], 0.f);
-            df_tap(z2, mz2, ring[sp][1][q], 0.f);
-          }
+          zm = df_tap3(mz0, make_float2(ring[sm][0][q], 0.f), mz1, a0, mz2, make_float2(ring[sp][0][q], 0.f));
+          if (y3) z2 = df_tap3(mz0, make_float2(ring[sm][1][q], 0.f), mz1, b0, mz2, make_float2(ring[sp][1][q], 0.f));
+        } else {
+          zm = DF{mz1 * a0.x, 0.f};
+          if (y3) z2 = DF{mz1 * b0.x, 0.f};
         }
       }
-      zst[0][q] = zm.h;
-      zst[1][q] = zm.l;
-      zst[2][q] = z2.h;
-      zst[3][q] = z2.l;
+      zst[0][q] = make_float2(zm.h, zm.l);
+      zst[1][q] = make_float2(z2.h, z2.l);
     }
     __syncthreads();
     // ---- y stage: My Zm, Ky Zm and My Z2 ----
     for (int q = tid; q < LZ_YC; q += LZ_NT) {
       const int c = q % LZ_BW, by = q / LZ_BW + 1;
-      DF ymm = {0.f, 0.f}, ykm = {0.f, 0.f}, yz = {0.f, 0.f};
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int o = (by + t - 1) * LZ_BW + c;
-        const float zh = zst[0][o], zl = zst[1][o];
-        df_tap(ymm, wy[1][t][by], zh, zl);
-        df_tap(ykm, wy[0][t][by], zh, zl);
-        if (y3) df_tap(yz, wy[1][t][by], zst[2][o], zst[3][o]);
-      }
-      yst[0][q] = ymm.h;
-      yst[1][q] = ymm.l;
-      yst[2][q] = ykm.h;
-      yst[3][q] = ykm.l;
-      yst[4][q] = yz.h;
-      yst[5][q] = yz.l;
+      const int o = by * LZ_BW + c;
+      const float2 zu = zst[0][o - LZ_BW], zc0 = zst[0][o], zd = zst[0][o + LZ_BW];
+      const DF ymm = df_tap3(wy[1][0][by], zu, wy[1][1][by], zc0, wy[1][2][by], zd);
+      const DF ykm = df_tap3(wy[0][0][by], zu, wy[0][1][by], zc0, wy[0][2][by], zd);
+      DF yz = {0.f, 0.f};
+      if (y3) yz = df_tap3(wy[1][0][by], zst[1][o - LZ_BW], wy[1][1][by], zst[1][o], wy[1][2][by], zst[1][o + LZ_BW]);
+      yst[0][q] = make_float2(ymm.h, ymm.l);
+      yst[1][q] = make_float2(ykm.h, ykm.l);
+      yst[2][q] = make_float2(yz.h, yz.l);
     }
     __syncthreads();
     // ---- x stage: Kx Ymm, Mx Ykm, Mx Y3 (and Mx Ymm), then the output ----
@@ -923,17 +914,15 @@ __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
       const int q = tid + u * LZ_NT;
       const int tx = q % LZ_TX, ty = q / LZ_TX, gi = i0 + tx, gj = j0 + ty;
       if (gi >= nx || gj >= ny) continue;
-      const int bx = tx + 1;
-      DF skx = {0.f, 0.f}, sky = {0.f, 0.f}, s3 = {0.f, 0.f}, smm = {0.f, 0.f};
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        const int o = ty * LZ_BW + bx + t - 1;
-        const float kx = wx[0][t][bx], mx = wx[1][t][bx];
-        df_tap(skx, kx, yst[0][o], yst[1][o]);
-        df_tap(sky, mx, yst[2][o], yst[3][o]);
-        if (y3) df_tap(s3, mx, yst[4][o], yst[5][o]);
-        if (MODE == LZ_RESID && a.want_m) df_tap(smm, mx, yst[0][o], yst[1][o]);
-      }
+      const int bx = tx + 1, o0 = ty * LZ_BW + bx;
+      const float kx0 = wx[0][0][bx], kx1 = wx[0][1][bx], kx2 = wx[0][2][bx];
+      const float mx0 = wx[1][0][bx], mx1 = wx[1][1][bx], mx2 = wx[1][2][bx];
+      const float2 m0 = yst[0][o0 - 1], m1 = yst[0][o0], m2 = yst[0][o0 + 1];
+      const DF skx = df_tap3(kx0, m0, kx1, m1, kx2, m2);
+      const DF sky = df_tap3(mx0, yst[1][o0 - 1], mx1, yst[1][o0], mx2, yst[1][o0 + 1]);
+      DF s3 = {0.f, 0.f}, smm = {0.f, 0.f};
+      if (y3) s3 = df_tap3(mx0, yst[2][o0 - 1], mx1, yst[2][o0], mx2, yst[2][o0 + 1]);
+      if (MODE == LZ_RESID && a.want_m) smm = df_tap3(mx0, m0, mx1, m1, mx2, m2);
       DF v = {0.f, 0.f};
       df_wadd(v, a.wh[0], a.wl[0], skx);
       df_wadd(v, a.wh[1], a.wl[1], sky);
