@@ -992,6 +992,30 @@ bool on_other_device(const gd_stack *s, const void *p) {
 
 // Device view of a caller array: device pointers pass through; host arrays
 // are copied (if `in`) into staging buffer `slot`.
+// A host array in pinned memory the GPU can address (allocated by
+// cudaHostAlloc, or registered and mapped): its device address, else
+// nullptr.
+float *mapped_host(const void *p) {
+  cudaPointerAttributes at;
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? static_cast<float *>(at.devicePointer) : nullptr;
+}
+// n floats between a host array and the device: pinned host memory moves
+// with the wide copy kernel (many loads in flight across the CPU-GPU link:
+// faster than one copy-engine transfer there), other host memory with
+// cudaMemcpyAsync.
+cudaError_t copy_h2d(float *dst, const float *src, size_t n, cudaStream_t st) {
+  if (const float *m = mapped_host(src)) return launch_copy_wide(dst, m, n, st);
+  return cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyHostToDevice, st);
+}
+cudaError_t copy_d2h(float *dst, const float *src, size_t n, cudaStream_t st) {
+  if (float *m = mapped_host(dst)) return launch_copy_wide(m, src, n, st);
+  return cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+}
+
 int resolve(gd_stack *s, const float *p, bool in, int slot, float **dev) {
   if (!p) {
     *dev = nullptr;
@@ -1012,7 +1036,7 @@ int resolve(gd_stack *s, const float *p, bool in, int slot, float **dev) {
     if (st != GD_OK) return st;
   }
   if (in) {
-    CK(cudaMemcpyAsync(s->stage[slot], p, n * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    CK(copy_h2d(s->stage[slot], p, n, s->stream));
   }
   *dev = s->stage[slot];
   return GD_OK;
@@ -1216,7 +1240,7 @@ int solve_linear(gd_stack *s, int system, const float *I0h, const float *I1h, fl
     rep->rel_residual = rel;
     rep->rho_per_cycle = cycles > 0 && rel0 > 0 ? std::pow(rel / rel0, 1.0 / cycles) : NAN;
   }
-  if (out_host) CK(cudaMemcpyAsync(outh, out, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  if (out_host) CK(copy_d2h(outh, out, n, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   if (s->prof_on) prof_collect(s);
   return report(rep, status);
@@ -1381,7 +1405,7 @@ int solve(gd_stack *s, int system, const float *I0h, const float *I1h, float *ou
     rep->rel_residual_out = std::sqrt(h[S_RR]) / denom;
   }
   if (out_host) {
-    CK(cudaMemcpyAsync(outh, out, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(copy_d2h(outh, out, n, s->stream));
   }
   CK(cudaStreamSynchronize(s->stream));
   if (s->prof_on) prof_collect(s);
@@ -1545,7 +1569,7 @@ int gd_ad_then_sp(gd_stack *s, const float *I0h, float *I2h, gd_weights w_ad, do
   st = gd_screened_poisson_slices(s, I0, I1, I2h, alpha, ctl_sp, nullptr, rep_sp);
   if (st != GD_OK && st != GD_ERR_NOT_CONVERGED) return st;
   if (I1h && !i1_dev) {
-    CK(cudaMemcpyAsync(I1h, I1, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+    CK(copy_d2h(I1h, I1, n, s->stream));
     CK(cudaStreamSynchronize(s->stream));
   }
   return st != GD_OK ? st : st_ad;
@@ -1590,7 +1614,7 @@ int gd_npr_rhs(gd_stack *s, const float *I0h, float *bh, gd_weights w, double la
     CK(launch_npr_rhs(I0, b, s->nx, s->ny, s->nz, w.alpha, w.beta_x, w.beta_y, w.beta_z, lambda, sigma,
                       s->stream));
   }
-  if (b_host) CK(cudaMemcpyAsync(bh, b, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  if (b_host) CK(copy_d2h(bh, b, n, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   if (s->prof_on) prof_collect(s);
   return GD_OK;
@@ -1663,7 +1687,7 @@ int gd_vcycle(gd_stack *s, int system, gd_weights w, const float *bh, float *xh,
     rep->history[1] = rel;
     rep->rho_per_cycle = ncycles > 0 && rel0 > 0 ? std::pow(rel / rel0, 1.0 / ncycles) : NAN;
   }
-  if (x_host) CK(cudaMemcpyAsync(xh, x, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  if (x_host) CK(copy_d2h(xh, x, n, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   if (s->prof_on) prof_collect(s);
   return report(rep, GD_OK);
@@ -1741,7 +1765,7 @@ int gd_smooth(gd_stack *s, gd_weights w, const float *bh, float *xh, int nsweeps
     if (launch_copy(x, lr.x, n, s->stream) != cudaSuccess) st = GD_ERR_CUDA;
   }
   if (st == GD_OK && x_host)
-    if (cudaMemcpyAsync(xh, x, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    if (copy_d2h(xh, x, n, s->stream) != cudaSuccess)
       st = GD_ERR_CUDA;
   cudaStreamSynchronize(s->stream);
   tmp_plan.L.clear();

@@ -116,6 +116,9 @@ cudaError_t launch_fdm(int nx, int ny, int nz, const float *Vx, const float *Vy,
                        cudaStream_t st);
 cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st);
 cudaError_t launch_copy(float *dst, const float *src, size_t n, cudaStream_t st);
+// the same copy in 16-byte pieces with several loads in flight per thread
+// (falls back to launch_copy when a pointer is not 16-byte aligned)
+cudaError_t launch_copy_wide(float *dst, const float *src, size_t n, cudaStream_t st);
 // b = alpha I0 - div(W V) of the NPR gradient filter (gd_kernels.cu)
 cudaError_t launch_npr_rhs(const float *I0, float *b, int nx, int ny, int nz, double alpha, double wx,
                            double wy, double wz, double lam, double sigma, cudaStream_t st);

@@ -430,6 +430,21 @@ __global__ void k_copy(float *__restrict__ d, const float *__restrict__ s, size_
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) d[q] = s[q];
 }
 
+// 16-byte copy with four loads in flight per thread: many requests
+// outstanding at once, which a copy across the CPU-GPU link needs
+__global__ void k_copy4(float4 *__restrict__ d, const float4 *__restrict__ s, size_t n4) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; q + 3 * stride < n4; q += 4 * stride) {
+    const float4 a = s[q], b = s[q + stride], c = s[q + 2 * stride], e = s[q + 3 * stride];
+    d[q] = a;
+    d[q + stride] = b;
+    d[q + 2 * stride] = c;
+    d[q + 3 * stride] = e;
+  }
+  for (; q < n4; q += stride) d[q] = s[q];
+}
+
 int grid_for(size_t n, int per_block, int cap) {
   size_t g = (n + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -550,6 +565,17 @@ cudaError_t launch_fill(float *p, size_t n, float v, cudaStream_t st) {
 
 cudaError_t launch_copy(float *dst, const float *src, size_t n, cudaStream_t st) {
   k_copy<<<grid_for(n, NT, num_sms() * 8), NT, 0, st>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_wide(float *dst, const float *src, size_t n, cudaStream_t st) {
+  if (((uintptr_t)dst & 15) || ((uintptr_t)src & 15)) return launch_copy(dst, src, n, st);
+  const size_t n4 = n / 4;
+  if (n4) {
+    k_copy4<<<grid_for(n4, NT, num_sms() * 16), NT, 0, st>>>(reinterpret_cast<float4 *>(dst),
+                                                            reinterpret_cast<const float4 *>(src), n4);
+  }
+  if (n % 4) k_copy<<<1, 32, 0, st>>>(dst + 4 * n4, src + 4 * n4, n % 4);
   return cudaGetLastError();
 }
 
