@@ -179,6 +179,7 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
       }
     }
     const bool zint = !ZC || (k >= L.ilo[2] && k <= L.ihi[2]);
+    const float idg_int = 1.f / L.cst[13];  // interior cells' diagonal, inverted once
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
 #pragma unroll
@@ -188,9 +189,10 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
         const int bx = pk & 255, by = pk >> 8;
         const int ci = i0 - FS_R + bx, cj = j0 - FS_R + by;
         const int o = by * FS_BW + bx;
-        // columns bx - 1 .. bx + 1 of a row as two aligned float2 loads
+        // columns bx - 1 .. bx + 1 of a row as two aligned float2 loads; bx
+        // has the colour's x parity (i0 and FS_R are even), known here
         const int o2 = (by - 1) * FS_BW + ((bx - 1) & ~1);
-        const bool odd = bx & 1;
+        const bool odd = (c & 1) != 0;
         auto row3 = [&](const float *pl, int bb, float &v0, float &v1, float &v2) {
           const float2 lo = *reinterpret_cast<const float2 *>(pl + o2 + bb * FS_BW);
           const float2 hi = *reinterpret_cast<const float2 *>(pl + o2 + bb * FS_BW + 2);
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
             }
           }
           ax = (az[0] + az[2]) + az[1];
-          dg = L.cst[13];
+          dg = 0.f;  // interior: the reciprocal of the constant diagonal below
         } else {
           float kxr[3], mxr[3], kyr[3], myr[3];
 #pragma unroll
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
           }
           dg = mxr[1] * myr[1] * Z1[1] + (L.wy * mxr[1] * kyr[1] + L.wx * kxr[1] * myr[1]) * MZ[1];
         }
-        const float v = pc[o] + (bq[c][m] - ax) / dg;
+        const float v = dg == 0.f ? pc[o] + (bq[c][m] - ax) * idg_int : pc[o] + (bq[c][m] - ax) / dg;
         pc[o] = v;
         if (ci >= i0 && ci < i0 + FS_TX && cj >= j0 && cj < j0 + FS_TY)
           xout[(size_t)k * plane + (size_t)cj * nx + ci] = v;
