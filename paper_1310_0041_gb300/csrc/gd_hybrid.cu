@@ -125,14 +125,22 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
   };
 
   // this thread's colour cells are the same on every plane: their box
-  // coordinates packed as bx | by << 8 (-1: none), computed once
+  // coordinates packed as bx | by << 8, bit 16 set when the cell's x and y
+  // factor rows are the uniform interior rows, bit 17 when it lies in the
+  // tile (-1: none), computed once
   int cell[4][FS_CPT];
 #pragma unroll
   for (int c = 0; c < 4; ++c)
 #pragma unroll
     for (int m = 0; m < FS_CPT; ++m) {
       int ci, cj;
-      cell[c][m] = colour_cell(c, m, ci, cj) ? (ci - i0 + FS_R) | ((cj - j0 + FS_R) << 8) : -1;
+      if (colour_cell(c, m, ci, cj)) {
+        const bool xyint = ci >= L.ilo[0] && ci <= L.ihi[0] && cj >= L.ilo[1] && cj <= L.ihi[1];
+        const bool tile = ci >= i0 && ci < i0 + FS_TX && cj >= j0 && cj < j0 + FS_TY;
+        cell[c][m] = (ci - i0 + FS_R) | ((cj - j0 + FS_R) << 8) | (xyint ? 1 << 16 : 0) | (tile ? 1 << 17 : 0);
+      } else {
+        cell[c][m] = -1;
+      }
     }
   if (ZC) {
     load_box(cur_slot(k0), xc, k0);
@@ -150,7 +158,7 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
 #pragma unroll
       for (int m = 0; m < FS_CPT; ++m) {
         const int pk = cell[c][m];
-        bq[c][m] = pk >= 0 ? b[(size_t)k * plane + (size_t)(j0 - FS_R + (pk >> 8)) * nx + (i0 - FS_R + (pk & 255))]
+        bq[c][m] = pk >= 0 ? b[(size_t)k * plane + (size_t)(j0 - FS_R + ((pk >> 8) & 255)) * nx + (i0 - FS_R + (pk & 255))]
                            : 0.f;
       }
     cp_async_wait0();
@@ -186,7 +194,7 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
       for (int m = 0; m < FS_CPT; ++m) {
         const int pk = cell[c][m];
         if (pk < 0) continue;
-        const int bx = pk & 255, by = pk >> 8;
+        const int bx = pk & 255, by = (pk >> 8) & 255;
         const int ci = i0 - FS_R + bx, cj = j0 - FS_R + by;
         const int o = by * FS_BW + bx;
         // columns bx - 1 .. bx + 1 of a row as two aligned float2 loads; bx
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
           v2 = odd ? hi.x : hi.y;
         };
         float ax = 0.f, dg;
-        if (zint && ci >= L.ilo[0] && ci <= L.ihi[0] && cj >= L.ilo[1] && cj <= L.ihi[1]) {
+        if (zint && (pk & (1 << 16))) {
           float az[3] = {0.f, 0.f, 0.f};  // one chain per plane
 #pragma unroll
           for (int zc = 0; zc < 3; ++zc) {
@@ -243,8 +251,7 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
         }
         const float v = dg == 0.f ? pc[o] + (bq[c][m] - ax) * idg_int : pc[o] + (bq[c][m] - ax) / dg;
         pc[o] = v;
-        if (ci >= i0 && ci < i0 + FS_TX && cj >= j0 && cj < j0 + FS_TY)
-          xout[(size_t)k * plane + (size_t)cj * nx + ci] = v;
+        if (pk & (1 << 17)) xout[(size_t)k * plane + (size_t)cj * nx + ci] = v;
       }
       if (c < 3) __syncthreads();
     }
