@@ -79,9 +79,25 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
   extern __shared__ __align__(16) float fsm[];
   float *cur = fsm;                // two slots: the updated planes k, k + 2 (or k, k + 1)
   float *nbs = fsm + 2 * FS_BC;    // three slots: neighbour planes (coupled levels)
+  // factor rows of the box's columns and rows ([K|M][tap][column / row]),
+  // taps that leave the domain set to 0 (boundary cells' coefficients)
+  __shared__ float fx[2][3][FS_BW], fy[2][3][FS_BH];
   const int tid = threadIdx.x;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i0 = blockIdx.x * FS_TX, j0 = blockIdx.y * FS_TY;
+  for (int q = tid; q < 3 * FS_BW; q += FS_NT) {
+    const int c = q % FS_BW, t = q / FS_BW, gi = i0 - FS_R + c, nb = gi + t - 1;
+    const bool ok = gi >= 0 && gi < nx && nb >= 0 && nb < nx;
+    fx[0][t][c] = ok ? L.kx[3 * gi + t] : 0.f;
+    fx[1][t][c] = ok ? L.mx[3 * gi + t] : 0.f;
+  }
+  for (int q = tid; q < 3 * FS_BH; q += FS_NT) {
+    const int c = q % FS_BH, t = q / FS_BH, gj = j0 - FS_R + c, nb = gj + t - 1;
+    const bool ok = gj >= 0 && gj < ny && nb >= 0 && nb < ny;
+    fy[0][t][c] = ok ? L.ky[3 * gj + t] : 0.f;
+    fy[1][t][c] = ok ? L.my[3 * gj + t] : 0.f;
+  }
+  // (the first step's barrier orders these writes before their use)
   const int zs = blockIdx.z * zchunk, ze = min(zs + zchunk, nz);
   const size_t plane = (size_t)nx * ny;
   const int kstep = ZC ? 2 : 1;
@@ -226,28 +242,32 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
           ax = (az[0] + az[2]) + az[1];
           dg = 0.f;  // interior: the reciprocal of the constant diagonal below
         } else {
-          float kxr[3], mxr[3], kyr[3], myr[3];
-#pragma unroll
-          for (int t = 0; t < 3; ++t) {
-            const bool xin = ci + t - 1 >= 0 && ci + t - 1 < nx, yin = cj + t - 1 >= 0 && cj + t - 1 < ny;
-            kxr[t] = xin ? L.kx[3 * ci + t] : 0.f;
-            mxr[t] = xin ? L.mx[3 * ci + t] : 0.f;
-            kyr[t] = yin ? L.ky[3 * cj + t] : 0.f;
-            myr[t] = yin ? L.my[3 * cj + t] : 0.f;
-          }
+          // cf(a, b, c) = mx(a) P(b, c) + kx(a) Q(b, c), P = my(b) Z1(c) +
+          // wy ky(b) MZ(c), Q = wx my(b) MZ(c) (the per-axis factoring; taps
+          // leaving the domain are 0 in the tables)
+          const float kx0 = fx[0][0][bx], kx1 = fx[0][1][bx], kx2 = fx[0][2][bx];
+          const float mx0 = fx[1][0][bx], mx1 = fx[1][1][bx], mx2 = fx[1][2][bx];
+          float dgp = 0.f, dgq = 0.f;
 #pragma unroll
           for (int zc = 0; zc < 3; ++zc) {
             if (!ZC && zc != 1) continue;
             const float *pl = zc == 0 ? pm : (zc == 1 ? pc : pp);
 #pragma unroll
-            for (int bb = 0; bb < 3; ++bb)
-#pragma unroll
-              for (int aa = 0; aa < 3; ++aa) {
-                const float cf = mxr[aa] * myr[bb] * Z1[zc] + (L.wy * mxr[aa] * kyr[bb] + L.wx * kxr[aa] * myr[bb]) * MZ[zc];
-                ax = fmaf(cf, pl[o + (bb - 1) * FS_BW + aa - 1], ax);
+            for (int bb = 0; bb < 3; ++bb) {
+              const float myb = fy[1][bb][by], kyb = fy[0][bb][by];
+              const float P = myb * Z1[zc] + L.wy * kyb * MZ[zc], Q = L.wx * myb * MZ[zc];
+              if (zc == 1 && bb == 1) {
+                dgp = P;
+                dgq = Q;
               }
+              float v0, v1, v2;
+              row3(pl, bb, v0, v1, v2);
+              ax = fmaf(fmaf(mx0, P, kx0 * Q), v0, ax);
+              ax = fmaf(fmaf(mx1, P, kx1 * Q), v1, ax);
+              ax = fmaf(fmaf(mx2, P, kx2 * Q), v2, ax);
+            }
           }
-          dg = mxr[1] * myr[1] * Z1[1] + (L.wy * mxr[1] * kyr[1] + L.wx * kxr[1] * myr[1]) * MZ[1];
+          dg = fmaf(mx1, dgp, kx1 * dgq);
         }
         const float v = dg == 0.f ? pc[o] + (bq[c][m] - ax) * idg_int : pc[o] + (bq[c][m] - ax) / dg;
         pc[o] = v;
@@ -275,11 +295,29 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, 
                                                       float *__restrict__ r) {
   constexpr int NS = 8;
   __shared__ __align__(16) float ring[NS][GZ_BC];
+  // factor rows of the box's columns and rows ([K|M][tap][column / row]),
+  // taps that leave the domain set to 0 (boundary cells' coefficients)
+  __shared__ float fx[2][3][GZ_BW], fy[2][3][GZ_BH];
   const int tid = threadIdx.x;
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i0 = blockIdx.x * GZ_TX, j0 = blockIdx.y * GZ_TY;
   const int zs = blockIdx.z * zchunk, ze = min(zs + zchunk, nz);
   const size_t plane = (size_t)nx * ny;
+  if (!SIX) {
+    for (int q = tid; q < 3 * GZ_BW; q += GZ_NT) {
+      const int c = q % GZ_BW, t = q / GZ_BW, gi = i0 - 4 + c, nb = gi + t - 1;
+      const bool ok = gi >= 0 && gi < nx && nb >= 0 && nb < nx;
+      fx[0][t][c] = ok ? L.kx[3 * gi + t] : 0.f;
+      fx[1][t][c] = ok ? L.mx[3 * gi + t] : 0.f;
+    }
+    for (int q = tid; q < 3 * GZ_BH; q += GZ_NT) {
+      const int c = q % GZ_BH, t = q / GZ_BH, gj = j0 - 1 + c, nb = gj + t - 1;
+      const bool ok = gj >= 0 && gj < ny && nb >= 0 && nb < ny;
+      fy[0][t][c] = ok ? L.ky[3 * gj + t] : 0.f;
+      fy[1][t][c] = ok ? L.my[3 * gj + t] : 0.f;
+    }
+    // (the first step's barrier orders these writes before their use)
+  }
   auto load_plane = [&](int p) {
     float *dst = ring[(p + NS) & (NS - 1)];
     const bool pin = p >= 0 && p < nz;
@@ -397,21 +435,16 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, 
 #pragma unroll
             for (int m = 0; m < 4; ++m) acc[m] = fmaf(cs[0], v[m], fmaf(cs[1], v[m + 1], fmaf(cs[2], v[m + 2], acc[m])));
           } else {
-            const int gjb = gj + bb - 1;
-            const bool yin = gjb >= 0 && gjb < ny;
-            const float myb = yin ? L.my[3 * gj + bb] : 0.f, kyb = yin ? L.ky[3 * gj + bb] : 0.f;
+            // cf(a, bb, c) = mx(a) P + kx(a) Q with the row's P, Q below (the
+            // per-axis factoring; taps leaving the domain are 0 in the tables)
+            const float myb = fy[1][bb][ty + 1], kyb = fy[0][bb][ty + 1];
+            const float P = myb * Z1[c] + L.wy * kyb * MZ[c], Q = L.wx * myb * MZ[c];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
-              const int gi = gi0 + m;
-              if (gi >= nx) continue;
+              const int col = cb + 4 + m;  // box column of cell m
 #pragma unroll
-              for (int aa = 0; aa < 3; ++aa) {
-                const int gia = gi + aa - 1;
-                if (gia < 0 || gia >= nx) continue;
-                const float mxa = L.mx[3 * gi + aa], kxa = L.kx[3 * gi + aa];
-                const float cf = mxa * myb * Z1[c] + (L.wy * mxa * kyb + L.wx * kxa * myb) * MZ[c];
-                acc[m] = fmaf(cf, v[m + aa], acc[m]);
-              }
+              for (int aa = 0; aa < 3; ++aa)
+                acc[m] = fmaf(fmaf(fx[1][aa][col], P, fx[0][aa][col] * Q), v[m + aa], acc[m]);
             }
           }
         }
