@@ -126,7 +126,8 @@ typedef struct {
  *           ..., 4, 2], 1) per axis; an axis of one node, and z for the
  *           per-slice step, keep mass 1), the right-hand sides are the same
  *           operators applied to I0 and I1, the residual of the float-pair
- *           iterate is evaluated in FP64; B-spline transfers, Galerkin
+ *           iterate is evaluated in compensated float arithmetic (exact
+ *           integer-scaled factors, TwoSum); B-spline transfers, Galerkin
  *           levels.  gd_vcycle, gd_residual and gd_smooth evaluate the
  *           6-point operator and return GD_ERR_UNSUPPORTED on such a stack.
  *         Hybrid and Linear need prec = GD_PREC_FP32 (else GD_ERR_UNSUPPORTED).

@@ -1085,9 +1085,10 @@ void rep_init(gd_report *rep) {
 }
 
 // Solve one of the two systems with iterative refinement on the float pair.
-// The Linear discretisation's driver: the right-hand side once as an FP64
-// float pair, then V-cycles on the correction with the float-pair iterate
-// updated and its residual evaluated in FP64 after each; AD keeps the plain
+// The Linear discretisation's driver: the right-hand side once as a float
+// pair, then V-cycles on the correction with the float-pair iterate updated
+// (TwoSum) and its residual evaluated in compensated float arithmetic after
+// each; AD keeps the plain
 // sum of I0 by a constant shift of the output (the constant is A's null
 // space, so the shift changes no residual).
 int solve_linear(gd_stack *s, int system, const float *I0h, const float *I1h, float *outh, double w[4],

@@ -52,12 +52,12 @@ __device__ __forceinline__ void cp_async16z(float *dst, const float *src, bool o
 
 // One Gauss-Seidel sweep of a 27-point level with the in-plane colours
 // fused, out of place.  The eight colours (parities of i, j, k) run in the
-// order of the colour launches: on a coupled level the even planes' four
-// in-plane colours (launch pz = 0: every plane read from xin, the even
-// planes written to xout), then the odd planes' (pz = 1: the odd planes
-// read from xin, their even neighbours from xout, the odd planes written to
-// xout); an uncoupled level takes the four colours on every plane in one
-// launch.  A CTA owns an FS_TX x FS_TY tile of a plane and relaxes colour c
+// order (i, j) = (0,0), (1,0), (0,1), (1,1) on the even planes, then the same
+// on the odd planes: on a coupled level, launch pz = 0 reads every plane
+// from xin and writes the even planes to xout, then launch pz = 1 reads the
+// odd planes from xin and their even neighbours from xout and writes the odd
+// planes to xout; an uncoupled level takes the four colours on every plane
+// in one launch.  A CTA owns an FS_TX x FS_TY tile of a plane and relaxes colour c
 // (c = px + 2 py) on the tile and a ring of 3 - c cells around it in shared
 // memory, in place: colour c + 1 on a ring one narrower reads exactly the
 // colour-c values it needs.  Ring cells are computed from the same values,
@@ -1015,10 +1015,10 @@ __global__ void __launch_bounds__(LZ_NT, 2) k_lz(HLevelDev L, LzArgs a) {
   }
 }
 
-// (h, l) += e in float-pair arithmetic (TwoSum, then renormalised: the pair
-// keeps ~48 bits, as the FP64 update it replaces kept 53 -- GB300's FP64
-// pipe made that streaming pass five times slower than its bytes); block
-// sums of the new iterate (slot S_X), accumulated per thread as a float pair
+// (h, l) += e in float-pair arithmetic (TwoSum, then renormalised: ~48 bits,
+// against FP64's 53; GB300's narrow FP64 pipe would make this streaming pass
+// several times slower than its bytes); block sums of the new iterate (slot
+// S_X), accumulated per thread as a float pair
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   s = a + b;
   const float bb = s - a;
