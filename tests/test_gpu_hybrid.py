@@ -36,7 +36,9 @@ def run(torch, shape, disc, bz=10.0, alpha=0.01, tol_ad=1e-8, tol_sp=1e-9):
 
 
 @pytest.mark.parametrize("shape,bz", [((16, 64, 64), 10.0), ((11, 29, 37), 10.0), ((8, 96, 72), 0.1),
-                                      ((1, 70, 52), 10.0), ((24, 40, 36), 1.0)])
+                                      ((1, 70, 52), 10.0), ((24, 40, 36), 1.0),
+                                      # tile seams in x and y with ragged last tiles, odd nz
+                                      ((9, 70, 150), 10.0)])
 def test_hybrid_matches_exact_solutions(torch, shape, bz):
     I0, I1, I2, r1, r2 = run(torch, shape, gd.GD_DISC_HYBRID, bz=bz)
     assert r1["status"] == gd.GD_OK and r2["status"] == gd.GD_OK, (r1, r2)

@@ -21,7 +21,11 @@ def torch():
 
 
 @pytest.mark.parametrize("shape,bz", [((12, 40, 48), 10.0), ((7, 29, 37), 10.0), ((6, 33, 20), 0.1),
-                                      ((1, 45, 52), 10.0), ((16, 64, 64), 1.0)])
+                                      ((1, 45, 52), 10.0), ((16, 64, 64), 1.0),
+                                      # three 64-column tiles with a ragged third (and three
+                                      # 32-row tiles, ragged), an odd plane count: the fused
+                                      # sweep's recompute rings across tile seams
+                                      ((9, 70, 150), 10.0)])
 def test_linear_matches_oracle(torch, shape, bz):
     nz, ny, nx = shape
     I0h = gdsynth.em_stack(nx, ny, nz, seed=23 + nz).astype(np.float32)
