@@ -749,14 +749,20 @@ int vcycle_hybrid(gd_stack *s, int nu1, int nu2, bool zero_init, bool sum_e) {
       for (int k = 0; k < nu1; ++k)
         if ((st = gs(v)) != GD_OK) return st;
     }
-    {
-      ProfScope ps(s, P_RESTRICT, (double)v.n * 12.0);
-      CK(launch_h_resid(v.hd, l == 0 && six0, v.x, v.b, v.t, s->stream));
-    }
-    {
-      ProfScope ps(s, P_RESTRICT, (double)v.n * 4.0 + (double)c.n * 4.0);
-      CK(launch_h_restrict(v.d.nx, v.d.ny, v.d.nz, v.fx, v.fy, v.fz, c.d.nx, c.d.ny, c.d.nz, v.t, c.b,
-                           s->stream));
+    if (v.fz && !v.fx && !v.fy && v.hd.wz != 0.f && v.d.nz > 1) {
+      // halved along z only: residual and restriction in one z-march
+      ProfScope ps(s, P_RESTRICT, (double)v.n * 8.0 + (double)c.n * 4.0);
+      CK(launch_h_resid_rz(v.hd, l == 0 && six0, v.x, v.b, c.b, c.d.nz, s->stream));
+    } else {
+      {
+        ProfScope ps(s, P_RESTRICT, (double)v.n * 12.0);
+        CK(launch_h_resid(v.hd, l == 0 && six0, v.x, v.b, v.t, s->stream));
+      }
+      {
+        ProfScope ps(s, P_RESTRICT, (double)v.n * 4.0 + (double)c.n * 4.0);
+        CK(launch_h_restrict(v.d.nx, v.d.ny, v.d.nz, v.fx, v.fy, v.fz, c.d.nx, c.d.ny, c.d.nz, v.t, c.b,
+                             s->stream));
+      }
     }
   }
   if ((st = coarsest_solve(s, L[nl - 1])) != GD_OK) return st;

@@ -289,10 +289,17 @@ __global__ void __launch_bounds__(FS_NT, 3) k_h_gsf(HLevelDev L, int pz, int zch
 // factoring as the sweep, taps leaving the domain set to 0).
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
-template <bool ZC, bool SIX>
+// RZ (coupled levels halved along z only): instead of r, the coarse
+// right-hand side bc = P^T r of the B-spline transfer, accumulated per column
+// in registers (coarse plane K takes 1/2 r(2K - 1) + r(2K) + 1/2 r(2K + 1),
+// the last odd fine plane all of its residual when K + 1 does not exist);
+// chunks are even, each also evaluates the plane before it for that plane's
+// half, and the chunk holding fine plane 2K stores coarse plane K.
+template <bool ZC, bool SIX, bool RZ = false>
 __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, int vec, int vec_br,
                                                       const float *__restrict__ x, const float *__restrict__ b,
-                                                      float *__restrict__ r) {
+                                                      float *__restrict__ r, float *__restrict__ bc = nullptr,
+                                                      int ncz = 0) {
   constexpr int NS = 8;
   __shared__ __align__(16) float ring[NS][GZ_BC];
   // factor rows of the box's columns and rows ([K|M][tap][column / row]),
@@ -345,16 +352,19 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, 
   const bool xy_int = gi0 >= L.ilo[0] && gi0 + 3 <= L.ihi[0] && gj >= L.ilo[1] && gj <= L.ihi[1];
   const int cb = 4 * l;  // box column of the float4 left of the cells
 
+  // the first plane evaluated (RZ: the one before the chunk, for its half)
+  const int ks = (RZ && zs > 0) ? zs - 1 : zs;
   // one copy group per plane, two planes ahead of the step that reads them
   if (ZC) {
-    load_plane(zs - 1);
-    load_plane(zs);
-    load_plane(zs + 1);
-    load_plane(zs + 2);
+    load_plane(ks - 1);
+    load_plane(ks);
+    load_plane(ks + 1);
+    load_plane(ks + 2);
   } else {
-    load_plane(zs);
-    load_plane(zs + 1);
+    load_plane(ks);
+    load_plane(ks + 1);
   }
+  float carry[4] = {0.f, 0.f, 0.f, 0.f};  // RZ: the half of r(2K - 1) owed to coarse plane K
   // b of this thread's cells, loaded a step ahead of its use
   const size_t orow = (size_t)gj * nx + gi0;
   auto load_b = [&](int k, float *bv) {
@@ -372,8 +382,8 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, 
     }
   };
   float bn[4] = {0.f, 0.f, 0.f, 0.f};
-  load_b(zs, bn);
-  for (int k = zs; k < ze; ++k) {
+  load_b(ks, bn);
+  for (int k = ks; k < ze; ++k) {
     float bk[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) bk[m] = bn[m];
@@ -461,7 +471,46 @@ __global__ void __launch_bounds__(GZ_NT, 3) k_h_residz(HLevelDev L, int zchunk, 
           acc[m] = cnt * xo[m] - acc[m];
         }
       }
-      if (vec_br) {  // nx % 4 == 0 and 16-byte aligned b, r: the four cells are one float4
+      if (RZ) {
+        float rv[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) rv[m] = bk[m] - acc[m];
+        bool store = false;
+        int K = 0;
+        float cv[4];
+        if ((k & 1) == 0) {
+          // even fine plane 2K: its whole residual, plus the half carried
+          K = k >> 1;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            cv[m] = carry[m] + rv[m];
+            carry[m] = cv[m];  // (completed by the next, odd, plane)
+          }
+          store = k == nz - 1;  // no plane 2K + 1: coarse plane K is complete
+        } else {
+          // odd fine plane 2K + 1: half to K (all of it when K + 1 does not
+          // exist), half carried to K + 1
+          K = (k - 1) >> 1;
+          const bool last = ((k + 1) >> 1) >= ncz;
+#pragma unroll
+          for (int m = 0; m < 4; ++m) {
+            const float h = last ? rv[m] : 0.5f * rv[m];
+            cv[m] = carry[m] + h;
+            carry[m] = last ? 0.f : 0.5f * rv[m];
+          }
+          store = 2 * K >= zs;  // plane 2K in this chunk (not the one before it)
+        }
+        if (store) {
+          const size_t oc = (size_t)K * plane + orow;
+          if (vec_br) {  // (vec_br covers bc here)
+            *reinterpret_cast<float4 *>(bc + oc) = make_float4(cv[0], cv[1], cv[2], cv[3]);
+          } else {
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+              if (gi0 + m < nx) bc[oc + m] = cv[m];
+          }
+        }
+      } else if (vec_br) {  // nx % 4 == 0 and 16-byte aligned b, r: the four cells are one float4
         *reinterpret_cast<float4 *>(r + o) = make_float4(bk[0] - acc[0], bk[1] - acc[1], bk[2] - acc[2], bk[3] - acc[3]);
       } else {
 #pragma unroll
@@ -593,7 +642,7 @@ namespace {
 // loaded beyond it)
 template <typename K>
 int resid_chunk(K kernel, int slot_idx, long tiles, int nz, int h) {
-  static int slots_cache[6] = {0, 0, 0, 0, 0, 0};
+  static int slots_cache[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int &slots = slots_cache[slot_idx];
   if (!slots) {
     int occ = 0, dev = 0, sms = 0;
@@ -708,6 +757,28 @@ cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const f
     }
   }
 #undef GD_RZ
+  return cudaGetLastError();
+}
+
+cudaError_t launch_h_resid_rz(const HLevelDev &L, bool six, const float *x, const float *b, float *bc, int ncz,
+                              cudaStream_t st) {
+  const int gx = (L.nx + GZ_TX - 1) / GZ_TX, gy = (L.ny + GZ_TY - 1) / GZ_TY;
+  const long tiles = (long)gx * gy;
+  const bool nx4 = (L.nx & 3) == 0;
+  const int vec = (nx4 && ((uintptr_t)x & 15) == 0) ? 1 : 0;
+  const int vec_bc = (nx4 && ((uintptr_t)b & 15) == 0 && ((uintptr_t)bc & 15) == 0) ? 1 : 0;
+  int chunk;
+#define GD_RZZ(S, I)                                                                                   \
+  chunk = resid_chunk(k_h_residz<true, S, true>, I, tiles, L.nz, 3);                                    \
+  chunk += chunk & 1; /* even: both fine planes 2K, 2K + 1 of a coarse plane in one chunk */          \
+  k_h_residz<true, S, true><<<dim3(gx, gy, (L.nz + chunk - 1) / chunk), GZ_NT, 0, st>>>(                \
+      L, chunk, vec, vec_bc, x, b, nullptr, bc, ncz);
+  if (six) {
+    GD_RZZ(true, 6)
+  } else {
+    GD_RZZ(false, 7)
+  }
+#undef GD_RZZ
   return cudaGetLastError();
 }
 

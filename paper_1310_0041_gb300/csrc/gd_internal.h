@@ -144,6 +144,10 @@ int h_gsf_launches(const HLevelDev &L);
 // r = b - A x (six: the fine 6-point operator, factors unused)
 cudaError_t launch_h_resid(const HLevelDev &L, bool six, const float *x, const float *b, float *r,
                            cudaStream_t st);
+// A coupled level halved along z only: bc = P^T (b - A x) in one z-march
+// (no r array); six: the fine 6-point operator
+cudaError_t launch_h_resid_rz(const HLevelDev &L, bool six, const float *x, const float *b, float *bc, int ncz,
+                              cudaStream_t st);
 // bc = P^T r and x += P e with the first-order B-spline transfers along the
 // halved axes (fx, fy, fz)
 cudaError_t launch_h_restrict(int nx, int ny, int nz, int fx, int fy, int fz, int cnx, int cny, int cnz,
