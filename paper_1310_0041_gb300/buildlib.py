@@ -22,6 +22,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgd.so")
 SOURCES = ["gd_kernels.cu", "gd_zmarch.cu", "gd_host.cu", "gd_batch.cu", "gd_hybrid.cu", "gd_learn.cu",
            "gd_eig.cpp"]
+# sources compiled in parts (-D<macro>=0 .. n-1), one object each, so that a
+# unit holding many kernel instantiations compiles on several cores
+PARTS = {"gd_zmarch.cu": ("GD_ZMARCH_PART", 5)}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -48,12 +51,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
               "-I", INCLUDE, "-I", CSRC, *extra_flags]
     jobs = []
     objs = []
+    units = []
     for src in SOURCES:
+        if src in PARTS:
+            macro, n = PARTS[src]
+            units += [(src, "%s.p%d.o" % (src, k), ["-D%s=%d" % (macro, k)]) for k in range(n)]
+        else:
+            units.append((src, src + ".o", []))
+    for src, oname, defs in units:
         path = os.path.join(CSRC, src)
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(BUILD, oname)
         objs.append(obj)
         if force or _stale(obj, [path, *headers]):
-            cmd = [cc, *common, "-c", path, "-o", obj]
+            cmd = [cc, *common, *defs, "-c", path, "-o", obj]
             if src.endswith(".cpp"):
                 cmd[1:1] = ["-x", "c++"]
             jobs.append(cmd)

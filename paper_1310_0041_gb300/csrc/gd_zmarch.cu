@@ -41,6 +41,33 @@
 
 #include "gd_internal.h"
 
+// The file compiles as one translation unit, or in parts that the build
+// compiles in parallel (-DGD_ZMARCH_PART=0 .. 4): part 0 holds the launchers'
+// front ends and the restriction, parts 1 and 2 the sweep instantiations
+// over float32 and bfloat16 levels, parts 3 and 4 the outer pass's over a
+// float32 and a bfloat16 correction.  Each kernel instantiation belongs to
+// exactly one part.
+#ifndef GD_ZMARCH_PART
+#define GD_ZMARCH_PART -1
+#endif
+#define GD_ZM_PART(n) (GD_ZMARCH_PART < 0 || GD_ZMARCH_PART == (n))
+#if GD_ZMARCH_PART >= 0
+#pragma nv_diag_suppress 177  // helpers that another part uses
+#endif
+
+// sweep launchers by element type of the level (esz_c: the coarse level's)
+cudaError_t zsweep_f32(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc, const ZSweepArgs &a,
+                       bool zero_in, bool prolong, bool sum, int esz_c, dim3 grid, int *nblocks_out,
+                       cudaStream_t st);
+cudaError_t zsweep_bf16(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc, const ZSweepArgs &a,
+                        bool zero_in, bool prolong, bool sum, int esz_c, dim3 grid, int *nblocks_out,
+                        cudaStream_t st);
+// outer-pass launchers by element type of the correction e
+cudaError_t zouter_f32(const CUtensorMap *m, const OuterArgs &a, int rhs_mode, double *err, dim3 grid,
+                       int *nblocks_out, cudaStream_t st);
+cudaError_t zouter_bf16(const CUtensorMap *m, const OuterArgs &a, int rhs_mode, double *err, dim3 grid,
+                        int *nblocks_out, cudaStream_t st);
+
 namespace {
 
 constexpr int ZX = 64;            // tile x extent
@@ -98,6 +125,7 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+#if GD_ZM_PART(0)
 // Self-test of the bounded wait: one thread initialises an mbarrier that
 // expects one arrival, never arrives, and polls it `limit` times with the
 // same try_wait and suspend hint the kernels use; a wait that gives up sets
@@ -123,6 +151,7 @@ __global__ void k_wait_selftest(uint32_t limit, int *flag) {
   }
   *flag = done ? 0 : 1;
 }
+#endif
 
 
 __device__ __forceinline__ float mass_of(int i, int n, int s, int l) {
@@ -1862,6 +1891,50 @@ cudaError_t run_zouter_t(const CUtensorMap *m, const OuterArgs &a, int rhs_mode,
 
 }  // namespace
 
+#if GD_ZM_PART(1)
+cudaError_t zsweep_f32(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc, const ZSweepArgs &a,
+                       bool zero_in, bool prolong, bool sum, int esz_c, dim3 grid, int *nblocks_out,
+                       cudaStream_t st) {
+  const ZPlan zp{(int)(grid.x * grid.y), a.L.nz, level_coupled(a.L), level_coupled(a.L), nblocks_out};
+  if (esz_c == 2 && prolong)
+    return run_zsweep_variant<float, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
+  return run_zsweep_variant<float, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
+}
+#endif
+
+#if GD_ZM_PART(2)
+cudaError_t zsweep_bf16(const CUtensorMap &mx, const CUtensorMap &mb, const CUtensorMap &mc, const ZSweepArgs &a,
+                        bool zero_in, bool prolong, bool sum, int esz_c, dim3 grid, int *nblocks_out,
+                        cudaStream_t st) {
+  const ZPlan zp{(int)(grid.x * grid.y), a.L.nz, level_coupled(a.L), level_coupled(a.L), nblocks_out};
+  if (esz_c == 2 || !prolong)
+    return run_zsweep_variant<half_t, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
+  return run_zsweep_variant<half_t, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
+}
+#endif
+
+#if GD_ZM_PART(3) || GD_ZM_PART(4)
+namespace {
+ZPlan outer_plan(const OuterArgs &a, dim3 grid, int *nblocks_out) {
+  const bool coupled = (a.bz != 0.f) && (a.nz > 1);
+  return ZPlan{(int)(grid.x * grid.y), a.nz, coupled, coupled, nblocks_out};
+}
+}  // namespace
+#endif
+#if GD_ZM_PART(3)
+cudaError_t zouter_f32(const CUtensorMap *m, const OuterArgs &a, int rhs_mode, double *err, dim3 grid,
+                       int *nblocks_out, cudaStream_t st) {
+  return run_zouter_t<float>(m, a, rhs_mode, outer_plan(a, grid, nblocks_out), err, grid, st);
+}
+#endif
+#if GD_ZM_PART(4)
+cudaError_t zouter_bf16(const CUtensorMap *m, const OuterArgs &a, int rhs_mode, double *err, dim3 grid,
+                        int *nblocks_out, cudaStream_t st) {
+  return run_zouter_t<half_t>(m, a, rhs_mode, outer_plan(a, grid, nblocks_out), err, grid, st);
+}
+#endif
+
+#if GD_ZM_PART(0)
 bool zmarch_usable(const LevelDev &L, int esz) { return encoder() && ((size_t)L.nx * esz) % 16 == 0; }
 
 cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zero_in, bool prolong,
@@ -1874,7 +1947,6 @@ cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zer
   if (!make_map(&mb, b, L.nx, L.ny, L.nz, box_w(esz), rows_b, esz)) return cudaErrorNotSupported;
   if (((uintptr_t)a.xout & 15) != 0) return cudaErrorNotSupported;
   const int gx = (L.nx + ZX - 1) / ZX, gy = (L.ny + SY - 1) / SY;
-  const ZPlan zp{gx * gy, L.nz, level_coupled(L), level_coupled(L), nblocks_out};
   dim3 grid(gx, gy, 1);
   // prolongation: a map over the coarse level for the staging copies (and
   // L2 prefetches) of the boxes the correction reads (x: 32 coarse cells +
@@ -1891,12 +1963,8 @@ cudaError_t launch_zsweep(ZSweepArgs a, const void *xin, const void *b, bool zer
     a.cpf = make_map(&mc, a.xc, a.ncx, a.ncy, ncz, cw, ch, esz_c) ? 1 : 0;
     if (!a.cpf) mc = mx;
   }
-  if (esz == 4 && esz_c == 2 && prolong)
-    return run_zsweep_variant<float, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
-  if (esz == 4) return run_zsweep_variant<float, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
-  if (esz_c == 2 || !prolong)
-    return run_zsweep_variant<half_t, half_t>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
-  return run_zsweep_variant<half_t, float>(mx, mb, mc, a, zero_in, prolong, sum, grid, zp, st);
+  if (esz == 4) return zsweep_f32(mx, mb, mc, a, zero_in, prolong, sum, esz_c, grid, nblocks_out, st);
+  return zsweep_bf16(mx, mb, mc, a, zero_in, prolong, sum, esz_c, grid, nblocks_out, st);
 }
 
 cudaError_t launch_zrestrict(ZSweepArgs a, const void *x, const void *b, int esz, int esz_c, cudaStream_t st) {
@@ -1931,11 +1999,9 @@ cudaError_t launch_zouter(const OuterArgs &a, int rhs_mode, int esz_e, double *e
   if (((uintptr_t)a.xh_out & 15) || ((uintptr_t)a.xl_out & 15) || ((uintptr_t)a.r_out & 15))
     return cudaErrorNotSupported;
   const int gx = (a.nx + ZX - 1) / ZX, gy = (a.ny + OuterGeo::OY - 1) / OuterGeo::OY;
-  const bool coupled = (a.bz != 0.f) && (a.nz > 1);
-  const ZPlan zp{gx * gy, a.nz, coupled, coupled, nblocks_out};
   dim3 grid(gx, gy, 1);
-  if (esz_e == 2) return run_zouter_t<half_t>(m, a, rhs_mode, zp, err, grid, st);
-  return run_zouter_t<float>(m, a, rhs_mode, zp, err, grid, st);
+  if (esz_e == 2) return zouter_bf16(m, a, rhs_mode, err, grid, nblocks_out, st);
+  return zouter_f32(m, a, rhs_mode, err, grid, nblocks_out, st);
 }
 
 int zouter_max_blocks(int nx, int ny, int nz) {
@@ -1960,3 +2026,4 @@ int zmarch_wait_selftest(unsigned limit, cudaStream_t st) {
   if (e != cudaSuccess) return -1;
   return h;
 }
+#endif  // GD_ZM_PART(0)
