@@ -284,9 +284,9 @@ int gd_profile_query(gd_stack *s, int k, char *name, int name_len, long long *la
  *   cuda_stream: a cudaStream_t or NULL; returns after the sweeps complete.
  * It allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The address is kept for the life of the
- * process, so it assumes the device's context is not reset in between.  All calls on a device share the one scratch
+ * (cudaGetSymbolAddress) with that device current.  The address is kept for
+ * the life of the process, so it assumes the device's context is not reset in
+ * between.  All calls on a device share the one scratch
  * array, which keeps the last call's contents (each call overwrites what it
  * reads): calls that overlap on the GPU (other streams, other threads) race.
  */
